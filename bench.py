@@ -1,0 +1,288 @@
+#!/usr/bin/env python3
+"""Benchmark of the per-frame haemoglobin estimator on GB300.
+
+Workload: one 1920x1080 8-bit RGB frame per rank per step (synthetic, seeded),
+3 Haar levels, Tikhonov lambda = 1e-3 (relative), 128 x 128 concentration grid,
+sigma_l = 0.02.  A step is one call of the whole path (log-attenuation, Haar
+analysis, Tikhonov on the directional bands, grid posterior on the low pass,
+inverse Haar, THb/SO2) through the C ABI.
+
+Timing: W untimed warm-up steps, then K timed steps, each bracketed by CUDA
+events on the launch stream; a 256 MiB buffer is rewritten between timed steps
+(outside the events) so every step starts with the frame out of L2.  A barrier
+and a device synchronisation bracket the timed loop; the slowest rank's time
+counts.  `e2e` repeats the measurement through hb_estimate_host (pinned host
+frame in, THb/SO2 back to pinned host memory, copies inside the timed region).
+
+--impl reference times the FP64 CPU oracle on the host cores instead (a bounded
+sample of the same workload) and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "1080p frames/s and p99 frame latency (THb+SO2) vs plain pipeline, same GB300, <=1e-4 rel err"
+UNIT = "frames/s"
+SM_COUNT = 152
+EX2_PER_CLK_PER_SM = 32          # MUFU ex2 lanes per clock per SM on GB300
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded CPU-oracle sample length")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) taken during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def workload():
+    from paper_1706_07263_gb300 import synth
+    return synth.HD_1080
+
+
+def make_inputs(rank: int):
+    from paper_1706_07263_gb300 import synth
+    wl = workload()
+    mix = synth.make_mixing(wl.seed)
+    fr = synth.make_frame(wl.seed + 1000 * rank, wl.H, wl.W, mix.A, wl.nblobs, wl.smin, wl.smax, wl.noise, wl.fmt)
+    return wl, mix, fr
+
+
+def cpu_oracle_sample(budget_s: float):
+    """Time the FP64 oracle (as it stands) on whole frames of the workload, all host cores."""
+    import oracle
+    from paper_1706_07263_gb300 import synth
+    wl, mix, fr = make_inputs(0)
+    grid = synth.grid_spec(wl)
+    cores = os.cpu_count() or 1
+    oracle.build()
+    frames, t0 = 0, time.perf_counter()
+    while True:
+        oracle.estimate(fr.rgb, mix.A, grid, wl.levels, wl.lam, nthreads=cores)
+        frames += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or frames >= 50:
+            break
+    return {"value": frames / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{frames} whole {wl.W}x{wl.H} u8 frame(s) in {el:.1f} s, FP64 C oracle, "
+                      f"{cores} threads over low-pass pixels"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = workload()
+    budget = max(5.0, min(args.cpu_seconds, 120.0))
+    cb = cpu_oracle_sample(budget)
+    line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl.name, "width": wl.W, "height": wl.H, "levels": wl.levels,
+                       "grid": list(wl.grid), "input": wl.fmt, "l2": "n/a (host)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1706_07263_gb300 import Context, build, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+
+    # CPU baseline first (rank 0, N = 1), before any process pool or GPU timing.
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_base = cpu_oracle_sample(args.cpu_seconds)
+
+    wl, mix, fr = make_inputs(rank)
+    grid = synth.grid_spec(wl)
+    H, W = wl.H, wl.W
+    stream = torch.cuda.Stream(device=dev)
+    frame = torch.from_numpy(fr.rgb).to(dev)
+    thb = torch.empty((H, W), dtype=torch.float32, device=dev)
+    so2 = torch.empty_like(thb)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ctx = Context(mix.A, grid, wl.levels, wl.lam, W, H, wl.fmt)
+    hl, wl_ = ctx.lowpass_shape()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx.estimate(frame, thb, so2, stream=stream)
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        launches0 = ctx.launch_count()
+        ctx.timing_start(3 * args.steps)
+        barrier()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            ctx.estimate(frame, thb, so2, stream=stream)
+            ev[k][1].record(stream)
+        barrier()
+        launches = ctx.launch_count() - launches0
+        stage = ctx.timing_read()
+        clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms * 1e-3)
+
+    # end to end through the host entry point: pinned frame in, pinned THb/SO2 out
+    host_frame = torch.from_numpy(fr.rgb).pin_memory()
+    host_thb = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    host_so2 = torch.empty_like(host_thb).pin_memory()
+    for _ in range(args.warmup):
+        ctx.estimate_host(host_frame.numpy(), host_thb, host_so2, stream=stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.estimate_host(host_frame.numpy(), host_thb, host_so2, stream=stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # roofline of the dominant kernel (grid posterior): one ex2 per grid node
+    post_ms, post_n = stage["lowpass"]
+    post_avg_s = post_ms / max(post_n, 1) * 1e-3
+    nodes = hl * wl_ * wl.grid[0] * wl.grid[1]
+    achieved = nodes / post_avg_s / 1e12
+    peak = SM_COUNT * EX2_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    stages = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1]} for k, v in stage.items()
+              if v[1]}
+    q = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "width": W, "height": H, "levels": wl.levels, "grid": list(wl.grid),
+                   "sigma_l": wl.sigma_l, "lambda": wl.lam, "input": "u8 HWC", "frames_per_rank_per_step": 1,
+                   "l2": "256 MiB buffer rewritten between timed steps", "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": q[len(q) // 2], "p99": q[min(len(q) - 1, int(round(0.99 * (len(q) - 1))))],
+                       "max": q[-1]},
+        "megapixels_per_s": value * W * H / 1e6,
+        "stages": stages,
+        "roofline": {"bound": "alu", "kernel": "posterior (grid posterior mean, one MUFU ex2 per grid node)",
+                     "achieved": achieved, "peak": peak, "unit": "Texp/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "peak_note": "152 SMs x 32 ex2/clk/SM x 2070 MHz (unit count measured by probe)"},
+        "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W * 3,
+                "d2h_bytes_per_step": 2 * H * W * 4},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu_base,
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,151 @@
+/*
+ * hb.h -- C ABI of the GB300 haemoglobin estimator (libhb.so).
+ *
+ * The method ("Fast Estimation of Haemoglobin Concentration in Tissue Via
+ * Wavelet Decomposition", Section 2) turns one RGB frame into oxy- and
+ * deoxy-haemoglobin concentration maps:
+ *   1. log-attenuation y = -ln(max(I, eps)) of every channel (Eq. 8's -log);
+ *   2. n levels of the 2x2-window Haar transform (Eq. 1-2);
+ *   3. the Tikhonov operator M = (A^T A + gamma I)^-1 A^T on every directional
+ *      (detail) coefficient, 3 colour values in, 2 concentrations out (Eq. 5);
+ *   4. a Bayesian estimate on the low-pass band: the posterior mean of
+ *      c = (HbO2, Hb) over a discretised concentration grid with a flat prior
+ *      and Gaussian likelihood exp(-|ybar - A c|^2 / (2 sigma^2));
+ *   5. the inverse transform (Eq. 4, H = H*);
+ *   6. THb = HbO2 + Hb and SO2 = HbO2 / THb (Section 3, Fig. 1-2).
+ *
+ * Conventions for every entry point:
+ *   - every function returns hb_status; nothing throws across the ABI;
+ *   - "_dev" pointers are CUDA device pointers on the device current when the
+ *     context was created; "_host" pointers are host memory (pinned is faster);
+ *   - the caller owns every frame and output buffer; the context owns the
+ *     operator, the grid constants, its scratch and its own streams/events;
+ *   - work is enqueued on the caller's stream (a cudaStream_t passed as void*,
+ *     NULL = legacy default stream) and is asynchronous: a fault inside a
+ *     kernel surfaces as HB_ERR_CUDA from a later call or synchronisation;
+ *   - a context is not thread-safe and its scratch is shared by all calls made
+ *     with it: calls with the same context must not overlap on different
+ *     streams.
+ */
+#ifndef HB_H
+#define HB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hb_ctx hb_ctx;
+
+typedef enum {
+    HB_OK = 0,
+    HB_ERR_ARG = 1,     /* NULL pointer, bad enum, misaligned or too-small stride */
+    HB_ERR_SHAPE = 2,   /* non-positive size, levels outside 0..6, grid < 1 node */
+    HB_ERR_CUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    HB_ERR_OOM = 4,     /* device or pinned-host allocation failed */
+    HB_ERR_BUDGET = 5,  /* admission refused: the request does not fit the memory budget */
+    HB_ERR_TIMEOUT = 6, /* a bounded wait ran out */
+    HB_ERR_STATE = 7    /* call not valid in the object's current state */
+} hb_status;
+
+/* Mixing model: A[c][j] is the attenuation of colour channel c (R, G, B) per
+ * unit concentration (uM) of chromophore j (HbO2, Hb), so y = A c for a
+ * noiseless pixel (Beer-Lambert, Section 2). */
+typedef struct {
+    double A[3][2];
+} hb_mixing;
+
+/* Concentration grid of the Bayesian low-pass estimate: n0 x n1 nodes, inclusive
+ * linear spacing c0 = lo0 + i (hi0 - lo0) / (n0 - 1), c1 = lo1 + j (hi1 - lo1) / (n1 - 1)
+ * (a single node sits at lo when n = 1); sigma_l is the likelihood standard
+ * deviation in log-attenuation units. */
+typedef struct {
+    int n0, n1;
+    double lo0, hi0, lo1, hi1;
+    double sigma_l;
+} hb_grid;
+
+/* Input pixel formats: interleaved RGB, channel fastest, rows row_stride_bytes apart. */
+enum {
+    HB_IN_F32_HWC = 0, /* float intensities; eps = 1e-6 */
+    HB_IN_U8_HWC = 1   /* 8-bit codes k meaning k / 255; eps = 1 / 255 */
+};
+
+/* Flags of hb_create. */
+enum {
+    HB_LAMBDA_ABSOLUTE = 1u << 0,  /* gamma = lambda; default gamma = lambda * trace(A^T A) / 2 */
+    HB_LOWPASS_TIKHONOV = 1u << 1, /* low pass through M as well (the all-Tikhonov comparison) */
+    HB_FUSED = 1u << 3             /* one fused kernel per frame instead of three */
+};
+
+/* Per-stage timing slots reported by hb_timing_read. */
+enum { HB_STAGE_ANALYSIS = 0, HB_STAGE_LOWPASS = 1, HB_STAGE_SYNTHESIS = 2, HB_STAGE_FUSED = 3, HB_NUM_STAGES = 4 };
+
+/* Create a context for frames of width x height pixels.
+ *   mix, grid  : copied; grid must have n0, n1 >= 1, hi >= lo, sigma_l > 0.
+ *   levels     : Haar levels n, 0..6.  0 = no decomposition (Bayesian estimate on
+ *                every pixel, the full-resolution comparison).  Sizes that are not
+ *                multiples of 2^n are edge-replicated internally and cropped on output.
+ *   lambda     : Tikhonov constant (Eq. 5, Gamma = gamma I); see HB_LAMBDA_ABSOLUTE.
+ *   in_format  : HB_IN_F32_HWC or HB_IN_U8_HWC.
+ * Precomputes M, the grid constants and the log table in FP64 on the host,
+ * uploads them and allocates the context's scratch (the low-pass band and its
+ * concentration estimate).  *out is NULL on failure. */
+hb_status hb_create(const hb_mixing *mix, const hb_grid *grid, int levels, double lambda, int width, int height,
+                    int in_format, unsigned flags, hb_ctx **out);
+
+/* Release the context and everything it owns; NULL is a no-op.  Synchronises
+ * the device work the context enqueued. */
+void hb_destroy(hb_ctx *ctx);
+
+/* One frame -> THb and SO2 maps (the proposed method, steps 1-6).
+ *   frame_dev        : height rows of width*3 values (u8 or f32 per in_format),
+ *                      row_stride_bytes apart (>= width*3*element size).
+ *   thb_dev, so2_dev : height*width floats each, row-major, contiguous.  THb in
+ *                      the units of 1/A (uM); SO2 as a fraction, 0 where THb <= 0.
+ * Asynchronous on `stream`. */
+hb_status hb_estimate(hb_ctx *ctx, const void *frame_dev, size_t row_stride_bytes, float *thb_dev, float *so2_dev,
+                      void *stream);
+
+/* Same computation on host buffers: copies the frame host->device, runs
+ * hb_estimate into context-owned device buffers, copies THb and SO2
+ * device->host, and synchronises `stream` before returning. */
+hb_status hb_estimate_host(hb_ctx *ctx, const void *frame_host, size_t row_stride_bytes, float *thb_host,
+                           float *so2_host, void *stream);
+
+/* Intermediate results of the same pipeline, for testing.  Any output may be NULL.
+ *   ybar_dev  : hl*wl*3 doubles, low-pass band divided by 2^n (block mean of y).
+ *   conc_dev  : hl*wl*2 floats, concentration low-pass coefficients 2^n * estimate.
+ *   hbo2_dev, hb_dev : height*width floats each.
+ * hl = ceil(height / 2^n), wl = ceil(width / 2^n). */
+hb_status hb_estimate_debug(hb_ctx *ctx, const void *frame_dev, size_t row_stride_bytes, double *ybar_dev,
+                            float *conc_dev, float *hbo2_dev, float *hb_dev, void *stream);
+
+/* The low-pass Bayesian step alone on caller-supplied block means: for each of
+ * npix rows of ybar_dev (3 doubles each) writes the posterior mean (HbO2, Hb)
+ * over the context's grid to conc_dev (2 floats each). */
+hb_status hb_posterior_mean(hb_ctx *ctx, const double *ybar_dev, long npix, float *conc_dev, void *stream);
+
+/* Low-pass band size of the context (hl, wl as above). */
+hb_status hb_lowpass_shape(const hb_ctx *ctx, int *hl, int *wl);
+
+/* Kernel launches the context has made since creation (all entry points). */
+long hb_launch_count(const hb_ctx *ctx);
+
+/* Optional per-stage timing with CUDA events recorded on the launch stream.
+ * hb_timing_start(ctx, max_launches) arms up to max_launches event pairs;
+ * hb_timing_read synchronises them and writes, per stage (HB_STAGE_*), the summed
+ * milliseconds and the number of timed launches, then disarms. */
+hb_status hb_timing_start(hb_ctx *ctx, int max_launches);
+hb_status hb_timing_read(hb_ctx *ctx, double ms[HB_NUM_STAGES], long launches[HB_NUM_STAGES]);
+
+/* Static description of a status code. */
+const char *hb_strerror(hb_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HB_H */

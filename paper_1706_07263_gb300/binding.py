@@ -1,0 +1,189 @@
+"""ctypes binding of libhb.so (include/hb.h).
+
+Argument marshalling only: tensors are passed as raw device pointers, streams as
+``cudaStream_t`` handles, and every step of the estimator runs in the library's
+CUDA kernels.  There is no CPU path: loading fails loudly when the library has
+not been built, and calls on tensors that are not on a CUDA device are refused.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhb.so")
+
+HB_IN_F32_HWC = 0
+HB_IN_U8_HWC = 1
+HB_LAMBDA_ABSOLUTE = 1 << 0
+HB_LOWPASS_TIKHONOV = 1 << 1
+HB_FUSED = 1 << 3
+STAGES = ("analysis", "lowpass", "synthesis", "fused")
+
+STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_SHAPE", 3: "HB_ERR_CUDA", 4: "HB_ERR_OOM", 5: "HB_ERR_BUDGET",
+          6: "HB_ERR_TIMEOUT", 7: "HB_ERR_STATE"}
+
+# Every symbol include/hb.h declares (checked by the CPU tests against the built library).
+EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_estimate_debug", "hb_posterior_mean",
+            "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_strerror")
+
+
+class HbError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+class _Mixing(ctypes.Structure):
+    _fields_ = [("A", (ctypes.c_double * 2) * 3)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("n0", ctypes.c_int), ("n1", ctypes.c_int), ("lo0", ctypes.c_double), ("hi0", ctypes.c_double),
+                ("lo1", ctypes.c_double), ("hi1", ctypes.c_double), ("sigma_l", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhb.so and declare its signatures.  Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run paper_1706_07263_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    P, I, L, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double, ctypes.c_size_t
+    lib.hb_create.argtypes = [ctypes.POINTER(_Mixing), ctypes.POINTER(_Grid), I, D, I, I, I, ctypes.c_uint,
+                              ctypes.POINTER(P)]
+    lib.hb_destroy.argtypes = [P]
+    lib.hb_destroy.restype = None
+    lib.hb_estimate.argtypes = [P, P, S, P, P, P]
+    lib.hb_estimate_host.argtypes = [P, P, S, P, P, P]
+    lib.hb_estimate_debug.argtypes = [P, P, S, P, P, P, P, P]
+    lib.hb_posterior_mean.argtypes = [P, P, L, P, P]
+    lib.hb_lowpass_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.hb_launch_count.argtypes = [P]
+    lib.hb_launch_count.restype = L
+    lib.hb_timing_start.argtypes = [P, I]
+    lib.hb_timing_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(L)]
+    lib.hb_strerror.argtypes = [I]
+    lib.hb_strerror.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        getattr(lib, name)
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise HbError(rc, what)
+
+
+def _dev_ptr(t, what):
+    if t is None:
+        return None
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One estimator configuration (hb_create); see include/hb.h for the semantics."""
+
+    def __init__(self, A, grid: dict, levels: int, lam: float, width: int, height: int, fmt: str = "u8",
+                 flags: int = 0):
+        lib = load()
+        mix = _Mixing()
+        A = np.asarray(A, dtype=np.float64).reshape(3, 2)
+        for c in range(3):
+            for j in range(2):
+                mix.A[c][j] = float(A[c, j])
+        g = _Grid(int(grid["n0"]), int(grid["n1"]), float(grid["lo0"]), float(grid["hi0"]), float(grid["lo1"]),
+                  float(grid["hi1"]), float(grid["sigma_l"]))
+        self.fmt = fmt
+        self.width, self.height, self.levels = width, height, levels
+        self._h = ctypes.c_void_p()
+        _check(lib.hb_create(ctypes.byref(mix), ctypes.byref(g), levels, float(lam), width, height,
+                             HB_IN_U8_HWC if fmt == "u8" else HB_IN_F32_HWC, flags, ctypes.byref(self._h)),
+               "hb_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().hb_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def lowpass_shape(self):
+        hl, wl = ctypes.c_int(), ctypes.c_int()
+        _check(load().hb_lowpass_shape(self._h, ctypes.byref(hl), ctypes.byref(wl)), "hb_lowpass_shape")
+        return hl.value, wl.value
+
+    def estimate(self, frame, thb, so2, stream=None, row_stride_bytes=None):
+        stride = row_stride_bytes if row_stride_bytes is not None else frame.stride(0) * frame.element_size()
+        _check(load().hb_estimate(self._h, _dev_ptr(frame, "frame"), stride, _dev_ptr(thb, "thb"),
+                                  _dev_ptr(so2, "so2"), _stream(stream)), "hb_estimate")
+
+    def estimate_host(self, frame: np.ndarray, thb: np.ndarray, so2: np.ndarray, stream=None):
+        """Host buffers in and out (NumPy or pinned CPU tensors)."""
+        def hp(a):
+            return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+        stride = frame.strides[0] if isinstance(frame, np.ndarray) else frame.stride(0) * frame.element_size()
+        _check(load().hb_estimate_host(self._h, hp(frame), stride, hp(thb), hp(so2), _stream(stream)),
+               "hb_estimate_host")
+
+    def estimate_debug(self, frame, ybar=None, conc=None, hbo2=None, hb=None, stream=None):
+        stride = frame.stride(0) * frame.element_size()
+        _check(load().hb_estimate_debug(self._h, _dev_ptr(frame, "frame"), stride, _dev_ptr(ybar, "ybar"),
+                                        _dev_ptr(conc, "conc"), _dev_ptr(hbo2, "hbo2"), _dev_ptr(hb, "hb"),
+                                        _stream(stream)), "hb_estimate_debug")
+
+    def posterior_mean(self, ybar, conc, stream=None):
+        npix = ybar.numel() // 3
+        _check(load().hb_posterior_mean(self._h, _dev_ptr(ybar, "ybar"), npix, _dev_ptr(conc, "conc"),
+                                        _stream(stream)), "hb_posterior_mean")
+
+    def launch_count(self) -> int:
+        return int(load().hb_launch_count(self._h))
+
+    def timing_start(self, max_launches: int):
+        _check(load().hb_timing_start(self._h, max_launches), "hb_timing_start")
+
+    def timing_read(self) -> dict:
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_long * 4)()
+        _check(load().hb_timing_read(self._h, ms, n), "hb_timing_read")
+        return {STAGES[k]: (ms[k], n[k]) for k in range(4)}
+
+
+def strerror(status: int) -> str:
+    return load().hb_strerror(status).decode()

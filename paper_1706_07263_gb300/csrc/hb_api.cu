@@ -1,0 +1,414 @@
+// hb_api.cu -- the C ABI declared in include/hb.h: argument checks, the host-side
+// FP64 preparation of the operator and grid constants, context-owned scratch,
+// and the launch sequence of one frame.
+#include "hb.h"
+#include "hb_common.cuh"
+
+#include <atomic>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using hb::BayesParams;
+using hb::BayesRec;
+using hb::TransformParams;
+
+struct hb_ctx {
+    int device = 0;
+    int W = 0, H = 0, levels = 0, fmt = 0;
+    unsigned flags = 0;
+    int hl = 0, wl = 0;
+    long npix_ll = 0;
+    double gamma = 0.0;
+    TransformParams tp{};
+    BayesParams bp{};
+    float2* d_lut = nullptr;      // 256 (hi, lo) log-attenuation values of the 8-bit codes
+    BayesRec* d_rec = nullptr;    // per low-pass pixel posterior constants
+    float2* d_chat = nullptr;     // per low-pass pixel posterior mean
+    float* d_partial = nullptr;   // posterior kernel: per-part partial sums
+    unsigned* d_count = nullptr;  // posterior kernel: per-pixel arrival counters (kept at zero)
+    long rec_cap = 0;             // capacity of the four arrays above in pixels
+    // device staging of hb_estimate_host
+    void* d_frame = nullptr;
+    float* d_thb = nullptr;
+    float* d_so2 = nullptr;
+    std::atomic<long> launches{0};
+    // per-stage timing
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_stage;
+    int ev_used = 0;
+    bool timing = false;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t elem_size(int fmt) { return fmt == HB_IN_U8_HWC ? 1 : 4; }
+
+// Operator of Eq. 5 and the grid constants, in FP64.
+void prepare(hb_ctx* c, const hb_mixing* mix, const hb_grid* g, double lambda) {
+    const double(*A)[2] = mix->A;
+    double G[2][2];
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) G[j][k] = A[0][j] * A[0][k] + A[1][j] * A[1][k] + A[2][j] * A[2][k];
+    c->gamma = (c->flags & HB_LAMBDA_ABSOLUTE) ? lambda : lambda * (G[0][0] + G[1][1]) / 2.0;
+    const double R00 = G[0][0] + c->gamma, R11 = G[1][1] + c->gamma, R01 = G[0][1];
+    const double det = R00 * R11 - R01 * R01;
+    for (int ch = 0; ch < 3; ++ch) {
+        c->tp.M[0 * 3 + ch] = (float)((R11 * A[ch][0] - R01 * A[ch][1]) / det);
+        c->tp.M[1 * 3 + ch] = (float)((-R01 * A[ch][0] + R00 * A[ch][1]) / det);
+    }
+    BayesParams& bp = c->bp;
+    bp.n0 = g->n0;
+    bp.n1 = g->n1;
+    bp.lo0 = g->lo0;
+    bp.lo1 = g->lo1;
+    bp.h0 = g->n0 > 1 ? (g->hi0 - g->lo0) / (g->n0 - 1) : 0.0;
+    bp.h1 = g->n1 > 1 ? (g->hi1 - g->lo1) / (g->n1 - 1) : 0.0;
+    // hull of the grid nodes (a single node when n = 1): the reference-node search box
+    bp.hi0 = g->n0 > 1 ? g->hi0 : g->lo0;
+    bp.hi1 = g->n1 > 1 ? g->hi1 : g->lo1;
+    for (int ch = 0; ch < 3; ++ch)
+        for (int j = 0; j < 2; ++j) {
+            bp.A[ch * 2 + j] = A[ch][j];
+            bp.Af[ch * 2 + j] = (float)A[ch][j];
+        }
+    bp.G00 = (float)G[0][0];
+    bp.G01 = (float)G[0][1];
+    bp.G11 = (float)G[1][1];
+    double gd = G[0][0] * G[1][1] - G[0][1] * G[0][1];
+    double r = 0.0;
+    if (!(gd > 1e-12 * G[0][0] * G[1][1])) r = 1e-6 * (G[0][0] + G[1][1] + 1e-300);  // near-collinear columns
+    gd = (G[0][0] + r) * (G[1][1] + r) - G[0][1] * G[0][1];
+    bp.Gi00 = (float)((G[1][1] + r) / gd);
+    bp.Gi01 = (float)(-G[0][1] / gd);
+    bp.Gi11 = (float)((G[0][0] + r) / gd);
+    // base-2 log-likelihood: log2(e) / (2 sigma^2) * (-|residual|^2)
+    const double kappa = 1.0 / (2.0 * g->sigma_l * g->sigma_l * std::log(2.0));
+    const double a0a0 = G[0][0], a0a1 = G[0][1], a1a1 = G[1][1];
+    bp.Aq = (float)(-kappa * bp.h0 * bp.h0 * a0a0);
+    bp.Bq = (float)(-kappa * bp.h0 * bp.h1 * a0a1);
+    bp.Cq = (float)(-kappa * bp.h1 * bp.h1 * a1a1);
+    for (int ch = 0; ch < 3; ++ch) {
+        bp.u_scale[ch] = 2.0 * kappa * bp.h0 * A[ch][0];
+        bp.v_scale[ch] = 2.0 * kappa * bp.h1 * A[ch][1];
+    }
+}
+
+hb_status ensure_rec(hb_ctx* c, long npix) {
+    if (npix <= c->rec_cap) return HB_OK;
+    cudaFree(c->d_rec);
+    cudaFree(c->d_chat);
+    cudaFree(c->d_partial);
+    cudaFree(c->d_count);
+    c->d_rec = nullptr;
+    c->d_chat = nullptr;
+    c->d_partial = nullptr;
+    c->d_count = nullptr;
+    c->rec_cap = 0;
+    if (cudaMalloc(&c->d_rec, sizeof(BayesRec) * npix) != cudaSuccess ||
+        cudaMalloc(&c->d_chat, sizeof(float2) * npix) != cudaSuccess ||
+        cudaMalloc(&c->d_partial, sizeof(float) * 3 * hb::kMaxParts * npix) != cudaSuccess ||
+        cudaMalloc(&c->d_count, sizeof(unsigned) * npix) != cudaSuccess) {
+        cudaGetLastError();
+        return HB_ERR_OOM;
+    }
+    if (cudaMemset(c->d_count, 0, sizeof(unsigned) * npix) != cudaSuccess) return HB_ERR_CUDA;
+    c->rec_cap = npix;
+    return HB_OK;
+}
+
+hb::PosteriorScratch post_scratch(const hb_ctx* c) { return hb::PosteriorScratch{c->d_partial, c->d_count, hb::kMaxParts}; }
+
+// Event bracket around one launch when timing is armed.
+struct StageTimer {
+    hb_ctx* c;
+    cudaStream_t s;
+    int slot = -1;
+    StageTimer(hb_ctx* c_, cudaStream_t s_, int stage) : c(c_), s(s_) {
+        if (c->timing && 2 * (c->ev_used + 1) <= (int)c->ev.size()) {
+            slot = c->ev_used++;
+            c->ev_stage[slot] = stage;
+            cudaEventRecord(c->ev[2 * slot], s);
+        }
+    }
+    ~StageTimer() {
+        if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], s);
+    }
+};
+
+hb_status check_frame_args(const hb_ctx* c, const void* frame, size_t stride) {
+    if (!frame) return HB_ERR_ARG;
+    const size_t es = elem_size(c->fmt);
+    if (stride < (size_t)c->W * 3 * es) return HB_ERR_ARG;
+    if (es == 4 && ((reinterpret_cast<uintptr_t>(frame) & 3) || (stride & 3))) return HB_ERR_ARG;
+    return HB_OK;
+}
+
+hb_status run_frame(hb_ctx* c, const void* frame, size_t stride, double* ybar, float* out0, float* out1,
+                    float2* conc_scaled, int debug, cudaStream_t s) {
+    cudaError_t e;
+    {
+        StageTimer t(c, s, HB_STAGE_ANALYSIS);
+        e = hb::launch_analysis(c->tp, c->bp, frame, stride, c->d_lut, ybar, c->d_rec, s);
+        c->launches++;
+    }
+    if (e != cudaSuccess) return HB_ERR_CUDA;
+    if (!(c->flags & HB_LOWPASS_TIKHONOV)) {
+        StageTimer t(c, s, HB_STAGE_LOWPASS);
+        e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, conc_scaled,
+                                 (float)(1 << c->levels), s);
+        c->launches++;
+    }
+    if (e != cudaSuccess) return HB_ERR_CUDA;
+    if (out0 || out1) {
+        StageTimer t(c, s, HB_STAGE_SYNTHESIS);
+        e = hb::launch_synthesis(c->tp, frame, stride, c->d_lut, c->d_chat, out0, out1, debug, s);
+        c->launches++;
+    }
+    return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+hb_status hb_create(const hb_mixing* mix, const hb_grid* grid, int levels, double lambda, int width, int height,
+                    int in_format, unsigned flags, hb_ctx** out) {
+    if (!out) return HB_ERR_ARG;
+    *out = nullptr;
+    if (!mix || !grid) return HB_ERR_ARG;
+    if (in_format != HB_IN_F32_HWC && in_format != HB_IN_U8_HWC) return HB_ERR_ARG;
+    if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_LOWPASS_TIKHONOV | HB_FUSED)) return HB_ERR_ARG;
+    if (width <= 0 || height <= 0 || levels < 0 || levels > hb::kMaxLevels) return HB_ERR_SHAPE;
+    if (grid->n0 < 1 || grid->n1 < 1 || !(grid->hi0 >= grid->lo0) || !(grid->hi1 >= grid->lo1) ||
+        !(grid->sigma_l > 0.0))
+        return HB_ERR_SHAPE;
+    if (levels == 0 && (flags & HB_LOWPASS_TIKHONOV)) return HB_ERR_ARG;
+    if (!std::isfinite(lambda) || lambda < 0.0) return HB_ERR_ARG;
+    for (int c = 0; c < 3; ++c)
+        for (int j = 0; j < 2; ++j)
+            if (!std::isfinite(mix->A[c][j])) return HB_ERR_ARG;
+
+    hb_ctx* c = new (std::nothrow) hb_ctx();
+    if (!c) return HB_ERR_OOM;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        cudaGetLastError();
+        return HB_ERR_CUDA;
+    }
+    c->W = width;
+    c->H = height;
+    c->levels = levels;
+    c->fmt = in_format;
+    c->flags = flags;
+    const int B = 1 << levels;
+    c->hl = (height + B - 1) / B;
+    c->wl = (width + B - 1) / B;
+    c->npix_ll = (long)c->hl * c->wl;
+    prepare(c, mix, grid, lambda);
+
+    TransformParams& tp = c->tp;
+    tp.H = height;
+    tp.W = width;
+    tp.levels = levels;
+    tp.fmt = in_format;
+    tp.eps = 1e-6f;
+    const int Wp = c->wl * B;
+    int tw = 2048 / B;
+    if (tw < B) tw = B;
+    if (tw > Wp) tw = Wp;
+    tp.tile_w = tw;
+    tp.hl = c->hl;
+    tp.wl = c->wl;
+    tp.tikhonov_lowpass = (flags & HB_LOWPASS_TIKHONOV) ? 1 : 0;
+
+    float2 lut[256];
+    for (int k = 0; k < 256; ++k) {
+        const double y = -std::log((double)(k > 0 ? k : 1) / 255.0);
+        const float hi = (float)y;
+        lut[k] = make_float2(hi, (float)(y - (double)hi));
+    }
+    hb_status st = HB_OK;
+    if (cudaMalloc(&c->d_lut, sizeof(lut)) != cudaSuccess) st = HB_ERR_OOM;
+    if (st == HB_OK && cudaMemcpy(c->d_lut, lut, sizeof(lut), cudaMemcpyHostToDevice) != cudaSuccess) st = HB_ERR_CUDA;
+    if (st == HB_OK) st = ensure_rec(c, c->npix_ll);
+    if (st != HB_OK) {
+        cudaGetLastError();
+        hb_destroy(c);
+        return st;
+    }
+    *out = c;
+    return HB_OK;
+}
+
+void hb_destroy(hb_ctx* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    cudaFree(c->d_lut);
+    cudaFree(c->d_rec);
+    cudaFree(c->d_chat);
+    cudaFree(c->d_partial);
+    cudaFree(c->d_count);
+    cudaFree(c->d_frame);
+    cudaFree(c->d_thb);
+    cudaFree(c->d_so2);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete c;
+}
+
+hb_status hb_estimate(hb_ctx* c, const void* frame_dev, size_t row_stride_bytes, float* thb_dev, float* so2_dev,
+                      void* stream) {
+    if (!c || !thb_dev || !so2_dev) return HB_ERR_ARG;
+    hb_status st = check_frame_args(c, frame_dev, row_stride_bytes);
+    if (st != HB_OK) return st;
+    DeviceGuard g(c->device);
+    return run_frame(c, frame_dev, row_stride_bytes, nullptr, thb_dev, so2_dev, nullptr, 0,
+                     static_cast<cudaStream_t>(stream));
+}
+
+hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_bytes, float* thb_host,
+                           float* so2_host, void* stream) {
+    if (!c || !frame_host || !thb_host || !so2_host) return HB_ERR_ARG;
+    const size_t es = elem_size(c->fmt);
+    const size_t row = (size_t)c->W * 3 * es;
+    if (row_stride_bytes < row) return HB_ERR_ARG;
+    DeviceGuard g(c->device);
+    const size_t npx = (size_t)c->W * c->H;
+    if (!c->d_frame) {
+        if (cudaMalloc(&c->d_frame, row * c->H) != cudaSuccess || cudaMalloc(&c->d_thb, npx * 4) != cudaSuccess ||
+            cudaMalloc(&c->d_so2, npx * 4) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->d_frame);
+            cudaFree(c->d_thb);
+            cudaFree(c->d_so2);
+            c->d_frame = nullptr;
+            c->d_thb = nullptr;
+            c->d_so2 = nullptr;
+            return HB_ERR_OOM;
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpy2DAsync(c->d_frame, row, frame_host, row_stride_bytes, row, c->H, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return HB_ERR_CUDA;
+    hb_status st = run_frame(c, c->d_frame, row, nullptr, c->d_thb, c->d_so2, nullptr, 0, s);
+    if (st != HB_OK) return st;
+    if (cudaMemcpyAsync(thb_host, c->d_thb, npx * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(so2_host, c->d_so2, npx * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return HB_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+}
+
+hb_status hb_estimate_debug(hb_ctx* c, const void* frame_dev, size_t row_stride_bytes, double* ybar_dev,
+                            float* conc_dev, float* hbo2_dev, float* hb_dev, void* stream) {
+    if (!c) return HB_ERR_ARG;
+    if ((hbo2_dev == nullptr) != (hb_dev == nullptr)) return HB_ERR_ARG;
+    if (conc_dev && (reinterpret_cast<uintptr_t>(conc_dev) & 7)) return HB_ERR_ARG;
+    hb_status st = check_frame_args(c, frame_dev, row_stride_bytes);
+    if (st != HB_OK) return st;
+    DeviceGuard g(c->device);
+    return run_frame(c, frame_dev, row_stride_bytes, ybar_dev, hbo2_dev, hb_dev, reinterpret_cast<float2*>(conc_dev),
+                     1, static_cast<cudaStream_t>(stream));
+}
+
+hb_status hb_posterior_mean(hb_ctx* c, const double* ybar_dev, long npix, float* conc_dev, void* stream) {
+    if (!c || npix < 0) return HB_ERR_ARG;
+    if (npix == 0) return HB_OK;
+    if (!ybar_dev || !conc_dev || (reinterpret_cast<uintptr_t>(conc_dev) & 7) ||
+        (reinterpret_cast<uintptr_t>(ybar_dev) & 7))
+        return HB_ERR_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (npix > c->rec_cap) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return HB_ERR_CUDA;
+        hb_status st = ensure_rec(c, npix);
+        if (st != HB_OK) return st;
+    }
+    cudaError_t e = hb::launch_setup(c->bp, ybar_dev, npix, c->d_rec, s);
+    c->launches++;
+    if (e != cudaSuccess) return HB_ERR_CUDA;
+    StageTimer t(c, s, HB_STAGE_LOWPASS);
+    e = hb::launch_posterior(c->bp, c->d_rec, npix, post_scratch(c), reinterpret_cast<float2*>(conc_dev), nullptr, 1.f,
+                             s);
+    c->launches++;
+    return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+}
+
+hb_status hb_lowpass_shape(const hb_ctx* c, int* hl, int* wl) {
+    if (!c || !hl || !wl) return HB_ERR_ARG;
+    *hl = c->hl;
+    *wl = c->wl;
+    return HB_OK;
+}
+
+long hb_launch_count(const hb_ctx* c) { return c ? c->launches.load() : 0; }
+
+hb_status hb_timing_start(hb_ctx* c, int max_launches) {
+    if (!c || max_launches <= 0) return HB_ERR_ARG;
+    DeviceGuard g(c->device);
+    while ((int)c->ev.size() < 2 * max_launches) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return HB_ERR_CUDA;
+        c->ev.push_back(e);
+    }
+    c->ev_stage.assign(c->ev.size() / 2, -1);
+    c->ev_used = 0;
+    c->timing = true;
+    return HB_OK;
+}
+
+hb_status hb_timing_read(hb_ctx* c, double ms[HB_NUM_STAGES], long launches[HB_NUM_STAGES]) {
+    if (!c || !ms || !launches) return HB_ERR_ARG;
+    if (!c->timing) return HB_ERR_STATE;
+    DeviceGuard g(c->device);
+    for (int k = 0; k < HB_NUM_STAGES; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    hb_status st = HB_OK;
+    for (int i = 0; i < c->ev_used; ++i) {
+        float t = 0.f;
+        if (cudaEventSynchronize(c->ev[2 * i + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t, c->ev[2 * i], c->ev[2 * i + 1]) != cudaSuccess) {
+            st = HB_ERR_CUDA;
+            break;
+        }
+        ms[c->ev_stage[i]] += t;
+        launches[c->ev_stage[i]] += 1;
+    }
+    c->timing = false;
+    c->ev_used = 0;
+    return st;
+}
+
+const char* hb_strerror(hb_status s) {
+    switch (s) {
+        case HB_OK: return "ok";
+        case HB_ERR_ARG: return "invalid argument";
+        case HB_ERR_SHAPE: return "invalid size or level count";
+        case HB_ERR_CUDA: return "CUDA error";
+        case HB_ERR_OOM: return "out of memory";
+        case HB_ERR_BUDGET: return "memory budget exceeded";
+        case HB_ERR_TIMEOUT: return "timed out";
+        case HB_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// hb_common.cuh -- parameter blocks and launch wrappers shared by the CUDA
+// translation units of libhb.  Internal: not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hb {
+
+constexpr int kThreads = 256;       // threads per CTA of every kernel here
+constexpr int kMaxLevels = 6;
+
+// Frame geometry and the per-coefficient Tikhonov operator (Eq. 5).
+struct TransformParams {
+    int H, W;                 // frame size in pixels
+    int levels;               // Haar levels n (0..6)
+    int fmt;                  // 0 = f32 HWC, 1 = u8 HWC
+    float eps;                // intensity floor before the logarithm (f32 input)
+    int tile_w;               // tile width in pixels (multiple of 2^n)
+    int hl, wl;               // low-pass band size: ceil(H / 2^n) x ceil(W / 2^n)
+    int tikhonov_lowpass;     // 1: low pass through M as well
+    float M[6];               // M[j*3 + c], j = HbO2/Hb, c = R/G/B
+};
+
+// Constants of the grid posterior, prepared in FP64 on the host.
+// Grid node (i, j) sits at (lo0 + i h0, lo1 + j h1).  Relative to a reference
+// node (i0, j0) the base-2 log-likelihood ratio of node (i0 + di, j0 + dj) is
+//   U di + V dj + Aq di^2 + 2 Bq di dj + Cq dj^2,
+// with U, V per pixel and Aq, Bq, Cq per grid.
+struct BayesParams {
+    int n0, n1;
+    double lo0, h0, lo1, h1, hi0, hi1;
+    double A[6];              // A[c*2 + j]
+    float Af[6];              // same, FP32
+    float G00, G01, G11;      // A^T A (FP32, for choosing the reference node)
+    float Gi00, Gi01, Gi11;   // (A^T A)^-1
+    double u_scale[3];        // 2 kappa h0 a0[c]: U = sum_c r0[c] u_scale[c]
+    double v_scale[3];        // 2 kappa h1 a1[c]
+    float Aq, Bq, Cq;
+};
+
+// Per low-pass pixel record written by the analysis kernel for the posterior kernel.
+struct __align__(16) BayesRec {
+    int i0, j0;               // reference node (nearest node to the box-constrained maximiser)
+    float U, V;               // linear coefficients of the log2-likelihood ratio
+};
+
+// Scratch of the posterior kernel: per-part partial sums of each pixel and a per-pixel
+// arrival counter (zero between launches; the kernel resets what it uses).
+struct PosteriorScratch {
+    float* partial;           // npix * max_parts * 3
+    unsigned* count;          // npix
+    int max_parts;
+};
+constexpr int kMaxParts = 8;
+
+// Launch wrappers (defined in the .cu files).  All return the launch status.
+cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
+                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s);
+cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s);
+cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
+                             float2* chat, float2* chat_scaled, float scale, cudaStream_t s);
+cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_t stride, const float2* lut,
+                             const float2* chat, float* out0, float* out1, int debug_conc, cudaStream_t s);
+size_t transform_smem_bytes(const TransformParams& tp);
+
+}  // namespace hb

@@ -1,0 +1,588 @@
+// hb_transform.cu -- the HBM-bound passes of the estimator.
+//
+//   analysis kernel  : frame tile -> log-attenuation -> n levels of the 2x2-window
+//                      Haar transform (Eq. 1-2) -> low-pass block means ybar, plus the
+//                      per-pixel constants of the grid posterior (reference node, U, V).
+//   synthesis kernel : frame tile -> log-attenuation -> n analysis levels -> Tikhonov
+//                      operator M on every directional coefficient (Eq. 5) -> low pass
+//                      from the posterior step -> n inverse levels (Eq. 4, H = H*) ->
+//                      THb and SO2 (Section 3).
+//
+// Both kernels work on tiles of one 2^n-row band of superblocks (2^n x 2^n pixel
+// blocks; Haar windows never cross a superblock, so tiles need no halo).  A tile is
+// copied from HBM with coalesced 16-byte loads into shared memory, and the whole
+// multi-level transform runs in place there (Mallat layout: after level l the low
+// pass of each 2^l block sits at its top-left position and the three directional
+// coefficients at the other window positions).
+//
+// Numerics.  Before the transform every pixel's log-attenuation has the value of
+// its superblock's top-left pixel subtracted (per channel).  The transform is
+// linear, so the directional coefficients are unchanged and the low pass shifts by
+// 2^n times that offset, which is added back in FP64 (analysis) or as the posterior
+// estimate after synthesis.  This keeps every FP32 sum at the scale of the
+// within-block variation instead of the level-n low pass (up to 2^n * 5.5).  For 8-bit
+// input the logarithm comes from a 256-entry table of FP64 values split as
+// float hi + float lo.
+#include "hb_common.cuh"
+
+#include <math.h>
+
+namespace hb {
+
+namespace {
+
+struct TileSmem {
+    unsigned char* raw;  // TH * TW * 3 elements of the input format
+    float2* lut;         // 256 entries (8-bit input)
+    float* D;            // 3 planes of TH * TW floats
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline size_t raw_bytes(int TH, int TW, int fmt) {
+    return align16((size_t)TH * TW * 3 * (fmt == 1 ? 1 : 4));
+}
+
+__device__ inline TileSmem carve(unsigned char* base, int TH, int TW, int fmt) {
+    TileSmem t;
+    t.raw = base;
+    t.lut = reinterpret_cast<float2*>(base + raw_bytes(TH, TW, fmt));
+    t.D = reinterpret_cast<float*>(base + raw_bytes(TH, TW, fmt) + 256 * sizeof(float2));
+    return t;
+}
+
+// Copy the TH x TW pixel tile at (ty0, tx0) into shared memory, replicating the
+// last row / column for positions outside the frame (edge padding).
+__device__ void load_tile(const TransformParams& tp, const unsigned char* frame, size_t stride, int ty0, int tx0,
+                          int TH, int TW, const float2* lut_g, TileSmem sm) {
+    const int es = tp.fmt == 1 ? 1 : 4;
+    const int rowbytes = TW * 3 * es;
+    if (tp.fmt == 1)
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) sm.lut[i] = lut_g[i];
+    for (int r = 0; r < TH; ++r) {
+        const int gy = min(ty0 + r, tp.H - 1);
+        const unsigned char* src = frame + (size_t)gy * stride + (size_t)tx0 * 3 * es;
+        unsigned char* dst = sm.raw + (size_t)r * rowbytes;
+        const bool vec = (tx0 + TW <= tp.W) && ((reinterpret_cast<uintptr_t>(src) & 15) == 0) && (rowbytes % 16 == 0);
+        if (vec) {
+            const uint4* s4 = reinterpret_cast<const uint4*>(src);
+            uint4* d4 = reinterpret_cast<uint4*>(dst);
+            for (int i = threadIdx.x; i < rowbytes / 16; i += blockDim.x) d4[i] = __ldg(s4 + i);
+        } else {
+            const unsigned char* rowp = frame + (size_t)gy * stride;
+            for (int e = threadIdx.x; e < TW * 3; e += blockDim.x) {
+                const int x = min(tx0 + e / 3, tp.W - 1);
+                const int ch = e % 3;
+                if (es == 1)
+                    dst[e] = rowp[(size_t)x * 3 + ch];
+                else
+                    reinterpret_cast<float*>(dst)[e] = reinterpret_cast<const float*>(rowp)[(size_t)x * 3 + ch];
+            }
+        }
+    }
+}
+
+// Log-attenuation of one raw sample as (hi, lo) with hi + lo = -ln(max(I, eps)).
+__device__ __forceinline__ float2 log_atten(const TransformParams& tp, const TileSmem& sm, int idx) {
+    if (tp.fmt == 1) return sm.lut[sm.raw[idx]];
+    const float I = reinterpret_cast<const float*>(sm.raw)[idx];
+    return make_float2(-logf(fmaxf(I, tp.eps)), 0.f);
+}
+
+// y(p) - y(top-left of p's superblock), per channel, into the three D planes.
+__device__ void offset_log(const TransformParams& tp, const TileSmem& sm, int TH, int TW) {
+    const int n = TH * TW;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int r = p / TW, c = p - r * TW;
+        const int cref = c & ~(TH - 1);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float2 y = log_atten(tp, sm, p * 3 + ch);
+            const float2 yr = log_atten(tp, sm, cref * 3 + ch);
+            sm.D[ch * n + r * TW + c] = (y.x - yr.x) + (y.y - yr.y);
+        }
+    }
+}
+
+// n in-place analysis levels on `nch` planes.  LL_ONLY skips the directional outputs.
+template <bool LL_ONLY>
+__device__ void analysis_levels(float* D, int nch, int TH, int TW, int levels) {
+    const int n = TH * TW;
+    for (int l = 1; l <= levels; ++l) {
+        const int s = 1 << (l - 1), step = 2 * s;
+        const int wr = TH / step, wc = TW / step, nwin = wr * wc;
+        for (int t = threadIdx.x; t < nwin * nch; t += blockDim.x) {
+            const int ch = t / nwin, w = t - ch * nwin;
+            const int r = (w / wc) * step, c = (w % wc) * step;
+            float* P = D + ch * n;
+            const float a = P[r * TW + c], b = P[r * TW + c + s];
+            const float cc = P[(r + s) * TW + c], d = P[(r + s) * TW + c + s];
+            const float s1 = a + b, s2 = cc + d;
+            P[r * TW + c] = 0.5f * (s1 + s2);                 // low pass
+            if (!LL_ONLY) {
+                const float d1 = a - b, d2 = cc - d;
+                P[r * TW + c + s] = 0.5f * (s1 - s2);         // rows differ    [1, 1,-1,-1]
+                P[(r + s) * TW + c] = 0.5f * (d1 - d2);       // diagonal       [1,-1,-1, 1]
+                P[(r + s) * TW + c + s] = 0.5f * (d1 + d2);   // columns differ [1,-1, 1,-1]
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// n in-place inverse levels (H is its own inverse) on `nch` planes.
+__device__ void synthesis_levels(float* D, int nch, int TH, int TW, int levels) {
+    const int n = TH * TW;
+    for (int l = levels; l >= 1; --l) {
+        const int s = 1 << (l - 1), step = 2 * s;
+        const int wr = TH / step, wc = TW / step, nwin = wr * wc;
+        for (int t = threadIdx.x; t < nwin * nch; t += blockDim.x) {
+            const int ch = t / nwin, w = t - ch * nwin;
+            const int r = (w / wc) * step, c = (w % wc) * step;
+            float* P = D + ch * n;
+            const float ll = P[r * TW + c], d1 = P[r * TW + c + s];
+            const float d2 = P[(r + s) * TW + c], d3 = P[(r + s) * TW + c + s];
+            const float p = ll + d1, q = ll - d1, u = d2 + d3, v = d2 - d3;
+            P[r * TW + c] = 0.5f * (p + u);
+            P[r * TW + c + s] = 0.5f * (p - u);
+            P[(r + s) * TW + c] = 0.5f * (q - v);
+            P[(r + s) * TW + c + s] = 0.5f * (q + v);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// Reference node and linear coefficients of the posterior for one low-pass pixel.
+// The reference node is the grid node nearest to the maximiser of the likelihood
+// over the (continuous) concentration box -- a 2-D box-constrained least-squares
+// problem solved exactly by checking the interior optimum and then the four
+// edges.  It only fixes where the log-likelihood is expanded (so that the FP32
+// sums near the posterior peak involve small numbers); any node gives the same
+// posterior mean in exact arithmetic.
+__device__ BayesRec bayes_setup(const double yb[3], const BayesParams& bp) {
+    const float y0 = (float)yb[0], y1 = (float)yb[1], y2 = (float)yb[2];
+    const float z0 = bp.Af[0] * y0 + bp.Af[2] * y1 + bp.Af[4] * y2;
+    const float z1 = bp.Af[1] * y0 + bp.Af[3] * y1 + bp.Af[5] * y2;
+    const float lo0 = (float)bp.lo0, hi0 = (float)bp.hi0, lo1 = (float)bp.lo1, hi1 = (float)bp.hi1;
+    float c0 = bp.Gi00 * z0 + bp.Gi01 * z1;
+    float c1 = bp.Gi01 * z0 + bp.Gi11 * z1;
+    if (!(c0 >= lo0 && c0 <= hi0 && c1 >= lo1 && c1 <= hi1)) {
+        // objective |y - A c|^2 - |y|^2 = c^T G c - 2 z^T c, minimised on each edge
+        float best = INFINITY, b0 = lo0, b1 = lo1;
+        for (int e = 0; e < 4; ++e) {
+            float a0, a1;
+            if (e < 2) {
+                a0 = e == 0 ? lo0 : hi0;
+                a1 = bp.G11 > 0.f ? (z1 - bp.G01 * a0) / bp.G11 : lo1;
+                a1 = fminf(fmaxf(a1, lo1), hi1);
+            } else {
+                a1 = e == 2 ? lo1 : hi1;
+                a0 = bp.G00 > 0.f ? (z0 - bp.G01 * a1) / bp.G00 : lo0;
+                a0 = fminf(fmaxf(a0, lo0), hi0);
+            }
+            const float f = a0 * (bp.G00 * a0 + 2.f * bp.G01 * a1) + bp.G11 * a1 * a1 - 2.f * (z0 * a0 + z1 * a1);
+            if (f < best) { best = f; b0 = a0; b1 = a1; }
+        }
+        c0 = b0;
+        c1 = b1;
+    }
+    BayesRec rec;
+    rec.i0 = bp.h0 > 0 ? min(max(__float2int_rn((c0 - lo0) / (float)bp.h0), 0), bp.n0 - 1) : 0;
+    rec.j0 = bp.h1 > 0 ? min(max(__float2int_rn((c1 - lo1) / (float)bp.h1), 0), bp.n1 - 1) : 0;
+    // residual at the reference node, FP64 (cancellation happens here)
+    const double cr0 = bp.lo0 + rec.i0 * bp.h0, cr1 = bp.lo1 + rec.j0 * bp.h1;
+    double U = 0.0, V = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double r = yb[c] - bp.A[c * 2] * cr0 - bp.A[c * 2 + 1] * cr1;
+        U += r * bp.u_scale[c];
+        V += r * bp.v_scale[c];
+    }
+    rec.U = (float)U;
+    rec.V = (float)V;
+    return rec;
+}
+
+namespace {
+
+__global__ void __launch_bounds__(kThreads) analysis_kernel(TransformParams tp, BayesParams bp,
+                                                            const unsigned char* __restrict__ frame, size_t stride,
+                                                            const float2* __restrict__ lut, double* __restrict__ ybar,
+                                                            BayesRec* __restrict__ rec) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int TH = 1 << tp.levels, TW = tp.tile_w;
+    const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+    TileSmem sm = carve(smem, TH, TW, tp.fmt);
+    load_tile(tp, frame, stride, ty0, tx0, TH, TW, lut, sm);
+    __syncthreads();
+    offset_log(tp, sm, TH, TW);
+    __syncthreads();
+    analysis_levels<true>(sm.D, 3, TH, TW, tp.levels);
+    const int nsb = TW / TH, n = TH * TW;
+    const double inv = 1.0 / (double)TH;
+    for (int t = threadIdx.x; t < nsb; t += blockDim.x) {
+        const int gx = tx0 / TH + t;
+        if (gx >= tp.wl) continue;
+        double yb[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float2 yr = log_atten(tp, sm, t * TH * 3 + ch);
+            yb[ch] = (double)yr.x + (double)yr.y + (double)sm.D[ch * n + t * TH] * inv;
+        }
+        const size_t o = (size_t)blockIdx.y * tp.wl + gx;
+        if (ybar) {
+            ybar[o * 3 + 0] = yb[0];
+            ybar[o * 3 + 1] = yb[1];
+            ybar[o * 3 + 2] = yb[2];
+        }
+        rec[o] = bayes_setup(yb, bp);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) setup_kernel(BayesParams bp, const double* __restrict__ ybar, long npix,
+                                                         BayesRec* __restrict__ rec) {
+    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    double yb[3] = {ybar[p * 3], ybar[p * 3 + 1], ybar[p * 3 + 2]};
+    rec[p] = bayes_setup(yb, bp);
+}
+
+__global__ void __launch_bounds__(kThreads) synthesis_kernel(TransformParams tp, const unsigned char* __restrict__ frame,
+                                                             size_t stride, const float2* __restrict__ lut,
+                                                             const float2* __restrict__ chat, float* __restrict__ out0,
+                                                             float* __restrict__ out1, int debug_conc) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int TH = 1 << tp.levels, TW = tp.tile_w;
+    const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+    TileSmem sm = carve(smem, TH, TW, tp.fmt);
+    load_tile(tp, frame, stride, ty0, tx0, TH, TW, lut, sm);
+    __syncthreads();
+    offset_log(tp, sm, TH, TW);
+    __syncthreads();
+    analysis_levels<false>(sm.D, 3, TH, TW, tp.levels);
+    // Tikhonov operator on every directional coefficient (3 colours -> 2 concentrations);
+    // the low-pass position takes 0 (posterior estimate added after synthesis) or, in the
+    // all-Tikhonov mode, M applied to the offset-free low pass.
+    const int n = TH * TW;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int r = p / TW, c = p - r * TW;
+        const float v0 = sm.D[p], v1 = sm.D[n + p], v2 = sm.D[2 * n + p];
+        const bool is_ll = (r == 0) && ((c & (TH - 1)) == 0);
+        float o0 = tp.M[0] * v0 + tp.M[1] * v1 + tp.M[2] * v2;
+        float o1 = tp.M[3] * v0 + tp.M[4] * v1 + tp.M[5] * v2;
+        if (is_ll && !tp.tikhonov_lowpass) o0 = o1 = 0.f;
+        sm.D[p] = o0;
+        sm.D[n + p] = o1;
+    }
+    __syncthreads();
+    synthesis_levels(sm.D, 2, TH, TW, tp.levels);
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int r = p / TW, c = p - r * TW;
+        const int gy = ty0 + r, gx = tx0 + c;
+        if (gy >= tp.H || gx >= tp.W) continue;
+        float off0, off1;
+        if (tp.tikhonov_lowpass) {
+            const int cref = c & ~(TH - 1);
+            const float2 ya = log_atten(tp, sm, cref * 3 + 0);
+            const float2 yb = log_atten(tp, sm, cref * 3 + 1);
+            const float2 yc = log_atten(tp, sm, cref * 3 + 2);
+            off0 = (tp.M[0] * ya.x + tp.M[1] * yb.x + tp.M[2] * yc.x) + (tp.M[0] * ya.y + tp.M[1] * yb.y + tp.M[2] * yc.y);
+            off1 = (tp.M[3] * ya.x + tp.M[4] * yb.x + tp.M[5] * yc.x) + (tp.M[3] * ya.y + tp.M[4] * yb.y + tp.M[5] * yc.y);
+        } else {
+            const float2 ch = chat[(size_t)blockIdx.y * tp.wl + (gx >> tp.levels)];
+            off0 = ch.x;
+            off1 = ch.y;
+        }
+        const float hbo2 = sm.D[p] + off0, hb = sm.D[n + p] + off1;
+        const size_t o = (size_t)gy * tp.W + gx;
+        if (debug_conc) {
+            out0[o] = hbo2;
+            out1[o] = hb;
+        } else {
+            const float thb = hbo2 + hb;
+            out0[o] = thb;
+            out1[o] = thb > 0.f ? hbo2 / thb : 0.f;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Register (warp-column) variants for n <= 4.  Lane l of a warp owns pixel column
+// x = 32 w + l for the 2^n rows of one superblock band, so a superblock spans 2^n
+// neighbouring lanes.  Level l pairs rows r, r+s inside the lane and columns x, x+s
+// across lanes (s = 2^(l-1), shuffle with lane ^ s); the in-place layout is the same
+// as in the shared-memory kernels (low pass at the window's top-left, directional
+// coefficients at the other three positions), and so is every FP32 operation.
+// ------------------------------------------------------------------------------------
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int L, bool LL_ONLY>
+__device__ __forceinline__ void warp_analysis(float (&v)[3][1 << L], int lane) {
+    constexpr int TH = 1 << L;
+#pragma unroll
+    for (int l = 1; l <= L; ++l) {
+        const int s = 1 << (l - 1);
+        const bool active = (lane & (s - 1)) == 0;
+        const bool right = (lane & s) != 0;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+            for (int r = 0; r < TH; r += 2 * s) {
+                const float x = v[ch][r], z = v[ch][r + s];
+                const float xp = __shfl_xor_sync(kFull, x, s), zp = __shfl_xor_sync(kFull, z, s);
+                const float a = right ? xp : x, b = right ? x : xp, c = right ? zp : z, d = right ? z : zp;
+                const float s1 = a + b, s2 = c + d, d1 = a - b, d2 = c - d;
+                if (active) {
+                    if (!right) {
+                        v[ch][r] = 0.5f * (s1 + s2);                    // low pass
+                        if (!LL_ONLY) v[ch][r + s] = 0.5f * (d1 - d2);  // diagonal
+                    } else if (!LL_ONLY) {
+                        v[ch][r] = 0.5f * (s1 - s2);                    // rows differ
+                        v[ch][r + s] = 0.5f * (d1 + d2);                // columns differ
+                    }
+                }
+            }
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void warp_synthesis(float (&c)[2][1 << L], int lane) {
+    constexpr int TH = 1 << L;
+#pragma unroll
+    for (int l = L; l >= 1; --l) {
+        const int s = 1 << (l - 1);
+        const bool active = (lane & (s - 1)) == 0;
+        const bool right = (lane & s) != 0;
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+            for (int r = 0; r < TH; r += 2 * s) {
+                const float x = c[ch][r], z = c[ch][r + s];
+                const float xp = __shfl_xor_sync(kFull, x, s), zp = __shfl_xor_sync(kFull, z, s);
+                const float ll = right ? xp : x, d1 = right ? x : xp, d2 = right ? zp : z, d3 = right ? z : zp;
+                const float p = ll + d1, q = ll - d1, u = d2 + d3, w = d2 - d3;
+                if (active) {
+                    if (!right) {
+                        c[ch][r] = 0.5f * (p + u);
+                        c[ch][r + s] = 0.5f * (q - w);
+                    } else {
+                        c[ch][r] = 0.5f * (p - u);
+                        c[ch][r + s] = 0.5f * (q + w);
+                    }
+                }
+            }
+    }
+}
+
+// Raw samples of the lane's column (codes or intensities), the superblock's top-left
+// log-attenuation (hi, lo) and the offset-free values d = y - y_ref.
+template <int L>
+__device__ __forceinline__ void warp_load(const TransformParams& tp, const unsigned char* __restrict__ frame,
+                                          size_t stride, const float2* lut, int by, int x, int lane,
+                                          float (&v)[3][1 << L], float2 (&yref)[3]) {
+    constexpr int TH = 1 << L;
+    const int xs = min(x, tp.W - 1);
+    const int src_lane = lane & ~(TH - 1);
+    if (tp.fmt == 1) {
+        int k[3][TH];
+#pragma unroll
+        for (int r = 0; r < TH; ++r) {
+            const unsigned char* row = frame + (size_t)min(by * TH + r, tp.H - 1) * stride + (size_t)xs * 3;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) k[ch][r] = __ldg(row + ch);
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const int kr = __shfl_sync(kFull, k[ch][0], src_lane);
+            yref[ch] = lut[kr];
+#pragma unroll
+            for (int r = 0; r < TH; ++r) {
+                const float2 y = lut[k[ch][r]];
+                v[ch][r] = (y.x - yref[ch].x) + (y.y - yref[ch].y);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < TH; ++r) {
+            const float* row =
+                reinterpret_cast<const float*>(frame + (size_t)min(by * TH + r, tp.H - 1) * stride) + (size_t)xs * 3;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) v[ch][r] = -logf(fmaxf(__ldg(row + ch), tp.eps));
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float yr = __shfl_sync(kFull, v[ch][0], src_lane);
+            yref[ch] = make_float2(yr, 0.f);
+#pragma unroll
+            for (int r = 0; r < TH; ++r) v[ch][r] = v[ch][r] - yr;
+        }
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams tp, BayesParams bp,
+                                                                 const unsigned char* __restrict__ frame,
+                                                                 size_t stride, const float2* __restrict__ lut_g,
+                                                                 double* __restrict__ ybar,
+                                                                 BayesRec* __restrict__ rec) {
+    constexpr int TH = 1 << L;
+    __shared__ float2 lut[256];
+    if (tp.fmt == 1)
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = lut_g[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32;
+    if (x0 >= tp.wl * TH) return;  // whole warp right of the padded frame
+    const int x = x0 + lane, by = blockIdx.y;
+    float v[3][TH];
+    float2 yref[3];
+    warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
+    warp_analysis<L, true>(v, lane);
+    if ((lane & (TH - 1)) == 0 && x < tp.wl * TH) {
+        double yb[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) yb[ch] = (double)yref[ch].x + (double)yref[ch].y + (double)v[ch][0] / TH;
+        const size_t o = (size_t)by * tp.wl + (x >> L);
+        if (ybar) {
+            ybar[o * 3 + 0] = yb[0];
+            ybar[o * 3 + 1] = yb[1];
+            ybar[o * 3 + 2] = yb[2];
+        }
+        rec[o] = bayes_setup(yb, bp);
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads) synthesis_warp_kernel(TransformParams tp,
+                                                                  const unsigned char* __restrict__ frame,
+                                                                  size_t stride, const float2* __restrict__ lut_g,
+                                                                  const float2* __restrict__ chat,
+                                                                  float* __restrict__ out0, float* __restrict__ out1,
+                                                                  int debug_conc) {
+    constexpr int TH = 1 << L;
+    __shared__ float2 lut[256];
+    if (tp.fmt == 1)
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = lut_g[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32;
+    if (x0 >= tp.wl * TH) return;
+    const int x = x0 + lane, by = blockIdx.y;
+    float v[3][TH];
+    float2 yref[3];
+    warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
+    warp_analysis<L, false>(v, lane);
+    // Tikhonov operator on every directional coefficient; the low-pass position takes 0
+    // (posterior estimate added after synthesis) or M applied to it (all-Tikhonov mode).
+    float c[2][TH];
+#pragma unroll
+    for (int r = 0; r < TH; ++r) {
+        const float v0 = v[0][r], v1 = v[1][r], v2 = v[2][r];
+        float o0 = tp.M[0] * v0 + tp.M[1] * v1 + tp.M[2] * v2;
+        float o1 = tp.M[3] * v0 + tp.M[4] * v1 + tp.M[5] * v2;
+        if (r == 0 && (lane & (TH - 1)) == 0 && !tp.tikhonov_lowpass) o0 = o1 = 0.f;
+        c[0][r] = o0;
+        c[1][r] = o1;
+    }
+    warp_synthesis<L>(c, lane);
+    float off0, off1;
+    if (tp.tikhonov_lowpass) {
+        off0 = (tp.M[0] * yref[0].x + tp.M[1] * yref[1].x + tp.M[2] * yref[2].x) +
+               (tp.M[0] * yref[0].y + tp.M[1] * yref[1].y + tp.M[2] * yref[2].y);
+        off1 = (tp.M[3] * yref[0].x + tp.M[4] * yref[1].x + tp.M[5] * yref[2].x) +
+               (tp.M[3] * yref[0].y + tp.M[4] * yref[1].y + tp.M[5] * yref[2].y);
+    } else {
+        const float2 ch = chat[(size_t)by * tp.wl + min(x >> L, tp.wl - 1)];
+        off0 = ch.x;
+        off1 = ch.y;
+    }
+    if (x >= tp.W) return;
+#pragma unroll
+    for (int r = 0; r < TH; ++r) {
+        const int gy = by * TH + r;
+        if (gy >= tp.H) break;
+        const float hbo2 = c[0][r] + off0, hb = c[1][r] + off1;
+        const size_t o = (size_t)gy * tp.W + x;
+        if (debug_conc) {
+            out0[o] = hbo2;
+            out1[o] = hb;
+        } else {
+            const float thb = hbo2 + hb;
+            out0[o] = thb;
+            out1[o] = thb > 0.f ? hbo2 / thb : 0.f;
+        }
+    }
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+size_t transform_smem_bytes(const TransformParams& tp) {
+    const int TH = 1 << tp.levels, TW = tp.tile_w;
+    return raw_bytes(TH, TW, tp.fmt) + 256 * sizeof(float2) + (size_t)3 * TH * TW * sizeof(float);
+}
+
+static dim3 tile_grid(const TransformParams& tp) {
+    const int TH = 1 << tp.levels;
+    const int Wp = tp.wl * TH;
+    return dim3((Wp + tp.tile_w - 1) / tp.tile_w, tp.hl);
+}
+
+cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
+                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s) {
+    const unsigned char* f = static_cast<const unsigned char*>(frame);
+    if (tp.levels <= 4) {
+        const int TH = 1 << tp.levels;
+        const dim3 grid((tp.wl * TH + kThreads - 1) / kThreads, tp.hl);
+        switch (tp.levels) {
+            case 0: analysis_warp_kernel<0><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec); break;
+            case 1: analysis_warp_kernel<1><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec); break;
+            case 2: analysis_warp_kernel<2><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec); break;
+            case 3: analysis_warp_kernel<3><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec); break;
+            default: analysis_warp_kernel<4><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec); break;
+        }
+        return cudaGetLastError();
+    }
+    const size_t sm = transform_smem_bytes(tp);
+    cudaError_t e = set_smem(analysis_kernel, sm);
+    if (e != cudaSuccess) return e;
+    analysis_kernel<<<tile_grid(tp), kThreads, sm, s>>>(tp, bp, f, stride, lut, ybar, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s) {
+    if (npix <= 0) return cudaSuccess;
+    setup_kernel<<<(unsigned)((npix + kThreads - 1) / kThreads), kThreads, 0, s>>>(bp, ybar, npix, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_t stride, const float2* lut,
+                             const float2* chat, float* out0, float* out1, int debug_conc, cudaStream_t s) {
+    const unsigned char* f = static_cast<const unsigned char*>(frame);
+    if (tp.levels <= 4) {
+        const int TH = 1 << tp.levels;
+        const dim3 grid((tp.wl * TH + kThreads - 1) / kThreads, tp.hl);
+        switch (tp.levels) {
+            case 0: synthesis_warp_kernel<0><<<grid, kThreads, 0, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc); break;
+            case 1: synthesis_warp_kernel<1><<<grid, kThreads, 0, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc); break;
+            case 2: synthesis_warp_kernel<2><<<grid, kThreads, 0, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc); break;
+            case 3: synthesis_warp_kernel<3><<<grid, kThreads, 0, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc); break;
+            default: synthesis_warp_kernel<4><<<grid, kThreads, 0, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc); break;
+        }
+        return cudaGetLastError();
+    }
+    const size_t sm = transform_smem_bytes(tp);
+    cudaError_t e = set_smem(synthesis_kernel, sm);
+    if (e != cudaSuccess) return e;
+    synthesis_kernel<<<tile_grid(tp), kThreads, sm, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc);
+    return cudaGetLastError();
+}
+
+}  // namespace hb

@@ -1,0 +1,256 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs.
+
+Tolerances (the arithmetic behind them is in the design notes):
+  * THb: max over pixels of |dTHb| / max(|THb_oracle|, 1 uM) <= 1e-4;
+  * SO2: max |dSO2| <= 1e-3 over pixels with THb_oracle >= 1 uM;
+  * block means ybar: |d| <= 2e-7 (float32 log table / logf against FP64 -log);
+  * posterior means: |d| <= 2e-4 uM + 2e-6 * |c| (FP32 sums of up to 2^14 weights).
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_1706_07263_gb300 import Context, HbError, build, synth  # noqa: E402
+from paper_1706_07263_gb300 import binding  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+NTH = os.cpu_count() or 1
+
+THB_TOL = 1e-4
+SO2_TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def _grid(n0, n1, sigma=0.02, lo0=0.0, hi0=150.0, lo1=0.0, hi1=100.0):
+    return dict(n0=n0, n1=n1, lo0=lo0, hi0=hi0, lo1=lo1, hi1=hi1, sigma_l=sigma)
+
+
+def run_gpu(frame_np, A, grid, levels, lam, flags=0, debug=False):
+    fmt = "u8" if frame_np.dtype == np.uint8 else "f32"
+    H, W, _ = frame_np.shape
+    frame = torch.from_numpy(np.ascontiguousarray(frame_np)).to(DEV)
+    with Context(A, grid, levels, lam, W, H, fmt, flags) as ctx:
+        thb = torch.empty((H, W), dtype=torch.float32, device=DEV)
+        so2 = torch.empty_like(thb)
+        ctx.estimate(frame, thb, so2)
+        out = {"thb": thb, "so2": so2}
+        if debug:
+            hl, wl = ctx.lowpass_shape()
+            out["ybar_ll"] = torch.empty((hl, wl, 3), dtype=torch.float64, device=DEV)
+            out["conc_ll"] = torch.empty((hl, wl, 2), dtype=torch.float32, device=DEV)
+            out["hbo2"] = torch.empty_like(thb)
+            out["hb"] = torch.empty_like(thb)
+            ctx.estimate_debug(frame, out["ybar_ll"], out["conc_ll"], out["hbo2"], out["hb"])
+        torch.cuda.synchronize()
+    return {k: v.cpu().numpy().astype(np.float64) for k, v in out.items()}
+
+
+def compare(got, ref):
+    thb_ref = ref["thb"]
+    rel = np.abs(got["thb"] - thb_ref) / np.maximum(np.abs(thb_ref), 1.0)
+    mask = thb_ref >= 1.0
+    so2 = np.abs(got["so2"] - ref["so2"])[mask]
+    return float(rel.max()), float(so2.max()) if so2.size else 0.0
+
+
+def check(got, ref, what=""):
+    thb_err, so2_err = compare(got, ref)
+    assert thb_err <= THB_TOL, f"{what} THb rel err {thb_err:.3e}"
+    assert so2_err <= SO2_TOL, f"{what} SO2 abs err {so2_err:.3e}"
+    assert np.all(np.isfinite(got["thb"])) and np.all(np.isfinite(got["so2"]))
+    return thb_err, so2_err
+
+
+def small_frame(seed, H, W, fmt="f32", noise=0.005, nblobs=4, smin=3.0, smax=10.0):
+    mix = synth.make_mixing(seed)
+    fr = synth.make_frame(seed, H, W, mix.A, nblobs, smin, smax, noise, fmt)
+    return mix.A, fr.rgb
+
+
+# ------------------------------------------------------------------------------------------
+# posterior step alone
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n0,n1,sigma", [(5, 7, 0.05), (64, 64, 0.02), (128, 128, 0.02), (128, 128, 0.005),
+                                         (128, 128, 0.1), (33, 100, 0.02), (1, 17, 0.02), (1, 1, 0.02),
+                                         (200, 300, 0.03), (16, 256, 0.01)])
+def test_posterior_mean_matches_oracle(n0, n1, sigma):
+    rng = np.random.default_rng(n0 * 1000 + n1)
+    A = synth.make_mixing(n0 + n1).A
+    grid = _grid(n0, n1, sigma)
+    c = np.stack([rng.uniform(-20, 170, 300), rng.uniform(-20, 120, 300)], axis=1)
+    yb = c @ A.T + rng.normal(0, 0.01, (300, 3))
+    yb[:5] = [[0, 0, 0], [3, 3, 3], [-0.5, 0.2, 1.0], [2.5, 0.1, 0.1], [1e-3, 1e-3, 1e-3]]
+    ref = oracle.posterior_mean(yb, A, grid, nthreads=NTH)
+    with Context(A, grid, 1, 1e-3, 8, 8, "u8") as ctx:
+        ybt = torch.from_numpy(yb).to(DEV)
+        out = torch.empty((yb.shape[0], 2), dtype=torch.float32, device=DEV)
+        ctx.posterior_mean(ybt, out)
+        torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref)
+    tol = 2e-4 + 2e-6 * np.abs(ref)
+    assert np.all(err <= tol), f"max err {err.max():.3e} at {np.unravel_index(err.argmax(), err.shape)}"
+
+
+def test_posterior_brute_force_tiny_image_4x4():
+    """A 4x4 frame at one level: 4 low-pass pixels, a 5x7 grid, against the oracle."""
+    A, rgb = small_frame(21, 4, 4, noise=0.02)
+    grid = _grid(5, 7, 0.05)
+    got = run_gpu(rgb, A, grid, 1, 1e-3, debug=True)
+    ref = oracle.estimate(rgb, A, grid, 1, 1e-3)
+    np.testing.assert_allclose(got["ybar_ll"], ref["ybar_ll"], atol=2e-7)
+    np.testing.assert_allclose(got["conc_ll"], ref["conc_ll"], atol=2 * (2e-4 + 2e-6 * 300))
+    check(got, ref, "4x4")
+
+
+# ------------------------------------------------------------------------------------------
+# whole pipeline
+# ------------------------------------------------------------------------------------------
+CASES = [
+    # (H, W, levels, fmt, grid (n0, n1), sigma, seed)
+    (8, 8, 1, "f32", (8, 8), 0.05, 1),
+    (8, 8, 3, "u8", (16, 16), 0.02, 2),
+    (13, 22, 2, "f32", (32, 24), 0.02, 3),
+    (37, 53, 3, "u8", (64, 64), 0.02, 4),
+    (64, 200, 4, "u8", (128, 128), 0.02, 5),
+    (70, 130, 5, "f32", (40, 40), 0.03, 6),
+    (128, 96, 6, "u8", (64, 32), 0.02, 7),
+    (1, 1, 2, "u8", (16, 16), 0.02, 8),
+    (1, 300, 3, "f32", (64, 64), 0.02, 9),
+    (300, 1, 1, "u8", (64, 64), 0.02, 10),
+    (20, 30, 0, "f32", (32, 32), 0.02, 11),
+    (96, 2100, 2, "u8", (128, 128), 0.005, 12),
+    (64, 64, 3, "u8", (128, 128), 0.1, 13),
+]
+
+
+@pytest.mark.parametrize("H,W,levels,fmt,g,sigma,seed", CASES)
+def test_pipeline_matches_oracle(H, W, levels, fmt, g, sigma, seed):
+    A, rgb = small_frame(seed, H, W, fmt, noise=0.01, nblobs=6, smin=max(2.0, W / 20), smax=max(4.0, W / 5))
+    grid = _grid(*g, sigma)
+    got = run_gpu(rgb, A, grid, levels, 1e-3, debug=True)
+    ref = oracle.estimate(rgb, A, grid, levels, 1e-3, nthreads=NTH)
+    np.testing.assert_allclose(got["ybar_ll"], ref["ybar_ll"], atol=2e-7)
+    tol_c = 2 * (1 << levels) * (2e-4 + 2e-6 * np.abs(ref["conc_ll"] / (1 << levels)))
+    assert np.all(np.abs(got["conc_ll"] - ref["conc_ll"]) <= tol_c)
+    check(got, ref, f"{H}x{W} L{levels}")
+    np.testing.assert_array_equal(got["thb"], got["hbo2"].astype(np.float32) + got["hb"].astype(np.float32))
+
+
+def test_small_256_float_frame():
+    """256x256 float frame, 1 level, 64x64 grid (the small configuration)."""
+    wl = synth.SMALL_256
+    mix, fr = synth.workload_inputs(wl)
+    grid = synth.grid_spec(wl)
+    got = run_gpu(fr.rgb, mix.A, grid, wl.levels, wl.lam)
+    ref = oracle.estimate(fr.rgb, mix.A, grid, wl.levels, wl.lam, nthreads=NTH)
+    thb_err, so2_err = check(got, ref, wl.name)
+    print(f"{wl.name}: THb max rel err {thb_err:.3e}, SO2 max abs err {so2_err:.3e}")
+
+
+def test_hd_1080_u8_frame():
+    """1920x1080 8-bit frame, 3 levels, 128x128 grid, elementwise against the oracle."""
+    wl = synth.HD_1080
+    mix, fr = synth.workload_inputs(wl)
+    grid = synth.grid_spec(wl)
+    got = run_gpu(fr.rgb, mix.A, grid, wl.levels, wl.lam, debug=True)
+    ref = oracle.estimate(fr.rgb, mix.A, grid, wl.levels, wl.lam, nthreads=NTH)
+    np.testing.assert_allclose(got["ybar_ll"], ref["ybar_ll"], atol=2e-7)
+    thb_err, so2_err = check(got, ref, wl.name)
+    print(f"{wl.name}: THb max rel err {thb_err:.3e}, SO2 max abs err {so2_err:.3e}")
+
+
+@pytest.mark.parametrize("levels", [1, 3])
+def test_all_tikhonov_mode_matches_oracle(levels):
+    A, rgb = small_frame(31, 48, 64, "u8", noise=0.01)
+    grid = _grid(16, 16)
+    got = run_gpu(rgb, A, grid, levels, 1e-3, flags=binding.HB_LOWPASS_TIKHONOV)
+    ref = oracle.estimate(rgb, A, grid, levels, 1e-3, lowpass="tikhonov")
+    check(got, ref, "tikhonov")
+
+
+def test_absolute_lambda_flag():
+    A, rgb = small_frame(32, 32, 32, "f32")
+    grid = _grid(32, 32)
+    got = run_gpu(rgb, A, grid, 2, 2e-5, flags=binding.HB_LAMBDA_ABSOLUTE)
+    ref = oracle.estimate(rgb, A, grid, 2, 2e-5, relative=False)
+    check(got, ref, "absolute lambda")
+
+
+def test_noiseless_constant_patch_recovers_node():
+    A = synth.make_mixing(1).A
+    n0, n1 = 31, 21
+    c_star = np.array([np.linspace(0, 150, n0)[12], np.linspace(0, 100, n1)[7]])
+    I = np.exp(-(A @ c_star)).astype(np.float32)
+    frame = np.broadcast_to(I, (32, 48, 3)).copy()
+    spacing = np.linalg.norm(A @ np.array([150 / 30, 0.0]))
+    grid = _grid(n0, n1, 0.25 * spacing)
+    got = run_gpu(frame, A, grid, 3, 1e-3, debug=True)
+    np.testing.assert_allclose(got["hbo2"], c_star[0], atol=1e-3)
+    np.testing.assert_allclose(got["hb"], c_star[1], atol=1e-3)
+
+
+# ------------------------------------------------------------------------------------------
+# boundary behaviour
+# ------------------------------------------------------------------------------------------
+def test_strided_frame_and_host_entry_match_plain_call():
+    A, rgb = small_frame(41, 40, 72, "u8")
+    grid = _grid(32, 32)
+    base = run_gpu(rgb, A, grid, 2, 1e-3)
+    padded = np.zeros((40, 72 * 3 + 37), dtype=np.uint8)
+    padded[:, :72 * 3] = rgb.reshape(40, -1)
+    frame = torch.from_numpy(padded).to(DEV)
+    with Context(A, grid, 2, 1e-3, 72, 40, "u8") as ctx:
+        thb = torch.empty((40, 72), dtype=torch.float32, device=DEV)
+        so2 = torch.empty_like(thb)
+        ctx.estimate(frame, thb, so2, row_stride_bytes=padded.strides[0])
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(thb.cpu().numpy(), base["thb"].astype(np.float32))
+        np.testing.assert_array_equal(so2.cpu().numpy(), base["so2"].astype(np.float32))
+        th = np.empty((40, 72), np.float32)
+        sh = np.empty((40, 72), np.float32)
+        ctx.estimate_host(padded, th, sh)
+        np.testing.assert_array_equal(th, base["thb"].astype(np.float32))
+        np.testing.assert_array_equal(sh, base["so2"].astype(np.float32))
+
+
+def test_repeated_calls_are_deterministic_and_counted():
+    A, rgb = small_frame(42, 64, 64, "u8")
+    grid = _grid(64, 64)
+    frame = torch.from_numpy(rgb).to(DEV)
+    with Context(A, grid, 3, 1e-3, 64, 64, "u8") as ctx:
+        outs = []
+        ctx.timing_start(16)
+        for _ in range(3):
+            thb = torch.empty((64, 64), dtype=torch.float32, device=DEV)
+            so2 = torch.empty_like(thb)
+            ctx.estimate(frame, thb, so2)
+            outs.append((thb, so2))
+        t = ctx.timing_read()
+        assert ctx.launch_count() == 9
+        assert t["analysis"][1] == 3 and t["lowpass"][1] == 3 and t["synthesis"][1] == 3
+        assert all(t[k][0] > 0 for k in ("analysis", "lowpass", "synthesis"))
+        for thb, so2 in outs[1:]:
+            assert torch.equal(thb, outs[0][0]) and torch.equal(so2, outs[0][1])
+
+
+def test_bad_stride_and_cpu_tensor_are_rejected():
+    A, rgb = small_frame(43, 16, 16, "f32")
+    with Context(A, _grid(8, 8), 1, 1e-3, 16, 16, "f32") as ctx:
+        frame = torch.from_numpy(rgb).to(DEV)
+        thb = torch.empty((16, 16), dtype=torch.float32, device=DEV)
+        with pytest.raises(HbError):
+            ctx.estimate(frame, thb, thb.clone(), row_stride_bytes=16 * 3 * 4 - 4)
+        with pytest.raises(ValueError):
+            ctx.estimate(torch.from_numpy(rgb), thb, thb.clone())

@@ -144,6 +144,34 @@ hb_status hb_timing_read(hb_ctx *ctx, double ms[HB_NUM_STAGES], long launches[HB
 /* Static description of a status code. */
 const char *hb_strerror(hb_status s);
 
+/* Largest npix that hb_posterior_mean_static accepts. */
+#define HB_STATIC_MAX_PIXELS 65536
+
+/* The low-pass posterior step without any memory allocation.  The paper has no
+ * counterpart to this entry point; it exists for callers that cannot call
+ * cudaMalloc: real-time frame loops that may not block on the device allocator
+ * (an allocation can synchronise the device and stall every stream), plug-ins
+ * whose host application owns all device memory through its own pool, and
+ * embedded deployments that must know their whole device footprint up front.
+ *
+ * Computes the same result as hb_posterior_mean (posterior mean of (HbO2, Hb) for
+ * each of npix rows of ybar_dev, 3 doubles each, written as 2 floats each to
+ * conc_dev), but takes the mixing model and grid directly instead of a context
+ * and keeps its working memory in one fixed array compiled into libhb.so
+ * (about 4.3 MiB per GPU, held from library load until process exit).
+ *   - npix > HB_STATIC_MAX_PIXELS returns HB_ERR_SHAPE and launches nothing;
+ *     npix == 0 returns HB_OK; ybar_dev and conc_dev must be 8-byte aligned.
+ *   - The first call on each device looks up that array's device address
+ *     (cudaGetSymbolAddress, with the device current); make that first call
+ *     before any stream capture starts.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; the call clears the part it needs before use.  Calls whose work
+ *     overlaps on the GPU (different streams, or threads without ordering)
+ *     race on the array and give wrong results: order them on one stream.
+ *   - Asynchronous on `stream`, like the other entry points. */
+hb_status hb_posterior_mean_static(const hb_mixing *mix, const hb_grid *grid, const double *ybar_dev, long npix,
+                                   float *conc_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

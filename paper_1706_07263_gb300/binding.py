@@ -27,7 +27,9 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_SHAPE", 3: "HB_ERR_CUDA", 4: "
 
 # Every symbol include/hb.h declares (checked by the CPU tests against the built library).
 EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_estimate_debug", "hb_posterior_mean",
-            "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_strerror")
+            "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_strerror",
+            "hb_posterior_mean_static")
+STATIC_MAX_PIXELS = 65536
 
 
 class HbError(RuntimeError):
@@ -72,6 +74,7 @@ def load(path: str = LIB_PATH):
     lib.hb_timing_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(L)]
     lib.hb_strerror.argtypes = [I]
     lib.hb_strerror.restype = ctypes.c_char_p
+    lib.hb_posterior_mean_static.argtypes = [ctypes.POINTER(_Mixing), ctypes.POINTER(_Grid), P, L, P, P]
     for name in EXPORTED:
         getattr(lib, name)
     _lib = lib
@@ -187,3 +190,25 @@ class Context:
 
 def strerror(status: int) -> str:
     return load().hb_strerror(status).decode()
+
+
+def posterior_mean_static(A, grid: dict, ybar, conc, stream=None):
+    """hb_posterior_mean_static: the posterior step with no allocation (see include/hb.h).
+
+    For callers that may not allocate device memory: real-time loops that must not
+    block on the allocator, plug-ins whose host owns all device memory, deployments
+    with a fixed device footprint.  ybar: CUDA float64 tensor (npix, 3); conc: CUDA
+    float32 tensor (npix, 2), npix <= STATIC_MAX_PIXELS.  The first call on a device
+    looks up the library's fixed working array and should precede any stream
+    capture; calls share that array, so they must not overlap on the GPU."""
+    lib = load()
+    mix = _Mixing()
+    A = np.asarray(A, dtype=np.float64).reshape(3, 2)
+    for c in range(3):
+        for j in range(2):
+            mix.A[c][j] = float(A[c, j])
+    g = _Grid(int(grid["n0"]), int(grid["n1"]), float(grid["lo0"]), float(grid["hi0"]), float(grid["lo1"]),
+              float(grid["hi1"]), float(grid["sigma_l"]))
+    npix = ybar.numel() // 3
+    _check(lib.hb_posterior_mean_static(ctypes.byref(mix), ctypes.byref(g), _dev_ptr(ybar, "ybar"), npix,
+                                        _dev_ptr(conc, "conc"), _stream(stream)), "hb_posterior_mean_static")

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -395,6 +396,84 @@ hb_status hb_timing_read(hb_ctx* c, double ms[HB_NUM_STAGES], long launches[HB_N
     c->timing = false;
     c->ev_used = 0;
     return st;
+}
+
+// ------------------------------------------------------------------------------------
+// Allocation-free posterior step.  Its working memory is this one file-scope device
+// array; host code passes its device address (looked up once per device) to the
+// same set-up and posterior kernels the context path uses.
+// ------------------------------------------------------------------------------------
+namespace {
+
+constexpr long kStaticPixels = HB_STATIC_MAX_PIXELS;
+constexpr int kStaticParts = 4;
+constexpr size_t kStaticRecBytes = sizeof(BayesRec) * kStaticPixels;
+constexpr size_t kStaticPartialBytes = sizeof(float) * 3 * kStaticParts * kStaticPixels;
+constexpr size_t kStaticCountBytes = sizeof(unsigned) * kStaticPixels;
+constexpr size_t kStaticBytes = kStaticRecBytes + kStaticPartialBytes + kStaticCountBytes;
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices];  // device address of g_static_scratch, per device
+
+// Device address of the array on the current device (looked up on first use).
+hb_status static_scratch_address(void** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return HB_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kStaticMaxDevices) return HB_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return HB_ERR_CUDA;
+        }
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return HB_OK;
+}
+
+}  // namespace
+
+hb_status hb_posterior_mean_static(const hb_mixing* mix, const hb_grid* grid, const double* ybar_dev, long npix,
+                                   float* conc_dev, void* stream) {
+    if (!mix || !grid || npix < 0) return HB_ERR_ARG;
+    if (grid->n0 < 1 || grid->n1 < 1 || !(grid->hi0 >= grid->lo0) || !(grid->hi1 >= grid->lo1) ||
+        !(grid->sigma_l > 0.0))
+        return HB_ERR_SHAPE;
+    for (int c = 0; c < 3; ++c)
+        for (int j = 0; j < 2; ++j)
+            if (!std::isfinite(mix->A[c][j])) return HB_ERR_ARG;
+    if (npix > kStaticPixels) return HB_ERR_SHAPE;
+    if (npix == 0) return HB_OK;
+    if (!ybar_dev || !conc_dev || (reinterpret_cast<uintptr_t>(ybar_dev) & 7) ||
+        (reinterpret_cast<uintptr_t>(conc_dev) & 7))
+        return HB_ERR_ARG;
+    void* base = nullptr;
+    hb_status st = static_scratch_address(&base);
+    if (st != HB_OK) return st;
+    // host-side constants only: the context object here is a parameter holder on the stack
+    hb_ctx holder;
+    prepare(&holder, mix, grid, 0.0);
+    unsigned char* b = static_cast<unsigned char*>(base);
+    BayesRec* rec = reinterpret_cast<BayesRec*>(b);
+    float* partial = reinterpret_cast<float*>(b + kStaticRecBytes);
+    unsigned* count = reinterpret_cast<unsigned*>(b + kStaticRecBytes + kStaticPartialBytes);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the arrival counters must start at zero; whatever an earlier call left is cleared
+    if (cudaMemsetAsync(count, 0, sizeof(unsigned) * npix, s) != cudaSuccess) return HB_ERR_CUDA;
+    if (hb::launch_setup(holder.bp, ybar_dev, npix, rec, s) != cudaSuccess) return HB_ERR_CUDA;
+    const hb::PosteriorScratch sc{partial, count, kStaticParts};
+    if (hb::launch_posterior(holder.bp, rec, npix, sc, reinterpret_cast<float2*>(conc_dev), nullptr, 1.f, s) !=
+        cudaSuccess)
+        return HB_ERR_CUDA;
+    return HB_OK;
 }
 
 const char* hb_strerror(hb_status s) {

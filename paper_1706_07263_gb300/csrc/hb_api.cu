@@ -106,6 +106,27 @@ void prepare(hb_ctx* c, const hb_mixing* mix, const hb_grid* g, double lambda) {
     for (int ch = 0; ch < 3; ++ch) {
         bp.u_scale[ch] = 2.0 * kappa * bp.h0 * A[ch][0];
         bp.v_scale[ch] = 2.0 * kappa * bp.h1 * A[ch][1];
+        bp.u_scalef[ch] = (float)bp.u_scale[ch];
+        bp.v_scalef[ch] = (float)bp.v_scale[ch];
+    }
+    bp.lo0f = (float)bp.lo0;
+    bp.hi0f = (float)bp.hi0;
+    bp.lo1f = (float)bp.lo1;
+    bp.hi1f = (float)bp.hi1;
+    bp.h0f = (float)bp.h0;
+    bp.h1f = (float)bp.h1;
+    bp.inv_h0f = bp.h0 > 0 ? (float)(1.0 / bp.h0) : 0.f;
+    bp.inv_h1f = bp.h1 > 0 ? (float)(1.0 / bp.h1) : 0.f;
+    bp.inv_G00 = G[0][0] > 0 ? (float)(1.0 / G[0][0]) : 0.f;
+    bp.inv_G11 = G[1][1] > 0 ? (float)(1.0 / G[1][1]) : 0.f;
+    auto split = [](double v, float& hi, float& lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
+    for (int ch = 0; ch < 3; ++ch) {
+        split(A[ch][0] * bp.lo0 + A[ch][1] * bp.lo1, bp.base_hi[ch], bp.base_lo[ch]);
+        split(A[ch][0] * bp.h0, bp.step0_hi[ch], bp.step0_lo[ch]);
+        split(A[ch][1] * bp.h1, bp.step1_hi[ch], bp.step1_lo[ch]);
     }
 }
 
@@ -159,25 +180,36 @@ hb_status check_frame_args(const hb_ctx* c, const void* frame, size_t stride) {
     return HB_OK;
 }
 
+// One frame.  Bayesian low pass with n <= 4: posterior straight from the frame, then
+// synthesis (launched with PDL unless per-stage timing is armed, since a timing event
+// between the two kernels would serialise them anyway).  n = 5, 6: analysis kernel
+// (block means and posterior records), posterior, synthesis.  All-Tikhonov mode: the
+// synthesis kernel alone.  ybar (debug) additionally runs the analysis kernel.
 hb_status run_frame(hb_ctx* c, const void* frame, size_t stride, double* ybar, float* out0, float* out1,
                     float2* conc_scaled, int debug, cudaStream_t s) {
-    cudaError_t e;
-    {
+    cudaError_t e = cudaSuccess;
+    const bool bayes = !(c->flags & HB_LOWPASS_TIKHONOV);
+    const bool direct = bayes && c->levels <= 4;
+    if (ybar || (bayes && !direct)) {
         StageTimer t(c, s, HB_STAGE_ANALYSIS);
         e = hb::launch_analysis(c->tp, c->bp, frame, stride, c->d_lut, ybar, c->d_rec, s);
         c->launches++;
     }
     if (e != cudaSuccess) return HB_ERR_CUDA;
-    if (!(c->flags & HB_LOWPASS_TIKHONOV)) {
+    if (bayes) {
         StageTimer t(c, s, HB_STAGE_LOWPASS);
-        e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, conc_scaled,
-                                 (float)(1 << c->levels), s);
+        const float scale = (float)(1 << c->levels);
+        if (direct)
+            e = hb::launch_posterior_frame(c->tp, c->bp, frame, stride, c->d_lut, post_scratch(c), c->d_chat,
+                                           conc_scaled, scale, s);
+        else
+            e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, conc_scaled, scale, s);
         c->launches++;
     }
     if (e != cudaSuccess) return HB_ERR_CUDA;
     if (out0 || out1) {
         StageTimer t(c, s, HB_STAGE_SYNTHESIS);
-        e = hb::launch_synthesis(c->tp, frame, stride, c->d_lut, c->d_chat, out0, out1, debug, s);
+        e = hb::launch_synthesis(c->tp, frame, stride, c->d_lut, c->d_chat, out0, out1, debug, bayes && !c->timing, s);
         c->launches++;
     }
     return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;

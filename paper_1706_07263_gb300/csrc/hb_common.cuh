@@ -37,6 +37,13 @@ struct BayesParams {
     double u_scale[3];        // 2 kappa h0 a0[c]: U = sum_c r0[c] u_scale[c]
     double v_scale[3];        // 2 kappa h1 a1[c]
     float Aq, Bq, Cq;
+    // FP32 copies for the per-pixel set-up (FP64 is slow on this GPU)
+    float lo0f, hi0f, lo1f, hi1f, h0f, h1f;
+    float inv_h0f, inv_h1f, inv_G00, inv_G11;  // reciprocals (0 where undefined)
+    float u_scalef[3], v_scalef[3];
+    // A c at the grid origin and per grid step, as float (hi, lo) pairs:
+    //   A c_ij = base + i * step0 + j * step1
+    float base_hi[3], base_lo[3], step0_hi[3], step0_lo[3], step1_hi[3], step1_lo[3];
 };
 
 // Per low-pass pixel record written by the analysis kernel for the posterior kernel.
@@ -60,8 +67,13 @@ cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, co
 cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s);
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
                              float2* chat, float2* chat_scaled, float scale, cudaStream_t s);
+// Posterior straight from the frame: each unit first forms its pixel's low-pass
+// block mean (the n-level Haar low pass of the superblock) and the posterior set-up.
+cudaError_t launch_posterior_frame(const TransformParams& tp, const BayesParams& bp, const void* frame,
+                                   size_t stride, const float2* lut, const PosteriorScratch& sc, float2* chat,
+                                   float2* chat_scaled, float scale, cudaStream_t s);
 cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_t stride, const float2* lut,
-                             const float2* chat, float* out0, float* out1, int debug_conc, cudaStream_t s);
+                             const float2* chat, float* out0, float* out1, int debug_conc, bool pdl, cudaStream_t s);
 size_t transform_smem_bytes(const TransformParams& tp);
 
 }  // namespace hb

@@ -24,6 +24,7 @@
 // input the logarithm comes from a 256-entry table of FP64 values split as
 // float hi + float lo.
 #include "hb_common.cuh"
+#include "hb_device.cuh"
 
 #include <math.h>
 
@@ -154,56 +155,6 @@ __device__ void synthesis_levels(float* D, int nch, int TH, int TW, int levels) 
 
 }  // namespace
 
-// Reference node and linear coefficients of the posterior for one low-pass pixel.
-// The reference node is the grid node nearest to the maximiser of the likelihood
-// over the (continuous) concentration box -- a 2-D box-constrained least-squares
-// problem solved exactly by checking the interior optimum and then the four
-// edges.  It only fixes where the log-likelihood is expanded (so that the FP32
-// sums near the posterior peak involve small numbers); any node gives the same
-// posterior mean in exact arithmetic.
-__device__ BayesRec bayes_setup(const double yb[3], const BayesParams& bp) {
-    const float y0 = (float)yb[0], y1 = (float)yb[1], y2 = (float)yb[2];
-    const float z0 = bp.Af[0] * y0 + bp.Af[2] * y1 + bp.Af[4] * y2;
-    const float z1 = bp.Af[1] * y0 + bp.Af[3] * y1 + bp.Af[5] * y2;
-    const float lo0 = (float)bp.lo0, hi0 = (float)bp.hi0, lo1 = (float)bp.lo1, hi1 = (float)bp.hi1;
-    float c0 = bp.Gi00 * z0 + bp.Gi01 * z1;
-    float c1 = bp.Gi01 * z0 + bp.Gi11 * z1;
-    if (!(c0 >= lo0 && c0 <= hi0 && c1 >= lo1 && c1 <= hi1)) {
-        // objective |y - A c|^2 - |y|^2 = c^T G c - 2 z^T c, minimised on each edge
-        float best = INFINITY, b0 = lo0, b1 = lo1;
-        for (int e = 0; e < 4; ++e) {
-            float a0, a1;
-            if (e < 2) {
-                a0 = e == 0 ? lo0 : hi0;
-                a1 = bp.G11 > 0.f ? (z1 - bp.G01 * a0) / bp.G11 : lo1;
-                a1 = fminf(fmaxf(a1, lo1), hi1);
-            } else {
-                a1 = e == 2 ? lo1 : hi1;
-                a0 = bp.G00 > 0.f ? (z0 - bp.G01 * a1) / bp.G00 : lo0;
-                a0 = fminf(fmaxf(a0, lo0), hi0);
-            }
-            const float f = a0 * (bp.G00 * a0 + 2.f * bp.G01 * a1) + bp.G11 * a1 * a1 - 2.f * (z0 * a0 + z1 * a1);
-            if (f < best) { best = f; b0 = a0; b1 = a1; }
-        }
-        c0 = b0;
-        c1 = b1;
-    }
-    BayesRec rec;
-    rec.i0 = bp.h0 > 0 ? min(max(__float2int_rn((c0 - lo0) / (float)bp.h0), 0), bp.n0 - 1) : 0;
-    rec.j0 = bp.h1 > 0 ? min(max(__float2int_rn((c1 - lo1) / (float)bp.h1), 0), bp.n1 - 1) : 0;
-    // residual at the reference node, FP64 (cancellation happens here)
-    const double cr0 = bp.lo0 + rec.i0 * bp.h0, cr1 = bp.lo1 + rec.j0 * bp.h1;
-    double U = 0.0, V = 0.0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const double r = yb[c] - bp.A[c * 2] * cr0 - bp.A[c * 2 + 1] * cr1;
-        U += r * bp.u_scale[c];
-        V += r * bp.v_scale[c];
-    }
-    rec.U = (float)U;
-    rec.V = (float)V;
-    return rec;
-}
 
 namespace {
 
@@ -221,23 +172,23 @@ __global__ void __launch_bounds__(kThreads) analysis_kernel(TransformParams tp, 
     __syncthreads();
     analysis_levels<true>(sm.D, 3, TH, TW, tp.levels);
     const int nsb = TW / TH, n = TH * TW;
-    const double inv = 1.0 / (double)TH;
+    const float inv = 1.f / (float)TH;
     for (int t = threadIdx.x; t < nsb; t += blockDim.x) {
         const int gx = tx0 / TH + t;
         if (gx >= tp.wl) continue;
-        double yb[3];
+        float yhi[3], ylo[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             const float2 yr = log_atten(tp, sm, t * TH * 3 + ch);
-            yb[ch] = (double)yr.x + (double)yr.y + (double)sm.D[ch * n + t * TH] * inv;
+            yhi[ch] = yr.x;
+            ylo[ch] = yr.y + sm.D[ch * n + t * TH] * inv;
         }
         const size_t o = (size_t)blockIdx.y * tp.wl + gx;
         if (ybar) {
-            ybar[o * 3 + 0] = yb[0];
-            ybar[o * 3 + 1] = yb[1];
-            ybar[o * 3 + 2] = yb[2];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) ybar[o * 3 + ch] = (double)yhi[ch] + (double)ylo[ch];
         }
-        rec[o] = bayes_setup(yb, bp);
+        rec[o] = bayes_setup(yhi, ylo, bp);
     }
 }
 
@@ -245,8 +196,14 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(BayesParams bp, const d
                                                          BayesRec* __restrict__ rec) {
     const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
-    double yb[3] = {ybar[p * 3], ybar[p * 3 + 1], ybar[p * 3 + 2]};
-    rec[p] = bayes_setup(yb, bp);
+    float yhi[3], ylo[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const double y = ybar[p * 3 + ch];
+        yhi[ch] = (float)y;
+        ylo[ch] = (float)(y - (double)yhi[ch]);
+    }
+    rec[p] = bayes_setup(yhi, ylo, bp);
 }
 
 __global__ void __launch_bounds__(kThreads) synthesis_kernel(TransformParams tp, const unsigned char* __restrict__ frame,
@@ -278,6 +235,7 @@ __global__ void __launch_bounds__(kThreads) synthesis_kernel(TransformParams tp,
     }
     __syncthreads();
     synthesis_levels(sm.D, 2, TH, TW, tp.levels);
+    if (!tp.tikhonov_lowpass) asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
         const int r = p / TW, c = p - r * TW;
         const int gy = ty0 + r, gx = tx0 + c;
@@ -441,16 +399,18 @@ __global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams
     warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
     warp_analysis<L, true>(v, lane);
     if ((lane & (TH - 1)) == 0 && x < tp.wl * TH) {
-        double yb[3];
+        float yhi[3], ylo[3];
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) yb[ch] = (double)yref[ch].x + (double)yref[ch].y + (double)v[ch][0] / TH;
+        for (int ch = 0; ch < 3; ++ch) {
+            yhi[ch] = yref[ch].x;
+            ylo[ch] = yref[ch].y + v[ch][0] * (1.f / TH);
+        }
         const size_t o = (size_t)by * tp.wl + (x >> L);
         if (ybar) {
-            ybar[o * 3 + 0] = yb[0];
-            ybar[o * 3 + 1] = yb[1];
-            ybar[o * 3 + 2] = yb[2];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) ybar[o * 3 + ch] = (double)yhi[ch] + (double)ylo[ch];
         }
-        rec[o] = bayes_setup(yb, bp);
+        rec[o] = bayes_setup(yhi, ylo, bp);
     }
 }
 
@@ -494,6 +454,8 @@ __global__ void __launch_bounds__(kThreads) synthesis_warp_kernel(TransformParam
         off1 = (tp.M[3] * yref[0].x + tp.M[4] * yref[1].x + tp.M[5] * yref[2].x) +
                (tp.M[3] * yref[0].y + tp.M[4] * yref[1].y + tp.M[5] * yref[2].y);
     } else {
+        // everything above is independent of the posterior step; wait for it here
+        asm volatile("griddepcontrol.wait;" ::: "memory");
         const float2 ch = chat[(size_t)by * tp.wl + min(x >> L, tp.wl - 1)];
         off0 = ch.x;
         off1 = ch.y;
@@ -511,7 +473,8 @@ __global__ void __launch_bounds__(kThreads) synthesis_warp_kernel(TransformParam
         } else {
             const float thb = hbo2 + hb;
             out0[o] = thb;
-            out1[o] = thb > 0.f ? hbo2 / thb : 0.f;
+            // SO2 needs 1e-3 absolute: the fast reciprocal-based division (2 ulp) is plenty
+            out1[o] = thb >= 1.17549435e-38f ? __fdividef(hbo2, thb) : (thb > 0.f ? hbo2 / thb : 0.f);
         }
     }
 }
@@ -563,26 +526,43 @@ cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, B
     return cudaGetLastError();
 }
 
+// Launch with or without programmatic dependent launch (PDL): with it, CTAs of this
+// kernel may start while the preceding kernel on the stream is still running; they do
+// all posterior-independent work and then wait (griddepcontrol.wait) for that kernel.
+template <typename... Args>
+static cudaError_t launch_maybe_pdl(void (*kernel)(Args...), dim3 grid, size_t smem, cudaStream_t s, bool pdl,
+                                    Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_t stride, const float2* lut,
-                             const float2* chat, float* out0, float* out1, int debug_conc, cudaStream_t s) {
+                             const float2* chat, float* out0, float* out1, int debug_conc, bool pdl, cudaStream_t s) {
     const unsigned char* f = static_cast<const unsigned char*>(frame);
     if (tp.levels <= 4) {
         const int TH = 1 << tp.levels;
         const dim3 grid((tp.wl * TH + kThreads - 1) / kThreads, tp.hl);
         switch (tp.levels) {
-            case 0: synthesis_warp_kernel<0><<<grid, kThreads, 0, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc); break;
-            case 1: synthesis_warp_kernel<1><<<grid, kThreads, 0, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc); break;
-            case 2: synthesis_warp_kernel<2><<<grid, kThreads, 0, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc); break;
-            case 3: synthesis_warp_kernel<3><<<grid, kThreads, 0, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc); break;
-            default: synthesis_warp_kernel<4><<<grid, kThreads, 0, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc); break;
+            case 0: return launch_maybe_pdl(synthesis_warp_kernel<0>, grid, 0, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
+            case 1: return launch_maybe_pdl(synthesis_warp_kernel<1>, grid, 0, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
+            case 2: return launch_maybe_pdl(synthesis_warp_kernel<2>, grid, 0, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
+            case 3: return launch_maybe_pdl(synthesis_warp_kernel<3>, grid, 0, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
+            default: return launch_maybe_pdl(synthesis_warp_kernel<4>, grid, 0, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
         }
-        return cudaGetLastError();
     }
     const size_t sm = transform_smem_bytes(tp);
     cudaError_t e = set_smem(synthesis_kernel, sm);
     if (e != cudaSuccess) return e;
-    synthesis_kernel<<<tile_grid(tp), kThreads, sm, s>>>(tp, f, stride, lut, chat, out0, out1, debug_conc);
-    return cudaGetLastError();
+    return launch_maybe_pdl(synthesis_kernel, tile_grid(tp), sm, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
 }
 
 }  // namespace hb

@@ -180,36 +180,32 @@ hb_status check_frame_args(const hb_ctx* c, const void* frame, size_t stride) {
     return HB_OK;
 }
 
-// One frame.  Bayesian low pass with n <= 4: posterior straight from the frame, then
-// synthesis (launched with PDL unless per-stage timing is armed, since a timing event
-// between the two kernels would serialise them anyway).  n = 5, 6: analysis kernel
-// (block means and posterior records), posterior, synthesis.  All-Tikhonov mode: the
-// synthesis kernel alone.  ybar (debug) additionally runs the analysis kernel.
+// One frame.  Bayesian low pass: analysis kernel (block means and the per-pixel
+// posterior records), posterior over the records, synthesis.  The posterior and the
+// synthesis are launched with programmatic dependent launch (each waits for its
+// predecessor inside the kernel) unless per-stage timing is armed, since timing events
+// between the kernels serialise them anyway.  All-Tikhonov mode: the synthesis alone.
 hb_status run_frame(hb_ctx* c, const void* frame, size_t stride, double* ybar, float* out0, float* out1,
                     float2* conc_scaled, int debug, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     const bool bayes = !(c->flags & HB_LOWPASS_TIKHONOV);
-    const bool direct = bayes && c->levels <= 4;
-    if (ybar || (bayes && !direct)) {
-        StageTimer t(c, s, HB_STAGE_ANALYSIS);
-        e = hb::launch_analysis(c->tp, c->bp, frame, stride, c->d_lut, ybar, c->d_rec, s);
-        c->launches++;
-    }
-    if (e != cudaSuccess) return HB_ERR_CUDA;
+    const bool pdl = !c->timing;
     if (bayes) {
+        {
+            StageTimer t(c, s, HB_STAGE_ANALYSIS);
+            e = hb::launch_analysis(c->tp, c->bp, frame, stride, c->d_lut, ybar, c->d_rec, s);
+            c->launches++;
+        }
+        if (e != cudaSuccess) return HB_ERR_CUDA;
         StageTimer t(c, s, HB_STAGE_LOWPASS);
-        const float scale = (float)(1 << c->levels);
-        if (direct)
-            e = hb::launch_posterior_frame(c->tp, c->bp, frame, stride, c->d_lut, post_scratch(c), c->d_chat,
-                                           conc_scaled, scale, s);
-        else
-            e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, conc_scaled, scale, s);
+        e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, conc_scaled,
+                                 (float)(1 << c->levels), pdl, s);
         c->launches++;
     }
     if (e != cudaSuccess) return HB_ERR_CUDA;
     if (out0 || out1) {
         StageTimer t(c, s, HB_STAGE_SYNTHESIS);
-        e = hb::launch_synthesis(c->tp, frame, stride, c->d_lut, c->d_chat, out0, out1, debug, bayes && !c->timing, s);
+        e = hb::launch_synthesis(c->tp, frame, stride, c->d_lut, c->d_chat, out0, out1, debug, bayes && pdl, s);
         c->launches++;
     }
     return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
@@ -378,7 +374,7 @@ hb_status hb_posterior_mean(hb_ctx* c, const double* ybar_dev, long npix, float*
     if (e != cudaSuccess) return HB_ERR_CUDA;
     StageTimer t(c, s, HB_STAGE_LOWPASS);
     e = hb::launch_posterior(c->bp, c->d_rec, npix, post_scratch(c), reinterpret_cast<float2*>(conc_dev), nullptr, 1.f,
-                             s);
+                             false, s);
     c->launches++;
     return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
 }
@@ -502,7 +498,7 @@ hb_status hb_posterior_mean_static(const hb_mixing* mix, const hb_grid* grid, co
     if (cudaMemsetAsync(count, 0, sizeof(unsigned) * npix, s) != cudaSuccess) return HB_ERR_CUDA;
     if (hb::launch_setup(holder.bp, ybar_dev, npix, rec, s) != cudaSuccess) return HB_ERR_CUDA;
     const hb::PosteriorScratch sc{partial, count, kStaticParts};
-    if (hb::launch_posterior(holder.bp, rec, npix, sc, reinterpret_cast<float2*>(conc_dev), nullptr, 1.f, s) !=
+    if (hb::launch_posterior(holder.bp, rec, npix, sc, reinterpret_cast<float2*>(conc_dev), nullptr, 1.f, false, s) !=
         cudaSuccess)
         return HB_ERR_CUDA;
     return HB_OK;

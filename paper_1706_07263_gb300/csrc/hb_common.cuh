@@ -66,12 +66,7 @@ cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, co
                             const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s);
 cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s);
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
-                             float2* chat, float2* chat_scaled, float scale, cudaStream_t s);
-// Posterior straight from the frame: each unit first forms its pixel's low-pass
-// block mean (the n-level Haar low pass of the superblock) and the posterior set-up.
-cudaError_t launch_posterior_frame(const TransformParams& tp, const BayesParams& bp, const void* frame,
-                                   size_t stride, const float2* lut, const PosteriorScratch& sc, float2* chat,
-                                   float2* chat_scaled, float scale, cudaStream_t s);
+                             float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s);
 cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_t stride, const float2* lut,
                              const float2* chat, float* out0, float* out1, int debug_conc, bool pdl, cudaStream_t s);
 size_t transform_smem_bytes(const TransformParams& tp);

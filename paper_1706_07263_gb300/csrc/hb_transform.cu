@@ -386,32 +386,49 @@ __global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams
                                                                  double* __restrict__ ybar,
                                                                  BayesRec* __restrict__ rec) {
     constexpr int TH = 1 << L;
+    constexpr int NSB = kThreads / TH;  // superblocks per CTA (kThreads columns)
     __shared__ float2 lut[256];
+    __shared__ float sb_hi[NSB][3], sb_lo[NSB][3];
     if (tp.fmt == 1)
         for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = lut_g[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32;
-    if (x0 >= tp.wl * TH) return;  // whole warp right of the padded frame
     const int x = x0 + lane, by = blockIdx.y;
-    float v[3][TH];
-    float2 yref[3];
-    warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
-    warp_analysis<L, true>(v, lane);
-    if ((lane & (TH - 1)) == 0 && x < tp.wl * TH) {
+    if (x0 < tp.wl * TH) {  // whole warps right of the padded frame skip the transform
+        float v[3][TH];
+        float2 yref[3];
+        warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
+        warp_analysis<L, true>(v, lane);
+        if ((lane & (TH - 1)) == 0) {
+            const int t = threadIdx.x / TH;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                sb_hi[t][ch] = yref[ch].x;
+                sb_lo[t][ch] = yref[ch].y + v[ch][0] * (1.f / TH);
+            }
+        }
+    }
+    __syncthreads();
+    // one superblock per thread for the posterior set-up, so whole warps do it together
+    for (int t = threadIdx.x; t < NSB; t += blockDim.x) {
+        const int gx = (blockIdx.x * kThreads) / TH + t;
+        if (gx >= tp.wl) continue;
         float yhi[3], ylo[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            yhi[ch] = yref[ch].x;
-            ylo[ch] = yref[ch].y + v[ch][0] * (1.f / TH);
+            yhi[ch] = sb_hi[t][ch];
+            ylo[ch] = sb_lo[t][ch];
         }
-        const size_t o = (size_t)by * tp.wl + (x >> L);
+        const size_t o = (size_t)by * tp.wl + gx;
         if (ybar) {
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) ybar[o * 3 + ch] = (double)yhi[ch] + (double)ylo[ch];
         }
         rec[o] = bayes_setup(yhi, ylo, bp);
     }
+    // the posterior kernel may be scheduled now; it waits for this grid before reading rec
+    asm volatile("griddepcontrol.launch_dependents;");
 }
 
 template <int L>

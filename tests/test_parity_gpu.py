@@ -238,10 +238,9 @@ def test_repeated_calls_are_deterministic_and_counted():
             ctx.estimate(frame, thb, so2)
             outs.append((thb, so2))
         t = ctx.timing_read()
-        # 3 levels: posterior straight from the frame, then synthesis -- two kernels per frame
-        assert ctx.launch_count() == 6
-        assert t["analysis"][1] == 0 and t["lowpass"][1] == 3 and t["synthesis"][1] == 3
-        assert all(t[k][0] > 0 for k in ("lowpass", "synthesis"))
+        assert ctx.launch_count() == 9   # analysis, posterior, synthesis per frame
+        assert t["analysis"][1] == 3 and t["lowpass"][1] == 3 and t["synthesis"][1] == 3
+        assert all(t[k][0] > 0 for k in ("analysis", "lowpass", "synthesis"))
         for thb, so2 in outs[1:]:
             assert torch.equal(thb, outs[0][0]) and torch.equal(so2, outs[0][1])
 

@@ -144,6 +144,62 @@ hb_status hb_timing_read(hb_ctx *ctx, double ms[HB_NUM_STAGES], long launches[HB
 /* Static description of a status code. */
 const char *hb_strerror(hb_status s);
 
+/* ------------------------------------------------------------------------------------
+ * Learned stand-in for the low-pass posterior (not part of the paper's method).
+ * A 3 -> 64 -> 64 -> 2 multilayer perceptron with exact GELU, BF16 weights and hidden
+ * activations (FP32 input) and FP32 accumulation maps a low-pass pixel's block-mean log-attenuation
+ * to a correction of the box-clipped least-squares concentration (normalised by the
+ * box extents); it is trained on the GPU on pairs produced by the posterior step.
+ * Parameters (FP32 masters, HB_MLP_NPARAMS floats): W1[64][3], b1[64], W2[64][64]
+ * (row = output unit), b2[64], W3[2][64], b3[2].
+ * ------------------------------------------------------------------------------------ */
+#define HB_MLP_NPARAMS 4546
+enum { HB_MODE_BAYES = 0, HB_MODE_MLP = 1 };
+
+/* Random initialisation (Glorot-uniform from a seeded splitmix64 stream, biases 0)
+ * and zeroed Adam state.  The input normalisation and the least-squares baseline are
+ * fixed by the context's mixing matrix and grid box. */
+hb_status hb_mlp_init(hb_ctx *ctx, unsigned seed);
+
+/* Copy the FP32 master parameters in / out (host arrays of HB_MLP_NPARAMS floats);
+ * set_params also refreshes the BF16 copies and zeroes the Adam state. */
+hb_status hb_mlp_set_params(hb_ctx *ctx, const float *params_host);
+hb_status hb_mlp_get_params(hb_ctx *ctx, float *params_host);
+
+/* Training pairs from one frame: the block means of the low-pass band (npix x 3
+ * floats) and the posterior means the exact step gives for them (npix x 2 floats, uM),
+ * npix = hl * wl of the context. */
+hb_status hb_lowpass_pairs(hb_ctx *ctx, const void *frame_dev, size_t row_stride_bytes, float *ybar_dev,
+                           float *conc_dev, void *stream);
+
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on minibatches
+ * of `batch` samples drawn with replacement from the n pairs (ybar_dev n x 3, target_dev
+ * n x 2 posterior means in uM) by a hash of (seed, step, position).  loss_host, if not
+ * NULL, receives the minibatch loss of every step (steps floats); the call then
+ * synchronises `stream`.  batch <= 65536. */
+hb_status hb_mlp_train(hb_ctx *ctx, const float *ybar_dev, const float *target_dev, long n, int steps, int batch,
+                       double lr, unsigned seed, float *loss_host, void *stream);
+
+/* Gradient of the mean loss over all n pairs (n <= 65536) with respect to the master
+ * parameters (grad_dev: HB_MLP_NPARAMS floats) and the loss itself (loss_dev: 1 float);
+ * the parameters are not changed. */
+hb_status hb_mlp_gradient(hb_ctx *ctx, const float *ybar_dev, const float *target_dev, long n, float *grad_dev,
+                          float *loss_dev, void *stream);
+
+/* Network estimate of the posterior mean for n block means (conc_dev: n x 2 floats). */
+hb_status hb_mlp_forward(hb_ctx *ctx, const float *ybar_dev, long n, float *conc_dev, void *stream);
+
+/* Low-pass mode of hb_estimate.  HB_MODE_MLP: the network replaces the posterior; on
+ * every frame the exact posterior is also evaluated on nsample seeded low-pass pixels
+ * (nsample >= 1), and if the mean of their errors exceeds tol -- a pixel's error being
+ * the larger of |dHbO2| / (hi0 - lo0) and |dHb| / (hi1 - lo1) -- the whole low pass of
+ * that frame is recomputed exactly (all on the device, no host round trip). */
+hb_status hb_set_lowpass_mode(hb_ctx *ctx, int mode, double tol, int nsample);
+
+/* Frames estimated in HB_MODE_MLP and how many of them fell back to the exact
+ * posterior (synchronises the context's device work). */
+hb_status hb_lowpass_stats(hb_ctx *ctx, long *mlp_frames, long *fallbacks);
+
 /* Largest npix that hb_posterior_mean_static accepts. */
 #define HB_STATIC_MAX_PIXELS 65536
 

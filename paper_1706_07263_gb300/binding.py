@@ -28,7 +28,12 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_SHAPE", 3: "HB_ERR_CUDA", 4: "
 # Every symbol include/hb.h declares (checked by the CPU tests against the built library).
 EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_estimate_debug", "hb_posterior_mean",
             "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_strerror",
+            "hb_mlp_init", "hb_mlp_set_params", "hb_mlp_get_params", "hb_lowpass_pairs", "hb_mlp_train",
+            "hb_mlp_gradient", "hb_mlp_forward", "hb_set_lowpass_mode", "hb_lowpass_stats",
             "hb_posterior_mean_static")
+MLP_NPARAMS = 4546
+HB_MODE_BAYES = 0
+HB_MODE_MLP = 1
 STATIC_MAX_PIXELS = 65536
 
 
@@ -75,6 +80,16 @@ def load(path: str = LIB_PATH):
     lib.hb_strerror.argtypes = [I]
     lib.hb_strerror.restype = ctypes.c_char_p
     lib.hb_posterior_mean_static.argtypes = [ctypes.POINTER(_Mixing), ctypes.POINTER(_Grid), P, L, P, P]
+    F = ctypes.POINTER(ctypes.c_float)
+    lib.hb_mlp_init.argtypes = [P, ctypes.c_uint]
+    lib.hb_mlp_set_params.argtypes = [P, F]
+    lib.hb_mlp_get_params.argtypes = [P, F]
+    lib.hb_lowpass_pairs.argtypes = [P, P, S, P, P, P]
+    lib.hb_mlp_train.argtypes = [P, P, P, L, I, I, D, ctypes.c_uint, F, P]
+    lib.hb_mlp_gradient.argtypes = [P, P, P, L, P, P, P]
+    lib.hb_mlp_forward.argtypes = [P, P, L, P, P]
+    lib.hb_set_lowpass_mode.argtypes = [P, I, D, I]
+    lib.hb_lowpass_stats.argtypes = [P, ctypes.POINTER(L), ctypes.POINTER(L)]
     for name in EXPORTED:
         getattr(lib, name)
     _lib = lib
@@ -174,6 +189,54 @@ class Context:
         npix = ybar.numel() // 3
         _check(load().hb_posterior_mean(self._h, _dev_ptr(ybar, "ybar"), npix, _dev_ptr(conc, "conc"),
                                         _stream(stream)), "hb_posterior_mean")
+
+    # -------------------------------------------------------------- learned stand-in
+    def mlp_init(self, seed: int = 0):
+        _check(load().hb_mlp_init(self._h, seed), "hb_mlp_init")
+
+    def mlp_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        if p.size != MLP_NPARAMS:
+            raise ValueError(f"expected {MLP_NPARAMS} parameters")
+        _check(load().hb_mlp_set_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "hb_mlp_set_params")
+
+    def mlp_get_params(self) -> np.ndarray:
+        p = np.empty(MLP_NPARAMS, dtype=np.float32)
+        _check(load().hb_mlp_get_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "hb_mlp_get_params")
+        return p
+
+    def lowpass_pairs(self, frame, ybar, conc, stream=None):
+        stride = frame.stride(0) * frame.element_size()
+        _check(load().hb_lowpass_pairs(self._h, _dev_ptr(frame, "frame"), stride, _dev_ptr(ybar, "ybar"),
+                                       _dev_ptr(conc, "conc"), _stream(stream)), "hb_lowpass_pairs")
+
+    def mlp_train(self, ybar, target, steps: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
+                  stream=None) -> np.ndarray:
+        losses = np.empty(max(steps, 1), dtype=np.float32)
+        _check(load().hb_mlp_train(self._h, _dev_ptr(ybar, "ybar"), _dev_ptr(target, "target"), ybar.numel() // 3,
+                                   steps, batch, float(lr), seed,
+                                   losses.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream(stream)),
+               "hb_mlp_train")
+        return losses[:steps]
+
+    def mlp_gradient(self, ybar, target, grad, loss, stream=None):
+        _check(load().hb_mlp_gradient(self._h, _dev_ptr(ybar, "ybar"), _dev_ptr(target, "target"),
+                                      ybar.numel() // 3, _dev_ptr(grad, "grad"), _dev_ptr(loss, "loss"),
+                                      _stream(stream)), "hb_mlp_gradient")
+
+    def mlp_forward(self, ybar, conc, stream=None):
+        _check(load().hb_mlp_forward(self._h, _dev_ptr(ybar, "ybar"), ybar.numel() // 3, _dev_ptr(conc, "conc"),
+                                     _stream(stream)), "hb_mlp_forward")
+
+    def set_lowpass_mode(self, mode: int, tol: float = 1e-3, nsample: int = 256):
+        _check(load().hb_set_lowpass_mode(self._h, mode, float(tol), nsample), "hb_set_lowpass_mode")
+
+    def lowpass_stats(self):
+        f, b = ctypes.c_long(), ctypes.c_long()
+        _check(load().hb_lowpass_stats(self._h, ctypes.byref(f), ctypes.byref(b)), "hb_lowpass_stats")
+        return f.value, b.value
 
     def launch_count(self) -> int:
         return int(load().hb_launch_count(self._h))

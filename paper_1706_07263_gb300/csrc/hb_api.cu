@@ -3,8 +3,10 @@
 // and the launch sequence of one frame.
 #include "hb.h"
 #include "hb_common.cuh"
+#include "hb_mlp.cuh"
 
 #include <atomic>
+#include <cstdint>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -36,6 +38,24 @@ struct hb_ctx {
     float* d_thb = nullptr;
     float* d_so2 = nullptr;
     std::atomic<long> launches{0};
+    // learned stand-in
+    float* d_mlp = nullptr;       // FP32 masters | Adam m | Adam v | BF16 copies | grad, 5 x kNParams
+    float* d_mlp_gpart = nullptr; // per-CTA partial gradients
+    float* d_mlp_lpart = nullptr; // per-CTA partial losses
+    float* d_mlp_loss = nullptr;  // loss per training step
+    long mlp_loss_cap = 0;
+    hb::MlpNorm mlp_norm{};
+    float mlp_ext0 = 1.f, mlp_ext1 = 1.f;  // box extents: the fallback check's error scale
+    double sigma_l = 0.0;
+    bool mlp_ready = false;
+    int adam_t = 0;
+    int lowpass_mode = HB_MODE_BAYES;
+    float mlp_tol = 1e-3f;
+    int mlp_nsample = 256;
+    float* d_ybar_f = nullptr;    // block means for the network (npix_ll x 3)
+    unsigned* d_flags = nullptr;  // [0] summed sampled error (float bits), [1] fallback count
+    long mlp_frames = 0;
+    unsigned frame_seq = 0;
     // per-stage timing
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_stage;
@@ -190,22 +210,43 @@ hb_status run_frame(hb_ctx* c, const void* frame, size_t stride, double* ybar, f
     cudaError_t e = cudaSuccess;
     const bool bayes = !(c->flags & HB_LOWPASS_TIKHONOV);
     const bool pdl = !c->timing;
+    const bool mlp = bayes && c->lowpass_mode == HB_MODE_MLP;
     if (bayes) {
         {
             StageTimer t(c, s, HB_STAGE_ANALYSIS);
-            e = hb::launch_analysis(c->tp, c->bp, frame, stride, c->d_lut, ybar, c->d_rec, s);
+            e = hb::launch_analysis(c->tp, c->bp, frame, stride, c->d_lut, ybar, c->d_rec, s,
+                                    mlp ? c->d_ybar_f : nullptr);
             c->launches++;
         }
         if (e != cudaSuccess) return HB_ERR_CUDA;
         StageTimer t(c, s, HB_STAGE_LOWPASS);
-        e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, conc_scaled,
-                                 (float)(1 << c->levels), pdl, s);
-        c->launches++;
+        const float scale = (float)(1 << c->levels);
+        if (mlp) {
+            // network estimate, sampled exact check, exact recomputation only if the check failed
+            float* err_sum = reinterpret_cast<float*>(c->d_flags);
+            e = hb::launch_mlp_forward(c->d_mlp + 3 * hb::kNParams, c->mlp_norm, c->d_ybar_f, c->npix_ll, c->d_chat,
+                                       c->d_flags, s);
+            if (e == cudaSuccess)
+                e = hb::launch_posterior_check(c->bp, c->d_rec, c->npix_ll, c->mlp_nsample, c->frame_seq++,
+                                               c->d_chat, 1.f / c->mlp_ext0, 1.f / c->mlp_ext1, err_sum, s);
+            // mean sampled error > tol  <=>  sum > tol * nsample
+            const float thr = c->mlp_tol * (float)c->mlp_nsample;
+            if (e == cudaSuccess)
+                e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, nullptr, scale,
+                                         false, s, hb::PosteriorGate{err_sum, thr, c->d_flags + 1});
+            c->launches += 3;
+            c->mlp_frames++;
+        } else {
+            e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, conc_scaled, scale,
+                                     pdl, s);
+            c->launches++;
+        }
     }
     if (e != cudaSuccess) return HB_ERR_CUDA;
     if (out0 || out1) {
         StageTimer t(c, s, HB_STAGE_SYNTHESIS);
-        e = hb::launch_synthesis(c->tp, frame, stride, c->d_lut, c->d_chat, out0, out1, debug, bayes && pdl, s);
+        e = hb::launch_synthesis(c->tp, frame, stride, c->d_lut, c->d_chat, out0, out1, debug, bayes && !mlp && pdl,
+                                 s);
         c->launches++;
     }
     return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
@@ -248,6 +289,7 @@ hb_status hb_create(const hb_mixing* mix, const hb_grid* grid, int levels, doubl
     c->hl = (height + B - 1) / B;
     c->wl = (width + B - 1) / B;
     c->npix_ll = (long)c->hl * c->wl;
+    c->sigma_l = grid->sigma_l;
     prepare(c, mix, grid, lambda);
 
     TransformParams& tp = c->tp;
@@ -293,6 +335,12 @@ void hb_destroy(hb_ctx* c) {
     cudaFree(c->d_chat);
     cudaFree(c->d_partial);
     cudaFree(c->d_count);
+    cudaFree(c->d_mlp);
+    cudaFree(c->d_mlp_gpart);
+    cudaFree(c->d_mlp_lpart);
+    cudaFree(c->d_mlp_loss);
+    cudaFree(c->d_ybar_f);
+    cudaFree(c->d_flags);
     cudaFree(c->d_frame);
     cudaFree(c->d_thb);
     cudaFree(c->d_so2);
@@ -424,6 +472,256 @@ hb_status hb_timing_read(hb_ctx* c, double ms[HB_NUM_STAGES], long launches[HB_N
     c->timing = false;
     c->ev_used = 0;
     return st;
+}
+
+// ------------------------------------------------------------------------------------
+// Learned stand-in: parameters, training, inference and the low-pass mode.
+// ------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kMlpMaxBlocks = 1024;  // batch <= 65536 samples (64 per training CTA)
+#ifndef HB_MLP_INPUT_SCALE
+#define HB_MLP_INPUT_SCALE 4.0
+#endif
+
+float bf16_round(float v) {  // round to nearest even on the upper 16 bits
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return v;
+    u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+    std::memcpy(&v, &u, 4);
+    return v;
+}
+
+uint64_t splitmix64(uint64_t& x) {  // Steele, Lea and Flood's SplitMix64 output function
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+hb_status ensure_mlp(hb_ctx* c) {
+    if (c->d_mlp) return HB_OK;
+    const size_t np = hb::kNParams;
+    if (cudaMalloc(&c->d_mlp, sizeof(float) * 5 * np) != cudaSuccess ||
+        cudaMalloc(&c->d_mlp_gpart, sizeof(float) * kMlpMaxBlocks * np) != cudaSuccess ||
+        cudaMalloc(&c->d_mlp_lpart, sizeof(float) * kMlpMaxBlocks) != cudaSuccess ||
+        cudaMalloc(&c->d_ybar_f, sizeof(float) * 3 * c->npix_ll) != cudaSuccess ||
+        cudaMalloc(&c->d_flags, sizeof(unsigned) * 2) != cudaSuccess) {
+        cudaGetLastError();
+        return HB_ERR_OOM;
+    }
+    if (cudaMemset(c->d_mlp, 0, sizeof(float) * 5 * np) != cudaSuccess ||
+        cudaMemset(c->d_flags, 0, sizeof(unsigned) * 2) != cudaSuccess)
+        return HB_ERR_CUDA;
+    // least-squares baseline, input transform and output scale (FP64 here)
+    const double* A = c->bp.A;
+    const double lo[2] = {c->bp.lo0, c->bp.lo1}, hi[2] = {c->bp.hi0, c->bp.hi1};
+    double G[2][2];
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) G[j][k] = A[0 + j] * A[0 + k] + A[2 + j] * A[2 + k] + A[4 + j] * A[4 + k];
+    const double det = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+    if (!(det > 0)) return HB_ERR_STATE;  // collinear columns: no least-squares baseline
+    const double Gi[2][2] = {{G[1][1] / det, -G[0][1] / det}, {-G[1][0] / det, G[0][0] / det}};
+    double P[2][3];
+    for (int ch = 0; ch < 3; ++ch) {
+        P[0][ch] = Gi[0][0] * A[ch * 2] + Gi[0][1] * A[ch * 2 + 1];
+        P[1][ch] = Gi[1][0] * A[ch * 2] + Gi[1][1] * A[ch * 2 + 1];
+    }
+    hb::MlpNorm& nm = c->mlp_norm;
+    const double K = HB_MLP_INPUT_SCALE;  // the box maps to [-K, K]
+    for (int j = 0; j < 2; ++j) {
+        const double half = hi[j] > lo[j] ? 0.5 * (hi[j] - lo[j]) : 1.0, centre = 0.5 * (lo[j] + hi[j]);
+        for (int ch = 0; ch < 3; ++ch) {
+            nm.Ap[j * 3 + ch] = (float)P[j][ch];
+            nm.T[j * 3 + ch] = (float)(K * P[j][ch] / half);
+        }
+        nm.t0[j] = (float)(-K * centre / half);
+    }
+    // unit normal of the range of A (cross product of its columns), in sigma_l units
+    const double nx = A[2] * A[5] - A[4] * A[3], ny = A[4] * A[1] - A[0] * A[5], nz = A[0] * A[3] - A[2] * A[1];
+    const double nn = std::sqrt(nx * nx + ny * ny + nz * nz), sl = c->sigma_l;
+    nm.T[6] = (float)(nx / nn / sl);
+    nm.T[7] = (float)(ny / nn / sl);
+    nm.T[8] = (float)(nz / nn / sl);
+    nm.t0[2] = 0.f;
+    nm.lo0 = (float)lo[0];
+    nm.hi0 = (float)hi[0];
+    nm.lo1 = (float)lo[1];
+    nm.hi1 = (float)hi[1];
+    nm.osc0 = (float)(sl * std::sqrt(Gi[0][0]));
+    nm.osc1 = (float)(sl * std::sqrt(Gi[1][1]));
+    c->mlp_ext0 = hi[0] > lo[0] ? (float)(hi[0] - lo[0]) : 1.f;
+    c->mlp_ext1 = hi[1] > lo[1] ? (float)(hi[1] - lo[1]) : 1.f;
+    return HB_OK;
+}
+
+// Upload masters, refresh the BF16 copies, zero the Adam state.
+hb_status put_params(hb_ctx* c, const float* host) {
+    const size_t np = hb::kNParams;
+    std::vector<float> buf(5 * np, 0.f);
+    for (size_t i = 0; i < np; ++i) {
+        buf[i] = host[i];
+        buf[3 * np + i] = bf16_round(host[i]);
+    }
+    if (cudaMemcpy(c->d_mlp, buf.data(), sizeof(float) * 5 * np, cudaMemcpyHostToDevice) != cudaSuccess)
+        return HB_ERR_CUDA;
+    c->adam_t = 0;
+    c->mlp_ready = true;
+    return HB_OK;
+}
+
+}  // namespace
+
+hb_status hb_mlp_init(hb_ctx* c, unsigned seed) {
+    if (!c) return HB_ERR_ARG;
+    DeviceGuard g(c->device);
+    hb_status st = ensure_mlp(c);
+    if (st != HB_OK) return st;
+    std::vector<float> p(hb::kNParams, 0.f);
+    uint64_t state = 0x6a09e667f3bcc909ull ^ (uint64_t)seed;
+    auto fill = [&](int off, int fan_out, int fan_in) {
+        const double b = std::sqrt(6.0 / (fan_in + fan_out));
+        for (int i = 0; i < fan_out * fan_in; ++i) {
+            const double u = (double)(splitmix64(state) >> 11) * (1.0 / 9007199254740992.0);
+            p[off + i] = (float)((2.0 * u - 1.0) * b);
+        }
+    };
+    fill(hb::kOffW1, hb::kHid, hb::kIn);
+    fill(hb::kOffW2, hb::kHid, hb::kHid);
+    fill(hb::kOffW3, hb::kOut, hb::kHid);
+    return put_params(c, p.data());
+}
+
+hb_status hb_mlp_set_params(hb_ctx* c, const float* params_host) {
+    if (!c || !params_host) return HB_ERR_ARG;
+    for (int i = 0; i < hb::kNParams; ++i)
+        if (!std::isfinite(params_host[i])) return HB_ERR_ARG;
+    DeviceGuard g(c->device);
+    hb_status st = ensure_mlp(c);
+    if (st != HB_OK) return st;
+    return put_params(c, params_host);
+}
+
+hb_status hb_mlp_get_params(hb_ctx* c, float* params_host) {
+    if (!c || !params_host) return HB_ERR_ARG;
+    if (!c->mlp_ready) return HB_ERR_STATE;
+    DeviceGuard g(c->device);
+    return cudaMemcpy(params_host, c->d_mlp, sizeof(float) * hb::kNParams, cudaMemcpyDeviceToHost) == cudaSuccess
+               ? HB_OK
+               : HB_ERR_CUDA;
+}
+
+hb_status hb_lowpass_pairs(hb_ctx* c, const void* frame_dev, size_t row_stride_bytes, float* ybar_dev,
+                           float* conc_dev, void* stream) {
+    if (!c || !ybar_dev || !conc_dev || (reinterpret_cast<uintptr_t>(conc_dev) & 7)) return HB_ERR_ARG;
+    hb_status st = check_frame_args(c, frame_dev, row_stride_bytes);
+    if (st != HB_OK) return st;
+    DeviceGuard g(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = hb::launch_analysis(c->tp, c->bp, frame_dev, row_stride_bytes, c->d_lut, nullptr, c->d_rec, s,
+                                        ybar_dev);
+    c->launches++;
+    if (e == cudaSuccess)
+        e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), reinterpret_cast<float2*>(conc_dev),
+                                 nullptr, 1.f, false, s);
+    c->launches++;
+    return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+}
+
+hb_status hb_mlp_train(hb_ctx* c, const float* ybar_dev, const float* target_dev, long n, int steps, int batch,
+                       double lr, unsigned seed, float* loss_host, void* stream) {
+    if (!c || !ybar_dev || !target_dev || n <= 0 || steps < 0 || batch <= 0 || !(lr > 0.0)) return HB_ERR_ARG;
+    if (batch > kMlpMaxBlocks * hb::kMlpTrainSamples) return HB_ERR_SHAPE;
+    if (!c->mlp_ready) return HB_ERR_STATE;
+    DeviceGuard g(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (steps > c->mlp_loss_cap) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return HB_ERR_CUDA;
+        cudaFree(c->d_mlp_loss);
+        c->d_mlp_loss = nullptr;
+        c->mlp_loss_cap = 0;
+        if (cudaMalloc(&c->d_mlp_loss, sizeof(float) * steps) != cudaSuccess) {
+            cudaGetLastError();
+            return HB_ERR_OOM;
+        }
+        c->mlp_loss_cap = steps;
+    }
+    const size_t np = hb::kNParams;
+    float *master = c->d_mlp, *m = c->d_mlp + np, *v = c->d_mlp + 2 * np, *wbf = c->d_mlp + 3 * np,
+          *grad = c->d_mlp + 4 * np;
+    const int nblocks = (batch + hb::kMlpTrainSamples - 1) / hb::kMlpTrainSamples;
+    for (int k = 0; k < steps; ++k) {
+        cudaError_t e = hb::launch_mlp_train(wbf, c->mlp_norm, ybar_dev, target_dev, n, batch, seed, k, 0,
+                                             c->d_mlp_gpart, c->d_mlp_lpart, s);
+        if (e == cudaSuccess)
+            e = hb::launch_mlp_adam(c->d_mlp_gpart, c->d_mlp_lpart, nblocks, batch, grad, c->d_mlp_loss + k, master,
+                                    m, v, wbf, (float)lr, 0.9f, 0.999f, 1e-8f, ++c->adam_t, s);
+        c->launches += 2;
+        if (e != cudaSuccess) return HB_ERR_CUDA;
+    }
+    if (loss_host && steps > 0) {
+        if (cudaMemcpyAsync(loss_host, c->d_mlp_loss, sizeof(float) * steps, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return HB_ERR_CUDA;
+    }
+    return HB_OK;
+}
+
+hb_status hb_mlp_gradient(hb_ctx* c, const float* ybar_dev, const float* target_dev, long n, float* grad_dev,
+                          float* loss_dev, void* stream) {
+    if (!c || !ybar_dev || !target_dev || !grad_dev || !loss_dev || n <= 0) return HB_ERR_ARG;
+    if (n > (long)kMlpMaxBlocks * hb::kMlpTrainSamples) return HB_ERR_SHAPE;
+    if (!c->mlp_ready) return HB_ERR_STATE;
+    DeviceGuard g(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t np = hb::kNParams;
+    const int nblocks = (int)((n + hb::kMlpTrainSamples - 1) / hb::kMlpTrainSamples);
+    cudaError_t e = hb::launch_mlp_train(c->d_mlp + 3 * np, c->mlp_norm, ybar_dev, target_dev, n, (int)n, 0, 0, 1,
+                                         c->d_mlp_gpart, c->d_mlp_lpart, s);
+    if (e == cudaSuccess)
+        e = hb::launch_mlp_adam(c->d_mlp_gpart, c->d_mlp_lpart, nblocks, (int)n, grad_dev, loss_dev, nullptr,
+                                nullptr, nullptr, nullptr, 0.f, 0.9f, 0.999f, 1e-8f, 1, s);
+    c->launches += 2;
+    return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+}
+
+hb_status hb_mlp_forward(hb_ctx* c, const float* ybar_dev, long n, float* conc_dev, void* stream) {
+    if (!c || !ybar_dev || !conc_dev || n < 0 || (reinterpret_cast<uintptr_t>(conc_dev) & 7)) return HB_ERR_ARG;
+    if (!c->mlp_ready) return HB_ERR_STATE;
+    if (n == 0) return HB_OK;
+    DeviceGuard g(c->device);
+    cudaError_t e = hb::launch_mlp_forward(c->d_mlp + 3 * hb::kNParams, c->mlp_norm, ybar_dev, n,
+                                           reinterpret_cast<float2*>(conc_dev), nullptr,
+                                           static_cast<cudaStream_t>(stream));
+    c->launches++;
+    return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+}
+
+hb_status hb_set_lowpass_mode(hb_ctx* c, int mode, double tol, int nsample) {
+    if (!c) return HB_ERR_ARG;
+    if (mode != HB_MODE_BAYES && mode != HB_MODE_MLP) return HB_ERR_ARG;
+    if (mode == HB_MODE_MLP) {
+        if (!(tol >= 0.0) || nsample < 1) return HB_ERR_ARG;
+        if (!c->mlp_ready) return HB_ERR_STATE;
+        if (c->flags & HB_LOWPASS_TIKHONOV) return HB_ERR_STATE;
+        c->mlp_tol = (float)tol;
+        c->mlp_nsample = nsample;
+    }
+    c->lowpass_mode = mode;
+    return HB_OK;
+}
+
+hb_status hb_lowpass_stats(hb_ctx* c, long* mlp_frames, long* fallbacks) {
+    if (!c || !mlp_frames || !fallbacks) return HB_ERR_ARG;
+    DeviceGuard g(c->device);
+    unsigned fb = 0;
+    if (c->d_flags && cudaMemcpy(&fb, c->d_flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HB_ERR_CUDA;
+    *mlp_frames = c->mlp_frames;
+    *fallbacks = fb;
+    return HB_OK;
 }
 
 // ------------------------------------------------------------------------------------

@@ -241,7 +241,13 @@ __device__ __forceinline__ void run_unit(const BayesParams& bp, const BayesRec& 
 template <int CPL>
 __global__ void HB_POST_BOUNDS posterior_kernel(BayesParams bp, const BayesRec* __restrict__ recs, long npix, int rs,
                                                 float* partial, unsigned* count, float2* __restrict__ chat,
-                                                float2* __restrict__ chat_scaled, float scale) {
+                                                float2* __restrict__ chat_scaled, float scale, PosteriorGate gate) {
+    // gated launch (fallback of the learned stand-in): run only when the summed sampled
+    // error of the stand-in exceeded its threshold (a NaN sum also runs)
+    if (gate.err_sum) {
+        if (*gate.err_sum <= gate.threshold) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(gate.fallbacks, 1u);
+    }
     const int lane = threadIdx.x & 31;
     const long nw = (long)gridDim.x * (kThreads / 32);
     const long units = npix * rs;
@@ -290,7 +296,8 @@ inline long parts_for(long npix, long warps, int max_parts, int n0) {
 
 template <int CPL>
 cudaError_t launch_cpl(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
-                       float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s) {
+                       float2* chat, float2* chat_scaled, float scale, bool pdl, const PosteriorGate& gate,
+                       cudaStream_t s) {
     int resident = 0, sms = 0;
     cudaError_t e = residency(posterior_kernel<CPL>, resident, sms);
     if (e != cudaSuccess) return e;
@@ -310,18 +317,81 @@ cudaError_t launch_cpl(const BayesParams& bp, const BayesRec* rec, long npix, co
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, posterior_kernel<CPL>, bp, rec, npix, (int)rs, sc.partial, sc.count, chat,
-                              chat_scaled, scale);
+                              chat_scaled, scale, gate);
 }
 
 }  // namespace
 
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
-                             float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s) {
+                             float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,
+                             const PosteriorGate& gate) {
     if (npix <= 0) return cudaSuccess;
-    if (bp.n1 <= 32) return launch_cpl<1>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, s);
-    if (bp.n1 <= 64) return launch_cpl<2>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, s);
-    if (bp.n1 <= 128) return launch_cpl<4>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, s);
-    return launch_cpl<8>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, s);
+    if (bp.n1 <= 32) return launch_cpl<1>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);
+    if (bp.n1 <= 64) return launch_cpl<2>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);
+    if (bp.n1 <= 128) return launch_cpl<4>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);
+    return launch_cpl<8>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);
+}
+
+namespace {
+
+// Exact posterior mean of a sample of pixels, compared with another estimate of them:
+// each pixel's error relative to the box extents (the larger of the two axes) is added
+// to *err_sum (a NaN error makes the sum NaN).
+template <int CPL>
+__global__ void __launch_bounds__(kThreads) posterior_check_kernel(BayesParams bp, const BayesRec* __restrict__ recs,
+                                                                   long npix, int nsample, unsigned seed,
+                                                                   const float2* __restrict__ est, float inv_ext0,
+                                                                   float inv_ext1, float* err_sum) {
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (w >= nsample) return;
+    unsigned h = seed * 0x9E3779B9U + (unsigned)w * 0x85EBCA6BU;
+    h ^= h >> 16;
+    h *= 0x7feb352dU;
+    h ^= h >> 15;
+    h *= 0x846ca68bU;
+    h ^= h >> 16;
+    const long p = (long)(h % (unsigned long)npix);
+    const BayesRec rec = recs[p];
+    float shift = 0.f, sw, sdi, sdj;
+    for (int pass = 0; pass < 2; ++pass) {
+        sw = sdi = sdj = 0.f;
+        grid_sums<CPL>(bp, rec, lane, 0, bp.n0, shift, sw, sdi, sdj);
+        sw = warp_sum(sw);
+        sdi = warp_sum(sdi);
+        sdj = warp_sum(sdj);
+        if (usable(sw, sdi, sdj)) break;
+        shift = warp_max(grid_max<CPL>(bp, rec, lane, 0, bp.n0));
+    }
+    if (lane == 0) {
+        const float c0 = fmaf(bp.h0f, sdi / sw, fmaf((float)rec.i0, bp.h0f, bp.lo0f));
+        const float c1 = fmaf(bp.h1f, sdj / sw, fmaf((float)rec.j0, bp.h1f, bp.lo1f));
+        const float2 e = est[p];
+        const float dx = fabsf(e.x - c0) * inv_ext0, dy = fabsf(e.y - c1) * inv_ext1;
+        const float err = isnan(dx) || isnan(dy) ? NAN : fmaxf(dx, dy);
+        atomicAdd(err_sum, err);
+    }
+}
+
+template <int CPL>
+cudaError_t launch_check_cpl(const BayesParams& bp, const BayesRec* rec, long npix, int nsample, unsigned seed,
+                             const float2* est, float inv_ext0, float inv_ext1, float* err_sum, cudaStream_t s) {
+    const int blocks = (nsample + kThreads / 32 - 1) / (kThreads / 32);
+    posterior_check_kernel<CPL><<<blocks, kThreads, 0, s>>>(bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1,
+                                                            err_sum);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_posterior_check(const BayesParams& bp, const BayesRec* rec, long npix, int nsample, unsigned seed,
+                                   const float2* est, float inv_ext0, float inv_ext1, float* err_sum,
+                                   cudaStream_t s) {
+    if (npix <= 0 || nsample <= 0) return cudaSuccess;
+    if (bp.n1 <= 32) return launch_check_cpl<1>(bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1, err_sum, s);
+    if (bp.n1 <= 64) return launch_check_cpl<2>(bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1, err_sum, s);
+    if (bp.n1 <= 128) return launch_check_cpl<4>(bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1, err_sum, s);
+    return launch_check_cpl<8>(bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1, err_sum, s);
 }
 
 }  // namespace hb

@@ -63,10 +63,20 @@ constexpr int kMaxParts = 8;
 
 // Launch wrappers (defined in the .cu files).  All return the launch status.
 cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
-                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s);
+                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f = nullptr);
 cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s);
+// Optional gate of the posterior launch: when err_sum is set the kernel runs only if the
+// float it holds exceeds threshold (and then counts one fallback).
+struct PosteriorGate {
+    const float* err_sum;
+    float threshold;
+    unsigned* fallbacks;
+};
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
-                             float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s);
+                             float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,
+                             const PosteriorGate& gate = PosteriorGate{nullptr, 0.f, nullptr});
+cudaError_t launch_posterior_check(const BayesParams& bp, const BayesRec* rec, long npix, int nsample, unsigned seed,
+                                   const float2* est, float inv_ext0, float inv_ext1, float* err_sum, cudaStream_t s);
 cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_t stride, const float2* lut,
                              const float2* chat, float* out0, float* out1, int debug_conc, bool pdl, cudaStream_t s);
 size_t transform_smem_bytes(const TransformParams& tp);

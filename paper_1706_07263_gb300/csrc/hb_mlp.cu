@@ -1,0 +1,416 @@
+// hb_mlp.cu -- learned stand-in for the low-pass posterior step: a 3 -> 64 -> 64 -> 2
+// multilayer perceptron with exact (erf) GELU, BF16 weights and activations and FP32
+// accumulation, trained on (block-mean log-attenuation -> posterior mean) pairs that the
+// posterior kernel produces.  The paper has no learned component; the network only
+// stands in for its low-pass Bayesian estimate.
+//
+// Model.  x = T ybar + t0;  z1 = W1 x + b1;  h1 = bf16(gelu(z1));
+//         z2 = W2 h1 + b2;  h2 = bf16(gelu(z2));  o = W3 h2 + b3;
+//         c = clip(A+ ybar, box) + osc * o          (A+ = pseudo-inverse of A)
+// so the network learns the residual of the posterior mean on the clipped
+// least-squares estimate (non-zero near the box edges, where the prior truncates the
+// likelihood), in units of the posterior standard deviation osc; its input is ybar in
+// least-squares coordinates (see MlpNorm).  Loss: mean over samples and both outputs
+// of (o - t)^2, t = (c_target - clip(A+ ybar)) / osc.
+//
+// Kernels.  mlp_train_kernel: a CTA of 4 warps takes 64 samples of a minibatch (16 per
+// warp), runs the forward pass, the loss gradient and the backward pass, and writes its
+// partial parameter gradients; the two 64x64 products per direction run on tensor cores
+// (mma.sync m16n8k16, BF16 in, FP32 accumulate), the 3- and 2-wide layers on the FP32
+// pipes.  mlp_adam_kernel adds the partials in a fixed order (deterministic) and applies
+// Adam to the FP32 master weights, refreshing the BF16 copies.  mlp_forward_kernel:
+// inference, persistent warps of 16 samples.  Weights are BF16; activations are rounded
+// to BF16 at h1 and h2, and so is the gradient dz2 fed to the tensor cores; the input x
+// stays FP32 (the correction varies fast near the box edges, so the input needs more
+// resolution than BF16's 8 bits); accumulation is FP32 throughout.
+#include "hb_common.cuh"
+#include "hb_mlp.cuh"
+
+#include <cuda_bf16.h>
+#include <math.h>
+
+namespace hb {
+namespace {
+
+constexpr int kWarpsT = 4;                 // warps per training CTA
+constexpr int kSamplesT = 16 * kWarpsT;    // samples per training CTA
+constexpr float kInvSqrt2 = 0.70710678118654752440f;
+constexpr float kInvSqrt2Pi = 0.39894228040143267794f;
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * kInvSqrt2)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.f + erff(z * kInvSqrt2)) + z * kInvSqrt2Pi * expf(-0.5f * z * z);
+}
+#ifndef HB_MLP_ACT_FP32
+#define HB_MLP_ACT_FP32 0  // 1: keep activations in FP32 (precision study only)
+#endif
+__device__ __forceinline__ float bf(float v) {
+#if HB_MLP_ACT_FP32
+    return v;
+#else
+    return __bfloat162float(__float2bfloat16_rn(v));
+#endif
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);  // .x = lo (low 16 bits)
+    return *reinterpret_cast<const unsigned*>(&p);
+}
+
+// D = A B + D for one m16n8k16 tile; a[4], b[2] packed bf16 pairs, d[4] FP32.
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Fragment helpers.  A(m, k) and B(k, n) are read through functors so that the same
+// code serves transposed operands.  Layout of m16n8k16 (PTX ISA): g = lane / 4,
+// q = lane % 4; A regs: (g, 2q..2q+1), (g+8, 2q..), (g, 2q+8..), (g+8, 2q+8..);
+// B regs: (k = 2q..2q+1, n = g), (k = 2q+8.., n = g); C: (g, 2q..2q+1), (g+8, 2q..).
+template <typename FA>
+__device__ __forceinline__ void load_a(unsigned (&a)[4], FA A, int m0, int k0, int lane) {
+    const int g = lane >> 2, q = lane & 3;
+    a[0] = pack_bf16(A(m0 + g, k0 + 2 * q), A(m0 + g, k0 + 2 * q + 1));
+    a[1] = pack_bf16(A(m0 + g + 8, k0 + 2 * q), A(m0 + g + 8, k0 + 2 * q + 1));
+    a[2] = pack_bf16(A(m0 + g, k0 + 2 * q + 8), A(m0 + g, k0 + 2 * q + 9));
+    a[3] = pack_bf16(A(m0 + g + 8, k0 + 2 * q + 8), A(m0 + g + 8, k0 + 2 * q + 9));
+}
+template <typename FB>
+__device__ __forceinline__ void load_b(unsigned (&b)[2], FB B, int k0, int n0, int lane) {
+    const int g = lane >> 2, q = lane & 3;
+    b[0] = pack_bf16(B(k0 + 2 * q, n0 + g), B(k0 + 2 * q + 1, n0 + g));
+    b[1] = pack_bf16(B(k0 + 2 * q + 8, n0 + g), B(k0 + 2 * q + 9, n0 + g));
+}
+
+// Parameters in shared memory (BF16 values held as float; they are exact in FP32).
+struct SmemParams {
+    float W1[kHid * kIn], b1[kHid], W2[kHid * kHid], b2[kHid], W3[kOut * kHid], b3[kOut];
+};
+
+__device__ void load_params(SmemParams& P, const float* __restrict__ wbf) {
+    for (int i = threadIdx.x; i < kNParams; i += blockDim.x) {
+        const float v = wbf[i];
+        if (i < kOffB1) P.W1[i - kOffW1] = v;
+        else if (i < kOffW2) P.b1[i - kOffB1] = v;
+        else if (i < kOffB2) P.W2[i - kOffW2] = v;
+        else if (i < kOffW3) P.b2[i - kOffB2] = v;
+        else if (i < kOffB3) P.W3[i - kOffW3] = v;
+        else P.b3[i - kOffB3] = v;
+    }
+}
+
+__device__ __forceinline__ float clip_ls(const MlpNorm& nm, const float y[3], int j) {
+    const float c = nm.Ap[j * 3] * y[0] + nm.Ap[j * 3 + 1] * y[1] + nm.Ap[j * 3 + 2] * y[2];
+    return j == 0 ? fminf(fmaxf(c, nm.lo0), nm.hi0) : fminf(fmaxf(c, nm.lo1), nm.hi1);
+}
+
+// Per-warp forward for 16 samples whose inputs are ys[s][3].  TRAIN keeps z1 and z2
+// for the backward pass; inference writes h2 straight from the tensor-core results.
+template <bool TRAIN>
+struct WarpBufT {
+    float x[16][kIn];
+    float h1[16][kHid], h2[16][kHid];
+    float z1[TRAIN ? 16 : 1][kHid], z2[TRAIN ? 16 : 1][kHid];
+    float o[16][kOut];
+};
+typedef WarpBufT<true> WarpBuf;
+
+template <bool TRAIN>
+__device__ void warp_forward(const SmemParams& P, const MlpNorm& nm, WarpBufT<TRAIN>& B, const float (*ys)[3],
+                             int lane) {
+    if (lane < 16)
+        for (int c = 0; c < kIn; ++c)
+            B.x[lane][c] = nm.T[c * 3] * ys[lane][0] + nm.T[c * 3 + 1] * ys[lane][1] + nm.T[c * 3 + 2] * ys[lane][2] +
+                           nm.t0[c];
+    __syncwarp();
+    // layer 1 (FP32 pipes): 16 samples x 64 units, 32 per lane
+    for (int e = lane; e < 16 * kHid; e += 32) {
+        const int s = e / kHid, u = e % kHid;
+        float z = P.b1[u];
+        for (int c = 0; c < kIn; ++c) z = fmaf(P.W1[u * kIn + c], B.x[s][c], z);
+        if (TRAIN) B.z1[s][u] = z;
+        B.h1[s][u] = bf(gelu(z));
+    }
+    __syncwarp();
+    // layer 2 on tensor cores: z2 (16 x 64) = h1 (16 x 64) W2^T
+    const int g = lane >> 2, q = lane & 3;
+    for (int nt = 0; nt < kHid / 8; ++nt) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int kt = 0; kt < kHid / 16; ++kt) {
+            unsigned a[4], b[2];
+            load_a(a, [&](int m, int k) { return B.h1[m][k]; }, 0, kt * 16, lane);
+            load_b(b, [&](int k, int n) { return P.W2[n * kHid + k]; }, kt * 16, nt * 8, lane);
+            mma16816(d, a, b);
+        }
+        const int n = nt * 8 + 2 * q;
+        const float z00 = d[0] + P.b2[n], z01 = d[1] + P.b2[n + 1];
+        const float z10 = d[2] + P.b2[n], z11 = d[3] + P.b2[n + 1];
+        if (TRAIN) {
+            B.z2[g][n] = z00;
+            B.z2[g][n + 1] = z01;
+            B.z2[g + 8][n] = z10;
+            B.z2[g + 8][n + 1] = z11;
+        }
+        B.h2[g][n] = bf(gelu(z00));
+        B.h2[g][n + 1] = bf(gelu(z01));
+        B.h2[g + 8][n] = bf(gelu(z10));
+        B.h2[g + 8][n + 1] = bf(gelu(z11));
+    }
+    __syncwarp();
+    // layer 3 (FP32 pipes): 16 samples x 2 outputs, one per lane
+    {
+        const int s = lane >> 1, j = lane & 1;
+        float o = P.b3[j];
+        for (int u = 0; u < kHid; ++u) o = fmaf(P.W3[j * kHid + u], B.h2[s][u], o);
+        B.o[s][j] = o;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ unsigned hash_u32(unsigned x) {
+    // integer hash (a variant of the well-known "lowbias32" mixing function)
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+struct TrainSmem {
+    SmemParams P;
+    WarpBuf W[kWarpsT];
+    float dz2[kSamplesT][kHid];  // BF16 values
+    float h1[kSamplesT][kHid];   // copy of the CTA's h1 for dW2
+    float dz1[kSamplesT][kHid];
+    float do_[kSamplesT][kOut];
+    float ys[kSamplesT][3];
+    float red[kWarpsT];
+};
+
+// One CTA: 64 samples of the minibatch -> partial gradients (kNParams floats) and the
+// partial sum of squared errors.  Samples index into (ybar, target) through a hash of
+// (seed, step, position) unless idx_direct is set (sample b of the batch is row b).
+__global__ void __launch_bounds__(32 * kWarpsT) mlp_train_kernel(const float* __restrict__ wbf, MlpNorm nm,
+                                                                 const float* __restrict__ ybar,
+                                                                 const float* __restrict__ target, long n, int batch,
+                                                                 unsigned seed, int step, int idx_direct,
+                                                                 float* __restrict__ gpart,
+                                                                 float* __restrict__ lpart) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    load_params(S.P, wbf);
+    // gather the CTA's samples
+    float* tgt_local = &S.do_[0][0];  // targets staged here, replaced by dL/do below
+    for (int s = threadIdx.x; s < kSamplesT; s += blockDim.x) {
+        const long b = (long)blockIdx.x * kSamplesT + s;
+        long r = 0;
+        const bool valid = b < batch;
+        if (valid) r = idx_direct ? b : (long)(hash_u32(seed ^ hash_u32((unsigned)step * 0x9E3779B9U + (unsigned)b)) % (unsigned long)n);
+        for (int c = 0; c < 3; ++c) S.ys[s][c] = valid ? ybar[r * 3 + c] : 0.f;
+        for (int j = 0; j < kOut; ++j) tgt_local[s * kOut + j] = valid ? target[r * 2 + j] : 0.f;
+    }
+    __syncthreads();
+    WarpBuf& B = S.W[warp];
+    const int s0 = warp * 16;
+    warp_forward<true>(S.P, nm, B, &S.ys[s0], lane);
+    // loss and dL/do = (o - t) / (batch * kOut) * 2  (mean over batch * 2 elements)
+    float sq = 0.f;
+    {
+        const int s = lane >> 1, j = lane & 1;
+        const long b = (long)blockIdx.x * kSamplesT + s0 + s;
+        const float* y = S.ys[s0 + s];
+        const float osc = j == 0 ? nm.osc0 : nm.osc1;
+        const float t = (tgt_local[(s0 + s) * kOut + j] - clip_ls(nm, y, j)) / osc;
+        const float err = b < batch ? B.o[s][j] - t : 0.f;
+        sq = err * err;
+        S.do_[s0 + s][j] = err * (2.f / ((float)batch * kOut));
+    }
+    for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+    if (lane == 0) S.red[warp] = sq;
+    __syncwarp();
+    // dz2 = (W3^T do) * gelu'(z2), rounded to BF16 for the tensor cores
+    for (int e = lane; e < 16 * kHid; e += 32) {
+        const int s = e / kHid, u = e % kHid;
+        const float dh = S.P.W3[u] * S.do_[s0 + s][0] + S.P.W3[kHid + u] * S.do_[s0 + s][1];
+        S.dz2[s0 + s][u] = bf(dh * gelu_grad(B.z2[s][u]));
+        S.h1[s0 + s][u] = B.h1[s][u];
+    }
+    __syncwarp();
+    // dh1 (16 x 64) = dz2 (16 x 64) W2 on tensor cores, then dz1 = dh1 * gelu'(z1)
+    {
+        const int g = lane >> 2, q = lane & 3;
+        for (int nt = 0; nt < kHid / 8; ++nt) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int kt = 0; kt < kHid / 16; ++kt) {
+                unsigned a[4], b[2];
+                load_a(a, [&](int m, int k) { return S.dz2[s0 + m][k]; }, 0, kt * 16, lane);
+                load_b(b, [&](int k, int nn) { return S.P.W2[k * kHid + nn]; }, kt * 16, nt * 8, lane);
+                mma16816(d, a, b);
+            }
+            const int nn = nt * 8 + 2 * q;
+            S.dz1[s0 + g][nn] = d[0] * gelu_grad(B.z1[g][nn]);
+            S.dz1[s0 + g][nn + 1] = d[1] * gelu_grad(B.z1[g][nn + 1]);
+            S.dz1[s0 + g + 8][nn] = d[2] * gelu_grad(B.z1[g + 8][nn]);
+            S.dz1[s0 + g + 8][nn + 1] = d[3] * gelu_grad(B.z1[g + 8][nn + 1]);
+        }
+    }
+    __syncthreads();
+    float* gp = gpart + (size_t)blockIdx.x * kNParams;
+    // dW2 (64 x 64) = dz2^T (64 x 64 samples) h1 (64 samples x 64): warp w takes rows 16w..16w+15
+    {
+        const int g = lane >> 2, q = lane & 3, m0 = warp * 16;
+        for (int nt = 0; nt < kHid / 8; ++nt) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int kt = 0; kt < kSamplesT / 16; ++kt) {
+                unsigned a[4], b[2];
+                load_a(a, [&](int m, int k) { return S.dz2[k][m]; }, m0, kt * 16, lane);
+                load_b(b, [&](int k, int nn) { return S.h1[k][nn]; }, kt * 16, nt * 8, lane);
+                mma16816(d, a, b);
+            }
+            const int nn = nt * 8 + 2 * q;
+            gp[kOffW2 + (m0 + g) * kHid + nn] = d[0];
+            gp[kOffW2 + (m0 + g) * kHid + nn + 1] = d[1];
+            gp[kOffW2 + (m0 + g + 8) * kHid + nn] = d[2];
+            gp[kOffW2 + (m0 + g + 8) * kHid + nn + 1] = d[3];
+        }
+    }
+    // the small layers and the biases: one thread per parameter, fixed-order sums over samples
+    for (int i = threadIdx.x; i < kNParams; i += blockDim.x) {
+        if (i >= kOffW2 && i < kOffB2) continue;
+        float acc = 0.f;
+        if (i < kOffB1) {
+            const int u = (i - kOffW1) / kIn, c = (i - kOffW1) % kIn;
+            for (int s = 0; s < kSamplesT; ++s) acc = fmaf(S.dz1[s][u], S.W[s / 16].x[s % 16][c], acc);
+        } else if (i < kOffW2) {
+            const int u = i - kOffB1;
+            for (int s = 0; s < kSamplesT; ++s) acc += S.dz1[s][u];
+        } else if (i < kOffW3) {
+            const int u = i - kOffB2;
+            for (int s = 0; s < kSamplesT; ++s) acc += S.dz2[s][u];
+        } else if (i < kOffB3) {
+            const int j = (i - kOffW3) / kHid, u = (i - kOffW3) % kHid;
+            for (int s = 0; s < kSamplesT; ++s) acc = fmaf(S.do_[s][j], S.W[s / 16].h2[s % 16][u], acc);
+        } else {
+            const int j = i - kOffB3;
+            for (int s = 0; s < kSamplesT; ++s) acc += S.do_[s][j];
+        }
+        gp[i] = acc;
+    }
+    if (threadIdx.x == 0) {
+        float l = 0.f;
+        for (int w = 0; w < kWarpsT; ++w) l += S.red[w];
+        lpart[blockIdx.x] = l;
+    }
+}
+
+__global__ void mlp_adam_kernel(const float* __restrict__ gpart, const float* __restrict__ lpart, int nblocks,
+                                int batch, float* __restrict__ grad, float* __restrict__ loss, float* __restrict__ master,
+                                float* __restrict__ m, float* __restrict__ v, float* __restrict__ wbf, float lr,
+                                float beta1, float beta2, float eps, int t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        float l = 0.f;
+        for (int b = 0; b < nblocks; ++b) l += lpart[b];
+        *loss = l / ((float)batch * kOut);
+    }
+    if (i >= kNParams) return;
+    float gsum = 0.f;
+    for (int b = 0; b < nblocks; ++b) gsum += gpart[(size_t)b * kNParams + i];
+    grad[i] = gsum;
+    if (lr > 0.f && master) {
+        const float mi = beta1 * m[i] + (1.f - beta1) * gsum;
+        const float vi = beta2 * v[i] + (1.f - beta2) * gsum * gsum;
+        m[i] = mi;
+        v[i] = vi;
+        const float mh = mi / (1.f - powf(beta1, (float)t)), vh = vi / (1.f - powf(beta2, (float)t));
+        const float w = master[i] - lr * mh / (sqrtf(vh) + eps);
+        master[i] = w;
+        wbf[i] = bf(w);
+    }
+}
+
+constexpr int kWarpsF = 8;
+struct FwdSmem {
+    SmemParams P;
+    WarpBufT<false> W[kWarpsF];
+    float ys[kWarpsF][16][3];
+};
+
+__global__ void __launch_bounds__(32 * kWarpsF) mlp_forward_kernel(const float* __restrict__ wbf, MlpNorm nm,
+                                                                   const float* __restrict__ ybar, long n,
+                                                                   float2* __restrict__ chat,
+                                                                   unsigned* __restrict__ err_reset) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw);
+    if (err_reset && blockIdx.x == 0 && threadIdx.x == 0) *err_reset = 0u;
+    load_params(S.P, wbf);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long ntile = (n + 15) / 16;
+    for (long tile = (long)blockIdx.x * kWarpsF + warp; tile < ntile; tile += (long)gridDim.x * kWarpsF) {
+        const long base = tile * 16;
+        if (lane < 16)
+            for (int c = 0; c < 3; ++c) S.ys[warp][lane][c] = base + lane < n ? ybar[(base + lane) * 3 + c] : 0.f;
+        __syncwarp();
+        warp_forward<false>(S.P, nm, S.W[warp], S.ys[warp], lane);
+        if (lane < 16 && base + lane < n) {
+            const float* y = S.ys[warp][lane];
+            const float c0 = clip_ls(nm, y, 0) + nm.osc0 * S.W[warp].o[lane][0];
+            const float c1 = clip_ls(nm, y, 1) + nm.osc1 * S.W[warp].o[lane][1];
+            chat[base + lane] = make_float2(c0, c1);
+        }
+        __syncwarp();
+    }
+}
+
+template <typename K>
+cudaError_t set_smem_attr(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
+
+cudaError_t launch_mlp_train(const float* wbf, const MlpNorm& nm, const float* ybar, const float* target, long n,
+                             int batch, unsigned seed, int step, int idx_direct, float* gpart, float* lpart,
+                             cudaStream_t s) {
+    const size_t sm = sizeof(TrainSmem);
+    cudaError_t e = set_smem_attr(mlp_train_kernel, sm);
+    if (e != cudaSuccess) return e;
+    const int blocks = (batch + kSamplesT - 1) / kSamplesT;
+    mlp_train_kernel<<<blocks, 32 * kWarpsT, sm, s>>>(wbf, nm, ybar, target, n, batch, seed, step, idx_direct, gpart,
+                                                       lpart);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_adam(const float* gpart, const float* lpart, int nblocks, int batch, float* grad, float* loss,
+                            float* master, float* m, float* v, float* wbf, float lr, float beta1, float beta2,
+                            float eps, int t, cudaStream_t s) {
+    mlp_adam_kernel<<<(kNParams + 255) / 256, 256, 0, s>>>(gpart, lpart, nblocks, batch, grad, loss, master, m, v,
+                                                            wbf, lr, beta1, beta2, eps, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_forward(const float* wbf, const MlpNorm& nm, const float* ybar, long n, float2* chat,
+                               unsigned* err_reset, cudaStream_t s) {
+    const size_t sm = sizeof(FwdSmem);
+    cudaError_t e = set_smem_attr(mlp_forward_kernel, sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long tiles = (n + 15) / 16;
+    long blocks = (tiles + kWarpsF - 1) / kWarpsF;
+    if (blocks > 2L * sms) blocks = 2L * sms;
+    if (blocks < 1) blocks = 1;
+    mlp_forward_kernel<<<(unsigned)blocks, 32 * kWarpsF, sm, s>>>(wbf, nm, ybar, n, chat, err_reset);
+    return cudaGetLastError();
+}
+
+}  // namespace hb

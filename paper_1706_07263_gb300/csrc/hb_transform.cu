@@ -161,7 +161,7 @@ namespace {
 __global__ void __launch_bounds__(kThreads) analysis_kernel(TransformParams tp, BayesParams bp,
                                                             const unsigned char* __restrict__ frame, size_t stride,
                                                             const float2* __restrict__ lut, double* __restrict__ ybar,
-                                                            BayesRec* __restrict__ rec) {
+                                                            BayesRec* __restrict__ rec, float* __restrict__ ybar_f) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int TH = 1 << tp.levels, TW = tp.tile_w;
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
@@ -187,6 +187,10 @@ __global__ void __launch_bounds__(kThreads) analysis_kernel(TransformParams tp, 
         if (ybar) {
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) ybar[o * 3 + ch] = (double)yhi[ch] + (double)ylo[ch];
+        }
+        if (ybar_f) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) ybar_f[o * 3 + ch] = yhi[ch] + ylo[ch];
         }
         rec[o] = bayes_setup(yhi, ylo, bp);
     }
@@ -384,7 +388,8 @@ __global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams
                                                                  const unsigned char* __restrict__ frame,
                                                                  size_t stride, const float2* __restrict__ lut_g,
                                                                  double* __restrict__ ybar,
-                                                                 BayesRec* __restrict__ rec) {
+                                                                 BayesRec* __restrict__ rec,
+                                                                 float* __restrict__ ybar_f) {
     constexpr int TH = 1 << L;
     constexpr int NSB = kThreads / TH;  // superblocks per CTA (kThreads columns)
     __shared__ float2 lut[256];
@@ -424,6 +429,10 @@ __global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams
         if (ybar) {
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) ybar[o * 3 + ch] = (double)yhi[ch] + (double)ylo[ch];
+        }
+        if (ybar_f) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) ybar_f[o * 3 + ch] = yhi[ch] + ylo[ch];
         }
         rec[o] = bayes_setup(yhi, ylo, bp);
     }
@@ -516,24 +525,24 @@ static dim3 tile_grid(const TransformParams& tp) {
 }
 
 cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
-                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s) {
+                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f) {
     const unsigned char* f = static_cast<const unsigned char*>(frame);
     if (tp.levels <= 4) {
         const int TH = 1 << tp.levels;
         const dim3 grid((tp.wl * TH + kThreads - 1) / kThreads, tp.hl);
         switch (tp.levels) {
-            case 0: analysis_warp_kernel<0><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec); break;
-            case 1: analysis_warp_kernel<1><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec); break;
-            case 2: analysis_warp_kernel<2><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec); break;
-            case 3: analysis_warp_kernel<3><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec); break;
-            default: analysis_warp_kernel<4><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec); break;
+            case 0: analysis_warp_kernel<0><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
+            case 1: analysis_warp_kernel<1><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
+            case 2: analysis_warp_kernel<2><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
+            case 3: analysis_warp_kernel<3><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
+            default: analysis_warp_kernel<4><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
         }
         return cudaGetLastError();
     }
     const size_t sm = transform_smem_bytes(tp);
     cudaError_t e = set_smem(analysis_kernel, sm);
     if (e != cudaSuccess) return e;
-    analysis_kernel<<<tile_grid(tp), kThreads, sm, s>>>(tp, bp, f, stride, lut, ybar, rec);
+    analysis_kernel<<<tile_grid(tp), kThreads, sm, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,161 @@
+"""The learned low-pass stand-in on the GPU: forward and gradient parity with the FP64
+reference (oracle/mlp.py), training, and the per-frame fallback to the exact posterior."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle import mlp  # noqa: E402
+from paper_1706_07263_gb300 import Context, HbError, binding, build, surrogate, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+GRID = dict(n0=128, n1=128, lo0=0.0, hi0=150.0, lo1=0.0, hi1=100.0, sigma_l=0.02)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """A network trained on pairs from seeded 512x512 frames (3 levels, 128x128 grid)."""
+    build.build()
+    wl = synth.Workload("train512", 512, 512, 3, (128, 128), 12, 10.0, 60.0, 0.01, "u8", 41)
+    mix = synth.make_mixing(1)
+    ctx = Context(mix.A, GRID, wl.levels, wl.lam, wl.W, wl.H, wl.fmt)
+    frames = surrogate.workload_frames(wl, mix, 12, 500)
+    ys, cs = surrogate.training_pairs(ctx, frames, DEV)
+    phases = ((3e-3, 3000), (1e-3, 3000), (3e-4, 3000), (1e-4, 3000))
+    losses = surrogate.train_phases(ctx, ys[:-4096], cs[:-4096], phases=phases, seed=3)
+    yield dict(ctx=ctx, A=mix.A, ys=ys, cs=cs, losses=losses, wl=wl, mix=mix)
+    ctx.close()
+
+
+def _pairs(n=4096, seed=0):
+    rng = np.random.default_rng(seed)
+    A = synth.make_mixing(1).A
+    c = np.stack([rng.uniform(-10, 160, n), rng.uniform(-10, 110, n)], 1)
+    ybar = (c @ A.T + rng.normal(0, 0.01, (n, 3))).astype(np.float32)
+    target = np.clip(c + rng.normal(0, 2, c.shape), [0, 0], [150, 100]).astype(np.float32)
+    return A, ybar, target
+
+
+def test_forward_matches_reference():
+    A, ybar, _ = _pairs()
+    with Context(A, GRID, 3, 1e-3, 64, 64, "u8") as ctx:
+        ctx.mlp_init(11)
+        params = ctx.mlp_get_params()
+        out = torch.empty((ybar.shape[0], 2), dtype=torch.float32, device=DEV)
+        ctx.mlp_forward(torch.from_numpy(ybar).to(DEV), out)
+        torch.cuda.synchronize()
+    nm = mlp.norm_for(A, GRID)
+    ref = mlp.forward(params, nm, ybar.astype(np.float64))
+    d = np.abs(out.cpu().numpy() - ref["c"]) / nm["ext"]
+    # FP32 vs FP64 sums differ by rounding; rarely a BF16 rounding of h1/h2 flips as well
+    assert np.quantile(d, 0.99) <= 1e-5, np.quantile(d, 0.99)
+    assert d.max() <= 5e-3, d.max()
+
+
+def test_gradient_matches_reference():
+    A, ybar, target = _pairs(seed=1)
+    with Context(A, GRID, 3, 1e-3, 64, 64, "u8") as ctx:
+        ctx.mlp_init(12)
+        params = ctx.mlp_get_params()
+        g = torch.empty(binding.MLP_NPARAMS, dtype=torch.float32, device=DEV)
+        loss = torch.empty(1, dtype=torch.float32, device=DEV)
+        ctx.mlp_gradient(torch.from_numpy(ybar).to(DEV), torch.from_numpy(target).to(DEV), g, loss)
+        torch.cuda.synchronize()
+    nm = mlp.norm_for(A, GRID)
+    ref_loss, ref_g = mlp.loss_and_grad(params, nm, ybar.astype(np.float64), target.astype(np.float64))
+    got = g.cpu().numpy().astype(np.float64)
+    assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-4)
+    assert np.linalg.norm(got - ref_g) <= 1e-3 * np.linalg.norm(ref_g)
+    for name, a, b in (("W1", mlp.OFF_W1, mlp.OFF_B1), ("W2", mlp.OFF_W2, mlp.OFF_B2), ("W3", mlp.OFF_W3, mlp.OFF_B3)):
+        assert np.linalg.norm(got[a:b] - ref_g[a:b]) <= 2e-3 * np.linalg.norm(ref_g[a:b]) + 1e-9, name
+
+
+def test_training_reduces_loss_and_fits_held_out_pairs(trained):
+    losses = trained["losses"]
+    assert np.all(np.isfinite(losses))
+    assert losses[-50:].mean() < 0.05 * losses[:10].mean()
+    ctx, ys, cs = trained["ctx"], trained["ys"], trained["cs"]
+    out = torch.empty((4096, 2), dtype=torch.float32, device=DEV)
+    ctx.mlp_forward(ys[-4096:], out)
+    torch.cuda.synchronize()
+    err = ((out - cs[-4096:]).abs().cpu().numpy() / np.array([150.0, 100.0])).max(axis=1)
+    assert err.mean() < 2e-3, err.mean()
+
+
+def _frame(trained, seed):
+    wl, mix = trained["wl"], trained["mix"]
+    fr = synth.make_frame(seed, wl.H, wl.W, mix.A, wl.nblobs, wl.smin, wl.smax, wl.noise, wl.fmt)
+    return torch.from_numpy(fr.rgb).to(DEV)
+
+
+def _run(ctx, frame):
+    thb = torch.empty(frame.shape[:2], dtype=torch.float32, device=DEV)
+    so2 = torch.empty_like(thb)
+    ctx.estimate(frame, thb, so2)
+    torch.cuda.synchronize()
+    return thb, so2
+
+
+def test_forced_fallback_reproduces_the_exact_path(trained):
+    ctx = trained["ctx"]
+    frame = _frame(trained, 900)
+    ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
+    thb0, so20 = _run(ctx, frame)
+    good = ctx.mlp_get_params()
+    bad = good.copy()
+    bad[mlp.OFF_B3:] = 0.5                       # every estimate off by half the box
+    ctx.mlp_set_params(bad)
+    ctx.set_lowpass_mode(binding.HB_MODE_MLP, 1e-3, 256)
+    f0, b0 = ctx.lowpass_stats()
+    thb1, so21 = _run(ctx, frame)
+    f1, b1 = ctx.lowpass_stats()
+    assert (f1 - f0, b1 - b0) == (1, 1)
+    assert torch.equal(thb0, thb1) and torch.equal(so20, so21)
+    ctx.mlp_set_params(good)
+    ctx.set_lowpass_mode(binding.HB_MODE_MLP, float("inf"), 256)   # never falls back
+    thb2, _ = _run(ctx, frame)
+    assert ctx.lowpass_stats()[1] == b1
+    # the network's THb differs from the exact path by its low-pass error: a few 1e-3 relative
+    # typically, more in the few blocks at the box edges where the network is least accurate
+    rel = ((thb2 - thb0).abs() / thb0.abs().clamp(min=1.0)).flatten()
+    assert rel.median().item() < 5e-3, rel.median().item()
+    absq = torch.quantile((thb2 - thb0).abs().flatten(), 0.99).item()
+    assert absq < 0.01 * 250.0, absq      # 99% of pixels within 1% of the THb range
+    ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
+
+
+def test_mlp_mode_is_faster_than_the_grid_posterior(trained):
+    """What the network gains: a 1920x1080 frame (3 levels, 128x128 grid) with the network,
+    its sampled check and the gated fallback, against the exact grid posterior."""
+    wl, mix = synth.HD_1080, trained["mix"]
+    fr = synth.make_frame(902, wl.H, wl.W, mix.A, wl.nblobs, wl.smin, wl.smax, wl.noise, wl.fmt)
+    frame = torch.from_numpy(fr.rgb).to(DEV)
+    thb = torch.empty((wl.H, wl.W), dtype=torch.float32, device=DEV)
+    so2 = torch.empty_like(thb)
+    times = {}
+    with Context(mix.A, GRID, wl.levels, wl.lam, wl.W, wl.H, wl.fmt) as ctx:
+        ctx.mlp_set_params(trained["ctx"].mlp_get_params())
+        for mode, tol in ((binding.HB_MODE_BAYES, 0.0), (binding.HB_MODE_MLP, float("inf"))):
+            ctx.set_lowpass_mode(mode, tol, 256)
+            for _ in range(3):
+                ctx.estimate(frame, thb, so2)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(20):
+                ctx.estimate(frame, thb, so2)
+            b.record()
+            torch.cuda.synchronize()
+            times[mode] = a.elapsed_time(b) / 20
+    assert times[binding.HB_MODE_MLP] < 0.5 * times[binding.HB_MODE_BAYES], times
+
+
+def test_mode_requires_a_network():
+    A = synth.make_mixing(2).A
+    with Context(A, GRID, 3, 1e-3, 64, 64, "u8") as ctx:
+        with pytest.raises(HbError):
+            ctx.set_lowpass_mode(binding.HB_MODE_MLP, 1e-3, 16)

@@ -200,6 +200,74 @@ hb_status hb_set_lowpass_mode(hb_ctx *ctx, int mode, double tol, int nsample);
  * posterior (synchronises the context's device work). */
 hb_status hb_lowpass_stats(hb_ctx *ctx, long *mlp_frames, long *fallbacks);
 
+/* ------------------------------------------------------------------------------------
+ * Serving: continuous batching of frames from many concurrent streams (an extension; the
+ * paper processes single frames).  A request-loop thread inside the library packs the
+ * frames waiting from all streams -- any mix of sizes and of 0..4 levels -- into batches
+ * that run as one launch per stage, two batches in flight on separate CUDA streams;
+ * frames that arrive while a batch runs join the next one.  Each stream owns `slots`
+ * frame slots (pinned host + device buffers) admitted against the server's budget.
+ * The mixing model, grid and lambda are shared by all streams.
+ * ------------------------------------------------------------------------------------ */
+typedef struct hb_server hb_server;
+
+/* One completed frame.  thb_host / so2_host (width*height floats each) stay valid until
+ * hb_release(stream_id, slot); latency_ms runs from the hb_submit call to the moment the
+ * results were in host memory. */
+typedef struct {
+    int stream_id;
+    int slot;
+    uint64_t tag;
+    double latency_ms;
+    const float *thb_host;
+    const float *so2_host;
+} hb_result;
+
+typedef struct {
+    long batches, frames, max_batch_frames, queued;
+    double mean_batch_frames;
+    size_t bytes_in_use, budget_bytes;
+} hb_server_info;
+
+enum { HB_SERVE_SEQUENTIAL = 1u << 4 }; /* one frame at a time, one batch in flight (baseline) */
+
+/* Create a server.  flags: HB_LAMBDA_ABSOLUTE, HB_SERVE_SEQUENTIAL.  budget_bytes bounds
+ * the device memory of all stream slots plus the two batches' scratch (sized for
+ * batch_lowpass_pixels low-pass pixels each); max_batch (1..64) bounds frames per batch.
+ * HB_ERR_BUDGET if the scratch alone exceeds the budget.  Starts the request loop. */
+hb_status hb_server_create(const hb_mixing *mix, const hb_grid *grid, double lambda, unsigned flags, int in_format,
+                           size_t budget_bytes, int max_batch, long batch_lowpass_pixels, hb_server **out);
+
+/* Stop the loop (frames not yet enqueued are dropped), wait for the GPU, free everything. */
+void hb_server_destroy(hb_server *srv);
+
+/* Admit a stream of width x height frames at `levels` (0..4) with `slots` frame slots.
+ * HB_ERR_BUDGET when its slots do not fit the remaining budget (nothing is allocated);
+ * HB_ERR_SHAPE when one frame's low pass exceeds a batch. */
+hb_status hb_stream_open(hb_server *srv, int width, int height, int levels, int slots, int *stream_id);
+
+/* Close a stream and return its memory to the budget.  HB_ERR_STATE while any of its
+ * frames is being submitted, queued, running, or completed but not yet released. */
+hb_status hb_stream_close(hb_server *srv, int stream_id);
+
+/* Queue one frame (host memory, copied before the call returns) with a caller tag.
+ * HB_ERR_STATE when all of the stream's slots are busy (poll, release and retry). */
+hb_status hb_submit(hb_server *srv, int stream_id, const void *frame_host, size_t row_stride_bytes, uint64_t tag);
+
+/* Up to max_results completed frames, waiting up to wait_us microseconds for the first.
+ * Returns HB_ERR_CUDA (with any results) if a batch failed to launch. */
+hb_status hb_poll(hb_server *srv, hb_result *out, int max_results, int *n_out, int wait_us);
+
+/* Hand a completed slot back to its stream. */
+hb_status hb_release(hb_server *srv, int stream_id, int slot);
+
+/* Hold (paused != 0) or resume the start of new batches; frames keep queueing while held
+ * and batches in flight finish.  Lets a caller release a burst of frames at once. */
+hb_status hb_server_pause(hb_server *srv, int paused);
+
+/* Counters of the server so far. */
+hb_status hb_server_stats(hb_server *srv, hb_server_info *out);
+
 /* Largest npix that hb_posterior_mean_static accepts. */
 #define HB_STATIC_MAX_PIXELS 65536
 

@@ -30,11 +30,24 @@ EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_es
             "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_strerror",
             "hb_mlp_init", "hb_mlp_set_params", "hb_mlp_get_params", "hb_lowpass_pairs", "hb_mlp_train",
             "hb_mlp_gradient", "hb_mlp_forward", "hb_set_lowpass_mode", "hb_lowpass_stats",
-            "hb_posterior_mean_static")
+            "hb_server_create", "hb_server_destroy", "hb_stream_open", "hb_stream_close", "hb_submit", "hb_poll",
+            "hb_release", "hb_server_pause", "hb_server_stats", "hb_posterior_mean_static")
+HB_SERVE_SEQUENTIAL = 1 << 4
 MLP_NPARAMS = 4546
 HB_MODE_BAYES = 0
 HB_MODE_MLP = 1
 STATIC_MAX_PIXELS = 65536
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_int), ("slot", ctypes.c_int), ("tag", ctypes.c_uint64),
+                ("latency_ms", ctypes.c_double), ("thb_host", ctypes.c_void_p), ("so2_host", ctypes.c_void_p)]
+
+
+class _ServerInfo(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_long), ("frames", ctypes.c_long), ("max_batch_frames", ctypes.c_long),
+                ("queued", ctypes.c_long), ("mean_batch_frames", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t)]
 
 
 class HbError(RuntimeError):
@@ -90,6 +103,17 @@ def load(path: str = LIB_PATH):
     lib.hb_mlp_forward.argtypes = [P, P, L, P, P]
     lib.hb_set_lowpass_mode.argtypes = [P, I, D, I]
     lib.hb_lowpass_stats.argtypes = [P, ctypes.POINTER(L), ctypes.POINTER(L)]
+    lib.hb_server_create.argtypes = [ctypes.POINTER(_Mixing), ctypes.POINTER(_Grid), D, ctypes.c_uint, I, S, I, L,
+                                     ctypes.POINTER(P)]
+    lib.hb_server_destroy.argtypes = [P]
+    lib.hb_server_destroy.restype = None
+    lib.hb_stream_open.argtypes = [P, I, I, I, I, ctypes.POINTER(I)]
+    lib.hb_stream_close.argtypes = [P, I]
+    lib.hb_submit.argtypes = [P, I, P, S, ctypes.c_uint64]
+    lib.hb_poll.argtypes = [P, ctypes.POINTER(_Result), I, ctypes.POINTER(I), I]
+    lib.hb_release.argtypes = [P, I, I]
+    lib.hb_server_stats.argtypes = [P, ctypes.POINTER(_ServerInfo)]
+    lib.hb_server_pause.argtypes = [P, I]
     for name in EXPORTED:
         getattr(lib, name)
     _lib = lib
@@ -249,6 +273,95 @@ class Context:
         n = (ctypes.c_long * 4)()
         _check(load().hb_timing_read(self._h, ms, n), "hb_timing_read")
         return {STAGES[k]: (ms[k], n[k]) for k in range(4)}
+
+
+def _structs(A, grid):
+    mix = _Mixing()
+    A = np.asarray(A, dtype=np.float64).reshape(3, 2)
+    for c in range(3):
+        for j in range(2):
+            mix.A[c][j] = float(A[c, j])
+    g = _Grid(int(grid["n0"]), int(grid["n1"]), float(grid["lo0"]), float(grid["hi0"]), float(grid["lo1"]),
+              float(grid["hi1"]), float(grid["sigma_l"]))
+    return mix, g
+
+
+class Server:
+    """Continuous-batching server of include/hb.h (hb_server_*).  Results come back as
+    NumPy views of the server's pinned host buffers, valid until release()."""
+
+    def __init__(self, A, grid: dict, lam: float, fmt: str = "u8", budget_bytes: int = 20 << 30, max_batch: int = 16,
+                 batch_lowpass_pixels: int = 2_000_000, sequential: bool = False, flags: int = 0):
+        lib = load()
+        mix, g = _structs(A, grid)
+        self._h = ctypes.c_void_p()
+        self.fmt = fmt
+        self.shapes = {}
+        fl = flags | (HB_SERVE_SEQUENTIAL if sequential else 0)
+        _check(lib.hb_server_create(ctypes.byref(mix), ctypes.byref(g), float(lam), fl,
+                                    HB_IN_U8_HWC if fmt == "u8" else HB_IN_F32_HWC, int(budget_bytes), max_batch,
+                                    int(batch_lowpass_pixels), ctypes.byref(self._h)), "hb_server_create")
+
+    def open_stream(self, width: int, height: int, levels: int, slots: int = 4) -> int:
+        sid = ctypes.c_int(-1)
+        _check(load().hb_stream_open(self._h, width, height, levels, slots, ctypes.byref(sid)), "hb_stream_open")
+        self.shapes[sid.value] = (height, width)
+        return sid.value
+
+    def close_stream(self, sid: int):
+        _check(load().hb_stream_close(self._h, sid), "hb_stream_close")
+        self.shapes.pop(sid, None)
+
+    def submit(self, sid: int, frame: np.ndarray, tag: int = 0) -> bool:
+        """Queue a frame; False when every slot of the stream is busy."""
+        fr = np.ascontiguousarray(frame)
+        rc = load().hb_submit(self._h, sid, ctypes.c_void_p(fr.ctypes.data), fr.strides[0], tag)
+        if rc == 7:
+            return False
+        _check(rc, "hb_submit")
+        return True
+
+    def poll(self, max_results: int = 64, wait_us: int = 0):
+        res = (_Result * max(max_results, 1))()
+        n = ctypes.c_int(0)
+        _check(load().hb_poll(self._h, res, max_results, ctypes.byref(n), wait_us), "hb_poll")
+        out = []
+        for k in range(n.value):
+            r = res[k]
+            h, w = self.shapes[r.stream_id]
+            fp = ctypes.POINTER(ctypes.c_float)
+            out.append(dict(stream=r.stream_id, slot=r.slot, tag=r.tag, latency_ms=r.latency_ms,
+                            thb=np.ctypeslib.as_array(ctypes.cast(r.thb_host, fp), shape=(h, w)),
+                            so2=np.ctypeslib.as_array(ctypes.cast(r.so2_host, fp), shape=(h, w))))
+        return out
+
+    def release(self, sid: int, slot: int):
+        _check(load().hb_release(self._h, sid, slot), "hb_release")
+
+    def pause(self, paused: bool = True):
+        _check(load().hb_server_pause(self._h, int(paused)), "hb_server_pause")
+
+    def stats(self) -> dict:
+        i = _ServerInfo()
+        _check(load().hb_server_stats(self._h, ctypes.byref(i)), "hb_server_stats")
+        return {k: getattr(i, k) for k, _ in _ServerInfo._fields_}
+
+    def close(self):
+        if self._h:
+            load().hb_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def strerror(status: int) -> str:

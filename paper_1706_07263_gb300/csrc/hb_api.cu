@@ -173,6 +173,22 @@ hb_status ensure_rec(hb_ctx* c, long npix) {
     return HB_OK;
 }
 
+}  // namespace
+
+namespace hb {
+// The FP64 preparation of the operator and grid constants for code outside a context.
+void prepare_constants(const hb_mixing* mix, const hb_grid* grid, double lambda, unsigned flags, float M[6],
+                       BayesParams& bp) {
+    hb_ctx holder;
+    holder.flags = flags;
+    prepare(&holder, mix, grid, lambda);
+    for (int k = 0; k < 6; ++k) M[k] = holder.tp.M[k];
+    bp = holder.bp;
+}
+}  // namespace hb
+
+namespace {
+
 hb::PosteriorScratch post_scratch(const hb_ctx* c) { return hb::PosteriorScratch{c->d_partial, c->d_count, hb::kMaxParts}; }
 
 // Event bracket around one launch when timing is armed.

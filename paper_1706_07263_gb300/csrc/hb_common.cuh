@@ -61,6 +61,20 @@ struct PosteriorScratch {
 };
 constexpr int kMaxParts = 8;
 
+// One frame of a serving batch: its geometry, buffers, and where its tiles and low-pass
+// pixels sit in the batch-wide grid and arrays.
+struct FrameJob {
+    TransformParams tp;
+    const unsigned char* frame;
+    size_t stride;
+    float* thb;
+    float* so2;
+    long ll_offset;           // first low-pass pixel of this frame in the batch arrays
+    int tile_begin;           // first CTA of this frame in the batched grids
+    int tiles_x;              // tile columns (tiles = tiles_x * hl)
+};
+constexpr int kMaxBatchJobs = 64;
+
 // Launch wrappers (defined in the .cu files).  All return the launch status.
 cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
                             const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f = nullptr);
@@ -80,5 +94,11 @@ cudaError_t launch_posterior_check(const BayesParams& bp, const BayesRec* rec, l
 cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_t stride, const float2* lut,
                              const float2* chat, float* out0, float* out1, int debug_conc, bool pdl, cudaStream_t s);
 size_t transform_smem_bytes(const TransformParams& tp);
+// Serving batches: one launch per stage for all jobs (levels 0..4 per job).  jobs is a
+// device array of njobs entries; total_tiles = sum of tiles_x * hl.
+cudaError_t launch_batch_analysis(const BayesParams& bp, const FrameJob* jobs, int njobs, int total_tiles, int fmt,
+                                  const float2* lut, BayesRec* rec_all, cudaStream_t s);
+cudaError_t launch_batch_synthesis(const FrameJob* jobs, int njobs, int total_tiles, int fmt, const float2* lut,
+                                   const float2* chat_all, cudaStream_t s);
 
 }  // namespace hb

@@ -383,23 +383,20 @@ __device__ __forceinline__ void warp_load(const TransformParams& tp, const unsig
     }
 }
 
+// Analysis of one tile (tile column tx of superblock band by): block means of the
+// tile's superblocks and their posterior records.  sb_hi / sb_lo: kThreads x 3 floats of
+// shared memory.  Called by whole CTAs.
 template <int L>
-__global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams tp, BayesParams bp,
-                                                                 const unsigned char* __restrict__ frame,
-                                                                 size_t stride, const float2* __restrict__ lut_g,
-                                                                 double* __restrict__ ybar,
-                                                                 BayesRec* __restrict__ rec,
-                                                                 float* __restrict__ ybar_f) {
+__device__ __forceinline__ void analysis_tile(const TransformParams& tp, const BayesParams& bp,
+                                              const unsigned char* __restrict__ frame, size_t stride,
+                                              const float2* lut, int tx, int by, double* __restrict__ ybar,
+                                              BayesRec* __restrict__ rec, float* __restrict__ ybar_f,
+                                              float (*sb_hi)[3], float (*sb_lo)[3]) {
     constexpr int TH = 1 << L;
-    constexpr int NSB = kThreads / TH;  // superblocks per CTA (kThreads columns)
-    __shared__ float2 lut[256];
-    __shared__ float sb_hi[NSB][3], sb_lo[NSB][3];
-    if (tp.fmt == 1)
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = lut_g[i];
-    __syncthreads();
+    constexpr int NSB = kThreads / TH;  // superblocks per tile (kThreads columns)
     const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32;
-    const int x = x0 + lane, by = blockIdx.y;
+    const int x0 = (tx * (kThreads / 32) + (threadIdx.x >> 5)) * 32;
+    const int x = x0 + lane;
     if (x0 < tp.wl * TH) {  // whole warps right of the padded frame skip the transform
         float v[3][TH];
         float2 yref[3];
@@ -417,7 +414,7 @@ __global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams
     __syncthreads();
     // one superblock per thread for the posterior set-up, so whole warps do it together
     for (int t = threadIdx.x; t < NSB; t += blockDim.x) {
-        const int gx = (blockIdx.x * kThreads) / TH + t;
+        const int gx = (tx * kThreads) / TH + t;
         if (gx >= tp.wl) continue;
         float yhi[3], ylo[3];
 #pragma unroll
@@ -436,26 +433,42 @@ __global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams
         }
         rec[o] = bayes_setup(yhi, ylo, bp);
     }
+}
+
+__device__ __forceinline__ void load_lut(const TransformParams& tp, const float2* __restrict__ lut_g, float2* lut) {
+    if (tp.fmt == 1)
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = lut_g[i];
+    __syncthreads();
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams tp, BayesParams bp,
+                                                                 const unsigned char* __restrict__ frame,
+                                                                 size_t stride, const float2* __restrict__ lut_g,
+                                                                 double* __restrict__ ybar,
+                                                                 BayesRec* __restrict__ rec,
+                                                                 float* __restrict__ ybar_f) {
+    __shared__ float2 lut[256];
+    __shared__ float sb_hi[kThreads][3], sb_lo[kThreads][3];
+    load_lut(tp, lut_g, lut);
+    analysis_tile<L>(tp, bp, frame, stride, lut, blockIdx.x, blockIdx.y, ybar, rec, ybar_f, sb_hi, sb_lo);
     // the posterior kernel may be scheduled now; it waits for this grid before reading rec
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
+// Synthesis of one tile: analysis, Tikhonov operator on the directional coefficients,
+// inverse transform, THb and SO2 (or HbO2 and Hb when debug_conc).  Whole warps return
+// early, so it must be called last in a kernel.
 template <int L>
-__global__ void __launch_bounds__(kThreads) synthesis_warp_kernel(TransformParams tp,
-                                                                  const unsigned char* __restrict__ frame,
-                                                                  size_t stride, const float2* __restrict__ lut_g,
-                                                                  const float2* __restrict__ chat,
-                                                                  float* __restrict__ out0, float* __restrict__ out1,
-                                                                  int debug_conc) {
+__device__ __forceinline__ void synthesis_tile(const TransformParams& tp, const unsigned char* __restrict__ frame,
+                                               size_t stride, const float2* lut, const float2* __restrict__ chat,
+                                               float* __restrict__ out0, float* __restrict__ out1, int debug_conc,
+                                               int tx, int by) {
     constexpr int TH = 1 << L;
-    __shared__ float2 lut[256];
-    if (tp.fmt == 1)
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = lut_g[i];
-    __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32;
+    const int x0 = (tx * (kThreads / 32) + (threadIdx.x >> 5)) * 32;
     if (x0 >= tp.wl * TH) return;
-    const int x = x0 + lane, by = blockIdx.y;
+    const int x = x0 + lane;
     float v[3][TH];
     float2 yref[3];
     warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
@@ -503,6 +516,19 @@ __global__ void __launch_bounds__(kThreads) synthesis_warp_kernel(TransformParam
             out1[o] = thb >= 1.17549435e-38f ? __fdividef(hbo2, thb) : (thb > 0.f ? hbo2 / thb : 0.f);
         }
     }
+}
+
+
+template <int L>
+__global__ void __launch_bounds__(kThreads) synthesis_warp_kernel(TransformParams tp,
+                                                                  const unsigned char* __restrict__ frame,
+                                                                  size_t stride, const float2* __restrict__ lut_g,
+                                                                  const float2* __restrict__ chat,
+                                                                  float* __restrict__ out0, float* __restrict__ out1,
+                                                                  int debug_conc) {
+    __shared__ float2 lut[256];
+    load_lut(tp, lut_g, lut);
+    synthesis_tile<L>(tp, frame, stride, lut, chat, out0, out1, debug_conc, blockIdx.x, blockIdx.y);
 }
 
 template <typename K>
@@ -589,6 +615,80 @@ cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_
     cudaError_t e = set_smem(synthesis_kernel, sm);
     if (e != cudaSuccess) return e;
     return launch_maybe_pdl(synthesis_kernel, tile_grid(tp), sm, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
+}
+
+// ------------------------------------------------------------------------------------
+// Serving batches: every CTA finds its frame in the job table (jobs sorted by
+// tile_begin) and runs the single-frame tile body for that frame's level count, so
+// frames of different sizes and levels share one launch per stage.
+// ------------------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ int find_job(const FrameJob* jobs, int njobs, int block) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {  // last job with tile_begin <= block
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile_begin <= block) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) batch_analysis_kernel(BayesParams bp, const FrameJob* __restrict__ jobs,
+                                                                  int njobs, int fmt, const float2* __restrict__ lut_g,
+                                                                  BayesRec* __restrict__ rec_all) {
+    __shared__ float2 lut[256];
+    __shared__ float sb_hi[kThreads][3], sb_lo[kThreads][3];
+    if (fmt == 1)
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = lut_g[i];
+    __syncthreads();
+    const FrameJob& job = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int local = blockIdx.x - job.tile_begin;
+    const int by = local / job.tiles_x, tx = local - by * job.tiles_x;
+    BayesRec* rec = rec_all + job.ll_offset;
+    switch (job.tp.levels) {
+        case 0: analysis_tile<0>(job.tp, bp, job.frame, job.stride, lut, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+        case 1: analysis_tile<1>(job.tp, bp, job.frame, job.stride, lut, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+        case 2: analysis_tile<2>(job.tp, bp, job.frame, job.stride, lut, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+        case 3: analysis_tile<3>(job.tp, bp, job.frame, job.stride, lut, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+        default: analysis_tile<4>(job.tp, bp, job.frame, job.stride, lut, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) batch_synthesis_kernel(const FrameJob* __restrict__ jobs, int njobs, int fmt,
+                                                                   const float2* __restrict__ lut_g,
+                                                                   const float2* __restrict__ chat_all) {
+    __shared__ float2 lut[256];
+    if (fmt == 1)
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = lut_g[i];
+    __syncthreads();
+    const FrameJob& job = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int local = blockIdx.x - job.tile_begin;
+    const int by = local / job.tiles_x, tx = local - by * job.tiles_x;
+    const float2* chat = chat_all + job.ll_offset;
+    switch (job.tp.levels) {
+        case 0: synthesis_tile<0>(job.tp, job.frame, job.stride, lut, chat, job.thb, job.so2, 0, tx, by); break;
+        case 1: synthesis_tile<1>(job.tp, job.frame, job.stride, lut, chat, job.thb, job.so2, 0, tx, by); break;
+        case 2: synthesis_tile<2>(job.tp, job.frame, job.stride, lut, chat, job.thb, job.so2, 0, tx, by); break;
+        case 3: synthesis_tile<3>(job.tp, job.frame, job.stride, lut, chat, job.thb, job.so2, 0, tx, by); break;
+        default: synthesis_tile<4>(job.tp, job.frame, job.stride, lut, chat, job.thb, job.so2, 0, tx, by); break;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_batch_analysis(const BayesParams& bp, const FrameJob* jobs, int njobs, int total_tiles, int fmt,
+                                  const float2* lut, BayesRec* rec_all, cudaStream_t s) {
+    if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
+    batch_analysis_kernel<<<total_tiles, kThreads, 0, s>>>(bp, jobs, njobs, fmt, lut, rec_all);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_synthesis(const FrameJob* jobs, int njobs, int total_tiles, int fmt, const float2* lut,
+                                   const float2* chat_all, cudaStream_t s) {
+    if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
+    batch_synthesis_kernel<<<total_tiles, kThreads, 0, s>>>(jobs, njobs, fmt, lut, chat_all);
+    return cudaGetLastError();
 }
 
 }  // namespace hb

@@ -48,6 +48,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded CPU-oracle sample length")
+    ap.add_argument("--quick", action="store_true", help="headline only: no stand-in, serving or stereo runs")
+    ap.add_argument("--mlp-frames", type=int, default=62, help="generator frames for the stand-in's training pairs")
+    ap.add_argument("--mlp-eval-frames", type=int, default=8)
+    ap.add_argument("--mlp-tol", type=float, default=1e-3)
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--stereo-frames", type=int, default=300)
+    ap.add_argument("--stereo-pool", type=int, default=6)
     return ap.parse_args()
 
 
@@ -123,8 +130,10 @@ def make_inputs(rank: int):
     return wl, mix, fr
 
 
-def cpu_oracle_sample(budget_s: float):
-    """Time the FP64 oracle (as it stands) on whole frames of the workload, all host cores."""
+def cpu_oracle_sample(budget_s: float, keep=None):
+    """Time the FP64 oracle (as it stands) on whole frames of the workload, all host cores.
+    If `keep` is a dict, the oracle's THb/SO2 of the timed frame are stored in it: the
+    parity figures of the JSON line compare the GPU outputs with them."""
     import oracle
     from paper_1706_07263_gb300 import synth
     wl, mix, fr = make_inputs(0)
@@ -133,14 +142,272 @@ def cpu_oracle_sample(budget_s: float):
     oracle.build()
     frames, t0 = 0, time.perf_counter()
     while True:
-        oracle.estimate(fr.rgb, mix.A, grid, wl.levels, wl.lam, nthreads=cores)
+        out = oracle.estimate(fr.rgb, mix.A, grid, wl.levels, wl.lam, nthreads=cores)
         frames += 1
         el = time.perf_counter() - t0
         if el >= budget_s or frames >= 50:
             break
+    if keep is not None:
+        keep["thb"], keep["so2"] = out["thb"], out["so2"]
     return {"value": frames / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{frames} whole {wl.W}x{wl.H} u8 frame(s) in {el:.1f} s, FP64 C oracle, "
                       f"{cores} threads over low-pass pixels"}
+
+
+def errors(thb, so2, ref_thb, ref_so2):
+    """THb: max and median of |d| / max(|ref|, 1 uM); SO2: max |d| where ref THb >= 1 uM."""
+    thb = np.asarray(thb, np.float64)
+    rel = np.abs(thb - ref_thb) / np.maximum(np.abs(ref_thb), 1.0)
+    mask = ref_thb >= 1.0
+    d = np.abs(np.asarray(so2, np.float64) - ref_so2)[mask]
+    return {"thb_max_rel": float(rel.max()), "thb_median_rel": float(np.median(rel)),
+            "so2_max_abs": float(d.max()) if d.size else 0.0, "so2_median_abs": float(np.median(d)) if d.size else 0.0}
+
+
+def quantiles(v):
+    v = np.sort(np.asarray(v, np.float64))
+    if v.size == 0:
+        return {"p50": None, "p99": None, "max": None}
+    return {"p50": float(v[v.size // 2]), "p99": float(v[min(v.size - 1, int(round(0.99 * (v.size - 1))))]),
+            "max": float(v[-1])}
+
+
+def measure_small(args, dev):
+    """256x256 float frame, 1 level, 64x64 grid: per-frame latency of the plain path."""
+    import torch
+    from paper_1706_07263_gb300 import Context, synth
+    wl = synth.SMALL_256
+    mix, fr = synth.workload_inputs(wl)
+    frame = torch.from_numpy(fr.rgb).to(dev)
+    thb = torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev)
+    so2 = torch.empty_like(thb)
+    with Context(mix.A, synth.grid_spec(wl), wl.levels, wl.lam, wl.W, wl.H, wl.fmt) as ctx:
+        for _ in range(10):
+            ctx.estimate(frame, thb, so2)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(50)]
+        torch.cuda.synchronize(dev)
+        for a, b in ev:
+            a.record()
+            ctx.estimate(frame, thb, so2)
+            b.record()
+        torch.cuda.synchronize(dev)
+    lat = [a.elapsed_time(b) for a, b in ev]
+    return {"workload": wl.name, "latency_ms": quantiles(lat), "frames_per_s": 1e3 / float(np.mean(lat))}
+
+
+def measure_surrogate(args, dev, flush, oracle_out):
+    """Learned low-pass stand-in: trained on pairs from generator frames of the 1080p
+    workload, then timed on held-out frames against the plain path, with its errors."""
+    import torch
+    from paper_1706_07263_gb300 import Context, binding, surrogate, synth
+    wl = synth.HD_1080
+    mix = synth.make_mixing(wl.seed)
+    grid = synth.grid_spec(wl)
+    t0 = time.perf_counter()
+    frames = surrogate.workload_frames(wl, mix, args.mlp_frames, 100)
+    gen_s = time.perf_counter() - t0
+    ctx = Context(mix.A, grid, wl.levels, wl.lam, wl.W, wl.H, wl.fmt)
+    ys, cs = surrogate.training_pairs(ctx, frames, dev)
+    del frames
+    n = ys.shape[0]
+    ntr = int(0.9 * n)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    losses = surrogate.train_phases(ctx, ys[:ntr], cs[:ntr])
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    steps = len(losses)
+    out = torch.empty((n - ntr, 2), dtype=torch.float32, device=dev)
+    ctx.mlp_forward(ys[ntr:], out)
+    torch.cuda.synchronize(dev)
+    held = ((out - cs[ntr:]).abs().cpu().numpy() / np.array([grid["hi0"] - grid["lo0"], grid["hi1"] - grid["lo1"]]))
+    held = held.max(axis=1)
+    # held-out frames (generator seeds not used in training) + the bench frame (seed of the workload)
+    evals = [torch.from_numpy(synth.make_frame(5000 + k, wl.H, wl.W, mix.A, wl.nblobs, wl.smin, wl.smax,
+                                               wl.noise, wl.fmt).rgb).to(dev) for k in range(args.mlp_eval_frames)]
+    bench_fr = torch.from_numpy(make_inputs(0)[2].rgb).to(dev)
+    thb = torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev)
+    so2 = torch.empty_like(thb)
+
+    def timed(mode, tol):
+        ctx.set_lowpass_mode(mode, tol, 256)
+        for k in range(3):
+            ctx.estimate(evals[k % len(evals)], thb, so2)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        f0 = ctx.lowpass_stats()
+        for k, (a, b) in enumerate(ev):
+            flush.zero_()
+            a.record()
+            ctx.estimate(evals[k % len(evals)], thb, so2)
+            b.record()
+        torch.cuda.synchronize(dev)
+        f1 = ctx.lowpass_stats()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return 1e3 / float(np.mean(ms)), ms, (f1[0] - f0[0], f1[1] - f0[1])
+
+    plain_fps, _, _ = timed(binding.HB_MODE_BAYES, 0.0)
+    mlp_fps, mlp_ms, (mlp_frames, fallbacks) = timed(binding.HB_MODE_MLP, args.mlp_tol)
+    # errors on the bench frame: network path vs plain path vs oracle
+    res = {}
+    for mode in (binding.HB_MODE_BAYES, binding.HB_MODE_MLP):
+        ctx.set_lowpass_mode(mode, float("inf"), 256)
+        ctx.estimate(bench_fr, thb, so2)
+        torch.cuda.synchronize(dev)
+        res[mode] = (thb.cpu().numpy().copy(), so2.cpu().numpy().copy())
+    ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
+    ctx.close()
+    line = {"workload": f"{wl.name} stand-in, {n} pairs from {args.mlp_frames} generator frames",
+            "train": {"pairs": int(ntr), "steps": int(steps), "batch": 4096, "seconds": train_s,
+                      "final_loss": float(np.mean(losses[-100:])), "frame_generation_s": gen_s},
+            "held_out_error_rel_box": {"mean": float(held.mean()), "median": float(np.median(held)),
+                                       "p99": float(np.quantile(held, 0.99)), "max": float(held.max())},
+            "frames_per_s": mlp_fps, "plain_frames_per_s": plain_fps, "speedup_vs_plain": mlp_fps / plain_fps,
+            "latency_ms": quantiles(mlp_ms),
+            "fallback": {"tol_mean_sampled_error": args.mlp_tol, "frames": mlp_frames, "fell_back": fallbacks},
+            "vs_plain_path": errors(res[1][0], res[1][1], res[0][0].astype(np.float64), res[0][1].astype(np.float64))}
+    if oracle_out:
+        line["vs_oracle"] = errors(res[1][0], res[1][1], oracle_out["thb"], oracle_out["so2"])
+    return line
+
+
+def measure_serving(args, dev):
+    """Concurrent streams (4 x 640x480, 4 x 1280x720, 4 x 1920x1080; 2-4 levels each),
+    Poisson arrivals per stream with jitter, paced in real time; continuous batching
+    against sequential per-frame launches on the same arrival trace."""
+    import threading as th
+    from paper_1706_07263_gb300 import Server, synth
+    wl = synth.HD_1080
+    mix = synth.make_mixing(3)
+    grid = synth.grid_spec(wl)
+    sizes = [(640, 480)] * 4 + [(1280, 720)] * 4 + [(1920, 1080)] * 4
+    rng = np.random.default_rng(3)
+    levels = [int(v) for v in rng.choice([2, 3, 4], len(sizes))]
+    pool = [[synth.make_frame(300 + 7 * i + k, h, w, mix.A, 16, 10.0, 80.0, 0.01, "u8").rgb for k in range(2)]
+            for i, (w, h) in enumerate(sizes)]
+
+    def trace(rate_scale, horizon, seed):
+        r = np.random.default_rng(seed)
+        ev = []
+        for i in range(len(sizes)):
+            t = 0.0
+            while True:
+                t += r.exponential(1.0 / (30.0 * rate_scale))
+                if t >= horizon:
+                    break
+                ev.append((t + r.uniform(0, 0.002), i))
+        ev.sort()
+        return ev
+
+    def run(sequential, rate_scale, horizon):
+        events = trace(rate_scale, horizon, 11)
+        lat, done, dropped = [], [0], [0]
+        with Server(mix.A, grid, wl.lam, max_batch=1 if sequential else 16, batch_lowpass_pixels=2_000_000,
+                    sequential=sequential) as srv:
+            sids = [srv.open_stream(w, h, lv, slots=8) for (w, h), lv in zip(sizes, levels)]
+            stop = [False]
+
+            def poller():
+                while not stop[0] or done[0] < len(events) - dropped[0]:
+                    for r in srv.poll(128, wait_us=2000):
+                        lat.append(r["latency_ms"])
+                        srv.release(r["stream"], r["slot"])
+                        done[0] += 1
+                    if stop[0] and time.perf_counter() > deadline[0]:
+                        break
+
+            deadline = [float("inf")]
+            pt = th.Thread(target=poller, daemon=True)
+            pt.start()
+            t0 = time.perf_counter()
+            for k, (t, i) in enumerate(events):
+                dt = t0 + t - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                if not srv.submit(sids[i], pool[i][k & 1], k):
+                    dropped[0] += 1
+            stop[0] = True
+            deadline[0] = time.perf_counter() + 10.0
+            pt.join()
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        return {"offered_frames_per_s": len(events) / horizon, "frames": done[0], "dropped": dropped[0],
+                "frames_per_s": done[0] / wall, "latency_ms": quantiles(lat),
+                "mean_batch_frames": st["mean_batch_frames"], "max_batch_frames": st["max_batch_frames"]}
+
+    out = {"workload": "12 streams: 4x640x480, 4x1280x720, 4x1920x1080 u8, levels " + ",".join(map(str, levels)) +
+                       ", 128x128 grid, Poisson 30 Hz per stream (+U(0,2) ms jitter)",
+           "horizon_s": args.serve_seconds}
+    out["batched"] = run(False, 1.0, args.serve_seconds)
+    out["per_frame"] = run(True, 1.0, args.serve_seconds)
+    out["saturation"] = {}
+    for k in (4, 16):
+        out["saturation"][f"x{k}"] = {"batched": run(False, float(k), args.serve_seconds / 2),
+                                      "per_frame": run(True, float(k), args.serve_seconds / 2)}
+    return out
+
+
+def measure_stereo(args, dev):
+    """Stereo video: two 1920x1080 float streams; each frame copied host->device on a copy
+    stream while the previous frame is estimated on the compute stream."""
+    import torch
+    from paper_1706_07263_gb300 import Context, synth
+    wl = synth.HD_1080
+    mix = synth.make_mixing(2)
+    grid = synth.grid_spec(wl)
+    rng = np.random.default_rng(2)
+    pool = []
+    base = rng.integers(0, 1 << 30)
+    for eye in range(2):
+        for k in range(args.stereo_pool):
+            fr = synth.make_frame(int(base) + 100 * eye + k, wl.H, wl.W, mix.A, wl.nblobs, wl.smin, wl.smax, wl.noise,
+                                  "f32")
+            pool.append(torch.from_numpy(fr.rgb).pin_memory())
+    ctx = Context(mix.A, grid, wl.levels, wl.lam, wl.W, wl.H, "f32")
+    copy_s, comp_s = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    dbuf = [torch.empty((wl.H, wl.W, 3), dtype=torch.float32, device=dev) for _ in range(2)]
+    thb = [torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev) for _ in range(2)]
+    so2 = [torch.empty_like(t) for t in thb]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
+    for e in freed:
+        e.record(comp_s)
+    total = 2 * args.stereo_frames
+
+    def run(n):
+        for i in range(n):
+            b = i & 1
+            eye = i & 1
+            src = pool[eye * args.stereo_pool + (i // 2) % args.stereo_pool]
+            with torch.cuda.stream(copy_s):
+                copy_s.wait_event(freed[b])
+                dbuf[b].copy_(src, non_blocking=True)
+                copied[b].record(copy_s)
+            with torch.cuda.stream(comp_s):
+                comp_s.wait_event(copied[b])
+                ctx.estimate(dbuf[b], thb[eye], so2[eye], stream=comp_s)
+                freed[b].record(comp_s)
+
+    run(8)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    run(total)
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - t0
+    # per-pass HBM rates from per-kernel timing of a few frames
+    ctx.timing_start(64)
+    for k in range(8):
+        ctx.estimate(dbuf[k & 1], thb[0], so2[0])
+    torch.cuda.synchronize(dev)
+    st = ctx.timing_read()
+    ctx.close()
+    fbytes = wl.H * wl.W * 12
+    a_ms = st["analysis"][0] / max(st["analysis"][1], 1)
+    s_ms = st["synthesis"][0] / max(st["synthesis"][1], 1)
+    return {"workload": f"2 eyes x {args.stereo_frames} frames of 1920x1080 f32, 3 levels, 128x128 grid "
+                        f"({args.stereo_pool} distinct frames per eye cycled)",
+            "frames_per_s": total / el, "h2d_gb_per_s": total * fbytes / el / 1e9,
+            "analysis_pass_gb_per_s": fbytes / (a_ms * 1e-3) / 1e9,
+            "synthesis_pass_gb_per_s": (fbytes + wl.H * wl.W * 8) / (s_ms * 1e-3) / 1e9}
 
 
 def run_reference(args):
@@ -174,8 +441,9 @@ def run_ours(args):
 
     # CPU baseline first (rank 0, N = 1), before any process pool or GPU timing.
     cpu_base = None
+    oracle_out = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_base = cpu_oracle_sample(args.cpu_seconds)
+        cpu_base = cpu_oracle_sample(args.cpu_seconds, keep=oracle_out)
 
     wl, mix, fr = make_inputs(rank)
     grid = synth.grid_spec(wl)
@@ -276,7 +544,16 @@ def run_ours(args):
         "clocks": clk,
         "cpu_baseline": cpu_base,
     }
+    if oracle_out:
+        ctx.estimate(frame, thb, so2, stream=stream)
+        torch.cuda.synchronize(dev)
+        line["parity_vs_oracle"] = errors(thb.cpu().numpy(), so2.cpu().numpy(), oracle_out["thb"], oracle_out["so2"])
     ctx.close()
+    if rank == 0 and world == 1 and not args.quick:
+        line["small_256"] = measure_small(args, dev)
+        line["surrogate"] = measure_surrogate(args, dev, flush, oracle_out)
+        line["serving"] = measure_serving(args, dev)
+        line["stereo_stream"] = measure_stereo(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -35,9 +35,25 @@ import numpy as np  # noqa: E402
 
 METRIC = "1080p frames/s and p99 frame latency (THb+SO2) vs plain pipeline, same GB300, <=1e-4 rel err"
 UNIT = "frames/s"
+# DRAM traffic of one posterior launch on this workload from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/posterior_kernel_frame1080p_u8_l3_g128.md),
+# valid only while the kernel's sources hash to the value recorded with it.
+POSTERIOR_TRAFFIC = {"bytes": 563968, "sources_sha256_16": "d92a7b12ff4411c7",
+                     "sources": ("paper_1706_07263_gb300/csrc/hb_bayes.cu", "paper_1706_07263_gb300/csrc/hb_common.cuh",
+                                 "paper_1706_07263_gb300/csrc/hb_device.cuh")}
 SM_COUNT = 152
 EX2_PER_CLK_PER_SM = 32          # MUFU ex2 lanes per clock per SM on GB300
 SM_MAX_MHZ = 2070.0
+
+
+def posterior_traffic():
+    """Bytes per posterior launch, or None if the kernel changed since the capture."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in POSTERIOR_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return POSTERIOR_TRAFFIC["bytes"] if h.hexdigest()[:16] == POSTERIOR_TRAFFIC["sources_sha256_16"] else None
 
 
 def parse():
@@ -193,6 +209,36 @@ def measure_small(args, dev):
         torch.cuda.synchronize(dev)
     lat = [a.elapsed_time(b) for a, b in ev]
     return {"workload": wl.name, "latency_ms": quantiles(lat), "frames_per_s": 1e3 / float(np.mean(lat))}
+
+
+def measure_table1(args, dev, flush):
+    """The comparison of Table 1 on this GPU and the 1080p frame: the grid posterior on every
+    pixel, Tikhonov on every coefficient, and the proposed method at 1 and 3 levels."""
+    import torch
+    from paper_1706_07263_gb300 import Context, binding, synth
+    wl, mix, fr = make_inputs(0)
+    grid = synth.grid_spec(wl)
+    frame = torch.from_numpy(fr.rgb).to(dev)
+    thb = torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev)
+    so2 = torch.empty_like(thb)
+    rows = [("bayes_full_resolution", 0, 0, 5, 3.54), ("tikhonov_full_resolution", 1, binding.HB_LOWPASS_TIKHONOV, 50, 43.5),
+            ("proposed_w1", 1, 0, 20, 12.7), ("proposed_w3", 3, 0, 50, 14.4)]
+    out = {"frame": wl.name, "note": "paper_hz: the paper's CUDA timings on an unnamed GPU and ~1 MP frames, context only"}
+    for name, levels, flags, steps, paper_hz in rows:
+        with Context(mix.A, grid, levels, wl.lam, wl.W, wl.H, wl.fmt, flags) as ctx:
+            for _ in range(2):
+                ctx.estimate(frame, thb, so2)
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ctx.estimate(frame, thb, so2)
+                b.record()
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        out[name] = {"levels": levels, "frames_per_s": 1e3 / float(np.mean(ms)), "paper_hz": paper_hz}
+    return out
 
 
 def measure_surrogate(args, dev, flush, oracle_out):
@@ -430,7 +476,7 @@ def run_reference(args):
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_1706_07263_gb300 import Context, build, synth
+    from paper_1706_07263_gb300 import Context, build, replicas, synth
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -488,13 +534,9 @@ def run_ours(args):
         stage = ctx.timing_read()
         clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, frames_all = replicas.aggregate(sum(step_ms), args.steps, device=dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms * 1e-3)
+    value = frames_all / (total_ms * 1e-3)
 
     # end to end through the host entry point: pinned frame in, pinned THb/SO2 out
     host_frame = torch.from_numpy(fr.rgb).pin_memory()
@@ -507,11 +549,7 @@ def run_ours(args):
     for _ in range(args.steps):
         ctx.estimate_host(host_frame.numpy(), host_thb, host_so2, stream=stream)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s, e2e_frames = replicas.aggregate(time.perf_counter() - t0, args.steps, device=dev)
 
     # roofline of the dominant kernel (grid posterior): one ex2 per grid node
     post_ms, post_n = stage["lowpass"]
@@ -535,10 +573,10 @@ def run_ours(args):
         "stages": stages,
         "roofline": {"bound": "alu", "kernel": "posterior (grid posterior mean, one MUFU ex2 per grid node)",
                      "achieved": achieved, "peak": peak, "unit": "Texp/s", "frac": achieved / peak,
-                     "traffic": None,
+                     "traffic": posterior_traffic(),
                      "timing": "CUDA events around each posterior launch, K more steps after the timed region",
                      "peak_note": "152 SMs x 32 ex2/clk/SM x 2070 MHz (unit count measured by probe)"},
-        "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W * 3,
+        "e2e": {"value": e2e_frames / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W * 3,
                 "d2h_bytes_per_step": 2 * H * W * 4},
         "gpu_launches": launches,
         "clocks": clk,
@@ -551,6 +589,7 @@ def run_ours(args):
     ctx.close()
     if rank == 0 and world == 1 and not args.quick:
         line["small_256"] = measure_small(args, dev)
+        line["table1_analogue"] = measure_table1(args, dev, flush)
         line["surrogate"] = measure_surrogate(args, dev, flush, oracle_out)
         line["serving"] = measure_serving(args, dev)
         line["stereo_stream"] = measure_stereo(args, dev)

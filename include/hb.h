@@ -77,11 +77,13 @@ enum {
 enum {
     HB_LAMBDA_ABSOLUTE = 1u << 0,  /* gamma = lambda; default gamma = lambda * trace(A^T A) / 2 */
     HB_LOWPASS_TIKHONOV = 1u << 1, /* low pass through M as well (the all-Tikhonov comparison) */
-    HB_FUSED = 1u << 3             /* one fused kernel per frame instead of three */
+    HB_FULL_GRID = 1u << 2         /* posterior enumerates every grid node; by default the rows whose
+                                      every weight is exactly zero in FP32 (below 2^-150 relative to
+                                      the reference node) are skipped, which leaves the sums unchanged */
 };
 
 /* Per-stage timing slots reported by hb_timing_read. */
-enum { HB_STAGE_ANALYSIS = 0, HB_STAGE_LOWPASS = 1, HB_STAGE_SYNTHESIS = 2, HB_STAGE_FUSED = 3, HB_NUM_STAGES = 4 };
+enum { HB_STAGE_ANALYSIS = 0, HB_STAGE_LOWPASS = 1, HB_STAGE_SYNTHESIS = 2, HB_NUM_STAGES = 3 };
 
 /* Create a context for frames of width x height pixels.
  *   mix, grid  : copied; grid must have n0, n1 >= 1, hi >= lo, sigma_l > 0.
@@ -135,11 +137,15 @@ hb_status hb_lowpass_shape(const hb_ctx *ctx, int *hl, int *wl);
 long hb_launch_count(const hb_ctx *ctx);
 
 /* Optional per-stage timing with CUDA events recorded on the launch stream.
- * hb_timing_start(ctx, max_launches) arms up to max_launches event pairs;
- * hb_timing_read synchronises them and writes, per stage (HB_STAGE_*), the summed
- * milliseconds and the number of timed launches, then disarms. */
+ * hb_timing_start(ctx, max_launches) arms up to max_launches event pairs and zeroes the
+ * node counter; hb_timing_read synchronises them and writes, per stage (HB_STAGE_*), the
+ * summed milliseconds and the number of timed launches, then disarms.
+ * hb_timing_nodes (while armed, before hb_timing_read) synchronises the device and writes
+ * the number of grid nodes the posterior launches since hb_timing_start enumerated
+ * (rows x n1 per pixel; see HB_FULL_GRID), the work the posterior's roofline counts. */
 hb_status hb_timing_start(hb_ctx *ctx, int max_launches);
 hb_status hb_timing_read(hb_ctx *ctx, double ms[HB_NUM_STAGES], long launches[HB_NUM_STAGES]);
+hb_status hb_timing_nodes(hb_ctx *ctx, unsigned long long *nodes);
 
 /* Static description of a status code. */
 const char *hb_strerror(hb_status s);
@@ -231,7 +237,7 @@ typedef struct {
 
 enum { HB_SERVE_SEQUENTIAL = 1u << 4 }; /* one frame at a time, one batch in flight (baseline) */
 
-/* Create a server.  flags: HB_LAMBDA_ABSOLUTE, HB_SERVE_SEQUENTIAL.  budget_bytes bounds
+/* Create a server.  flags: HB_LAMBDA_ABSOLUTE, HB_FULL_GRID, HB_SERVE_SEQUENTIAL.  budget_bytes bounds
  * the device memory of all stream slots plus the two batches' scratch (sized for
  * batch_lowpass_pixels low-pass pixels each); max_batch (1..64) bounds frames per batch.
  * HB_ERR_BUDGET if the scratch alone exceeds the budget.  Starts the request loop. */

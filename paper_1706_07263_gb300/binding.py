@@ -19,19 +19,19 @@ HB_IN_F32_HWC = 0
 HB_IN_U8_HWC = 1
 HB_LAMBDA_ABSOLUTE = 1 << 0
 HB_LOWPASS_TIKHONOV = 1 << 1
-HB_FUSED = 1 << 3
-STAGES = ("analysis", "lowpass", "synthesis", "fused")
+STAGES = ("analysis", "lowpass", "synthesis")
 
 STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_SHAPE", 3: "HB_ERR_CUDA", 4: "HB_ERR_OOM", 5: "HB_ERR_BUDGET",
           6: "HB_ERR_TIMEOUT", 7: "HB_ERR_STATE"}
 
 # Every symbol include/hb.h declares (checked by the CPU tests against the built library).
 EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_estimate_debug", "hb_posterior_mean",
-            "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_strerror",
+            "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_timing_nodes", "hb_strerror",
             "hb_mlp_init", "hb_mlp_set_params", "hb_mlp_get_params", "hb_lowpass_pairs", "hb_mlp_train",
             "hb_mlp_gradient", "hb_mlp_forward", "hb_set_lowpass_mode", "hb_lowpass_stats",
             "hb_server_create", "hb_server_destroy", "hb_stream_open", "hb_stream_close", "hb_submit", "hb_poll",
             "hb_release", "hb_server_pause", "hb_server_stats", "hb_posterior_mean_static")
+HB_FULL_GRID = 1 << 2
 HB_SERVE_SEQUENTIAL = 1 << 4
 MLP_NPARAMS = 4546
 HB_MODE_BAYES = 0
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
     lib.hb_launch_count.restype = L
     lib.hb_timing_start.argtypes = [P, I]
     lib.hb_timing_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(L)]
+    lib.hb_timing_nodes.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong)]
     lib.hb_strerror.argtypes = [I]
     lib.hb_strerror.restype = ctypes.c_char_p
     lib.hb_posterior_mean_static.argtypes = [ctypes.POINTER(_Mixing), ctypes.POINTER(_Grid), P, L, P, P]
@@ -268,11 +269,17 @@ class Context:
     def timing_start(self, max_launches: int):
         _check(load().hb_timing_start(self._h, max_launches), "hb_timing_start")
 
+    def timing_nodes(self) -> int:
+        """Grid nodes the posterior enumerated since timing_start (synchronises the device)."""
+        v = ctypes.c_ulonglong(0)
+        _check(load().hb_timing_nodes(self._h, ctypes.byref(v)), "hb_timing_nodes")
+        return int(v.value)
+
     def timing_read(self) -> dict:
-        ms = (ctypes.c_double * 4)()
-        n = (ctypes.c_long * 4)()
+        ms = (ctypes.c_double * len(STAGES))()
+        n = (ctypes.c_long * len(STAGES))()
         _check(load().hb_timing_read(self._h, ms, n), "hb_timing_read")
-        return {STAGES[k]: (ms[k], n[k]) for k in range(4)}
+        return {STAGES[k]: (ms[k], n[k]) for k in range(len(STAGES))}
 
 
 def _structs(A, grid):

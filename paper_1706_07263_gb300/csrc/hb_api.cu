@@ -53,7 +53,10 @@ struct hb_ctx {
     float mlp_tol = 1e-3f;
     int mlp_nsample = 256;
     float* d_ybar_f = nullptr;    // block means for the network (npix_ll x 3)
-    unsigned* d_flags = nullptr;  // [0] summed sampled error (float bits), [1] fallback count
+    unsigned* d_flags = nullptr;  // [0] check arrivals, [1] fallback count, [2] run the exact posterior
+    float* d_err = nullptr;       // per sampled pixel error of the stand-in (mlp_err_cap)
+    int mlp_err_cap = 0;
+    unsigned long long* d_nodes = nullptr;  // grid nodes enumerated by timed posterior launches
     long mlp_frames = 0;
     unsigned frame_seq = 0;
     // per-stage timing
@@ -139,6 +142,32 @@ void prepare(hb_ctx* c, const hb_mixing* mix, const hb_grid* g, double lambda) {
     bp.inv_h1f = bp.h1 > 0 ? (float)(1.0 / bp.h1) : 0.f;
     bp.inv_G00 = G[0][0] > 0 ? (float)(1.0 / G[0][0]) : 0.f;
     bp.inv_G11 = G[1][1] > 0 ? (float)(1.0 / G[1][1]) : 0.f;
+    // rows of the grid that can hold a non-zero FP32 weight (see BayesParams::sup_rows)
+    {
+        const double aq = -kappa * bp.h0 * bp.h0 * a0a0, bq = -kappa * bp.h0 * bp.h1 * a0a1,
+                     cq = -kappa * bp.h1 * bp.h1 * a1a1;
+        double alpha = 0.0, rr = 0.0, cc = 0.0;
+        if (cq < 0.0) {
+            alpha = -(aq - bq * bq / cq);
+            rr = bq / cq;
+            cc = -1.0 / (4.0 * cq);
+        } else if (bq == 0.0) {  // a single grid column: t = Aq di^2 + U di
+            alpha = -aq;
+        }
+        const double mg = std::fabs(aq) * g->n0 * g->n0 + 2.0 * std::fabs(bq) * g->n0 * g->n1 +
+                          std::fabs(cq) * g->n1 * g->n1;
+        bp.sup_rows = (!(c->flags & HB_FULL_GRID) && g->n0 > 1 && alpha > 0.0 && std::isfinite(alpha) &&
+                       std::isfinite(rr) && std::isfinite(cc) && std::isfinite(mg) && mg < 1e30)
+                          ? 1
+                          : 0;
+        bp.sup_alpha = (float)alpha;
+        bp.sup_r = (float)rr;
+        bp.sup_c = (float)cc;
+        bp.sup_mg = (float)mg;
+        bp.sup_inv_alpha = alpha > 0.0 ? (float)(-0.5 / alpha) : 0.f;
+        bp.sup_inv_aq = aq < 0.0 ? (float)(0.5 / aq) : 0.f;
+        bp.sup_inv_k1 = (cq < 0.0 && aq < 0.0 && rr != 0.0 && std::isfinite(1.0 / rr)) ? (float)(-1.0 / rr) : 0.f;
+    }
     auto split = [](double v, float& hi, float& lo) {
         hi = (float)v;
         lo = (float)(v - (double)hi);
@@ -189,7 +218,9 @@ void prepare_constants(const hb_mixing* mix, const hb_grid* grid, double lambda,
 
 namespace {
 
-hb::PosteriorScratch post_scratch(const hb_ctx* c) { return hb::PosteriorScratch{c->d_partial, c->d_count, hb::kMaxParts}; }
+hb::PosteriorScratch post_scratch(const hb_ctx* c) {
+    return hb::PosteriorScratch{c->d_partial, c->d_count, hb::kMaxParts, c->timing ? c->d_nodes : nullptr};
+}
 
 // Event bracket around one launch when timing is armed.
 struct StageTimer {
@@ -238,18 +269,17 @@ hb_status run_frame(hb_ctx* c, const void* frame, size_t stride, double* ybar, f
         StageTimer t(c, s, HB_STAGE_LOWPASS);
         const float scale = (float)(1 << c->levels);
         if (mlp) {
-            // network estimate, sampled exact check, exact recomputation only if the check failed
-            float* err_sum = reinterpret_cast<float*>(c->d_flags);
+            // network estimate, sampled exact check, exact recomputation only if the check
+            // failed; each kernel waits for its predecessor in-kernel (PDL)
             e = hb::launch_mlp_forward(c->d_mlp + 3 * hb::kNParams, c->mlp_norm, c->d_ybar_f, c->npix_ll, c->d_chat,
-                                       c->d_flags, s);
+                                       pdl, s);
             if (e == cudaSuccess)
                 e = hb::launch_posterior_check(c->bp, c->d_rec, c->npix_ll, c->mlp_nsample, c->frame_seq++,
-                                               c->d_chat, 1.f / c->mlp_ext0, 1.f / c->mlp_ext1, err_sum, s);
-            // mean sampled error > tol  <=>  sum > tol * nsample
-            const float thr = c->mlp_tol * (float)c->mlp_nsample;
+                                               c->d_chat, 1.f / c->mlp_ext0, 1.f / c->mlp_ext1, c->d_err, c->mlp_tol,
+                                               c->d_flags, pdl, s);
             if (e == cudaSuccess)
-                e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, nullptr, scale,
-                                         false, s, hb::PosteriorGate{err_sum, thr, c->d_flags + 1});
+                e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, nullptr, scale, pdl,
+                                         s, hb::PosteriorGate{c->d_flags + 2});
             c->launches += 3;
             c->mlp_frames++;
         } else {
@@ -261,8 +291,7 @@ hb_status run_frame(hb_ctx* c, const void* frame, size_t stride, double* ybar, f
     if (e != cudaSuccess) return HB_ERR_CUDA;
     if (out0 || out1) {
         StageTimer t(c, s, HB_STAGE_SYNTHESIS);
-        e = hb::launch_synthesis(c->tp, frame, stride, c->d_lut, c->d_chat, out0, out1, debug, bayes && !mlp && pdl,
-                                 s);
+        e = hb::launch_synthesis(c->tp, frame, stride, c->d_lut, c->d_chat, out0, out1, debug, bayes && pdl, s);
         c->launches++;
     }
     return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
@@ -278,7 +307,7 @@ hb_status hb_create(const hb_mixing* mix, const hb_grid* grid, int levels, doubl
     *out = nullptr;
     if (!mix || !grid) return HB_ERR_ARG;
     if (in_format != HB_IN_F32_HWC && in_format != HB_IN_U8_HWC) return HB_ERR_ARG;
-    if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_LOWPASS_TIKHONOV | HB_FUSED)) return HB_ERR_ARG;
+    if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_LOWPASS_TIKHONOV | HB_FULL_GRID)) return HB_ERR_ARG;
     if (width <= 0 || height <= 0 || levels < 0 || levels > hb::kMaxLevels) return HB_ERR_SHAPE;
     if (grid->n0 < 1 || grid->n1 < 1 || !(grid->hi0 >= grid->lo0) || !(grid->hi1 >= grid->lo1) ||
         !(grid->sigma_l > 0.0))
@@ -357,6 +386,8 @@ void hb_destroy(hb_ctx* c) {
     cudaFree(c->d_mlp_loss);
     cudaFree(c->d_ybar_f);
     cudaFree(c->d_flags);
+    cudaFree(c->d_err);
+    cudaFree(c->d_nodes);
     cudaFree(c->d_frame);
     cudaFree(c->d_thb);
     cudaFree(c->d_so2);
@@ -461,8 +492,24 @@ hb_status hb_timing_start(hb_ctx* c, int max_launches) {
         c->ev.push_back(e);
     }
     c->ev_stage.assign(c->ev.size() / 2, -1);
+    if (!c->d_nodes && cudaMalloc(&c->d_nodes, sizeof(unsigned long long)) != cudaSuccess) {
+        c->d_nodes = nullptr;
+        cudaGetLastError();
+        return HB_ERR_OOM;
+    }
+    if (cudaMemset(c->d_nodes, 0, sizeof(unsigned long long)) != cudaSuccess) return HB_ERR_CUDA;
     c->ev_used = 0;
     c->timing = true;
+    return HB_OK;
+}
+
+hb_status hb_timing_nodes(hb_ctx* c, unsigned long long* nodes) {
+    if (!c || !nodes) return HB_ERR_ARG;
+    if (!c->timing || !c->d_nodes) return HB_ERR_STATE;
+    DeviceGuard g(c->device);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(nodes, c->d_nodes, sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HB_ERR_CUDA;
     return HB_OK;
 }
 
@@ -523,12 +570,12 @@ hb_status ensure_mlp(hb_ctx* c) {
         cudaMalloc(&c->d_mlp_gpart, sizeof(float) * kMlpMaxBlocks * np) != cudaSuccess ||
         cudaMalloc(&c->d_mlp_lpart, sizeof(float) * kMlpMaxBlocks) != cudaSuccess ||
         cudaMalloc(&c->d_ybar_f, sizeof(float) * 3 * c->npix_ll) != cudaSuccess ||
-        cudaMalloc(&c->d_flags, sizeof(unsigned) * 2) != cudaSuccess) {
+        cudaMalloc(&c->d_flags, sizeof(unsigned) * 4) != cudaSuccess) {
         cudaGetLastError();
         return HB_ERR_OOM;
     }
     if (cudaMemset(c->d_mlp, 0, sizeof(float) * 5 * np) != cudaSuccess ||
-        cudaMemset(c->d_flags, 0, sizeof(unsigned) * 2) != cudaSuccess)
+        cudaMemset(c->d_flags, 0, sizeof(unsigned) * 4) != cudaSuccess)
         return HB_ERR_CUDA;
     // least-squares baseline, input transform and output scale (FP64 here)
     const double* A = c->bp.A;
@@ -709,7 +756,7 @@ hb_status hb_mlp_forward(hb_ctx* c, const float* ybar_dev, long n, float* conc_d
     if (n == 0) return HB_OK;
     DeviceGuard g(c->device);
     cudaError_t e = hb::launch_mlp_forward(c->d_mlp + 3 * hb::kNParams, c->mlp_norm, ybar_dev, n,
-                                           reinterpret_cast<float2*>(conc_dev), nullptr,
+                                           reinterpret_cast<float2*>(conc_dev), false,
                                            static_cast<cudaStream_t>(stream));
     c->launches++;
     return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
@@ -722,6 +769,17 @@ hb_status hb_set_lowpass_mode(hb_ctx* c, int mode, double tol, int nsample) {
         if (!(tol >= 0.0) || nsample < 1) return HB_ERR_ARG;
         if (!c->mlp_ready) return HB_ERR_STATE;
         if (c->flags & HB_LOWPASS_TIKHONOV) return HB_ERR_STATE;
+        if (nsample > c->mlp_err_cap) {
+            DeviceGuard g(c->device);
+            cudaFree(c->d_err);
+            c->d_err = nullptr;
+            c->mlp_err_cap = 0;
+            if (cudaMalloc(&c->d_err, sizeof(float) * nsample) != cudaSuccess) {
+                cudaGetLastError();
+                return HB_ERR_OOM;
+            }
+            c->mlp_err_cap = nsample;
+        }
         c->mlp_tol = (float)tol;
         c->mlp_nsample = nsample;
     }

@@ -1,38 +1,19 @@
 // hb_bayes.cu -- posterior mean of (HbO2, Hb) over the concentration grid for every
-// low-pass pixel (the Bayesian estimate on the low-pass band, Section 2).
+// low-pass pixel (the Bayesian estimate on the low-pass band, Section 2); the per-pixel
+// sums are in hb_posterior.cuh.
 //
-// For a pixel with block-mean log-attenuation ybar the posterior over grid node k is
-// proportional to exp(-|ybar - A c_k|^2 / (2 sigma^2)) (flat prior).  Expanded around
-// a reference node c_ref = (i0, j0) with residual r0 = ybar - A c_ref, the base-2 log
-// weight of node (i0 + di, j0 + dj) relative to the reference is
-//
-//     t = U di + V dj + Aq di^2 + 2 Bq di dj + Cq dj^2
-//       = di * (Aq di + Q_j) + P_j,     Q_j = U + 2 Bq dj,  P_j = V dj + Cq dj^2,
-//
-// i.e. the -(|r0|^2 - 2 r0.A delta + |A delta|^2) expansion with the per-pixel terms
-// (U, V from r0) and the per-grid terms (Aq, Bq, Cq from |A delta|^2) separated.  The
-// weight is 2^t (MUFU ex2).  The reference node is the node nearest the likelihood's
-// maximiser over the grid's hull, so its weight is exactly 1 and no node's weight can
-// overflow; a pixel whose sums still come out non-finite (only possible for inputs far
-// outside the model) is recomputed with an explicit maximum pass.
-//
-// Work split: a unit is (pixel, part); lane l of a warp takes grid columns l, l+32,
-// l+64, ... and the rs parts of a pixel take contiguous row ranges (rs = 1 unless there
-// are fewer pixels than resident warps: a split costs partial sums and an atomic
-// hand-off).  Warps are persistent (one grid of resident CTAs walks all units) and
-// prefetch the next unit's record.  Per pair of grid nodes a lane issues two packed
-// FP32x2 FMAs for the exponents, two MUFU ex2 and two packed instructions for the sums
-// (sum w and sum w*di per column; sum w*dj follows from the column sums).  Warp shuffles
-// combine lanes; when a pixel is split, the last part to finish (atomic counter) adds
-// the parts' sums in a fixed order, so results do not depend on scheduling.
+// Work split: a unit is (pixel, part); the rs parts of a pixel take contiguous ranges of
+// its support rows (rs = 1 unless there are fewer pixels than resident warps: a split
+// costs partial sums and an atomic hand-off).  Warps are persistent (one grid of resident
+// CTAs walks all units) and prefetch the next unit's record.  Warp shuffles combine
+// lanes; when a pixel is split, the last part to finish (atomic counter) adds the parts'
+// sums in a fixed order, so results do not depend on scheduling.
 #include "hb_common.cuh"
 #include "hb_device.cuh"
+#include "hb_posterior.cuh"
 
 #include <math.h>
 
-#ifndef HB_POST_UNROLL
-#define HB_POST_UNROLL 4   // grid rows per unrolled step of the posterior loop
-#endif
 #ifdef HB_POST_MINB       // minimum resident CTAs per SM requested from the register allocator
 #define HB_POST_BOUNDS __launch_bounds__(kThreads, HB_POST_MINB)
 #else
@@ -41,135 +22,6 @@
 
 namespace hb {
 namespace {
-
-typedef unsigned long long u64;
-constexpr int kPostUnroll = HB_POST_UNROLL;
-
-__device__ __forceinline__ u64 pk(float a, float b) {
-    u64 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk(u64 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-    u64 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ u64 add2(u64 a, u64 b) {
-    u64 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ float ex2(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Column constants of one lane for the column block starting at j_base.
-template <int CPL>
-__device__ __forceinline__ void column_terms(const BayesParams& bp, const BayesRec& rec, int lane, int j_base,
-                                             float shift, float (&dj)[CPL], float (&P)[CPL], float (&Q)[CPL]) {
-#pragma unroll
-    for (int s = 0; s < CPL; ++s) {
-        const int j = j_base + lane + 32 * s;
-        dj[s] = (float)(j - rec.j0);
-        P[s] = j < bp.n1 ? fmaf(bp.Cq * dj[s], dj[s], rec.V * dj[s]) - shift : -INFINITY;
-        Q[s] = fmaf(2.f * bp.Bq, dj[s], rec.U);
-    }
-}
-
-// sum w, sum w di, sum w dj over rows [rb, re) and the lane's columns (all column blocks),
-// with weights 2^(t - shift).
-template <int CPL>
-__device__ __forceinline__ void grid_sums(const BayesParams& bp, const BayesRec& rec, int lane, int rb, int re,
-                                          float shift, float& sw, float& sdi, float& sdj) {
-    for (int jb = 0; jb < bp.n1; jb += 32 * CPL) {
-        float dj[CPL], P[CPL], Q[CPL];
-        column_terms<CPL>(bp, rec, lane, jb, shift, dj, P, Q);
-        float S[CPL], T[CPL];
-        if constexpr (CPL == 1) {
-            S[0] = 0.f;
-            T[0] = 0.f;
-            float di = (float)(rb - rec.i0);
-#pragma unroll 4
-            for (int i = rb; i < re; ++i, di += 1.f) {
-                const float w = ex2(fmaf(di, fmaf(bp.Aq, di, Q[0]), P[0]));
-                S[0] += w;
-                T[0] = fmaf(w, di, T[0]);
-            }
-        } else {
-            u64 Pp[CPL / 2], Qp[CPL / 2], Sp[CPL / 2], Tp[CPL / 2];
-#pragma unroll
-            for (int q = 0; q < CPL / 2; ++q) {
-                Pp[q] = pk(P[2 * q], P[2 * q + 1]);
-                Qp[q] = pk(Q[2 * q], Q[2 * q + 1]);
-                Sp[q] = pk(0.f, 0.f);
-                Tp[q] = pk(0.f, 0.f);
-            }
-            const u64 AA = pk(bp.Aq, bp.Aq), ONE = pk(1.f, 1.f);
-            const float di0 = (float)(rb - rec.i0);
-            u64 dd = pk(di0, di0);
-#pragma unroll kPostUnroll
-            for (int i = rb; i < re; ++i) {
-#pragma unroll
-                for (int q = 0; q < CPL / 2; ++q) {
-                    const u64 X = fma2(dd, AA, Qp[q]);
-                    const u64 t = fma2(dd, X, Pp[q]);
-                    float t0, t1;
-                    upk(t, t0, t1);
-                    const u64 w = pk(ex2(t0), ex2(t1));
-                    Sp[q] = add2(Sp[q], w);
-                    Tp[q] = fma2(w, dd, Tp[q]);
-                }
-                dd = add2(dd, ONE);
-            }
-#pragma unroll
-            for (int q = 0; q < CPL / 2; ++q) {
-                upk(Sp[q], S[2 * q], S[2 * q + 1]);
-                upk(Tp[q], T[2 * q], T[2 * q + 1]);
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < CPL; ++s) {
-            sw += S[s];
-            sdi += T[s];
-            sdj = fmaf(S[s], dj[s], sdj);
-        }
-    }
-}
-
-// Largest exponent t over rows [rb, re) and the lane's columns.
-template <int CPL>
-__device__ float grid_max(const BayesParams& bp, const BayesRec& rec, int lane, int rb, int re) {
-    float m = -INFINITY;
-    for (int jb = 0; jb < bp.n1; jb += 32 * CPL) {
-        float dj[CPL], P[CPL], Q[CPL];
-        column_terms<CPL>(bp, rec, lane, jb, 0.f, dj, P, Q);
-        float di = (float)(rb - rec.i0);
-        for (int i = rb; i < re; ++i, di += 1.f)
-#pragma unroll
-            for (int s = 0; s < CPL; ++s) m = fmaxf(m, fmaf(di, fmaf(bp.Aq, di, Q[s]), P[s]));
-    }
-    return m;
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return v;
-}
-
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
-    return v;
-}
-
-__device__ __forceinline__ bool usable(float sw, float sdi, float sdj) {
-    return sw > 0.f && isfinite(sw) && isfinite(sdi) && isfinite(sdj);
-}
 
 // Posterior mean from the sums, in FP32 (the output is FP32): c = c_ref + h * (sum w d / sum w).
 __device__ __forceinline__ void write_mean(const BayesParams& bp, const BayesRec& rec, long p, float sw, float sdi,
@@ -188,8 +40,11 @@ __device__ __forceinline__ void write_mean(const BayesParams& bp, const BayesRec
 template <int CPL>
 __device__ __forceinline__ void run_unit(const BayesParams& bp, const BayesRec& rec, long p, int part, int rs,
                                          int lane, float* partial, unsigned* count, float2* chat,
-                                         float2* chat_scaled, float scale) {
-    int rb = (int)((long)bp.n0 * part / rs), re = (int)((long)bp.n0 * (part + 1) / rs);
+                                         float2* chat_scaled, float scale, unsigned long long& nodes) {
+    int lo, hi;
+    support_rows(bp, rec, lo, hi);
+    int rb = lo + (int)((long)(hi - lo) * part / rs), re = lo + (int)((long)(hi - lo) * (part + 1) / rs);
+    nodes += (unsigned long long)(re - rb) * (unsigned)bp.n1;
     float shift = 0.f;
     bool whole = rs == 1;  // sums cover the whole pixel
     while (true) {
@@ -232,6 +87,7 @@ __device__ __forceinline__ void run_unit(const BayesParams& bp, const BayesRec& 
         }
         rb = 0;
         re = bp.n0;
+        nodes += 2ull * (unsigned)bp.n0 * (unsigned)bp.n1;
         shift = warp_max(grid_max<CPL>(bp, rec, lane, 0, bp.n0));
         if (!(shift != 0.f)) shift = -1.f;  // any non-zero shift marks the second pass
     }
@@ -241,29 +97,29 @@ __device__ __forceinline__ void run_unit(const BayesParams& bp, const BayesRec& 
 template <int CPL>
 __global__ void HB_POST_BOUNDS posterior_kernel(BayesParams bp, const BayesRec* __restrict__ recs, long npix, int rs,
                                                 float* partial, unsigned* count, float2* __restrict__ chat,
-                                                float2* __restrict__ chat_scaled, float scale, PosteriorGate gate) {
-    // gated launch (fallback of the learned stand-in): run only when the summed sampled
-    // error of the stand-in exceeded its threshold (a NaN sum also runs)
-    if (gate.err_sum) {
-        if (*gate.err_sum <= gate.threshold) return;
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(gate.fallbacks, 1u);
-    }
+                                                float2* __restrict__ chat_scaled, float scale, PosteriorGate gate,
+                                                unsigned long long* nodes_out) {
     const int lane = threadIdx.x & 31;
     const long nw = (long)gridDim.x * (kThreads / 32);
     const long units = npix * rs;
     long u = (long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    // launched with PDL after the analysis kernel: wait for its records, then let the
-    // synthesis kernel be scheduled
+    // launched with PDL after the kernel that writes the records (or the gate's errors):
+    // wait for it, then let the next kernel be scheduled
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
+    // gated launch (fallback of the learned stand-in): run only when the sampled check
+    // before this kernel decided so
+    if (gate.run && *gate.run == 0u) return;
     BayesRec next = {0, 0, 0.f, 0.f};
     if (u < units) next = recs[u / rs];
+    unsigned long long nodes = 0;
     for (; u < units; u += nw) {
         const long p = u / rs;
         const BayesRec rec = next;
         if (u + nw < units) next = recs[(u + nw) / rs];
-        run_unit<CPL>(bp, rec, p, (int)(u - p * rs), rs, lane, partial, count, chat, chat_scaled, scale);
+        run_unit<CPL>(bp, rec, p, (int)(u - p * rs), rs, lane, partial, count, chat, chat_scaled, scale, nodes);
     }
+    if (nodes_out && lane == 0 && nodes) atomicAdd(nodes_out, nodes);
 }
 
 // Resident CTAs per SM for a kernel (cached per device and kernel) and the SM count.
@@ -317,7 +173,7 @@ cudaError_t launch_cpl(const BayesParams& bp, const BayesRec* rec, long npix, co
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, posterior_kernel<CPL>, bp, rec, npix, (int)rs, sc.partial, sc.count, chat,
-                              chat_scaled, scale, gate);
+                              chat_scaled, scale, gate, sc.nodes);
 }
 
 }  // namespace
@@ -334,64 +190,83 @@ cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long np
 
 namespace {
 
-// Exact posterior mean of a sample of pixels, compared with another estimate of them:
-// each pixel's error relative to the box extents (the larger of the two axes) is added
-// to *err_sum (a NaN error makes the sum NaN).
+// The learned stand-in's sampled check: one sampled pixel per CTA (cta_posterior_mean
+// shares its support rows out over the CTA's warps; the check is latency-bound: few
+// pixels, each wanted quickly).  err[k] = the larger of the two axes' errors of est
+// relative to the box extents (NaN if either is).  The last CTA to arrive adds all the
+// errors in index order and leaves the decision in sync[2].
 template <int CPL>
 __global__ void __launch_bounds__(kThreads) posterior_check_kernel(BayesParams bp, const BayesRec* __restrict__ recs,
                                                                    long npix, int nsample, unsigned seed,
                                                                    const float2* __restrict__ est, float inv_ext0,
-                                                                   float inv_ext1, float* err_sum) {
-    const int lane = threadIdx.x & 31;
-    const int w = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    if (w >= nsample) return;
-    unsigned h = seed * 0x9E3779B9U + (unsigned)w * 0x85EBCA6BU;
-    h ^= h >> 16;
-    h *= 0x7feb352dU;
-    h ^= h >> 15;
-    h *= 0x846ca68bU;
-    h ^= h >> 16;
-    const long p = (long)(h % (unsigned long)npix);
-    const BayesRec rec = recs[p];
-    float shift = 0.f, sw, sdi, sdj;
-    for (int pass = 0; pass < 2; ++pass) {
-        sw = sdi = sdj = 0.f;
-        grid_sums<CPL>(bp, rec, lane, 0, bp.n0, shift, sw, sdi, sdj);
-        sw = warp_sum(sw);
-        sdi = warp_sum(sdi);
-        sdj = warp_sum(sdj);
-        if (usable(sw, sdi, sdj)) break;
-        shift = warp_max(grid_max<CPL>(bp, rec, lane, 0, bp.n0));
+                                                                   float inv_ext1, float* err, float tol,
+                                                                   unsigned* sync) {
+    __shared__ float part[kThreads / 32][3];
+    __shared__ unsigned last;
+    __shared__ float red[kThreads];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    for (int k = blockIdx.x; k < nsample; k += gridDim.x) {
+        const long p = sample_pixel(seed, k, npix);
+        const float2 c = cta_posterior_mean<CPL>(bp, recs[p], part);
+        if (threadIdx.x == 0) {
+            const float2 e = est[p];
+            const float dx = fabsf(e.x - c.x) * inv_ext0, dy = fabsf(e.y - c.y) * inv_ext1;
+            err[k] = isnan(dx) || isnan(dy) ? NAN : fmaxf(dx, dy);
+            __threadfence();
+        }
     }
-    if (lane == 0) {
-        const float c0 = fmaf(bp.h0f, sdi / sw, fmaf((float)rec.i0, bp.h0f, bp.lo0f));
-        const float c1 = fmaf(bp.h1f, sdj / sw, fmaf((float)rec.j0, bp.h1f, bp.lo1f));
-        const float2 e = est[p];
-        const float dx = fabsf(e.x - c0) * inv_ext0, dy = fabsf(e.y - c1) * inv_ext1;
-        const float err = isnan(dx) || isnan(dy) ? NAN : fmaxf(dx, dy);
-        atomicAdd(err_sum, err);
+    if (threadIdx.x == 0) last = atomicAdd(&sync[0], 1u) == gridDim.x - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const volatile float* ev = err;
+    float e = 0.f;
+    for (int k = threadIdx.x; k < nsample; k += kThreads) e += ev[k];
+    red[threadIdx.x] = e;
+    __syncthreads();
+#pragma unroll
+    for (int h = kThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const bool run = !(red[0] / (float)nsample <= tol);
+        sync[2] = run ? 1u : 0u;
+        if (run) sync[1] += 1u;
+        sync[0] = 0u;
     }
 }
 
 template <int CPL>
 cudaError_t launch_check_cpl(const BayesParams& bp, const BayesRec* rec, long npix, int nsample, unsigned seed,
-                             const float2* est, float inv_ext0, float inv_ext1, float* err_sum, cudaStream_t s) {
-    const int blocks = (nsample + kThreads / 32 - 1) / (kThreads / 32);
-    posterior_check_kernel<CPL><<<blocks, kThreads, 0, s>>>(bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1,
-                                                            err_sum);
-    return cudaGetLastError();
+                             const float2* est, float inv_ext0, float inv_ext1, float* err, float tol, unsigned* sync,
+                             bool pdl, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nsample < 4096 ? nsample : 4096));
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, posterior_check_kernel<CPL>, bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1,
+                              err, tol, sync);
 }
 
 }  // namespace
 
 cudaError_t launch_posterior_check(const BayesParams& bp, const BayesRec* rec, long npix, int nsample, unsigned seed,
-                                   const float2* est, float inv_ext0, float inv_ext1, float* err_sum,
-                                   cudaStream_t s) {
+                                   const float2* est, float inv_ext0, float inv_ext1, float* err, float tol,
+                                   unsigned* sync, bool pdl, cudaStream_t s) {
     if (npix <= 0 || nsample <= 0) return cudaSuccess;
-    if (bp.n1 <= 32) return launch_check_cpl<1>(bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1, err_sum, s);
-    if (bp.n1 <= 64) return launch_check_cpl<2>(bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1, err_sum, s);
-    if (bp.n1 <= 128) return launch_check_cpl<4>(bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1, err_sum, s);
-    return launch_check_cpl<8>(bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1, err_sum, s);
+#define HB_CHECK_ARGS bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1, err, tol, sync, pdl, s
+    if (bp.n1 <= 32) return launch_check_cpl<1>(HB_CHECK_ARGS);
+    if (bp.n1 <= 64) return launch_check_cpl<2>(HB_CHECK_ARGS);
+    if (bp.n1 <= 128) return launch_check_cpl<4>(HB_CHECK_ARGS);
+    return launch_check_cpl<8>(HB_CHECK_ARGS);
+#undef HB_CHECK_ARGS
 }
 
 }  // namespace hb

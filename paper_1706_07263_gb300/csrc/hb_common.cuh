@@ -44,7 +44,18 @@ struct BayesParams {
     // A c at the grid origin and per grid step, as float (hi, lo) pairs:
     //   A c_ij = base + i * step0 + j * step1
     float base_hi[3], base_lo[3], step0_hi[3], step0_lo[3], step1_hi[3], step1_lo[3];
+    // Rows whose every weight is exactly zero in FP32 are not enumerated.  Over real dj the
+    // largest exponent of row di is  -sup_alpha di^2 + (U - sup_r V) di + sup_c V^2;  rows
+    // where that stays below -(kSupportCut + 1e-6 * (sup_mg + |U| n0 + |V| n1)) have all
+    // 2^t below 2^-150 (the FP32 evaluation error of t is far inside the margin), which
+    // ex2.approx.ftz returns as 0.  sup_rows = 0 enumerates every row.
+    int sup_rows;
+    float sup_alpha, sup_r, sup_c, sup_mg;
+    float sup_inv_alpha;      // 0.5 / (-sup_alpha)
+    float sup_inv_aq;         // 0.5 / Aq
+    float sup_inv_k1;         // 1 / (-sup_r) where the edge-column pieces apply, else 0
 };
+constexpr float kSupportCut = 150.f;
 
 // Per low-pass pixel record written by the analysis kernel for the posterior kernel.
 struct __align__(16) BayesRec {
@@ -58,6 +69,7 @@ struct PosteriorScratch {
     float* partial;           // npix * max_parts * 3
     unsigned* count;          // npix
     int max_parts;
+    unsigned long long* nodes = nullptr;  // optional: grid nodes enumerated, added per warp
 };
 constexpr int kMaxParts = 8;
 
@@ -79,18 +91,23 @@ constexpr int kMaxBatchJobs = 64;
 cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
                             const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f = nullptr);
 cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s);
-// Optional gate of the posterior launch: when err_sum is set the kernel runs only if the
-// float it holds exceeds threshold (and then counts one fallback).
+// Optional gate of the posterior launch: when run is set the kernel does nothing unless
+// *run is non-zero (the decision launch_posterior_check leaves behind).
 struct PosteriorGate {
-    const float* err_sum;
-    float threshold;
-    unsigned* fallbacks;
+    const unsigned* run;
 };
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
                              float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,
-                             const PosteriorGate& gate = PosteriorGate{nullptr, 0.f, nullptr});
+                             const PosteriorGate& gate = PosteriorGate{nullptr});
+// Exact posterior of nsample pseudo-randomly drawn pixels (seeded) against another
+// estimate of them: err[k] = the larger of |d c0| inv_ext0 and |d c1| inv_ext1 for the
+// k-th drawn pixel (NaN if either is).  The last CTA to finish adds the errors in index
+// order and sets sync[2] = 1 when their mean exceeds tol or is NaN (then also sync[1] += 1),
+// else 0; sync[0] is its arrival counter (zero before and after).  pdl as for
+// launch_posterior.
 cudaError_t launch_posterior_check(const BayesParams& bp, const BayesRec* rec, long npix, int nsample, unsigned seed,
-                                   const float2* est, float inv_ext0, float inv_ext1, float* err_sum, cudaStream_t s);
+                                   const float2* est, float inv_ext0, float inv_ext1, float* err, float tol,
+                                   unsigned* sync, bool pdl, cudaStream_t s);
 cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_t stride, const float2* lut,
                              const float2* chat, float* out0, float* out1, int debug_conc, bool pdl, cudaStream_t s);
 size_t transform_smem_bytes(const TransformParams& tp);

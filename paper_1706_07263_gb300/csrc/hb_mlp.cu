@@ -1,5 +1,5 @@
 // hb_mlp.cu -- learned stand-in for the low-pass posterior step: a 3 -> 64 -> 64 -> 2
-// multilayer perceptron with exact (erf) GELU, BF16 weights and activations and FP32
+// multilayer perceptron with erf GELU, BF16 weights and activations and FP32
 // accumulation, trained on (block-mean log-attenuation -> posterior mean) pairs that the
 // posterior kernel produces.  The paper has no learned component; the network only
 // stands in for its low-pass Bayesian estimate.
@@ -19,8 +19,9 @@
 // (mma.sync m16n8k16, BF16 in, FP32 accumulate), the 3- and 2-wide layers on the FP32
 // pipes.  mlp_adam_kernel adds the partials in a fixed order (deterministic) and applies
 // Adam to the FP32 master weights, refreshing the BF16 copies.  mlp_forward_kernel:
-// inference, persistent warps of 16 samples.  Weights are BF16; activations are rounded
-// to BF16 at h1 and h2, and so is the gradient dz2 fed to the tensor cores; the input x
+// inference, 8 samples per warp held in tensor-core fragments.  Weights are BF16;
+// activations are rounded to BF16 at h1 and h2, and so is the gradient dz2 fed to the
+// tensor cores; erf is evaluated to FP32 accuracy (see gelu); the input x
 // stays FP32 (the correction varies fast near the box edges, so the input needs more
 // resolution than BF16's 8 bits); accumulation is FP32 throughout.
 #include "hb_common.cuh"
@@ -37,7 +38,24 @@ constexpr int kSamplesT = 16 * kWarpsT;    // samples per training CTA
 constexpr float kInvSqrt2 = 0.70710678118654752440f;
 constexpr float kInvSqrt2Pi = 0.39894228040143267794f;
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * kInvSqrt2)); }
+// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 with erf by Abramowitz & Stegun 7.1.26
+// (Hastings' rational approximation):
+//   1 - erf(x) = (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2),  t = 1 / (1 + p x),
+// x >= 0, |error| <= 1.5e-7 -- the accuracy of FP32 erff, in a third of the instructions
+// (one reciprocal and one exponential on the MUFU).  1 + erf is formed as 2 - q for z >= 0
+// and as q itself for z < 0 (erf is odd), so no digits cancel on the negative side.
+__device__ __forceinline__ float gelu(float z) {
+    const float x = z * kInvSqrt2, ax = fabsf(x);
+    float t, e;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(0.3275911f, ax, 1.f)));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-1.4426950408889634f * ax * ax));
+    float poly = fmaf(1.061405429f, t, -1.453152027f);
+    poly = fmaf(poly, t, 1.421413741f);
+    poly = fmaf(poly, t, -0.284496736f);
+    poly = fmaf(poly, t, 0.254829592f);
+    const float q = poly * t * e;
+    return 0.5f * z * (x >= 0.f ? 2.f - q : q);
+}
 __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.f + erff(z * kInvSqrt2)) + z * kInvSqrt2Pi * expf(-0.5f * z * z);
 }
@@ -334,37 +352,110 @@ __global__ void mlp_adam_kernel(const float* __restrict__ gpart, const float* __
     }
 }
 
+// Inference.  One warp computes 8 samples at a time entirely in registers, with layer 2
+// transposed: z2^T (64 units x 8 samples) = W2 h1^T, so W2 is the m16n8k16 A operand
+// (staged once per CTA as ready-made fragments) and the 8 samples are N.  Lane (g, q)
+// (g = lane / 4, q = lane % 4) evaluates layer 1 for sample g at exactly the hidden units
+// its B fragments hold (k = 16 kt + 2q + {0, 1, 8, 9}), so h1 goes from the FP32 pipes
+// straight into the tensor-core operands; the accumulators come back holding units
+// 16 mt + g + {0, 8} of samples 2q, 2q + 1, where GELU, the BF16 rounding of h2 and the
+// lane's share of layer 3 are applied, and shuffles over g finish layer 3.
 constexpr int kWarpsF = 8;
-struct FwdSmem {
-    SmemParams P;
-    WarpBufT<false> W[kWarpsF];
-    float ys[kWarpsF][16][3];
+struct InferSmem {
+    uint4 w2f[kHid / 16][kHid / 16][32];  // W2 A fragments per (m tile, k tile, lane)
+    float4 l1[kHid];                      // W1[u][0..2], b1[u]
+    float4 l3[kHid];                      // b2[u], W3[0][u], W3[1][u], 0
+    float b3[kOut];
 };
 
 __global__ void __launch_bounds__(32 * kWarpsF) mlp_forward_kernel(const float* __restrict__ wbf, MlpNorm nm,
                                                                    const float* __restrict__ ybar, long n,
-                                                                   float2* __restrict__ chat,
-                                                                   unsigned* __restrict__ err_reset) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw);
-    if (err_reset && blockIdx.x == 0 && threadIdx.x == 0) *err_reset = 0u;
-    load_params(S.P, wbf);
+                                                                   float2* __restrict__ chat) {
+    __shared__ InferSmem S;
+    // the weights do not come from the preceding kernel: stage them before waiting on it
+    for (int i = threadIdx.x; i < (kHid / 16) * (kHid / 16) * 32; i += blockDim.x) {
+        const int l = i & 31, kt = (i >> 5) % (kHid / 16), mt = i / (32 * (kHid / 16));
+        const float* w0 = wbf + kOffW2 + (mt * 16 + (l >> 2)) * kHid + kt * 16 + 2 * (l & 3);
+        const float* w8 = w0 + 8 * kHid;
+        S.w2f[mt][kt][l] = make_uint4(pack_bf16(w0[0], w0[1]), pack_bf16(w8[0], w8[1]), pack_bf16(w0[8], w0[9]),
+                                      pack_bf16(w8[8], w8[9]));
+    }
+    for (int u = threadIdx.x; u < kHid; u += blockDim.x) {
+        S.l1[u] = make_float4(wbf[kOffW1 + u * kIn], wbf[kOffW1 + u * kIn + 1], wbf[kOffW1 + u * kIn + 2],
+                              wbf[kOffB1 + u]);
+        S.l3[u] = make_float4(wbf[kOffB2 + u], wbf[kOffW3 + u], wbf[kOffW3 + kHid + u], 0.f);
+    }
+    if (threadIdx.x < kOut) S.b3[threadIdx.x] = wbf[kOffB3 + threadIdx.x];
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long ntile = (n + 15) / 16;
+    // launched after the kernel that writes ybar (programmatic dependent launch, or a
+    // plain launch where this returns at once)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    const long ntile = (n + 7) / 8;
     for (long tile = (long)blockIdx.x * kWarpsF + warp; tile < ntile; tile += (long)gridDim.x * kWarpsF) {
-        const long base = tile * 16;
-        if (lane < 16)
-            for (int c = 0; c < 3; ++c) S.ys[warp][lane][c] = base + lane < n ? ybar[(base + lane) * 3 + c] : 0.f;
-        __syncwarp();
-        warp_forward<false>(S.P, nm, S.W[warp], S.ys[warp], lane);
-        if (lane < 16 && base + lane < n) {
-            const float* y = S.ys[warp][lane];
-            const float c0 = clip_ls(nm, y, 0) + nm.osc0 * S.W[warp].o[lane][0];
-            const float c1 = clip_ls(nm, y, 1) + nm.osc1 * S.W[warp].o[lane][1];
-            chat[base + lane] = make_float2(c0, c1);
+        const long r = tile * 8 + g;
+        float y[3], x[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) y[c] = r < n ? ybar[r * 3 + c] : 0.f;
+#pragma unroll
+        for (int c = 0; c < kIn; ++c)
+            x[c] = nm.T[c * 3] * y[0] + nm.T[c * 3 + 1] * y[1] + nm.T[c * 3 + 2] * y[2] + nm.t0[c];
+        // layer 1 into the B fragments of layer 2 (k = unit, n = sample g)
+        unsigned bfr[kHid / 16][2];
+#pragma unroll
+        for (int kt = 0; kt < kHid / 16; ++kt) {
+            float h[4];  // units 16 kt + 2q + {0, 1, 8, 9}
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float4 w = S.l1[kt * 16 + 2 * q + (v & 1) + 8 * (v >> 1)];
+                float z = w.w;
+                z = fmaf(w.x, x[0], z);
+                z = fmaf(w.y, x[1], z);
+                z = fmaf(w.z, x[2], z);
+                h[v] = gelu(z);
+            }
+            bfr[kt][0] = pack_bf16(h[0], h[1]);
+            bfr[kt][1] = pack_bf16(h[2], h[3]);
         }
-        __syncwarp();
+        // layer 2 on the tensor cores, layer 3 from the accumulators
+        float o00 = 0.f, o01 = 0.f, o10 = 0.f, o11 = 0.f;  // (sample 2q / 2q + 1, output 0 / 1)
+#pragma unroll
+        for (int mt = 0; mt < kHid / 16; ++mt) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < kHid / 16; ++kt) {
+                const uint4 aw = S.w2f[mt][kt][lane];
+                const unsigned af[4] = {aw.x, aw.y, aw.z, aw.w};
+                mma16816(d, af, bfr[kt]);
+            }
+            // d: (unit mt*16 + g, samples 2q, 2q+1), (unit mt*16 + g + 8, samples 2q, 2q+1)
+            const float4 la = S.l3[mt * 16 + g], lb = S.l3[mt * 16 + g + 8];
+            const float h00 = bf(gelu(d[0] + la.x)), h01 = bf(gelu(d[1] + la.x));
+            const float h10 = bf(gelu(d[2] + lb.x)), h11 = bf(gelu(d[3] + lb.x));
+            o00 = fmaf(la.y, h00, fmaf(lb.y, h10, o00));
+            o01 = fmaf(la.z, h00, fmaf(lb.z, h10, o01));
+            o10 = fmaf(la.y, h01, fmaf(lb.y, h11, o10));
+            o11 = fmaf(la.z, h01, fmaf(lb.z, h11, o11));
+        }
+#pragma unroll
+        for (int off = 4; off <= 16; off <<= 1) {
+            o00 += __shfl_xor_sync(0xffffffffu, o00, off);
+            o01 += __shfl_xor_sync(0xffffffffu, o01, off);
+            o10 += __shfl_xor_sync(0xffffffffu, o10, off);
+            o11 += __shfl_xor_sync(0xffffffffu, o11, off);
+        }
+        // lanes g = 0 and g = 1 hold samples 2q and 2q + 1; they need those samples' ybar
+        const int s = 2 * q + (g & 1);
+        const long rs = tile * 8 + s;
+        const float ya = __shfl_sync(0xffffffffu, y[0], 4 * s), yb = __shfl_sync(0xffffffffu, y[1], 4 * s),
+                    yc = __shfl_sync(0xffffffffu, y[2], 4 * s);
+        if (g < 2 && rs < n) {
+            const float ys[3] = {ya, yb, yc};
+            const float o0 = (g & 1) ? o10 : o00, o1 = (g & 1) ? o11 : o01;
+            chat[rs] = make_float2(clip_ls(nm, ys, 0) + nm.osc0 * (o0 + S.b3[0]),
+                                   clip_ls(nm, ys, 1) + nm.osc1 * (o1 + S.b3[1]));
+        }
     }
 }
 
@@ -397,20 +488,26 @@ cudaError_t launch_mlp_adam(const float* gpart, const float* lpart, int nblocks,
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_forward(const float* wbf, const MlpNorm& nm, const float* ybar, long n, float2* chat,
-                               unsigned* err_reset, cudaStream_t s) {
-    const size_t sm = sizeof(FwdSmem);
-    cudaError_t e = set_smem_attr(mlp_forward_kernel, sm);
-    if (e != cudaSuccess) return e;
+cudaError_t launch_mlp_forward(const float* wbf, const MlpNorm& nm, const float* ybar, long n, float2* chat, bool pdl,
+                               cudaStream_t s) {
     int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long tiles = (n + 15) / 16;
-    long blocks = (tiles + kWarpsF - 1) / kWarpsF;
-    if (blocks > 2L * sms) blocks = 2L * sms;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long tiles = (n + 7) / 8;
+    long blocks = (tiles + kWarpsF - 1) / kWarpsF;  // one tile per warp while that fits
+    if (blocks > 8L * sms) blocks = 8L * sms;
     if (blocks < 1) blocks = 1;
-    mlp_forward_kernel<<<(unsigned)blocks, 32 * kWarpsF, sm, s>>>(wbf, nm, ybar, n, chat, err_reset);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(32 * kWarpsF);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, mlp_forward_kernel, wbf, nm, ybar, n, chat);
 }
 
 }  // namespace hb

@@ -39,7 +39,9 @@ cudaError_t launch_mlp_train(const float* wbf, const MlpNorm& nm, const float* y
 cudaError_t launch_mlp_adam(const float* gpart, const float* lpart, int nblocks, int batch, float* grad, float* loss,
                             float* master, float* m, float* v, float* wbf, float lr, float beta1, float beta2,
                             float eps, int t, cudaStream_t s);
-cudaError_t launch_mlp_forward(const float* wbf, const MlpNorm& nm, const float* ybar, long n, float2* chat,
-                               unsigned* err_reset, cudaStream_t s);
+// Inference for n samples; pdl: launched as a programmatic dependent of the preceding
+// kernel in the stream (the kernel waits for it before reading ybar).
+cudaError_t launch_mlp_forward(const float* wbf, const MlpNorm& nm, const float* ybar, long n, float2* chat, bool pdl,
+                               cudaStream_t s);
 
 }  // namespace hb

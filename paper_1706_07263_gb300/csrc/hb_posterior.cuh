@@ -1,0 +1,299 @@
+// hb_posterior.cuh -- the grid posterior's per-pixel sums, shared by the posterior
+// kernel and the learned stand-in's sampled check.  Internal to libhb.
+//
+// For a pixel with block-mean log-attenuation ybar the posterior over grid node k is
+// proportional to exp(-|ybar - A c_k|^2 / (2 sigma^2)) (flat prior).  Expanded around
+// a reference node c_ref = (i0, j0) with residual r0 = ybar - A c_ref, the base-2 log
+// weight of node (i0 + di, j0 + dj) relative to the reference is
+//
+//     t = U di + V dj + Aq di^2 + 2 Bq di dj + Cq dj^2
+//       = di * (Aq di + Q_j) + P_j,     Q_j = U + 2 Bq dj,  P_j = V dj + Cq dj^2,
+//
+// i.e. the -(|r0|^2 - 2 r0.A delta + |A delta|^2) expansion with the per-pixel terms
+// (U, V from r0) and the per-grid terms (Aq, Bq, Cq from |A delta|^2) separated.  The
+// weight is 2^t (MUFU ex2).  The reference node is the node nearest the likelihood's
+// maximiser over the grid's hull, so its weight is exactly 1 and no node's weight can
+// overflow; a pixel whose sums still come out non-finite (only possible for inputs far
+// outside the model) is recomputed with an explicit maximum pass.
+//
+// Only the grid rows that can hold a non-zero FP32 weight are enumerated (support_rows):
+// outside them every 2^t is below 2^-150 and ex2.approx.ftz returns exactly 0, so the
+// sums are the same as over the whole grid.
+//
+// Lane l of a warp takes grid columns l, l+32, l+64, ... (CPL columns per lane).  Per
+// pair of grid nodes a lane issues two packed FP32x2 FMAs for the exponents, two MUFU ex2
+// and two packed instructions for the sums (sum w and sum w*di per column; sum w*dj
+// follows from the column sums).
+#pragma once
+
+#include "hb_common.cuh"
+
+#include <math.h>
+
+#ifndef HB_POST_UNROLL
+#define HB_POST_UNROLL 4   // grid rows per unrolled step of the posterior loop
+#endif
+
+namespace hb {
+namespace {
+
+typedef unsigned long long u64;
+constexpr int kPostUnroll = HB_POST_UNROLL;
+
+__device__ __forceinline__ u64 pk(float a, float b) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(u64 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Column constants of one lane for the column block starting at j_base.
+template <int CPL>
+__device__ __forceinline__ void column_terms(const BayesParams& bp, const BayesRec& rec, int lane, int j_base,
+                                             float shift, float (&dj)[CPL], float (&P)[CPL], float (&Q)[CPL]) {
+#pragma unroll
+    for (int s = 0; s < CPL; ++s) {
+        const int j = j_base + lane + 32 * s;
+        dj[s] = (float)(j - rec.j0);
+        P[s] = j < bp.n1 ? fmaf(bp.Cq * dj[s], dj[s], rec.V * dj[s]) - shift : -INFINITY;
+        Q[s] = fmaf(2.f * bp.Bq, dj[s], rec.U);
+    }
+}
+
+// sum w, sum w di, sum w dj over rows [rb, re) and the lane's columns (all column blocks),
+// with weights 2^(t - shift).
+template <int CPL>
+__device__ __forceinline__ void grid_sums(const BayesParams& bp, const BayesRec& rec, int lane, int rb, int re,
+                                          float shift, float& sw, float& sdi, float& sdj) {
+    for (int jb = 0; jb < bp.n1; jb += 32 * CPL) {
+        float dj[CPL], P[CPL], Q[CPL];
+        column_terms<CPL>(bp, rec, lane, jb, shift, dj, P, Q);
+        float S[CPL], T[CPL];
+        if constexpr (CPL == 1) {
+            S[0] = 0.f;
+            T[0] = 0.f;
+            float di = (float)(rb - rec.i0);
+#pragma unroll 4
+            for (int i = rb; i < re; ++i, di += 1.f) {
+                const float w = ex2(fmaf(di, fmaf(bp.Aq, di, Q[0]), P[0]));
+                S[0] += w;
+                T[0] = fmaf(w, di, T[0]);
+            }
+        } else {
+            u64 Pp[CPL / 2], Qp[CPL / 2], Sp[CPL / 2], Tp[CPL / 2];
+#pragma unroll
+            for (int q = 0; q < CPL / 2; ++q) {
+                Pp[q] = pk(P[2 * q], P[2 * q + 1]);
+                Qp[q] = pk(Q[2 * q], Q[2 * q + 1]);
+                Sp[q] = pk(0.f, 0.f);
+                Tp[q] = pk(0.f, 0.f);
+            }
+            const u64 AA = pk(bp.Aq, bp.Aq), ONE = pk(1.f, 1.f);
+            const float di0 = (float)(rb - rec.i0);
+            u64 dd = pk(di0, di0);
+#pragma unroll kPostUnroll
+            for (int i = rb; i < re; ++i) {
+#pragma unroll
+                for (int q = 0; q < CPL / 2; ++q) {
+                    const u64 X = fma2(dd, AA, Qp[q]);
+                    const u64 t = fma2(dd, X, Pp[q]);
+                    float t0, t1;
+                    upk(t, t0, t1);
+                    const u64 w = pk(ex2(t0), ex2(t1));
+                    Sp[q] = add2(Sp[q], w);
+                    Tp[q] = fma2(w, dd, Tp[q]);
+                }
+                dd = add2(dd, ONE);
+            }
+#pragma unroll
+            for (int q = 0; q < CPL / 2; ++q) {
+                upk(Sp[q], S[2 * q], S[2 * q + 1]);
+                upk(Tp[q], T[2 * q], T[2 * q + 1]);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) {
+            sw += S[s];
+            sdi += T[s];
+            sdj = fmaf(S[s], dj[s], sdj);
+        }
+    }
+}
+
+// Largest exponent t over rows [rb, re) and the lane's columns.
+template <int CPL>
+__device__ float grid_max(const BayesParams& bp, const BayesRec& rec, int lane, int rb, int re) {
+    float m = -INFINITY;
+    for (int jb = 0; jb < bp.n1; jb += 32 * CPL) {
+        float dj[CPL], P[CPL], Q[CPL];
+        column_terms<CPL>(bp, rec, lane, jb, 0.f, dj, P, Q);
+        float di = (float)(rb - rec.i0);
+        for (int i = rb; i < re; ++i, di += 1.f)
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) m = fmaxf(m, fmaf(di, fmaf(bp.Aq, di, Q[s]), P[s]));
+    }
+    return m;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// {x : qa x^2 + qb x + qc >= 0} for qa < 0 as [lo, hi] (lo > hi when empty); inv = 0.5 / qa.
+// The approximate square root is far inside the row of widening the caller adds.
+__device__ __forceinline__ void superlevel(float qa, float qb, float qc, float inv, float& lo, float& hi) {
+    const float disc = fmaf(qb, qb, -4.f * qa * qc);
+    if (!(disc >= 0.f)) {
+        lo = INFINITY;
+        hi = -INFINITY;
+        return;
+    }
+    const float sq = sqrt_approx(disc);
+    lo = (sq - qb) * inv;
+    hi = (-qb - sq) * inv;
+}
+
+// Rows [lo, hi) of the grid that can hold a non-zero FP32 weight for this pixel (every
+// row when the bound is off or not finite).  The largest exponent of row di over the
+// grid's columns is the row maximum over real dj where that maximiser dj*(di) lies on the
+// grid, else the exponent at the nearer edge column: a concave function of di made of
+// three quadratic pieces.  The rows kept are the union over the pieces of (rows where the
+// piece reaches -cut) within (rows where the piece applies, widened by one), widened by
+// one more row; the reference row (weight exactly 1) is always kept.
+__device__ __forceinline__ void support_rows(const BayesParams& bp, const BayesRec& rec, int& lo, int& hi) {
+    lo = 0;
+    hi = bp.n0;
+    if (!bp.sup_rows) return;
+    const float cut = fmaf(1e-6f, fmaf(fabsf(rec.U), (float)bp.n0, fmaf(fabsf(rec.V), (float)bp.n1, bp.sup_mg)),
+                           kSupportCut);
+    // unconstrained row maximum: -alpha di^2 + (U - r V) di + c V^2
+    float rlo, rhi;
+    superlevel(-bp.sup_alpha, fmaf(-bp.sup_r, rec.V, rec.U), fmaf(rec.V * rec.V, bp.sup_c, cut), bp.sup_inv_alpha,
+               rlo, rhi);
+    const float k1 = -bp.sup_r;  // dj*(di) = k0 + k1 di
+    if (bp.sup_inv_k1 != 0.f && rlo <= rhi) {
+        const float k0 = 2.f * rec.V * bp.sup_c;
+        const float ea = (-(float)rec.j0 - k0) * bp.sup_inv_k1, eb = ((float)(bp.n1 - 1 - rec.j0) - k0) * bp.sup_inv_k1;
+        // where dj* falls left of the grid (a), on it (m), right of it (b)
+        const float da_lo = k1 > 0.f ? -INFINITY : ea - 1.f, da_hi = k1 > 0.f ? ea + 1.f : INFINITY;
+        const float db_lo = k1 > 0.f ? eb - 1.f : -INFINITY, db_hi = k1 > 0.f ? INFINITY : eb + 1.f;
+        const float dm_lo = fminf(ea, eb) - 1.f, dm_hi = fmaxf(ea, eb) + 1.f;
+        float ulo = INFINITY, uhi = -INFINITY;
+        auto join = [&](float a0, float a1, float b0, float b1) {
+            const float x0 = fmaxf(a0, b0), x1 = fminf(a1, b1);
+            if (x0 <= x1) {
+                ulo = fminf(ulo, x0);
+                uhi = fmaxf(uhi, x1);
+            }
+        };
+        join(rlo, rhi, dm_lo, dm_hi);
+        float slo, shi;
+        const float ja = -(float)rec.j0, jb = (float)(bp.n1 - 1 - rec.j0);
+        superlevel(bp.Aq, fmaf(2.f * bp.Bq, ja, rec.U), fmaf(fmaf(bp.Cq, ja, rec.V), ja, cut), bp.sup_inv_aq, slo, shi);
+        join(slo, shi, da_lo, da_hi);
+        superlevel(bp.Aq, fmaf(2.f * bp.Bq, jb, rec.U), fmaf(fmaf(bp.Cq, jb, rec.V), jb, cut), bp.sup_inv_aq, slo, shi);
+        join(slo, shi, db_lo, db_hi);
+        if (!isnan(ulo) && !isnan(uhi) && ulo <= uhi) {
+            rlo = fmaxf(rlo, ulo);
+            rhi = fminf(rhi, uhi);
+        }
+    }
+    if (!(rlo <= rhi) || isnan(rlo) || isnan(rhi)) return;
+    const float lim = (float)bp.n0 + 2.f;
+    const int a = rec.i0 + (int)floorf(fmaxf(rlo, -lim)) - 1;
+    const int z = rec.i0 + (int)ceilf(fminf(rhi, lim)) + 2;
+    lo = min(max(a, 0), rec.i0);
+    hi = max(min(z, bp.n0), rec.i0 + 1);
+}
+
+__device__ __forceinline__ bool usable(float sw, float sdi, float sdj) {
+    return sw > 0.f && isfinite(sw) && isfinite(sdi) && isfinite(sdj);
+}
+
+// The k-th pixel of a seeded pseudo-random sample of npix pixels (an integer hash of
+// (seed, k); draws may repeat).
+__device__ __forceinline__ long sample_pixel(unsigned seed, int k, long npix) {
+    unsigned h = seed * 0x9E3779B9U + (unsigned)k * 0x85EBCA6BU;
+    h ^= h >> 16;
+    h *= 0x7feb352dU;
+    h ^= h >> 15;
+    h *= 0x846ca68bU;
+    h ^= h >> 16;
+    return (long)(h % (unsigned long)npix);
+}
+
+// Posterior mean of one pixel computed by a whole CTA (every thread calls it): the support
+// rows are shared out over the CTA's warps, whose sums are added in warp order.  The
+// result is valid in warp 0.  part: shared scratch of kThreads / 32 x 3 floats.
+template <int CPL>
+__device__ float2 cta_posterior_mean(const BayesParams& bp, const BayesRec& rec, float (*part)[3]) {
+    constexpr int kWarps = kThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int lo, hi;
+    support_rows(bp, rec, lo, hi);
+    const int rb = lo + (hi - lo) * warp / kWarps, re = lo + (hi - lo) * (warp + 1) / kWarps;
+    float sw = 0.f, sdi = 0.f, sdj = 0.f;
+    grid_sums<CPL>(bp, rec, lane, rb, re, 0.f, sw, sdi, sdj);
+    sw = warp_sum(sw);
+    sdi = warp_sum(sdi);
+    sdj = warp_sum(sdj);
+    if (lane == 0) {
+        part[warp][0] = sw;
+        part[warp][1] = sdi;
+        part[warp][2] = sdj;
+    }
+    __syncthreads();
+    float2 c = make_float2(0.f, 0.f);
+    if (warp == 0) {
+        sw = sdi = sdj = 0.f;
+        for (int w = 0; w < kWarps; ++w) {
+            sw += part[w][0];
+            sdi += part[w][1];
+            sdj += part[w][2];
+        }
+        if (!usable(sw, sdi, sdj)) {  // far outside the model: all rows, explicit maximum shift
+            const float shift = warp_max(grid_max<CPL>(bp, rec, lane, 0, bp.n0));
+            sw = sdi = sdj = 0.f;
+            grid_sums<CPL>(bp, rec, lane, 0, bp.n0, shift, sw, sdi, sdj);
+            sw = warp_sum(sw);
+            sdi = warp_sum(sdi);
+            sdj = warp_sum(sdj);
+        }
+        c.x = fmaf(bp.h0f, sdi / sw, fmaf((float)rec.i0, bp.h0f, bp.lo0f));
+        c.y = fmaf(bp.h1f, sdj / sw, fmaf((float)rec.j0, bp.h1f, bp.lo1f));
+    }
+    __syncthreads();
+    return c;
+}
+
+}  // namespace
+}  // namespace hb

@@ -171,6 +171,55 @@ def test_hd_1080_u8_frame():
     print(f"{wl.name}: THb max rel err {thb_err:.3e}, SO2 max abs err {so2_err:.3e}")
 
 
+def test_support_rows_leave_the_result_bit_identical():
+    """The posterior skips grid rows whose every FP32 weight is exactly zero; with one warp
+    per pixel (1080p: more pixels than resident warps) the sums, and so every output, are
+    bit-identical to enumerating the whole grid (HB_FULL_GRID), and the node counter shows
+    the work saved."""
+    wl = synth.HD_1080
+    mix, fr = synth.workload_inputs(wl)
+    grid = synth.grid_spec(wl)
+    frame = torch.from_numpy(fr.rgb).to(DEV)
+    outs, nodes = {}, {}
+    for flags in (0, binding.HB_FULL_GRID):
+        with Context(mix.A, grid, wl.levels, wl.lam, wl.W, wl.H, wl.fmt, flags) as ctx:
+            thb = torch.empty((wl.H, wl.W), dtype=torch.float32, device=DEV)
+            so2 = torch.empty_like(thb)
+            ctx.timing_start(4)
+            ctx.estimate(frame, thb, so2)
+            nodes[flags] = ctx.timing_nodes()
+            ctx.timing_read()
+            outs[flags] = (thb, so2)
+    hl, wl_ = (wl.H + 7) // 8, (wl.W + 7) // 8
+    assert nodes[binding.HB_FULL_GRID] == hl * wl_ * grid["n0"] * grid["n1"]
+    assert 0 < nodes[0] < 0.5 * nodes[binding.HB_FULL_GRID]
+    assert torch.equal(outs[0][0], outs[binding.HB_FULL_GRID][0])
+    assert torch.equal(outs[0][1], outs[binding.HB_FULL_GRID][1])
+
+
+@pytest.mark.parametrize("n0,n1,sigma", [(128, 128, 0.02), (200, 300, 0.005), (64, 16, 0.1), (128, 1, 0.02)])
+def test_support_rows_posterior_alone_matches_full_grid(n0, n1, sigma):
+    """Few pixels (a pixel split over several warps): the row bound changes only how rows
+    are shared out, so both variants agree with the oracle and with each other."""
+    rng = np.random.default_rng(7 * n0 + n1)
+    A = synth.make_mixing(5).A
+    grid = _grid(n0, n1, sigma)
+    c = np.stack([rng.uniform(-20, 170, 200), rng.uniform(-20, 120, 200)], axis=1)
+    yb = c @ A.T + rng.normal(0, 0.01, (200, 3))
+    ref = oracle.posterior_mean(yb, A, grid, nthreads=NTH)
+    got = []
+    for flags in (0, binding.HB_FULL_GRID):
+        with Context(A, grid, 1, 1e-3, 8, 8, "u8", flags) as ctx:
+            out = torch.empty((yb.shape[0], 2), dtype=torch.float32, device=DEV)
+            ctx.posterior_mean(torch.from_numpy(yb).to(DEV), out)
+            torch.cuda.synchronize()
+            got.append(out.cpu().numpy().astype(np.float64))
+    tol = 2e-4 + 2e-6 * np.abs(ref)
+    for g in got:
+        assert np.all(np.abs(g - ref) <= tol)
+    assert np.all(np.abs(got[0] - got[1]) <= tol)
+
+
 @pytest.mark.parametrize("levels", [1, 3])
 def test_all_tikhonov_mode_matches_oracle(levels):
     A, rgb = small_frame(31, 48, 64, "u8", noise=0.01)

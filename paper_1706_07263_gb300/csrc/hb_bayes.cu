@@ -26,8 +26,9 @@ namespace {
 // Posterior mean from the sums, in FP32 (the output is FP32): c = c_ref + h * (sum w d / sum w).
 __device__ __forceinline__ void write_mean(const BayesParams& bp, const BayesRec& rec, long p, float sw, float sdi,
                                            float sdj, float2* chat, float2* chat_scaled, float scale) {
-    const float c0 = fmaf(bp.h0f, sdi / sw, fmaf((float)rec.i0, bp.h0f, bp.lo0f));
-    const float c1 = fmaf(bp.h1f, sdj / sw, fmaf((float)rec.j0, bp.h1f, bp.lo1f));
+    const float inv = __frcp_rn(sw);
+    const float c0 = fmaf(bp.h0f, sdi * inv, fmaf((float)rec.i0, bp.h0f, bp.lo0f));
+    const float c1 = fmaf(bp.h1f, sdj * inv, fmaf((float)rec.j0, bp.h1f, bp.lo1f));
     chat[p] = make_float2(c0, c1);
     if (chat_scaled) chat_scaled[p] = make_float2(c0 * scale, c1 * scale);
 }
@@ -43,7 +44,11 @@ __device__ __forceinline__ void run_unit(const BayesParams& bp, const BayesRec& 
                                          float2* chat_scaled, float scale, unsigned long long& nodes) {
     int lo, hi;
     support_rows(bp, rec, lo, hi);
-    int rb = lo + (int)((long)(hi - lo) * part / rs), re = lo + (int)((long)(hi - lo) * (part + 1) / rs);
+    int rb = lo, re = hi;
+    if (rs > 1) {
+        rb = lo + (hi - lo) * part / rs;
+        re = lo + (hi - lo) * (part + 1) / rs;
+    }
     nodes += (unsigned long long)(re - rb) * (unsigned)bp.n1;
     float shift = 0.f;
     bool whole = rs == 1;  // sums cover the whole pixel
@@ -110,14 +115,17 @@ __global__ void HB_POST_BOUNDS posterior_kernel(BayesParams bp, const BayesRec* 
     // gated launch (fallback of the learned stand-in): run only when the sampled check
     // before this kernel decided so
     if (gate.run && *gate.run == 0u) return;
+    // (rs == 1 unless there are few pixels: the unit index is then the pixel index, and
+    // the 64-bit divisions below are skipped)
     BayesRec next = {0, 0, 0.f, 0.f};
-    if (u < units) next = recs[u / rs];
+    if (u < units) next = recs[rs == 1 ? u : u / rs];
     unsigned long long nodes = 0;
     for (; u < units; u += nw) {
-        const long p = u / rs;
+        const long p = rs == 1 ? u : u / rs;
         const BayesRec rec = next;
-        if (u + nw < units) next = recs[(u + nw) / rs];
-        run_unit<CPL>(bp, rec, p, (int)(u - p * rs), rs, lane, partial, count, chat, chat_scaled, scale, nodes);
+        if (u + nw < units) next = recs[rs == 1 ? u + nw : (u + nw) / rs];
+        run_unit<CPL>(bp, rec, p, rs == 1 ? 0 : (int)(u - p * rs), rs, lane, partial, count, chat, chat_scaled, scale,
+                      nodes);
     }
     if (nodes_out && lane == 0 && nodes) atomicAdd(nodes_out, nodes);
 }

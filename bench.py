@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--stereo-frames", type=int, default=300)
     ap.add_argument("--stereo-pool", type=int, default=6)
+    ap.add_argument("--pulse-frames", type=int, default=300)
     return ap.parse_args()
 
 
@@ -397,6 +398,41 @@ def measure_serving(args, dev):
     return out
 
 
+def measure_pulse(args, dev):
+    """Pulse recovery (Section 3.2 analogue): a stereo pair of pulsing videos (1.25 Hz,
+    360x640 u8, 3 levels, 128x128 grid, 300 frames per eye at 30 frames/s, 12 px
+    disparity), every frame estimated on the GPU; the patch-mean THb trace of each view
+    gives the rate.  Rendering is host-side and outside the timing."""
+    import torch
+    from paper_1706_07263_gb300 import Context, pulse, synth
+    A = synth.make_mixing(3).A
+    grid = dict(n0=128, n1=128, lo0=0.0, hi0=150.0, lo1=0.0, hi1=100.0, sigma_l=0.02)
+    H, W, n, f0 = 360, 640, args.pulse_frames, 1.25
+    out = {"workload": f"2 views x {n} frames of {W}x{H} u8 at 30 frames/s, 3 levels, 128x128 grid, "
+                       f"{f0} Hz pulse, 12 px disparity", "injected_hz": f0}
+    with Context(A, grid, 3, 1e-3, W, H, "u8") as ctx:
+        thb = torch.empty((H, W), dtype=torch.float32, device=dev)
+        so2 = torch.empty_like(thb)
+        for eye, sh in (("left", 0), ("right", 12)):
+            v = synth.pulse_video(11, H, W, A, f_pulse=f0, shift=sh)
+            frames = torch.from_numpy(np.stack([v.frame(k) for k in range(n)])).to(dev)
+            means = torch.empty(n, dtype=torch.float64, device=dev)
+            r0, r1, c0, c1 = 120, 240, 260 + sh, 380 + sh
+            for k in range(3):
+                ctx.estimate(frames[k], thb, so2)
+                means[k] = thb[r0:r1, c0:c1].double().mean()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for k in range(n):
+                ctx.estimate(frames[k], thb, so2)
+                means[k] = thb[r0:r1, c0:c1].double().mean()
+            torch.cuda.synchronize(dev)
+            el = time.perf_counter() - t0
+            trace = means.cpu().numpy()
+            out[eye] = {"rate_hz": pulse.pulse_rate(trace, v.fps), "frames_per_s_with_patch_mean": n / el}
+    return out
+
+
 def measure_stereo(args, dev):
     """Stereo video: two 1920x1080 float streams; each frame copied host->device on a copy
     stream while the previous frame is estimated on the compute stream."""
@@ -603,6 +639,7 @@ def run_ours(args):
         line["surrogate"] = measure_surrogate(args, dev, flush, oracle_out)
         line["serving"] = measure_serving(args, dev)
         line["stereo_stream"] = measure_stereo(args, dev)
+        line["pulse_recovery"] = measure_pulse(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

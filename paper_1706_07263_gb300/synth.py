@@ -170,3 +170,65 @@ def grid_spec(wl: Workload):
     """Grid dictionary: inclusive linspace nodes over the concentration box."""
     return dict(n0=wl.grid[0], n1=wl.grid[1], lo0=BOX_HBO2[0], hi0=BOX_HBO2[1],
                 lo1=BOX_HB[0], hi1=BOX_HB[1], sigma_l=wl.sigma_l)
+
+
+# ---------------------------------------------------------------------------------------------
+# Pulsing video (the stand-in for the tongue video of Section 3.2, whose total haemoglobin
+# shows the heart rate): static smooth fields whose concentrations, inside a soft tissue patch,
+# are scaled by 1 + depth * sin(2 pi f t + phase); every frame adds sensor noise and a small
+# global illumination jitter (a per-frame intensity factor), which makes the per-frame THb
+# trace noisy the way the paper's trace is.
+# ---------------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class PulseVideo:
+    A: np.ndarray
+    H: int
+    W: int
+    fps: float
+    f_pulse: float         # Hz
+    depth: float           # relative modulation of both concentrations at the patch centre
+    phase: float
+    hbo2: np.ndarray       # (H, W) static fields, uM
+    hb: np.ndarray
+    window: np.ndarray     # (H, W) modulation weight in [0, 1]
+    noise: float
+    jitter: float          # standard deviation of the per-frame intensity factor
+    fmt: str
+    seed: int
+    shift: int = 0         # horizontal disparity of this view, px (stereo pairs)
+
+    def fields(self, k: int):
+        """Ground-truth (HbO2, Hb) of frame k."""
+        s = 1.0 + self.depth * np.sin(2.0 * np.pi * self.f_pulse * k / self.fps + self.phase) * self.window
+        return self.hbo2 * s, self.hb * s
+
+    def frame(self, k: int) -> np.ndarray:
+        rng = np.random.default_rng((self.seed, self.shift, k))
+        hbo2, hb = self.fields(k)
+        att = hbo2[..., None] * self.A[:, 0] + hb[..., None] * self.A[:, 1]
+        I = np.exp(-att) * (1.0 + self.jitter * rng.standard_normal())
+        if self.noise > 0:
+            I = I + rng.normal(0.0, self.noise, I.shape)
+        if self.shift:
+            I = np.roll(I, self.shift, axis=1)
+        if self.fmt == "u8":
+            return np.rint(255.0 * np.clip(I, 0.0, 1.0)).astype(np.uint8)
+        return I.astype(np.float32)
+
+
+def pulse_video(seed: int, H: int, W: int, A: np.ndarray, fps: float = 30.0, f_pulse: float = 1.25,
+                depth: float = 0.03, nblobs: int = 8, noise: float = 0.01, jitter: float = 0.004,
+                fmt: str = "u8", shift: int = 0) -> PulseVideo:
+    """A pulsing video (see above).  The blobs are sized to the frame (sigma W/12..W/4) and
+    the tissue patch is a Gaussian window at the frame centre with sigma min(H, W) / 4."""
+    rng = np.random.default_rng(seed)
+    hbo2, hb, _ = make_fields(rng, H, W, nblobs, W / 12.0, W / 4.0)
+    # keep clear of the box edges so that the modulation stays inside the prior's support
+    hbo2 = 20.0 + 0.7 * hbo2
+    hb = 10.0 + 0.7 * hb
+    ys = np.arange(H) - (H - 1) / 2.0
+    xs = np.arange(W) - (W - 1) / 2.0
+    sg = min(H, W) / 4.0
+    window = np.outer(np.exp(-0.5 * (ys / sg) ** 2), np.exp(-0.5 * (xs / sg) ** 2))
+    phase = float(rng.uniform(0.0, 2.0 * np.pi))
+    return PulseVideo(A, H, W, fps, f_pulse, depth, phase, hbo2, hb, window, noise, jitter, fmt, seed, shift)

@@ -52,9 +52,11 @@ def _load():
         lib.hbo_haar_level_inv.argtypes = [D, D, D, D, i, i, i, D]
         lib.hbo_tikhonov_operator.argtypes = [D, d, i, D]
         lib.hbo_tikhonov_operator.restype = d
-        lib.hbo_posterior_mean.argtypes = [D, D, i, i, d, d, d, d, d, D]
-        lib.hbo_posterior_mean_many.argtypes = [D, l, D, i, i, d, d, d, d, d, i, D]
-        lib.hbo_estimate.argtypes = [V, i, i, i, l, D, d, i, i, i, d, d, d, d, d, i, i, i,
+        lib.hbo_tikhonov_operator_illum.argtypes = [D, d, i, D]
+        lib.hbo_tikhonov_operator_illum.restype = d
+        lib.hbo_posterior_mean.argtypes = [D, D, i, i, d, d, d, d, d, i, D]
+        lib.hbo_posterior_mean_many.argtypes = [D, l, D, i, i, d, d, d, d, d, i, i, D]
+        lib.hbo_estimate.argtypes = [V, i, i, i, l, D, d, i, i, i, d, d, d, d, d, i, i, i, i,
                                      D, D, D, D, D, D]
         lib.hbo_estimate.restype = i
         _lib = lib
@@ -126,29 +128,33 @@ def haar_inverse(ll: np.ndarray, details) -> np.ndarray:
     return cur
 
 
-def tikhonov_operator(A: np.ndarray, lam: float, relative: bool = True):
-    """Returns (M 2x3, gamma)."""
+def tikhonov_operator(A: np.ndarray, lam: float, relative: bool = True, illumination: bool = False):
+    """Returns (M 2x3, gamma); illumination: with the constant column of Eq. 8."""
     A = _f64(A).reshape(3, 2)
     M = np.empty((2, 3))
-    g = _load().hbo_tikhonov_operator(_p(A), float(lam), int(relative), _p(M))
+    fn = _load().hbo_tikhonov_operator_illum if illumination else _load().hbo_tikhonov_operator
+    g = fn(_p(A), float(lam), int(relative), _p(M))
     return M, g
 
 
-def posterior_mean(ybar: np.ndarray, A: np.ndarray, grid: dict, nthreads: int = 1) -> np.ndarray:
-    """Posterior mean (HbO2, Hb) for each row of ybar (..., 3)."""
+def posterior_mean(ybar: np.ndarray, A: np.ndarray, grid: dict, nthreads: int = 1,
+                   illumination: bool = False) -> np.ndarray:
+    """Posterior mean (HbO2, Hb) for each row of ybar (..., 3); illumination: with the
+    constant term of Eq. 8 integrated out."""
     yb = _f64(ybar)
     shape = yb.shape[:-1]
     yb = yb.reshape(-1, 3)
     A = _f64(A).reshape(3, 2)
     out = np.empty((yb.shape[0], 2))
     _load().hbo_posterior_mean_many(_p(yb), yb.shape[0], _p(A), grid["n0"], grid["n1"], grid["lo0"], grid["hi0"],
-                                    grid["lo1"], grid["hi1"], grid["sigma_l"], nthreads, _p(out))
+                                    grid["lo1"], grid["hi1"], grid["sigma_l"], int(illumination), nthreads, _p(out))
     return out.reshape(shape + (2,))
 
 
 def estimate(frame: np.ndarray, A: np.ndarray, grid: dict, levels: int, lam: float, relative: bool = True,
-             lowpass: str = "bayes", nthreads: int = 1) -> dict:
-    """Whole estimator on one HWC frame (uint8 codes or float32 intensities).
+             lowpass: str = "bayes", nthreads: int = 1, illumination: bool = False) -> dict:
+    """Whole estimator on one HWC frame (uint8 codes or float32 intensities); illumination:
+    with the constant (illumination) term of Eq. 8.
 
     Returns a dict of float64 arrays: hbo2, hb, thb, so2 (H, W); ybar_ll
     (hl, wl, 3); conc_ll (hl, wl, 2)."""
@@ -164,7 +170,7 @@ def estimate(frame: np.ndarray, A: np.ndarray, grid: dict, levels: int, lam: flo
     A = _f64(A).reshape(3, 2)
     rc = _load().hbo_estimate(fr.ctypes.data, FMT[fmt], H, W, fr.strides[0], _p(A), float(lam), int(relative),
                               grid["n0"], grid["n1"], grid["lo0"], grid["hi0"], grid["lo1"], grid["hi1"],
-                              grid["sigma_l"], levels, 0 if lowpass == "bayes" else 1, nthreads,
+                              grid["sigma_l"], levels, 0 if lowpass == "bayes" else 1, int(illumination), nthreads,
                               _p(out["hbo2"]), _p(out["hb"]), _p(out["thb"]), _p(out["so2"]),
                               _p(out["ybar_ll"]), _p(out["conc_ll"]))
     if rc != 0:

@@ -151,34 +151,83 @@ double hbo_tikhonov_operator(const double *A, double lambda, int relative, doubl
     return gamma;
 }
 
+/* The same operator with the constant column of Eq. 8 ("a constant term ... to account
+ * for global illumination changes"): xi = [A | 1] (3x3), M3 = (xi^T xi + gamma I)^-1 xi^T,
+ * and M = its HbO2 and Hb rows (the constant's row is dropped).  Gamma follows the same
+ * rule as above, from A alone.  The 3x3 inverse is the adjugate over the determinant.
+ * Returns gamma. */
+double hbo_tikhonov_operator_illum(const double *A, double lambda, int relative, double *M) {
+    double xi[3][3];
+    for (int c = 0; c < 3; ++c) {
+        xi[c][0] = A[c * 2 + 0];
+        xi[c][1] = A[c * 2 + 1];
+        xi[c][2] = 1.0;
+    }
+    double R[3][3];
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) {
+            double s = 0.0;
+            for (int c = 0; c < 3; ++c) s += xi[c][j] * xi[c][k];
+            R[j][k] = s;
+        }
+    double gamma = relative ? lambda * (R[0][0] + R[1][1]) / 2.0 : lambda;
+    for (int j = 0; j < 3; ++j) R[j][j] += gamma;
+    double adj[3][3];
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) {
+            /* cofactor of R[k][j] (transposed into the adjugate) */
+            int r0 = (k + 1) % 3, r1 = (k + 2) % 3, c0 = (j + 1) % 3, c1 = (j + 2) % 3;
+            adj[j][k] = R[r0][c0] * R[r1][c1] - R[r0][c1] * R[r1][c0];
+        }
+    double det = R[0][0] * adj[0][0] + R[0][1] * adj[1][0] + R[0][2] * adj[2][0];
+    for (int j = 0; j < 2; ++j)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += adj[j][k] * xi[c][k];
+            M[j * 3 + c] = s / det;
+        }
+    return gamma;
+}
+
 /* ---------------------------------------------------------------- step 5 */
 /* Posterior mean of c = (HbO2, Hb) over the inclusive grid
  *   c_ij = (lo0 + i (hi0-lo0)/(n0-1), lo1 + j (hi1-lo1)/(n1-1)),
  * flat prior, Gaussian likelihood  L_ij = -|ybar - A c_ij|^2 / (2 sigma^2)
- * evaluated as the direct residual.  Weights exp(L_ij - max L). */
+ * evaluated as the direct residual.  Weights exp(L_ij - max L).
+ * illum: the model carries the constant term of Eq. 8, ybar = A c + kappa (1,1,1), with a
+ * flat prior on kappa.  For each node the best kappa is the mean of the residual, and
+ * integrating kappa out leaves the likelihood of the residual minus its mean (up to a
+ * factor that is the same for every node), which is what is evaluated. */
 static double grid_node(int i, int n, double lo, double hi) { return n > 1 ? lo + (hi - lo) * (double)i / (double)(n - 1) : lo; }
 
+static double residual2(const double *ybar, const double *A, double c0, double c1, int illum) {
+    double r[3], m = 0.0, r2 = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+        r[ch] = ybar[ch] - A[ch * 2 + 0] * c0 - A[ch * 2 + 1] * c1;
+        m += r[ch] / 3.0;
+    }
+    for (int ch = 0; ch < 3; ++ch) {
+        double e = illum ? r[ch] - m : r[ch];
+        r2 += e * e;
+    }
+    return r2;
+}
+
 void hbo_posterior_mean(const double *ybar, const double *A, int n0, int n1, double lo0, double hi0, double lo1,
-                        double hi1, double sigma, double *out) {
+                        double hi1, double sigma, int illum, double *out) {
     double Lmax = -INFINITY;
     for (int i = 0; i < n0; ++i)
         for (int j = 0; j < n1; ++j) {
-            double c0 = grid_node(i, n0, lo0, hi0), c1 = grid_node(j, n1, lo1, hi1), r2 = 0.0;
-            for (int ch = 0; ch < 3; ++ch) {
-                double r = ybar[ch] - A[ch * 2 + 0] * c0 - A[ch * 2 + 1] * c1;
-                r2 += r * r;
-            }
+            double c0 = grid_node(i, n0, lo0, hi0), c1 = grid_node(j, n1, lo1, hi1);
+            double r2 = residual2(ybar, A, c0, c1, illum);
             double L = -r2 / (2.0 * sigma * sigma);
             if (L > Lmax) Lmax = L;
         }
     double sw = 0.0, s0 = 0.0, s1 = 0.0;
     for (int i = 0; i < n0; ++i)
         for (int j = 0; j < n1; ++j) {
-            double c0 = grid_node(i, n0, lo0, hi0), c1 = grid_node(j, n1, lo1, hi1), r2 = 0.0;
-            for (int ch = 0; ch < 3; ++ch) {
-                double r = ybar[ch] - A[ch * 2 + 0] * c0 - A[ch * 2 + 1] * c1;
-                r2 += r * r;
-            }
+            double c0 = grid_node(i, n0, lo0, hi0), c1 = grid_node(j, n1, lo1, hi1);
+            double r2 = residual2(ybar, A, c0, c1, illum);
             double w = exp(-r2 / (2.0 * sigma * sigma) - Lmax);
             sw += w;
             s0 += w * c0;
@@ -194,6 +243,7 @@ typedef struct {
     const double *A;
     int n0, n1;
     double lo0, hi0, lo1, hi1, sigma;
+    int illum;
     long begin, end;
     double *out;
 } post_job;
@@ -201,19 +251,19 @@ typedef struct {
 static void *post_worker(void *arg) {
     post_job *j = (post_job *)arg;
     for (long p = j->begin; p < j->end; ++p)
-        hbo_posterior_mean(j->ybar + 3 * p, j->A, j->n0, j->n1, j->lo0, j->hi0, j->lo1, j->hi1, j->sigma,
+        hbo_posterior_mean(j->ybar + 3 * p, j->A, j->n0, j->n1, j->lo0, j->hi0, j->lo1, j->hi1, j->sigma, j->illum,
                            j->out + 2 * p);
     return NULL;
 }
 
 void hbo_posterior_mean_many(const double *ybar, long npix, const double *A, int n0, int n1, double lo0,
-                             double hi0, double lo1, double hi1, double sigma, int nthreads, double *out) {
+                             double hi0, double lo1, double hi1, double sigma, int illum, int nthreads, double *out) {
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     pthread_t th[256];
     post_job jobs[256];
     for (int t = 0; t < nthreads; ++t) {
-        jobs[t] = (post_job){ybar, A, n0, n1, lo0, hi0, lo1, hi1, sigma,
+        jobs[t] = (post_job){ybar, A, n0, n1, lo0, hi0, lo1, hi1, sigma, illum,
                              npix * t / nthreads, npix * (t + 1) / nthreads, out};
     }
     if (nthreads == 1) {
@@ -227,7 +277,9 @@ void hbo_posterior_mean_many(const double *ybar, long npix, const double *A, int
 /* ---------------------------------------------------------------- whole estimator */
 /* Runs steps 1..7 on one frame.  lowpass_mode 0 = Bayesian on the low pass
  * (the proposed method), 1 = Tikhonov on the low pass as well (the
- * all-Tikhonov comparison of Table 1).  levels = 0 means no decomposition:
+ * all-Tikhonov comparison of Table 1).  illum = 1 adds the constant
+ * (illumination) term of Eq. 8 to both the Tikhonov operator and the posterior.
+ * levels = 0 means no decomposition:
  * the Bayesian estimate on every pixel (the full-resolution comparison).
  * Outputs (each may be NULL): hbo2, hb, thb, so2 (H*W); ybar_ll ((Hp>>n)*(Wp>>n)*3,
  * the low-pass band divided by 2^n); conc_ll ((Hp>>n)*(Wp>>n)*2, concentration
@@ -235,8 +287,8 @@ void hbo_posterior_mean_many(const double *ybar, long npix, const double *A, int
  * arguments / allocation failure. */
 int hbo_estimate(const void *frame, int fmt, int H, int W, long row_stride_bytes, const double *A, double lambda,
                  int lambda_relative, int n0, int n1, double lo0, double hi0, double lo1, double hi1,
-                 double sigma, int levels, int lowpass_mode, int nthreads, double *hbo2, double *hb, double *thb,
-                 double *so2, double *ybar_ll, double *conc_ll) {
+                 double sigma, int levels, int lowpass_mode, int illum, int nthreads, double *hbo2, double *hb,
+                 double *thb, double *so2, double *ybar_ll, double *conc_ll) {
     if (H <= 0 || W <= 0 || levels < 0 || levels > 6 || n0 < 1 || n1 < 1 || sigma <= 0) return -1;
     if (levels == 0 && lowpass_mode != 0) return -1;
     const double eps = fmt == HBO_FMT_U8 ? 1.0 / 255.0 : 1e-6;
@@ -244,7 +296,10 @@ int hbo_estimate(const void *frame, int fmt, int H, int W, long row_stride_bytes
     const int Hp = (H + blk - 1) / blk * blk, Wp = (W + blk - 1) / blk * blk;
     const int hl = Hp >> levels, wl = Wp >> levels;
     double M[6];
-    hbo_tikhonov_operator(A, lambda, lambda_relative, M);
+    if (illum)
+        hbo_tikhonov_operator_illum(A, lambda, lambda_relative, M);
+    else
+        hbo_tikhonov_operator(A, lambda, lambda_relative, M);
 
     double *y = malloc(sizeof(double) * (size_t)H * W * 3);
     double *yp = malloc(sizeof(double) * (size_t)Hp * Wp * 3);
@@ -293,7 +348,7 @@ int hbo_estimate(const void *frame, int fmt, int H, int W, long row_stride_bytes
         double scale = (double)blk; /* 2^n */
         for (size_t p = 0; p < (size_t)hl * wl * 3; ++p) yb[p] = cur[p] / scale;
         if (lowpass_mode == 0) {
-            hbo_posterior_mean_many(yb, (long)hl * wl, A, n0, n1, lo0, hi0, lo1, hi1, sigma, nthreads, cll);
+            hbo_posterior_mean_many(yb, (long)hl * wl, A, n0, n1, lo0, hi0, lo1, hi1, sigma, illum, nthreads, cll);
         } else {
             for (size_t p = 0; p < (size_t)hl * wl; ++p)
                 for (int j = 0; j < 2; ++j) {

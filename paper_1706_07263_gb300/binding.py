@@ -32,6 +32,7 @@ EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_es
             "hb_server_create", "hb_server_destroy", "hb_stream_open", "hb_stream_close", "hb_submit", "hb_poll",
             "hb_release", "hb_server_pause", "hb_server_stats", "hb_posterior_mean_static")
 HB_FULL_GRID = 1 << 2
+HB_ILLUMINATION = 1 << 5
 HB_SERVE_SEQUENTIAL = 1 << 4
 MLP_NPARAMS = 4546
 HB_MODE_BAYES = 0

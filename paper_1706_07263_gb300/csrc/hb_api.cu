@@ -84,18 +84,54 @@ size_t elem_size(int fmt) { return fmt == HB_IN_U8_HWC ? 1 : 4; }
 
 // Operator of Eq. 5 and the grid constants, in FP64.
 void prepare(hb_ctx* c, const hb_mixing* mix, const hb_grid* g, double lambda) {
-    const double(*A)[2] = mix->A;
+    const double(*Ain)[2] = mix->A;
     double G[2][2];
     for (int j = 0; j < 2; ++j)
-        for (int k = 0; k < 2; ++k) G[j][k] = A[0][j] * A[0][k] + A[1][j] * A[1][k] + A[2][j] * A[2][k];
+        for (int k = 0; k < 2; ++k) G[j][k] = Ain[0][j] * Ain[0][k] + Ain[1][j] * Ain[1][k] + Ain[2][j] * Ain[2][k];
     c->gamma = (c->flags & HB_LAMBDA_ABSOLUTE) ? lambda : lambda * (G[0][0] + G[1][1]) / 2.0;
-    const double R00 = G[0][0] + c->gamma, R11 = G[1][1] + c->gamma, R01 = G[0][1];
-    const double det = R00 * R11 - R01 * R01;
-    for (int ch = 0; ch < 3; ++ch) {
-        c->tp.M[0 * 3 + ch] = (float)((R11 * A[ch][0] - R01 * A[ch][1]) / det);
-        c->tp.M[1 * 3 + ch] = (float)((-R01 * A[ch][0] + R00 * A[ch][1]) / det);
+    if (!(c->flags & HB_ILLUMINATION)) {
+        const double R00 = G[0][0] + c->gamma, R11 = G[1][1] + c->gamma, R01 = G[0][1];
+        const double det = R00 * R11 - R01 * R01;
+        for (int ch = 0; ch < 3; ++ch) {
+            c->tp.M[0 * 3 + ch] = (float)((R11 * Ain[ch][0] - R01 * Ain[ch][1]) / det);
+            c->tp.M[1 * 3 + ch] = (float)((-R01 * Ain[ch][0] + R00 * Ain[ch][1]) / det);
+        }
+    } else {
+        // xi = [A | 1]: the HbO2 and Hb rows of (xi^T xi + gamma I)^-1 xi^T (Eq. 8's constant term)
+        double xi[3][3], R[3][3], Ri[3][3];
+        for (int ch = 0; ch < 3; ++ch) {
+            xi[ch][0] = Ain[ch][0];
+            xi[ch][1] = Ain[ch][1];
+            xi[ch][2] = 1.0;
+        }
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
+                R[j][k] = xi[0][j] * xi[0][k] + xi[1][j] * xi[1][k] + xi[2][j] * xi[2][k] + (j == k ? c->gamma : 0.0);
+        const double det = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) -
+                           R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
+                           R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) {
+                const int a0 = (k + 1) % 3, a1 = (k + 2) % 3, b0 = (j + 1) % 3, b1 = (j + 2) % 3;
+                Ri[j][k] = (R[a0][b0] * R[a1][b1] - R[a0][b1] * R[a1][b0]) / det;
+            }
+        for (int j = 0; j < 2; ++j)
+            for (int ch = 0; ch < 3; ++ch)
+                c->tp.M[j * 3 + ch] = (float)(Ri[j][0] * xi[ch][0] + Ri[j][1] * xi[ch][1] + Ri[j][2] * xi[ch][2]);
     }
+    // The posterior's mixing matrix.  With the illumination term the likelihood after
+    // integrating kappa out is that of P (ybar - A c), P = I - (1,1,1)(1,1,1)^T / 3; using
+    // P A in place of A gives it exactly, since the part of ybar along (1,1,1) is the same
+    // for every node and cancels from the weights relative to the reference node.
+    double A[3][2];
+    for (int j = 0; j < 2; ++j) {
+        const double m = (c->flags & HB_ILLUMINATION) ? (Ain[0][j] + Ain[1][j] + Ain[2][j]) / 3.0 : 0.0;
+        for (int ch = 0; ch < 3; ++ch) A[ch][j] = Ain[ch][j] - m;
+    }
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) G[j][k] = A[0][j] * A[0][k] + A[1][j] * A[1][k] + A[2][j] * A[2][k];
     BayesParams& bp = c->bp;
+    bp.illum = (c->flags & HB_ILLUMINATION) ? 1 : 0;
     bp.n0 = g->n0;
     bp.n1 = g->n1;
     bp.lo0 = g->lo0;
@@ -307,7 +343,8 @@ hb_status hb_create(const hb_mixing* mix, const hb_grid* grid, int levels, doubl
     *out = nullptr;
     if (!mix || !grid) return HB_ERR_ARG;
     if (in_format != HB_IN_F32_HWC && in_format != HB_IN_U8_HWC) return HB_ERR_ARG;
-    if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_LOWPASS_TIKHONOV | HB_FULL_GRID)) return HB_ERR_ARG;
+    if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_LOWPASS_TIKHONOV | HB_FULL_GRID | HB_ILLUMINATION))
+        return HB_ERR_ARG;
     if (width <= 0 || height <= 0 || levels < 0 || levels > hb::kMaxLevels) return HB_ERR_SHAPE;
     if (grid->n0 < 1 || grid->n1 < 1 || !(grid->hi0 >= grid->lo0) || !(grid->hi1 >= grid->lo1) ||
         !(grid->sigma_l > 0.0))
@@ -768,7 +805,7 @@ hb_status hb_set_lowpass_mode(hb_ctx* c, int mode, double tol, int nsample) {
     if (mode == HB_MODE_MLP) {
         if (!(tol >= 0.0) || nsample < 1) return HB_ERR_ARG;
         if (!c->mlp_ready) return HB_ERR_STATE;
-        if (c->flags & HB_LOWPASS_TIKHONOV) return HB_ERR_STATE;
+        if (c->flags & (HB_LOWPASS_TIKHONOV | HB_ILLUMINATION)) return HB_ERR_STATE;
         if (nsample > c->mlp_err_cap) {
             DeviceGuard g(c->device);
             cudaFree(c->d_err);

@@ -54,6 +54,7 @@ struct BayesParams {
     float sup_inv_alpha;      // 0.5 / (-sup_alpha)
     float sup_inv_aq;         // 0.5 / Aq
     float sup_inv_k1;         // 1 / (-sup_r) where the edge-column pieces apply, else 0
+    int illum;                // 1: A holds (I - 11^T/3) A and the set-up removes ybar's channel mean
 };
 constexpr float kSupportCut = 150.f;
 

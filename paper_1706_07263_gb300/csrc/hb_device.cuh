@@ -34,9 +34,25 @@ __device__ __forceinline__ void dd_sub(float& hi, float& lo, float bh, float bl)
     lo = e - (hi - s);
 }
 
+// With the illumination term the block mean minus its channel mean, (I - 11^T / 3) ybar,
+// in double-float: the part along (1,1,1) cancels from the posterior, and removing it
+// here keeps the residual -- and so the rounding of U and V -- as small as without the
+// term (the posterior is much broader then, so its mean is that much more sensitive).
+__device__ __forceinline__ void dd_remove_mean(float (&hi)[3], float (&lo)[3]) {
+    float sh = hi[0], sl = lo[0];
+    dd_sub(sh, sl, -hi[1], -lo[1]);
+    dd_sub(sh, sl, -hi[2], -lo[2]);
+    const float mh = sh * (1.f / 3.f);
+    const float ml = (fmaf(-3.f, mh, sh) + sl) * (1.f / 3.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dd_sub(hi[c], lo[c], mh, ml);
+}
+
 }  // namespace detail
 
-__device__ __forceinline__ BayesRec bayes_setup(const float yhi[3], const float ylo[3], const BayesParams& bp) {
+__device__ __forceinline__ BayesRec bayes_setup(const float yhi_in[3], const float ylo_in[3], const BayesParams& bp) {
+    float yhi[3] = {yhi_in[0], yhi_in[1], yhi_in[2]}, ylo[3] = {ylo_in[0], ylo_in[1], ylo_in[2]};
+    if (bp.illum) detail::dd_remove_mean(yhi, ylo);
     const float y0 = yhi[0] + ylo[0], y1 = yhi[1] + ylo[1], y2 = yhi[2] + ylo[2];
     const float z0 = bp.Af[0] * y0 + bp.Af[2] * y1 + bp.Af[4] * y2;
     const float z1 = bp.Af[1] * y0 + bp.Af[3] * y1 + bp.Af[5] * y2;

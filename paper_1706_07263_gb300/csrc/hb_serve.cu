@@ -248,7 +248,8 @@ hb_status hb_server_create(const hb_mixing* mix, const hb_grid* grid, double lam
     *out = nullptr;
     if (!mix || !grid) return HB_ERR_ARG;
     if (in_format != HB_IN_F32_HWC && in_format != HB_IN_U8_HWC) return HB_ERR_ARG;
-    if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_FULL_GRID | HB_SERVE_SEQUENTIAL)) return HB_ERR_ARG;
+    if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_FULL_GRID | HB_ILLUMINATION | HB_SERVE_SEQUENTIAL))
+        return HB_ERR_ARG;
     if (max_batch < 1 || max_batch > hb::kMaxBatchJobs || batch_lowpass_pixels < 1) return HB_ERR_ARG;
     if (grid->n0 < 1 || grid->n1 < 1 || !(grid->hi0 >= grid->lo0) || !(grid->hi1 >= grid->lo1) ||
         !(grid->sigma_l > 0.0))
@@ -266,7 +267,8 @@ hb_status hb_server_create(const hb_mixing* mix, const hb_grid* grid, double lam
     srv->max_batch = max_batch;
     srv->cap_ll = batch_lowpass_pixels;
     srv->nbatch_slots = (flags & HB_SERVE_SEQUENTIAL) ? 1 : 2;
-    hb::prepare_constants(mix, grid, lambda, flags & (HB_LAMBDA_ABSOLUTE | HB_FULL_GRID), srv->M, srv->bp);
+    hb::prepare_constants(mix, grid, lambda, flags & (HB_LAMBDA_ABSOLUTE | HB_FULL_GRID | HB_ILLUMINATION), srv->M,
+                          srv->bp);
     const size_t need = 2 * batch_bytes(srv->cap_ll) + 256 * sizeof(float2);
     if (need > budget_bytes) {
         delete srv;

@@ -80,10 +80,14 @@ enum {
     HB_FULL_GRID = 1u << 2,        /* posterior enumerates every grid node; by default the rows whose
                                       every weight is exactly zero in FP32 (below 2^-150 relative to
                                       the reference node) are skipped, which leaves the sums unchanged */
-    HB_ILLUMINATION = 1u << 5      /* the constant term of Eq. 8 (global illumination): the Tikhonov
+    HB_ILLUMINATION = 1u << 5,     /* the constant term of Eq. 8 (global illumination): the Tikhonov
                                       operator solves over xi = [A | 1] and keeps the HbO2 and Hb rows;
                                       the posterior integrates a per-pixel offset kappa (1,1,1) out
                                       under a flat prior.  Not with the learned low pass. */
+    HB_LOWPASS_INTENSITY = 1u << 6 /* Eq. 3-8 literally for the low pass: the posterior sees
+                                      -log(block mean of the intensities) instead of the block mean of
+                                      -log I (directional bands unchanged).  Levels 0..4; not with
+                                      HB_LOWPASS_TIKHONOV nor the learned low pass. */
 };
 
 /* Per-stage timing slots reported by hb_timing_read. */
@@ -241,7 +245,8 @@ typedef struct {
 
 enum { HB_SERVE_SEQUENTIAL = 1u << 4 }; /* one frame at a time, one batch in flight (baseline) */
 
-/* Create a server.  flags: HB_LAMBDA_ABSOLUTE, HB_FULL_GRID, HB_ILLUMINATION, HB_SERVE_SEQUENTIAL.  budget_bytes bounds
+/* Create a server.  flags: HB_LAMBDA_ABSOLUTE, HB_FULL_GRID, HB_ILLUMINATION, HB_LOWPASS_INTENSITY,
+ * HB_SERVE_SEQUENTIAL.  budget_bytes bounds
  * the device memory of all stream slots plus the two batches' scratch (sized for
  * batch_lowpass_pixels low-pass pixels each); max_batch (1..64) bounds frames per batch.
  * HB_ERR_BUDGET if the scratch alone exceeds the budget.  Starts the request loop. */

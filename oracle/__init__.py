@@ -56,7 +56,7 @@ def _load():
         lib.hbo_tikhonov_operator_illum.restype = d
         lib.hbo_posterior_mean.argtypes = [D, D, i, i, d, d, d, d, d, i, D]
         lib.hbo_posterior_mean_many.argtypes = [D, l, D, i, i, d, d, d, d, d, i, i, D]
-        lib.hbo_estimate.argtypes = [V, i, i, i, l, D, d, i, i, i, d, d, d, d, d, i, i, i, i,
+        lib.hbo_estimate.argtypes = [V, i, i, i, l, D, d, i, i, i, d, d, d, d, d, i, i, i, i, i,
                                      D, D, D, D, D, D]
         lib.hbo_estimate.restype = i
         _lib = lib
@@ -152,9 +152,11 @@ def posterior_mean(ybar: np.ndarray, A: np.ndarray, grid: dict, nthreads: int = 
 
 
 def estimate(frame: np.ndarray, A: np.ndarray, grid: dict, levels: int, lam: float, relative: bool = True,
-             lowpass: str = "bayes", nthreads: int = 1, illumination: bool = False) -> dict:
+             lowpass: str = "bayes", nthreads: int = 1, illumination: bool = False,
+             intensity_lowpass: bool = False) -> dict:
     """Whole estimator on one HWC frame (uint8 codes or float32 intensities); illumination:
-    with the constant (illumination) term of Eq. 8.
+    with the constant (illumination) term of Eq. 8; intensity_lowpass: the low pass is -log
+    of the block mean of the intensities (Eq. 3-8 literally).
 
     Returns a dict of float64 arrays: hbo2, hb, thb, so2 (H, W); ybar_ll
     (hl, wl, 3); conc_ll (hl, wl, 2)."""
@@ -170,7 +172,8 @@ def estimate(frame: np.ndarray, A: np.ndarray, grid: dict, levels: int, lam: flo
     A = _f64(A).reshape(3, 2)
     rc = _load().hbo_estimate(fr.ctypes.data, FMT[fmt], H, W, fr.strides[0], _p(A), float(lam), int(relative),
                               grid["n0"], grid["n1"], grid["lo0"], grid["hi0"], grid["lo1"], grid["hi1"],
-                              grid["sigma_l"], levels, 0 if lowpass == "bayes" else 1, int(illumination), nthreads,
+                              grid["sigma_l"], levels, 0 if lowpass == "bayes" else 1, int(illumination),
+                              int(intensity_lowpass), nthreads,
                               _p(out["hbo2"]), _p(out["hb"]), _p(out["thb"]), _p(out["so2"]),
                               _p(out["ybar_ll"]), _p(out["conc_ll"]))
     if rc != 0:

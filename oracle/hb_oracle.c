@@ -60,6 +60,19 @@ void hbo_log_atten(const void *frame, int fmt, int H, int W, long row_stride_byt
     }
 }
 
+/* The floored intensities max(I, eps) themselves (for the intensity-domain low pass of
+ * Eq. 3-8, where the transform is applied to I and the logarithm taken after it). */
+void hbo_intensity(const void *frame, int fmt, int H, int W, long row_stride_bytes, double eps, double *out) {
+    for (int r = 0; r < H; ++r) {
+        const unsigned char *row = (const unsigned char *)frame + (long)r * row_stride_bytes;
+        for (int c = 0; c < W; ++c)
+            for (int ch = 0; ch < 3; ++ch) {
+                double I = fmt == HBO_FMT_U8 ? (double)row[c * 3 + ch] / 255.0 : (double)((const float *)row)[c * 3 + ch];
+                out[((long)r * W + c) * 3 + ch] = I < eps ? eps : I;
+            }
+    }
+}
+
 /* ---------------------------------------------------------------- step 2 */
 /* Edge replication: pixel (r, c) of the padded image is pixel
  * (min(r, H-1), min(c, W-1)) of the input. */
@@ -279,6 +292,8 @@ void hbo_posterior_mean_many(const double *ybar, long npix, const double *A, int
  * (the proposed method), 1 = Tikhonov on the low pass as well (the
  * all-Tikhonov comparison of Table 1).  illum = 1 adds the constant
  * (illumination) term of Eq. 8 to both the Tikhonov operator and the posterior.
+ * ll_intensity = 1 takes the low pass of Eq. 3-8 literally: -log of the low pass of the
+ * intensities (their block mean) instead of the low pass of -log I.
  * levels = 0 means no decomposition:
  * the Bayesian estimate on every pixel (the full-resolution comparison).
  * Outputs (each may be NULL): hbo2, hb, thb, so2 (H*W); ybar_ll ((Hp>>n)*(Wp>>n)*3,
@@ -287,10 +302,11 @@ void hbo_posterior_mean_many(const double *ybar, long npix, const double *A, int
  * arguments / allocation failure. */
 int hbo_estimate(const void *frame, int fmt, int H, int W, long row_stride_bytes, const double *A, double lambda,
                  int lambda_relative, int n0, int n1, double lo0, double hi0, double lo1, double hi1,
-                 double sigma, int levels, int lowpass_mode, int illum, int nthreads, double *hbo2, double *hb,
-                 double *thb, double *so2, double *ybar_ll, double *conc_ll) {
+                 double sigma, int levels, int lowpass_mode, int illum, int ll_intensity, int nthreads,
+                 double *hbo2, double *hb, double *thb, double *so2, double *ybar_ll, double *conc_ll) {
     if (H <= 0 || W <= 0 || levels < 0 || levels > 6 || n0 < 1 || n1 < 1 || sigma <= 0) return -1;
     if (levels == 0 && lowpass_mode != 0) return -1;
+    if (ll_intensity && lowpass_mode != 0) return -1;
     const double eps = fmt == HBO_FMT_U8 ? 1.0 / 255.0 : 1e-6;
     const int blk = 1 << levels;
     const int Hp = (H + blk - 1) / blk * blk, Wp = (W + blk - 1) / blk * blk;
@@ -344,9 +360,41 @@ int hbo_estimate(const void *frame, int fmt, int H, int W, long row_stride_bytes
     double *cll = ok ? malloc(sizeof(double) * (size_t)hl * wl * 2) : NULL;
     double *yb = ok ? malloc(sizeof(double) * (size_t)hl * wl * 3) : NULL;
     ok = ok && cll && yb;
+    if (ok && ll_intensity) {
+        /* Eq. 3-8 for the low pass: the n-level low pass of the (floored, padded)
+         * intensities, then -log of it divided by 2^n, i.e. of the block mean. */
+        double *ii = malloc(sizeof(double) * (size_t)H * W * 3), *ip = malloc(sizeof(double) * (size_t)Hp * Wp * 3);
+        ok = ii && ip;
+        if (ok) {
+            hbo_intensity(frame, fmt, H, W, row_stride_bytes, eps, ii);
+            hbo_pad_edge(ii, H, W, 3, Hp, Wp, ip);
+            double *icur = ip;
+            int ih = Hp, iw = Wp;
+            for (int l = 1; ok && l <= levels; ++l) {
+                size_t n = (size_t)(ih / 2) * (iw / 2) * 3;
+                double *ll = malloc(sizeof(double) * n), *d1 = malloc(sizeof(double) * n),
+                       *d2 = malloc(sizeof(double) * n), *d3 = malloc(sizeof(double) * n);
+                ok = ll && d1 && d2 && d3;
+                if (ok) hbo_haar_level(icur, ih, iw, 3, ll, d1, d2, d3);
+                free(d1);
+                free(d2);
+                free(d3);
+                if (icur != ip) free(icur);
+                icur = ll;
+                ih /= 2;
+                iw /= 2;
+            }
+            if (ok)
+                for (size_t p = 0; p < (size_t)hl * wl * 3; ++p) yb[p] = -log(icur[p] / (double)blk);
+            if (icur != ip) free(icur);
+        }
+        free(ii);
+        free(ip);
+    }
     if (ok) {
         double scale = (double)blk; /* 2^n */
-        for (size_t p = 0; p < (size_t)hl * wl * 3; ++p) yb[p] = cur[p] / scale;
+        if (!ll_intensity)
+            for (size_t p = 0; p < (size_t)hl * wl * 3; ++p) yb[p] = cur[p] / scale;
         if (lowpass_mode == 0) {
             hbo_posterior_mean_many(yb, (long)hl * wl, A, n0, n1, lo0, hi0, lo1, hi1, sigma, illum, nthreads, cll);
         } else {

@@ -343,8 +343,10 @@ hb_status hb_create(const hb_mixing* mix, const hb_grid* grid, int levels, doubl
     *out = nullptr;
     if (!mix || !grid) return HB_ERR_ARG;
     if (in_format != HB_IN_F32_HWC && in_format != HB_IN_U8_HWC) return HB_ERR_ARG;
-    if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_LOWPASS_TIKHONOV | HB_FULL_GRID | HB_ILLUMINATION))
+    if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_LOWPASS_TIKHONOV | HB_FULL_GRID | HB_ILLUMINATION |
+                            HB_LOWPASS_INTENSITY))
         return HB_ERR_ARG;
+    if ((flags & HB_LOWPASS_INTENSITY) && ((flags & HB_LOWPASS_TIKHONOV) || levels > 4)) return HB_ERR_ARG;
     if (width <= 0 || height <= 0 || levels < 0 || levels > hb::kMaxLevels) return HB_ERR_SHAPE;
     if (grid->n0 < 1 || grid->n1 < 1 || !(grid->hi0 >= grid->lo0) || !(grid->hi1 >= grid->lo1) ||
         !(grid->sigma_l > 0.0))
@@ -388,6 +390,7 @@ hb_status hb_create(const hb_mixing* mix, const hb_grid* grid, int levels, doubl
     tp.hl = c->hl;
     tp.wl = c->wl;
     tp.tikhonov_lowpass = (flags & HB_LOWPASS_TIKHONOV) ? 1 : 0;
+    tp.ll_intensity = (flags & HB_LOWPASS_INTENSITY) ? 1 : 0;
 
     float2 lut[256];
     for (int k = 0; k < 256; ++k) {
@@ -805,7 +808,7 @@ hb_status hb_set_lowpass_mode(hb_ctx* c, int mode, double tol, int nsample) {
     if (mode == HB_MODE_MLP) {
         if (!(tol >= 0.0) || nsample < 1) return HB_ERR_ARG;
         if (!c->mlp_ready) return HB_ERR_STATE;
-        if (c->flags & (HB_LOWPASS_TIKHONOV | HB_ILLUMINATION)) return HB_ERR_STATE;
+        if (c->flags & (HB_LOWPASS_TIKHONOV | HB_ILLUMINATION | HB_LOWPASS_INTENSITY)) return HB_ERR_STATE;
         if (nsample > c->mlp_err_cap) {
             DeviceGuard g(c->device);
             cudaFree(c->d_err);

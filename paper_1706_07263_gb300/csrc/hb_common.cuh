@@ -19,6 +19,7 @@ struct TransformParams {
     int tile_w;               // tile width in pixels (multiple of 2^n)
     int hl, wl;               // low-pass band size: ceil(H / 2^n) x ceil(W / 2^n)
     int tikhonov_lowpass;     // 1: low pass through M as well
+    int ll_intensity;         // 1: ybar = -log(block mean of intensity), Eq. 8 (analysis, levels <= 4)
     float M[6];               // M[j*3 + c], j = HbO2/Hb, c = R/G/B
 };
 

@@ -85,6 +85,7 @@ struct Done {
 struct hb_server {
     int device = 0;
     int fmt = 1;
+    int ll_intensity = 0;  // HB_LOWPASS_INTENSITY
     BayesParams bp{};
     float M[6] = {0};
     float2* d_lut = nullptr;
@@ -248,7 +249,8 @@ hb_status hb_server_create(const hb_mixing* mix, const hb_grid* grid, double lam
     *out = nullptr;
     if (!mix || !grid) return HB_ERR_ARG;
     if (in_format != HB_IN_F32_HWC && in_format != HB_IN_U8_HWC) return HB_ERR_ARG;
-    if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_FULL_GRID | HB_ILLUMINATION | HB_SERVE_SEQUENTIAL))
+    if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_FULL_GRID | HB_ILLUMINATION | HB_LOWPASS_INTENSITY |
+                            HB_SERVE_SEQUENTIAL))
         return HB_ERR_ARG;
     if (max_batch < 1 || max_batch > hb::kMaxBatchJobs || batch_lowpass_pixels < 1) return HB_ERR_ARG;
     if (grid->n0 < 1 || grid->n1 < 1 || !(grid->hi0 >= grid->lo0) || !(grid->hi1 >= grid->lo1) ||
@@ -267,6 +269,7 @@ hb_status hb_server_create(const hb_mixing* mix, const hb_grid* grid, double lam
     srv->max_batch = max_batch;
     srv->cap_ll = batch_lowpass_pixels;
     srv->nbatch_slots = (flags & HB_SERVE_SEQUENTIAL) ? 1 : 2;
+    srv->ll_intensity = (flags & HB_LOWPASS_INTENSITY) ? 1 : 0;
     hb::prepare_constants(mix, grid, lambda, flags & (HB_LAMBDA_ABSOLUTE | HB_FULL_GRID | HB_ILLUMINATION), srv->M,
                           srv->bp);
     const size_t need = 2 * batch_bytes(srv->cap_ll) + 256 * sizeof(float2);
@@ -358,6 +361,7 @@ hb_status hb_stream_open(hb_server* srv, int width, int height, int levels, int 
     tp.wl = (width + B - 1) / B;
     tp.tile_w = hb::kThreads;
     tp.tikhonov_lowpass = 0;
+    tp.ll_intensity = srv->ll_intensity;
     for (int k = 0; k < 6; ++k) tp.M[k] = srv->M[k];
     st.npix_ll = (long)tp.hl * tp.wl;
     st.tiles_x = (tp.wl * B + hb::kThreads - 1) / hb::kThreads;

@@ -339,11 +339,14 @@ __device__ __forceinline__ void warp_synthesis(float (&c)[2][1 << L], int lane) 
 }
 
 // Raw samples of the lane's column (codes or intensities), the superblock's top-left
-// log-attenuation (hi, lo) and the offset-free values d = y - y_ref.
-template <int L>
+// log-attenuation (hi, lo) and the offset-free values d = y - y_ref.  SUMS: also the
+// column's sum of floored intensities per channel (ish + isl; for 8-bit input the exact
+// integer sum of the codes, each at least 1, i.e. in units of 1/255).
+template <int L, bool SUMS = false>
 __device__ __forceinline__ void warp_load(const TransformParams& tp, const unsigned char* __restrict__ frame,
                                           size_t stride, const float2* lut, int by, int x, int lane,
-                                          float (&v)[3][1 << L], float2 (&yref)[3]) {
+                                          float (&v)[3][1 << L], float2 (&yref)[3], float* ish = nullptr,
+                                          float* isl = nullptr) {
     constexpr int TH = 1 << L;
     const int xs = min(x, tp.W - 1);
     const int src_lane = lane & ~(TH - 1);
@@ -354,6 +357,16 @@ __device__ __forceinline__ void warp_load(const TransformParams& tp, const unsig
             const unsigned char* row = frame + (size_t)min(by * TH + r, tp.H - 1) * stride + (size_t)xs * 3;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) k[ch][r] = __ldg(row + ch);
+        }
+        if (SUMS) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                int t = 0;
+#pragma unroll
+                for (int r = 0; r < TH; ++r) t += max(k[ch][r], 1);
+                ish[ch] = (float)t;
+                isl[ch] = 0.f;
+            }
         }
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
@@ -366,12 +379,20 @@ __device__ __forceinline__ void warp_load(const TransformParams& tp, const unsig
             }
         }
     } else {
+        if (SUMS) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) ish[ch] = isl[ch] = 0.f;
+        }
 #pragma unroll
         for (int r = 0; r < TH; ++r) {
             const float* row =
                 reinterpret_cast<const float*>(frame + (size_t)min(by * TH + r, tp.H - 1) * stride) + (size_t)xs * 3;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) v[ch][r] = -logf(fmaxf(__ldg(row + ch), tp.eps));
+            for (int ch = 0; ch < 3; ++ch) {
+                const float I = fmaxf(__ldg(row + ch), tp.eps);
+                if (SUMS) detail::dd_sub(ish[ch], isl[ch], -I, 0.f);
+                v[ch][r] = -logf(I);
+            }
         }
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
@@ -400,14 +421,38 @@ __device__ __forceinline__ void analysis_tile(const TransformParams& tp, const B
     if (x0 < tp.wl * TH) {  // whole warps right of the padded frame skip the transform
         float v[3][TH];
         float2 yref[3];
-        warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
-        warp_analysis<L, true>(v, lane);
-        if ((lane & (TH - 1)) == 0) {
-            const int t = threadIdx.x / TH;
+        if (!tp.ll_intensity) {
+            warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
+            warp_analysis<L, true>(v, lane);
+            if ((lane & (TH - 1)) == 0) {
+                const int t = threadIdx.x / TH;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                sb_hi[t][ch] = yref[ch].x;
-                sb_lo[t][ch] = yref[ch].y + v[ch][0] * (1.f / TH);
+                for (int ch = 0; ch < 3; ++ch) {
+                    sb_hi[t][ch] = yref[ch].x;
+                    sb_lo[t][ch] = yref[ch].y + v[ch][0] * (1.f / TH);
+                }
+            }
+        } else {
+            // Eq. 8 literally: the low pass of the intensities, then -log of its block mean
+            float ish[3], isl[3];
+            warp_load<L, true>(tp, frame, stride, lut, by, x, lane, v, yref, ish, isl);
+#pragma unroll
+            for (int s = 1; s < TH; s <<= 1)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float oh = __shfl_xor_sync(kFull, ish[ch], s), ol = __shfl_xor_sync(kFull, isl[ch], s);
+                    detail::dd_sub(ish[ch], isl[ch], -oh, -ol);
+                }
+            if ((lane & (TH - 1)) == 0) {
+                const int t = threadIdx.x / TH;
+                const float d = (tp.fmt == 1 ? 255.f : 1.f) * (float)(TH * TH);  // exact
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float mh = __fdiv_rn(ish[ch], d);
+                    const float ml = __fdiv_rn(fmaf(-mh, d, ish[ch]) + isl[ch], d);
+                    sb_hi[t][ch] = -logf(mh);
+                    sb_lo[t][ch] = -__fdiv_rn(ml, mh);
+                }
             }
         }
     }

@@ -14,10 +14,16 @@
 
 #include <math.h>
 
-#ifdef HB_POST_MINB       // minimum resident CTAs per SM requested from the register allocator
-#define HB_POST_BOUNDS __launch_bounds__(kThreads, HB_POST_MINB)
+// Minimum resident CTAs per SM asked of the register allocator (measured on the 1080p
+// workload: 2 for the two-pixel kernel, which then keeps its 8 columns per lane in
+// registers; 4 for the one-pixel kernel up to 4 columns per lane).  HB_POST_MINB
+// overrides both.
+#ifdef HB_POST_MINB
+#define HB_POST_BOUNDS(cpl) __launch_bounds__(kThreads, HB_POST_MINB)
+#define HB_PAIR_BOUNDS __launch_bounds__(kThreads, HB_POST_MINB)
 #else
-#define HB_POST_BOUNDS __launch_bounds__(kThreads)
+#define HB_POST_BOUNDS(cpl) __launch_bounds__(kThreads, (cpl) >= 8 ? 3 : 4)
+#define HB_PAIR_BOUNDS __launch_bounds__(kThreads, 2)
 #endif
 
 namespace hb {
@@ -100,7 +106,7 @@ __device__ __forceinline__ void run_unit(const BayesParams& bp, const BayesRec& 
 
 // Posterior over precomputed per-pixel records (the stand-alone posterior entry point).
 template <int CPL>
-__global__ void HB_POST_BOUNDS posterior_kernel(BayesParams bp, const BayesRec* __restrict__ recs, long npix, int rs,
+__global__ void HB_POST_BOUNDS(CPL) posterior_kernel(BayesParams bp, const BayesRec* __restrict__ recs, long npix, int rs,
                                                 float* partial, unsigned* count, float2* __restrict__ chat,
                                                 float2* __restrict__ chat_scaled, float scale, PosteriorGate gate,
                                                 unsigned long long* nodes_out) {
@@ -130,19 +136,98 @@ __global__ void HB_POST_BOUNDS posterior_kernel(BayesParams bp, const BayesRec* 
     if (nodes_out && lane == 0 && nodes) atomicAdd(nodes_out, nodes);
 }
 
+// One round of the two-pixel kernel below: pixel 2r + half, its sums and its mean.
+template <int CPL>
+__device__ __forceinline__ void pair_round(const BayesParams& bp, const BayesRec& rec, long r, long npix, int gl,
+                                           int half, float2* chat, float2* chat_scaled, float scale,
+                                           unsigned long long& nodes) {
+    constexpr int G = 16;
+    const long p = 2 * r + half;
+    const bool valid = p < npix;
+    int lo, hi;
+    support_rows(bp, rec, lo, hi);
+    int rb = __reduce_min_sync(0xffffffffu, lo), re = __reduce_max_sync(0xffffffffu, hi);
+    if (valid) nodes += (unsigned long long)(re - rb) * (unsigned)bp.n1;
+    float shift = 0.f, sw, sdi, sdj;
+    for (int pass = 0;; ++pass) {
+        sw = sdi = sdj = 0.f;
+        grid_sums<CPL, G>(bp, rec, gl, rb, re, shift, sw, sdi, sdj);
+        sw = group_sum<G>(sw);
+        sdi = group_sum<G>(sdi);
+        sdj = group_sum<G>(sdj);
+        const bool bad = !usable(sw, sdi, sdj);
+        if (pass == 1 || !__any_sync(0xffffffffu, bad)) break;
+        const float m = group_max<G>(grid_max<CPL, G>(bp, rec, gl, 0, bp.n0));
+        shift = bad ? m : 0.f;
+        rb = 0;
+        re = bp.n0;
+        if (valid && bad) nodes += 2ull * (unsigned)bp.n0 * (unsigned)bp.n1;
+    }
+    if (valid && gl == 0) write_mean(bp, rec, p, sw, sdi, sdj, chat, chat_scaled, scale);
+}
+
+// Two pixels per warp: half-warp h (lanes 16h .. 16h+15) takes pixel 2r + h of round r, CPL
+// columns per lane.  The per-pixel fixed work (row bound, column constants, reductions,
+// epilogue) is then shared by two pixels in every warp instruction.  The warp enumerates the
+// union of the two pixels' support rows; rows outside a pixel's own support carry weights
+// that are exactly zero in FP32, so each pixel's sums equal those over its own rows, and
+// over the whole grid.  A pixel whose sums are not usable (inputs far outside the model) is
+// summed again over all rows with an explicit maximum shift; its partner repeats its own
+// sums unshifted, which leaves them unchanged.
+//
+// Rounds are dealt to CTAs interleaved (CTA b takes rounds b, b + B, b + 2B, ...: an even
+// sample of the frame each) and, inside a CTA, to whichever warp is free next through a
+// shared-memory counter, so that warps whose pixels have few support rows take more of
+// them.  Each warp holds its next round's record while it computes.  Which warp computes a
+// pixel does not change its result.
+template <int CPL>
+__global__ void HB_PAIR_BOUNDS posterior_pair_kernel(BayesParams bp, const BayesRec* __restrict__ recs, long npix,
+                                                     float2* __restrict__ chat, float2* __restrict__ chat_scaled,
+                                                     float scale, PosteriorGate gate, unsigned long long* nodes_out) {
+    const int lane = threadIdx.x & 31, gl = lane & 15, half = lane >> 4;
+    const long rounds = (npix + 1) / 2;
+    __shared__ unsigned ticket;
+    if (threadIdx.x == 0) ticket = 0u;
+    __syncthreads();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    if (gate.run && *gate.run == 0u) return;
+    unsigned long long nodes = 0;
+    auto next_round = [&]() {
+        unsigned k = 0;
+        if (lane == 0) k = atomicAdd(&ticket, 1u);
+        return (long)blockIdx.x + (long)__shfl_sync(0xffffffffu, k, 0) * gridDim.x;
+    };
+    auto load = [&](long r) { return recs[min(2 * r + half, npix - 1)]; };
+    long r0 = next_round();
+    BayesRec rec0 = {0, 0, 0.f, 0.f};
+    if (r0 < rounds) rec0 = load(r0);
+    while (r0 < rounds) {
+        const long r1 = next_round();
+        BayesRec rec1 = {0, 0, 0.f, 0.f};
+        if (r1 < rounds) rec1 = load(r1);
+        pair_round<CPL>(bp, rec0, r0, npix, gl, half, chat, chat_scaled, scale, nodes);
+        r0 = r1;
+        rec0 = rec1;
+    }
+    if (nodes_out && gl == 0 && nodes) atomicAdd(nodes_out, nodes);
+}
+
 // Resident CTAs per SM for a kernel (cached per device and kernel) and the SM count.
 template <typename K>
 cudaError_t residency(K kernel, int& resident, int& sms) {
+    static K cache_k[64];
     static int cache_res[64], cache_sms[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (cache_res[dev] == 0) {
+    if (cache_res[dev] == 0 || cache_k[dev] != kernel) {
         e = cudaDeviceGetAttribute(&cache_sms[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cache_res[dev], kernel, kThreads, 0);
         if (e != cudaSuccess) return e;
         if (cache_res[dev] < 1) cache_res[dev] = 1;
+        cache_k[dev] = kernel;
     }
     resident = cache_res[dev];
     sms = cache_sms[dev];
@@ -184,12 +269,48 @@ cudaError_t launch_cpl(const BayesParams& bp, const BayesRec* rec, long npix, co
                               chat_scaled, scale, gate, sc.nodes);
 }
 
+// The pair kernel when there are at least two pixels per resident warp (cudaErrorNotReady
+// when there are fewer: the caller then uses the one-pixel-per-unit kernel).
+template <int CPL>
+cudaError_t launch_pair(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
+                        float2* chat, float2* chat_scaled, float scale, bool pdl, const PosteriorGate& gate,
+                        cudaStream_t s) {
+    int resident = 0, sms = 0;
+    cudaError_t e = residency(posterior_pair_kernel<CPL>, resident, sms);
+    if (e != cudaSuccess) return e;
+    const long warps = (long)sms * resident * (kThreads / 32);
+    if (npix < 2 * warps) return cudaErrorNotReady;
+    const long rounds = (npix + 1) / 2;
+    long blocks = (rounds + kThreads / 32 - 1) / (kThreads / 32);
+    if (blocks > (long)sms * resident) blocks = (long)sms * resident;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, posterior_pair_kernel<CPL>, bp, rec, npix, chat, chat_scaled, scale, gate,
+                              sc.nodes);
+}
+
 }  // namespace
 
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
                              float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,
                              const PosteriorGate& gate) {
     if (npix <= 0) return cudaSuccess;
+#ifndef HB_POST_NO_PAIRS
+    if (bp.n1 <= 128) {
+        cudaError_t e = bp.n1 <= 16   ? launch_pair<1>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s)
+                        : bp.n1 <= 32 ? launch_pair<2>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s)
+                        : bp.n1 <= 64 ? launch_pair<4>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s)
+                                      : launch_pair<8>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);
+        if (e != cudaErrorNotReady) return e;
+    }
+#endif
     if (bp.n1 <= 32) return launch_cpl<1>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);
     if (bp.n1 <= 64) return launch_cpl<2>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);
     if (bp.n1 <= 128) return launch_cpl<4>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);

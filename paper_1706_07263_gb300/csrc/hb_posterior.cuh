@@ -62,13 +62,15 @@ __device__ __forceinline__ float ex2(float x) {
     return y;
 }
 
-// Column constants of one lane for the column block starting at j_base.
-template <int CPL>
+// Column constants of one lane for the column block starting at j_base.  A pixel is
+// handled by a group of G lanes (32: a warp; 16: half a warp); lane l of the group takes
+// columns j_base + l + G s.
+template <int CPL, int G = 32>
 __device__ __forceinline__ void column_terms(const BayesParams& bp, const BayesRec& rec, int lane, int j_base,
                                              float shift, float (&dj)[CPL], float (&P)[CPL], float (&Q)[CPL]) {
 #pragma unroll
     for (int s = 0; s < CPL; ++s) {
-        const int j = j_base + lane + 32 * s;
+        const int j = j_base + lane + G * s;
         dj[s] = (float)(j - rec.j0);
         P[s] = j < bp.n1 ? fmaf(bp.Cq * dj[s], dj[s], rec.V * dj[s]) - shift : -INFINITY;
         Q[s] = fmaf(2.f * bp.Bq, dj[s], rec.U);
@@ -77,12 +79,12 @@ __device__ __forceinline__ void column_terms(const BayesParams& bp, const BayesR
 
 // sum w, sum w di, sum w dj over rows [rb, re) and the lane's columns (all column blocks),
 // with weights 2^(t - shift).
-template <int CPL>
+template <int CPL, int G = 32>
 __device__ __forceinline__ void grid_sums(const BayesParams& bp, const BayesRec& rec, int lane, int rb, int re,
                                           float shift, float& sw, float& sdi, float& sdj) {
-    for (int jb = 0; jb < bp.n1; jb += 32 * CPL) {
+    for (int jb = 0; jb < bp.n1; jb += G * CPL) {
         float dj[CPL], P[CPL], Q[CPL];
-        column_terms<CPL>(bp, rec, lane, jb, shift, dj, P, Q);
+        column_terms<CPL, G>(bp, rec, lane, jb, shift, dj, P, Q);
         float S[CPL], T[CPL];
         if constexpr (CPL == 1) {
             S[0] = 0.f;
@@ -136,18 +138,32 @@ __device__ __forceinline__ void grid_sums(const BayesParams& bp, const BayesRec&
 }
 
 // Largest exponent t over rows [rb, re) and the lane's columns.
-template <int CPL>
+template <int CPL, int G = 32>
 __device__ float grid_max(const BayesParams& bp, const BayesRec& rec, int lane, int rb, int re) {
     float m = -INFINITY;
-    for (int jb = 0; jb < bp.n1; jb += 32 * CPL) {
+    for (int jb = 0; jb < bp.n1; jb += G * CPL) {
         float dj[CPL], P[CPL], Q[CPL];
-        column_terms<CPL>(bp, rec, lane, jb, 0.f, dj, P, Q);
+        column_terms<CPL, G>(bp, rec, lane, jb, 0.f, dj, P, Q);
         float di = (float)(rb - rec.i0);
         for (int i = rb; i < re; ++i, di += 1.f)
 #pragma unroll
             for (int s = 0; s < CPL; ++s) m = fmaxf(m, fmaf(di, fmaf(bp.Aq, di, Q[s]), P[s]));
     }
     return m;
+}
+
+// Sum / maximum over the G lanes of a group (xor shuffles stay inside aligned groups).
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ float group_max(float v) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -121,7 +121,11 @@ hb_status hb_estimate(hb_ctx *ctx, const void *frame_dev, size_t row_stride_byte
 
 /* Same computation on host buffers: copies the frame host->device, runs
  * hb_estimate into context-owned device buffers, copies THb and SO2
- * device->host, and synchronises `stream` before returning. */
+ * device->host, and synchronises `stream` before returning.  The frame is taken in
+ * bands of whole 2^n-row superblock bands (a band's pixels depend on no other band), so
+ * a band's input copy, its kernels on `stream` and the previous band's output copy
+ * overlap; the copies use two context-owned streams.  Results equal hb_estimate's.
+ * Pinned host buffers let the copies run asynchronously. */
 hb_status hb_estimate_host(hb_ctx *ctx, const void *frame_host, size_t row_stride_bytes, float *thb_host,
                            float *so2_host, void *stream);
 

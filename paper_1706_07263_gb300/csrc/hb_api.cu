@@ -5,6 +5,7 @@
 #include "hb_common.cuh"
 #include "hb_mlp.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cmath>
@@ -59,6 +60,9 @@ struct hb_ctx {
     unsigned long long* d_nodes = nullptr;  // grid nodes enumerated by timed posterior launches
     long mlp_frames = 0;
     unsigned frame_seq = 0;
+    // hb_estimate_host: copy streams and per-band events (created on first use)
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> host_ev;
     // per-stage timing
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_stage;
@@ -67,6 +71,14 @@ struct hb_ctx {
 };
 
 namespace {
+
+// Row bands of the pipelined host entry point.  Measured on a 1920x1080 u8 frame: 1 band
+// 201 us, 2 bands 173, 3 bands 162, 5 or 8 bands 177 (smaller bands run the kernels less
+// efficiently); the copies themselves need ~120 us at the host link's ~195 GB/s.
+#ifndef HB_HOST_BANDS
+#define HB_HOST_BANDS 3
+#endif
+constexpr int kHostBands = HB_HOST_BANDS;
 
 struct DeviceGuard {
     int prev = -1;
@@ -288,17 +300,31 @@ hb_status check_frame_args(const hb_ctx* c, const void* frame, size_t stride) {
 // synthesis are launched with programmatic dependent launch (each waits for its
 // predecessor inside the kernel) unless per-stage timing is armed, since timing events
 // between the kernels serialise them anyway.  All-Tikhonov mode: the synthesis alone.
-hb_status run_frame(hb_ctx* c, const void* frame, size_t stride, double* ybar, float* out0, float* out1,
-                    float2* conc_scaled, int debug, cudaStream_t s) {
+// A band of whole superblock rows of the frame: superblocks never straddle two bands, so a
+// band is processed as a frame of its own (its rows, the frame's width) whose low-pass
+// pixels sit at ll_off in the context's arrays.  Only the band holding the frame's last
+// row meets the bottom edge, so the edge replication is the whole frame's.
+struct Band {
+    TransformParams tp;
+    long ll_off;
+    long npix;
+};
+
+Band whole_frame(const hb_ctx* c) { return Band{c->tp, 0, c->npix_ll}; }
+
+hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, double* ybar, float* out0, float* out1,
+                   float2* conc_scaled, int debug, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     const bool bayes = !(c->flags & HB_LOWPASS_TIKHONOV);
     const bool pdl = !c->timing;
     const bool mlp = bayes && c->lowpass_mode == HB_MODE_MLP;
+    BayesRec* rec = c->d_rec + b.ll_off;
+    float2* chat = c->d_chat + b.ll_off;
     if (bayes) {
         {
             StageTimer t(c, s, HB_STAGE_ANALYSIS);
-            e = hb::launch_analysis(c->tp, c->bp, frame, stride, c->d_lut, ybar, c->d_rec, s,
-                                    mlp ? c->d_ybar_f : nullptr);
+            e = hb::launch_analysis(b.tp, c->bp, frame, stride, c->d_lut, ybar, rec, s,
+                                    mlp ? c->d_ybar_f + 3 * b.ll_off : nullptr);
             c->launches++;
         }
         if (e != cudaSuccess) return HB_ERR_CUDA;
@@ -307,30 +333,34 @@ hb_status run_frame(hb_ctx* c, const void* frame, size_t stride, double* ybar, f
         if (mlp) {
             // network estimate, sampled exact check, exact recomputation only if the check
             // failed; each kernel waits for its predecessor in-kernel (PDL)
-            e = hb::launch_mlp_forward(c->d_mlp + 3 * hb::kNParams, c->mlp_norm, c->d_ybar_f, c->npix_ll, c->d_chat,
-                                       pdl, s);
+            e = hb::launch_mlp_forward(c->d_mlp + 3 * hb::kNParams, c->mlp_norm, c->d_ybar_f + 3 * b.ll_off, b.npix,
+                                       chat, pdl, s);
             if (e == cudaSuccess)
-                e = hb::launch_posterior_check(c->bp, c->d_rec, c->npix_ll, c->mlp_nsample, c->frame_seq++,
-                                               c->d_chat, 1.f / c->mlp_ext0, 1.f / c->mlp_ext1, c->d_err, c->mlp_tol,
-                                               c->d_flags, pdl, s);
+                e = hb::launch_posterior_check(c->bp, rec, b.npix, c->mlp_nsample, c->frame_seq++, chat,
+                                               1.f / c->mlp_ext0, 1.f / c->mlp_ext1, c->d_err, c->mlp_tol, c->d_flags,
+                                               pdl, s);
             if (e == cudaSuccess)
-                e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, nullptr, scale, pdl,
-                                         s, hb::PosteriorGate{c->d_flags + 2});
+                e = hb::launch_posterior(c->bp, rec, b.npix, post_scratch(c), chat, nullptr, scale, pdl, s,
+                                         hb::PosteriorGate{c->d_flags + 2});
             c->launches += 3;
             c->mlp_frames++;
         } else {
-            e = hb::launch_posterior(c->bp, c->d_rec, c->npix_ll, post_scratch(c), c->d_chat, conc_scaled, scale,
-                                     pdl, s);
+            e = hb::launch_posterior(c->bp, rec, b.npix, post_scratch(c), chat, conc_scaled, scale, pdl, s);
             c->launches++;
         }
     }
     if (e != cudaSuccess) return HB_ERR_CUDA;
     if (out0 || out1) {
         StageTimer t(c, s, HB_STAGE_SYNTHESIS);
-        e = hb::launch_synthesis(c->tp, frame, stride, c->d_lut, c->d_chat, out0, out1, debug, bayes && pdl, s);
+        e = hb::launch_synthesis(b.tp, frame, stride, c->d_lut, chat, out0, out1, debug, bayes && pdl, s);
         c->launches++;
     }
     return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+}
+
+hb_status run_frame(hb_ctx* c, const void* frame, size_t stride, double* ybar, float* out0, float* out1,
+                    float2* conc_scaled, int debug, cudaStream_t s) {
+    return run_band(c, whole_frame(c), frame, stride, ybar, out0, out1, conc_scaled, debug, s);
 }
 
 }  // namespace
@@ -432,6 +462,9 @@ void hb_destroy(hb_ctx* c) {
     cudaFree(c->d_thb);
     cudaFree(c->d_so2);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->host_ev) cudaEventDestroy(e);
+    if (c->s_in) cudaStreamDestroy(c->s_in);
+    if (c->s_out) cudaStreamDestroy(c->s_out);
     cudaGetLastError();
     delete c;
 }
@@ -454,7 +487,7 @@ hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_
     if (row_stride_bytes < row) return HB_ERR_ARG;
     DeviceGuard g(c->device);
     const size_t npx = (size_t)c->W * c->H;
-    if (!c->d_frame) {
+    if (!c->d_frame) {  // staging buffers, allocated on first use
         if (cudaMalloc(&c->d_frame, row * c->H) != cudaSuccess || cudaMalloc(&c->d_thb, npx * 4) != cudaSuccess ||
             cudaMalloc(&c->d_so2, npx * 4) != cudaSuccess) {
             cudaGetLastError();
@@ -468,15 +501,68 @@ hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_
         }
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpy2DAsync(c->d_frame, row, frame_host, row_stride_bytes, row, c->H, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
+    // Bands of whole superblock rows, pipelined: band k's frame rows go up on s_in while
+    // band k-1 computes on s and band k-2's THb/SO2 rows come back on s_out.  The learned
+    // low pass takes the whole frame at once (its fallback decision is per frame).
+    // Bands are used only where every band's posterior takes the two-pixel kernel, as the
+    // whole frame's does: each pixel's result is then the same as in hb_estimate.
+    const int TH = 1 << c->levels;
+    const bool bayes = !(c->flags & HB_LOWPASS_TIKHONOV);
+    const bool mlp = bayes && c->lowpass_mode == HB_MODE_MLP;
+    int per = c->hl, nb = 1;
+    for (int want = kHostBands; !mlp && want > 1; --want) {
+        per = (c->hl + want - 1) / want;
+        nb = (c->hl + per - 1) / per;
+        const long smallest = (long)(c->hl - (nb - 1) * per) * c->wl;
+        if (nb > 1 && (!bayes || hb::posterior_uses_pairs(c->bp, smallest))) break;
+        per = c->hl;
+        nb = 1;
+    }
+    if (!c->s_in) {
+        if (cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return HB_ERR_CUDA;
+        }
+    }
+    while ((int)c->host_ev.size() < 2 * nb + 1) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HB_ERR_CUDA;
+        c->host_ev.push_back(e);
+    }
+    // the staging buffers may still be in use by work queued earlier on s
+    if (cudaEventRecord(c->host_ev[2 * nb], s) != cudaSuccess || cudaStreamWaitEvent(c->s_in, c->host_ev[2 * nb], 0) ||
+        cudaStreamWaitEvent(c->s_out, c->host_ev[2 * nb], 0))
         return HB_ERR_CUDA;
-    hb_status st = run_frame(c, c->d_frame, row, nullptr, c->d_thb, c->d_so2, nullptr, 0, s);
-    if (st != HB_OK) return st;
-    if (cudaMemcpyAsync(thb_host, c->d_thb, npx * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(so2_host, c->d_so2, npx * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return HB_ERR_CUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+    const unsigned char* fh = static_cast<const unsigned char*>(frame_host);
+    unsigned char* fd = static_cast<unsigned char*>(c->d_frame);
+    for (int k = 0; k < nb; ++k) {
+        const int r0 = k * per * TH, r1 = std::min(c->H, (k + 1) * per * TH);
+        if (cudaMemcpy2DAsync(fd + (size_t)r0 * row, row, fh + (size_t)r0 * row_stride_bytes, row_stride_bytes, row,
+                              r1 - r0, cudaMemcpyHostToDevice, c->s_in) != cudaSuccess ||
+            cudaEventRecord(c->host_ev[2 * k], c->s_in) != cudaSuccess)
+            return HB_ERR_CUDA;
+    }
+    for (int k = 0; k < nb; ++k) {
+        const int b0 = k * per, b1 = std::min(c->hl, (k + 1) * per);
+        const int r0 = b0 * TH, r1 = std::min(c->H, b1 * TH);
+        Band b = whole_frame(c);
+        b.tp.H = r1 - r0;
+        b.tp.hl = b1 - b0;
+        b.ll_off = (long)b0 * c->wl;
+        b.npix = (long)(b1 - b0) * c->wl;
+        const size_t o = (size_t)r0 * c->W, n = (size_t)(r1 - r0) * c->W;
+        if (cudaStreamWaitEvent(s, c->host_ev[2 * k], 0) != cudaSuccess) return HB_ERR_CUDA;
+        hb_status st = run_band(c, b, fd + (size_t)r0 * row, row, nullptr, c->d_thb + o, c->d_so2 + o, nullptr, 0, s);
+        if (st != HB_OK) return st;
+        if (cudaEventRecord(c->host_ev[2 * k + 1], s) != cudaSuccess ||
+            cudaStreamWaitEvent(c->s_out, c->host_ev[2 * k + 1], 0) != cudaSuccess ||
+            cudaMemcpyAsync(thb_host + o, c->d_thb + o, n * 4, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess ||
+            cudaMemcpyAsync(so2_host + o, c->d_so2 + o, n * 4, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess)
+            return HB_ERR_CUDA;
+    }
+    return cudaStreamSynchronize(c->s_out) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess ? HB_OK
+                                                                                                     : HB_ERR_CUDA;
 }
 
 hb_status hb_estimate_debug(hb_ctx* c, const void* frame_dev, size_t row_stride_bytes, double* ybar_dev,

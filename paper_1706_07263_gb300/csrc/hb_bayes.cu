@@ -298,6 +298,20 @@ cudaError_t launch_pair(const BayesParams& bp, const BayesRec* rec, long npix, c
 
 }  // namespace
 
+bool posterior_uses_pairs(const BayesParams& bp, long npix) {
+#ifdef HB_POST_NO_PAIRS
+    return false;
+#else
+    if (bp.n1 > 128) return false;
+    int resident = 0, sms = 0;
+    cudaError_t e = bp.n1 <= 16   ? residency(posterior_pair_kernel<1>, resident, sms)
+                    : bp.n1 <= 32 ? residency(posterior_pair_kernel<2>, resident, sms)
+                    : bp.n1 <= 64 ? residency(posterior_pair_kernel<4>, resident, sms)
+                                  : residency(posterior_pair_kernel<8>, resident, sms);
+    return e == cudaSuccess && npix >= 2L * sms * resident * (kThreads / 32);
+#endif
+}
+
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
                              float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,
                              const PosteriorGate& gate) {

@@ -101,6 +101,9 @@ struct PosteriorGate {
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
                              float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,
                              const PosteriorGate& gate = PosteriorGate{nullptr});
+// Whether launch_posterior takes npix pixels two per warp (each pixel's result then does not
+// depend on the other pixels of the launch).
+bool posterior_uses_pairs(const BayesParams& bp, long npix);
 // Exact posterior of nsample pseudo-randomly drawn pixels (seeded) against another
 // estimate of them: err[k] = the larger of |d c0| inv_ext0 and |d c1| inv_ext1 for the
 // k-th drawn pixel (NaN if either is).  The last CTA to finish adds the errors in index

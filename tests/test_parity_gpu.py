@@ -274,6 +274,32 @@ def test_strided_frame_and_host_entry_match_plain_call():
         np.testing.assert_array_equal(sh, base["so2"].astype(np.float32))
 
 
+@pytest.mark.parametrize("case", ["hd_bayes", "tikhonov"])
+def test_host_entry_in_bands_matches_the_device_call(case):
+    """hb_estimate_host pipelines the frame in bands of superblock rows (copies overlapping the
+    kernels); every pixel comes out bit-identical to hb_estimate on the same frame."""
+    if case == "hd_bayes":
+        wl = synth.HD_1080
+        mix, fr = synth.workload_inputs(wl)
+        A, rgb, grid, levels, flags = mix.A, fr.rgb, synth.grid_spec(wl), wl.levels, 0
+    else:
+        A, rgb = small_frame(44, 300, 500, "u8", noise=0.01, nblobs=6, smin=10.0, smax=60.0)
+        grid, levels, flags = _grid(16, 16), 2, binding.HB_LOWPASS_TIKHONOV
+    H, W, _ = rgb.shape
+    with Context(A, grid, levels, 1e-3, W, H, "u8", flags) as ctx:
+        thb = torch.empty((H, W), dtype=torch.float32, device=DEV)
+        so2 = torch.empty_like(thb)
+        ctx.estimate(torch.from_numpy(rgb).to(DEV), thb, so2)
+        torch.cuda.synchronize()
+        hf = torch.from_numpy(rgb).pin_memory()
+        th = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        sh = torch.empty_like(th).pin_memory()
+        for _ in range(2):
+            ctx.estimate_host(hf, th, sh)
+            np.testing.assert_array_equal(th.numpy(), thb.cpu().numpy())
+            np.testing.assert_array_equal(sh.numpy(), so2.cpu().numpy())
+
+
 def test_repeated_calls_are_deterministic_and_counted():
     A, rgb = small_frame(42, 64, 64, "u8")
     grid = _grid(64, 64)

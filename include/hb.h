@@ -125,7 +125,9 @@ hb_status hb_estimate(hb_ctx *ctx, const void *frame_dev, size_t row_stride_byte
  * bands of whole 2^n-row superblock bands (a band's pixels depend on no other band), so
  * a band's input copy, its kernels on `stream` and the previous band's output copy
  * overlap; the copies use two context-owned streams.  Results equal hb_estimate's.
- * Pinned host buffers let the copies run asynchronously. */
+ * Pinned host buffers let the copies run asynchronously.  A second call with the same
+ * buffers and the same (non-default) stream captures the sequence as a CUDA graph, which
+ * later calls with those buffers replay; other buffers or stage timing run it directly. */
 hb_status hb_estimate_host(hb_ctx *ctx, const void *frame_host, size_t row_stride_bytes, float *thb_host,
                            float *so2_host, void *stream);
 

@@ -19,6 +19,20 @@ using hb::BayesParams;
 using hb::BayesRec;
 using hb::TransformParams;
 
+// What a captured hb_estimate_host sequence depends on besides the context itself.
+struct HostKey {
+    const void* frame;
+    size_t stride;
+    float* thb;
+    float* so2;
+    cudaStream_t stream;
+    int first, nb;
+    bool operator==(const HostKey& o) const {
+        return frame == o.frame && stride == o.stride && thb == o.thb && so2 == o.so2 && stream == o.stream &&
+               first == o.first && nb == o.nb;
+    }
+};
+
 struct hb_ctx {
     int device = 0;
     int W = 0, H = 0, levels = 0, fmt = 0;
@@ -61,8 +75,12 @@ struct hb_ctx {
     long mlp_frames = 0;
     unsigned frame_seq = 0;
     // hb_estimate_host: copy streams and per-band events (created on first use)
-    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_alt = nullptr;
     std::vector<cudaEvent_t> host_ev;
+    HostKey hg_key{};                 // the buffers etc. of the last call, and its captured graph
+    bool hg_seen = false;
+    cudaGraphExec_t hg_exec = nullptr;
+    long hg_kernels = 0;
     // per-stage timing
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_stage;
@@ -72,9 +90,10 @@ struct hb_ctx {
 
 namespace {
 
-// Row bands of the pipelined host entry point.  Measured on a 1920x1080 u8 frame: 1 band
-// 201 us, 2 bands 173, 3 bands 162, 5 or 8 bands 177 (smaller bands run the kernels less
-// efficiently); the copies themselves need ~120 us at the host link's ~195 GB/s.
+// Row bands of the pipelined host entry point (at most).  The copies of a 1920x1080 u8
+// frame need ~95 us with both directions of the host link (~190 GB/s each) busy; a call
+// measures ~155 us with 3 to 5 bands (201 us unbanded), and the synthesis storing THb/SO2
+// straight into pinned host memory instead of the output copies measured the same.
 #ifndef HB_HOST_BANDS
 #define HB_HOST_BANDS 3
 #endif
@@ -465,6 +484,8 @@ void hb_destroy(hb_ctx* c) {
     for (cudaEvent_t e : c->host_ev) cudaEventDestroy(e);
     if (c->s_in) cudaStreamDestroy(c->s_in);
     if (c->s_out) cudaStreamDestroy(c->s_out);
+    if (c->s_alt) cudaStreamDestroy(c->s_alt);
+    if (c->hg_exec) cudaGraphExecDestroy(c->hg_exec);
     cudaGetLastError();
     delete c;
 }
@@ -478,6 +499,62 @@ hb_status hb_estimate(hb_ctx* c, const void* frame_dev, size_t row_stride_bytes,
     return run_frame(c, frame_dev, row_stride_bytes, nullptr, thb_dev, so2_dev, nullptr, 0,
                      static_cast<cudaStream_t>(stream));
 }
+
+}  // extern "C"
+
+namespace {
+
+// Everything of one hb_estimate_host call in stream order, ending with every side stream
+// joined back into s (so that the sequence can also be captured as a graph).
+hb_status enqueue_host_bands(hb_ctx* c, const void* frame_host, size_t row_stride_bytes, float* thb_host,
+                             float* so2_host, cudaStream_t s, const int* bounds, int nb) {
+    const int TH = 1 << c->levels;
+    const size_t row = (size_t)c->W * 3 * elem_size(c->fmt);
+    // the staging buffers may still be in use by work queued earlier on s
+    cudaEvent_t ev_start = c->host_ev[2 * nb], ev_alt = c->host_ev[2 * nb + 1], ev_out = c->host_ev[2 * nb + 2];
+    if (cudaEventRecord(ev_start, s) != cudaSuccess || cudaStreamWaitEvent(c->s_in, ev_start, 0) ||
+        cudaStreamWaitEvent(c->s_out, ev_start, 0) || cudaStreamWaitEvent(c->s_alt, ev_start, 0))
+        return HB_ERR_CUDA;
+    const unsigned char* fh = static_cast<const unsigned char*>(frame_host);
+    unsigned char* fd = static_cast<unsigned char*>(c->d_frame);
+    for (int k = 0; k < nb; ++k) {
+        const int r0 = bounds[k] * TH, r1 = std::min(c->H, bounds[k + 1] * TH);
+        if (cudaMemcpy2DAsync(fd + (size_t)r0 * row, row, fh + (size_t)r0 * row_stride_bytes, row_stride_bytes, row,
+                              r1 - r0, cudaMemcpyHostToDevice, c->s_in) != cudaSuccess ||
+            cudaEventRecord(c->host_ev[2 * k], c->s_in) != cudaSuccess)
+            return HB_ERR_CUDA;
+    }
+    for (int k = 0; k < nb; ++k) {
+        const int b0 = bounds[k], b1 = bounds[k + 1];
+        const int r0 = b0 * TH, r1 = std::min(c->H, b1 * TH);
+        Band b = whole_frame(c);
+        b.tp.H = r1 - r0;
+        b.tp.hl = b1 - b0;
+        b.ll_off = (long)b0 * c->wl;
+        b.npix = (long)(b1 - b0) * c->wl;
+        const size_t o = (size_t)r0 * c->W, n = (size_t)(r1 - r0) * c->W;
+        // alternate bands between two compute streams: neighbouring bands share no data, and
+        // one band's kernels fill the ramp and tail of the other's
+        cudaStream_t cs = (k & 1) ? c->s_alt : s;
+        if (cudaStreamWaitEvent(cs, c->host_ev[2 * k], 0) != cudaSuccess) return HB_ERR_CUDA;
+        hb_status st = run_band(c, b, fd + (size_t)r0 * row, row, nullptr, c->d_thb + o, c->d_so2 + o, nullptr, 0, cs);
+        if (st != HB_OK) return st;
+        if (cudaEventRecord(c->host_ev[2 * k + 1], cs) != cudaSuccess ||
+            cudaStreamWaitEvent(c->s_out, c->host_ev[2 * k + 1], 0) != cudaSuccess ||
+            cudaMemcpyAsync(thb_host + o, c->d_thb + o, n * 4, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess ||
+            cudaMemcpyAsync(so2_host + o, c->d_so2 + o, n * 4, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess)
+            return HB_ERR_CUDA;
+    }
+    // later work on s is ordered after every band and every copy
+    if (cudaEventRecord(ev_alt, c->s_alt) != cudaSuccess || cudaStreamWaitEvent(s, ev_alt, 0) != cudaSuccess ||
+        cudaEventRecord(ev_out, c->s_out) != cudaSuccess || cudaStreamWaitEvent(s, ev_out, 0) != cudaSuccess)
+        return HB_ERR_CUDA;
+    return HB_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_bytes, float* thb_host,
                            float* so2_host, void* stream) {
@@ -502,67 +579,88 @@ hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // Bands of whole superblock rows, pipelined: band k's frame rows go up on s_in while
-    // band k-1 computes on s and band k-2's THb/SO2 rows come back on s_out.  The learned
-    // low pass takes the whole frame at once (its fallback decision is per frame).
+    // band k-1 computes (on s or s_alt) and band k-2's THb/SO2 rows come back on s_out.  The
+    // learned low pass takes the whole frame at once (its fallback decision is per frame).
     // Bands are used only where every band's posterior takes the two-pixel kernel, as the
     // whole frame's does: each pixel's result is then the same as in hb_estimate.
-    const int TH = 1 << c->levels;
+    // The first band is kept small, so that the first output copy starts early: the fewest
+    // superblock rows that still take the two-pixel posterior (or a 2*kHostBands-th of the
+    // frame without a posterior); the other rows are shared evenly among the other bands,
+    // none smaller than the first.
     const bool bayes = !(c->flags & HB_LOWPASS_TIKHONOV);
     const bool mlp = bayes && c->lowpass_mode == HB_MODE_MLP;
-    int per = c->hl, nb = 1;
-    for (int want = kHostBands; !mlp && want > 1; --want) {
-        per = (c->hl + want - 1) / want;
-        nb = (c->hl + per - 1) / per;
-        const long smallest = (long)(c->hl - (nb - 1) * per) * c->wl;
-        if (nb > 1 && (!bayes || hb::posterior_uses_pairs(c->bp, smallest))) break;
-        per = c->hl;
-        nb = 1;
+    int bounds[kHostBands + 1] = {0, c->hl};
+    int nb = 1;
+    if (!mlp && kHostBands > 1) {
+        int first = std::max(1, c->hl / (2 * kHostBands));
+        if (bayes)
+            while (first < c->hl && !hb::posterior_uses_pairs(c->bp, (long)first * c->wl)) ++first;
+        const int rest = c->hl - first;
+        int m = std::min(kHostBands - 1, first > 0 ? rest / first : 0);
+        if (m >= 1) {
+            nb = m + 1;
+            bounds[1] = first;
+            for (int k = 1; k <= m; ++k) bounds[k + 1] = first + (int)((long)rest * k / m);
+        }
     }
     if (!c->s_in) {
         if (cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c->s_alt, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
             return HB_ERR_CUDA;
         }
     }
-    while ((int)c->host_ev.size() < 2 * nb + 1) {
+    while ((int)c->host_ev.size() < 2 * kHostBands + 3) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HB_ERR_CUDA;
         c->host_ev.push_back(e);
     }
-    // the staging buffers may still be in use by work queued earlier on s
-    if (cudaEventRecord(c->host_ev[2 * nb], s) != cudaSuccess || cudaStreamWaitEvent(c->s_in, c->host_ev[2 * nb], 0) ||
-        cudaStreamWaitEvent(c->s_out, c->host_ev[2 * nb], 0))
-        return HB_ERR_CUDA;
-    const unsigned char* fh = static_cast<const unsigned char*>(frame_host);
-    unsigned char* fd = static_cast<unsigned char*>(c->d_frame);
-    for (int k = 0; k < nb; ++k) {
-        const int r0 = k * per * TH, r1 = std::min(c->H, (k + 1) * per * TH);
-        if (cudaMemcpy2DAsync(fd + (size_t)r0 * row, row, fh + (size_t)r0 * row_stride_bytes, row_stride_bytes, row,
-                              r1 - r0, cudaMemcpyHostToDevice, c->s_in) != cudaSuccess ||
-            cudaEventRecord(c->host_ev[2 * k], c->s_in) != cudaSuccess)
-            return HB_ERR_CUDA;
+    // The same buffers, stream and banding twice in a row: capture the sequence as a CUDA
+    // graph, then replay it (one launch instead of some twenty calls).  Not for the learned
+    // low pass (whose sampled pixels change per frame), nor with stage timing armed, nor on
+    // the legacy default stream (which cannot be captured).
+    const HostKey key{frame_host, row_stride_bytes, thb_host, so2_host, s, bounds[1], nb};
+    const bool graphable = !mlp && !c->timing && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+    if (graphable && c->hg_exec && c->hg_key == key) {
+        if (cudaGraphLaunch(c->hg_exec, s) != cudaSuccess) return HB_ERR_CUDA;
+        c->launches += c->hg_kernels;
+        return cudaStreamSynchronize(s) == cudaSuccess ? HB_OK : HB_ERR_CUDA;
     }
-    for (int k = 0; k < nb; ++k) {
-        const int b0 = k * per, b1 = std::min(c->hl, (k + 1) * per);
-        const int r0 = b0 * TH, r1 = std::min(c->H, b1 * TH);
-        Band b = whole_frame(c);
-        b.tp.H = r1 - r0;
-        b.tp.hl = b1 - b0;
-        b.ll_off = (long)b0 * c->wl;
-        b.npix = (long)(b1 - b0) * c->wl;
-        const size_t o = (size_t)r0 * c->W, n = (size_t)(r1 - r0) * c->W;
-        if (cudaStreamWaitEvent(s, c->host_ev[2 * k], 0) != cudaSuccess) return HB_ERR_CUDA;
-        hb_status st = run_band(c, b, fd + (size_t)r0 * row, row, nullptr, c->d_thb + o, c->d_so2 + o, nullptr, 0, s);
+    if (graphable && c->hg_seen && c->hg_key == key) {
+        const long before = c->launches.load();
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return HB_ERR_CUDA;
+        hb_status st = enqueue_host_bands(c, frame_host, row_stride_bytes, thb_host, so2_host, s, bounds, nb);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+        const long kernels = c->launches.load() - before;
+        c->launches -= kernels;  // captured, not run
+        cudaGraphExec_t exec = nullptr;
+        if (st == HB_OK && ee == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+            if (c->hg_exec) cudaGraphExecDestroy(c->hg_exec);
+            c->hg_exec = exec;
+            c->hg_kernels = kernels;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (c->hg_exec && c->hg_key == key && exec) {
+            if (cudaGraphLaunch(c->hg_exec, s) != cudaSuccess) return HB_ERR_CUDA;
+            c->launches += c->hg_kernels;
+            return cudaStreamSynchronize(s) == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+        }
+        c->hg_seen = false;  // capture failed: stay eager
         if (st != HB_OK) return st;
-        if (cudaEventRecord(c->host_ev[2 * k + 1], s) != cudaSuccess ||
-            cudaStreamWaitEvent(c->s_out, c->host_ev[2 * k + 1], 0) != cudaSuccess ||
-            cudaMemcpyAsync(thb_host + o, c->d_thb + o, n * 4, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess ||
-            cudaMemcpyAsync(so2_host + o, c->d_so2 + o, n * 4, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess)
-            return HB_ERR_CUDA;
+    } else {
+        if (c->hg_exec && !(c->hg_key == key)) {  // a graph of other buffers: drop it
+            cudaGraphExecDestroy(c->hg_exec);
+            c->hg_exec = nullptr;
+        }
+        c->hg_key = key;
+        c->hg_seen = graphable;
     }
-    return cudaStreamSynchronize(c->s_out) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess ? HB_OK
-                                                                                                     : HB_ERR_CUDA;
+    hb_status st = enqueue_host_bands(c, frame_host, row_stride_bytes, thb_host, so2_host, s, bounds, nb);
+    if (st != HB_OK) return st;
+    return cudaStreamSynchronize(s) == cudaSuccess ? HB_OK : HB_ERR_CUDA;
 }
 
 hb_status hb_estimate_debug(hb_ctx* c, const void* frame_dev, size_t row_stride_bytes, double* ybar_dev,

@@ -197,6 +197,21 @@ def test_support_rows_leave_the_result_bit_identical():
     assert torch.equal(outs[0][1], outs[binding.HB_FULL_GRID][1])
 
 
+@pytest.mark.parametrize("n1", [16, 60, 128])
+def test_two_pixel_posterior_with_an_odd_pixel_count(n1):
+    """404x604 at 2 levels: 101 x 151 = 15,251 low-pass pixels (odd, enough for two pixels per
+    warp), so the last round has one empty half-warp; against the oracle, and bit-identical
+    to enumerating every node."""
+    A, rgb = small_frame(45, 404, 604, "u8", noise=0.01, nblobs=8, smin=20.0, smax=120.0)
+    grid = _grid(64, n1)
+    ref = oracle.estimate(rgb, A, grid, 2, 1e-3, nthreads=NTH)
+    got = run_gpu(rgb, A, grid, 2, 1e-3)
+    check(got, ref, f"odd pixels n1={n1}")
+    full = run_gpu(rgb, A, grid, 2, 1e-3, flags=binding.HB_FULL_GRID)
+    np.testing.assert_array_equal(got["thb"], full["thb"])
+    np.testing.assert_array_equal(got["so2"], full["so2"])
+
+
 @pytest.mark.parametrize("n0,n1,sigma", [(128, 128, 0.02), (200, 300, 0.005), (64, 16, 0.1), (128, 1, 0.02)])
 def test_support_rows_posterior_alone_matches_full_grid(n0, n1, sigma):
     """Few pixels (a pixel split over several warps): the row bound changes only how rows
@@ -294,10 +309,22 @@ def test_host_entry_in_bands_matches_the_device_call(case):
         hf = torch.from_numpy(rgb).pin_memory()
         th = torch.empty((H, W), dtype=torch.float32).pin_memory()
         sh = torch.empty_like(th).pin_memory()
-        for _ in range(2):
+        for _ in range(2):                      # the default stream: direct calls
             ctx.estimate_host(hf, th, sh)
             np.testing.assert_array_equal(th.numpy(), thb.cpu().numpy())
             np.testing.assert_array_equal(sh.numpy(), so2.cpu().numpy())
+        stream = torch.cuda.Stream()
+        for k in range(4):                      # a stream: direct, captured, then replayed
+            th.zero_()
+            sh.zero_()
+            n0 = ctx.launch_count()
+            ctx.estimate_host(hf, th, sh, stream=stream)
+            assert ctx.launch_count() > n0
+            np.testing.assert_array_equal(th.numpy(), thb.cpu().numpy())
+            np.testing.assert_array_equal(sh.numpy(), so2.cpu().numpy())
+        th2 = torch.empty_like(th).pin_memory()  # other buffers: the graph is not reused for them
+        ctx.estimate_host(hf, th2, sh, stream=stream)
+        np.testing.assert_array_equal(th2.numpy(), thb.cpu().numpy())
 
 
 def test_repeated_calls_are_deterministic_and_counted():

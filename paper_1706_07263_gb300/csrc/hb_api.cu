@@ -55,6 +55,8 @@ struct hb_ctx {
     std::atomic<long> launches{0};
     // learned stand-in
     float* d_mlp = nullptr;       // FP32 masters | Adam m | Adam v | BF16 copies | grad, 5 x kNParams
+    void* d_mlp_img = nullptr;    // the inference kernel's packed image of the BF16 parameters
+    bool mlp_img_dirty = true;    // parameters changed since the image was packed
     float* d_mlp_gpart = nullptr; // per-CTA partial gradients
     float* d_mlp_lpart = nullptr; // per-CTA partial losses
     float* d_mlp_loss = nullptr;  // loss per training step
@@ -319,6 +321,17 @@ hb_status check_frame_args(const hb_ctx* c, const void* frame, size_t stride) {
 // synthesis are launched with programmatic dependent launch (each waits for its
 // predecessor inside the kernel) unless per-stage timing is armed, since timing events
 // between the kernels serialise them anyway.  All-Tikhonov mode: the synthesis alone.
+// The packed image for inference, rebuilt on `s` if the parameters changed.
+const void* mlp_image(hb_ctx* c, cudaStream_t s, cudaError_t& e) {
+    if (c->mlp_img_dirty) {
+        e = hb::launch_mlp_pack(c->d_mlp + 3 * hb::kNParams, c->d_mlp_img, s);
+        c->launches++;
+        if (e != cudaSuccess) return nullptr;
+        c->mlp_img_dirty = false;
+    }
+    return c->d_mlp_img;
+}
+
 // A band of whole superblock rows of the frame: superblocks never straddle two bands, so a
 // band is processed as a frame of its own (its rows, the frame's width) whose low-pass
 // pixels sit at ll_off in the context's arrays.  Only the band holding the frame's last
@@ -352,8 +365,9 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
         if (mlp) {
             // network estimate, sampled exact check, exact recomputation only if the check
             // failed; each kernel waits for its predecessor in-kernel (PDL)
-            e = hb::launch_mlp_forward(c->d_mlp + 3 * hb::kNParams, c->mlp_norm, c->d_ybar_f + 3 * b.ll_off, b.npix,
-                                       chat, pdl, s);
+            const void* img = mlp_image(c, s, e);
+            if (img)
+                e = hb::launch_mlp_forward(img, c->mlp_norm, c->d_ybar_f + 3 * b.ll_off, b.npix, chat, pdl, s);
             if (e == cudaSuccess)
                 e = hb::launch_posterior_check(c->bp, rec, b.npix, c->mlp_nsample, c->frame_seq++, chat,
                                                1.f / c->mlp_ext0, 1.f / c->mlp_ext1, c->d_err, c->mlp_tol, c->d_flags,
@@ -470,6 +484,7 @@ void hb_destroy(hb_ctx* c) {
     cudaFree(c->d_partial);
     cudaFree(c->d_count);
     cudaFree(c->d_mlp);
+    cudaFree(c->d_mlp_img);
     cudaFree(c->d_mlp_gpart);
     cudaFree(c->d_mlp_lpart);
     cudaFree(c->d_mlp_loss);
@@ -791,6 +806,7 @@ hb_status ensure_mlp(hb_ctx* c) {
     if (c->d_mlp) return HB_OK;
     const size_t np = hb::kNParams;
     if (cudaMalloc(&c->d_mlp, sizeof(float) * 5 * np) != cudaSuccess ||
+        cudaMalloc(&c->d_mlp_img, hb::mlp_image_bytes()) != cudaSuccess ||
         cudaMalloc(&c->d_mlp_gpart, sizeof(float) * kMlpMaxBlocks * np) != cudaSuccess ||
         cudaMalloc(&c->d_mlp_lpart, sizeof(float) * kMlpMaxBlocks) != cudaSuccess ||
         cudaMalloc(&c->d_ybar_f, sizeof(float) * 3 * c->npix_ll) != cudaSuccess ||
@@ -855,10 +871,13 @@ hb_status put_params(hb_ctx* c, const float* host) {
         return HB_ERR_CUDA;
     c->adam_t = 0;
     c->mlp_ready = true;
+    c->mlp_img_dirty = true;
     return HB_OK;
 }
 
 }  // namespace
+
+
 
 hb_status hb_mlp_init(hb_ctx* c, unsigned seed) {
     if (!c) return HB_ERR_ARG;
@@ -945,6 +964,7 @@ hb_status hb_mlp_train(hb_ctx* c, const float* ybar_dev, const float* target_dev
             e = hb::launch_mlp_adam(c->d_mlp_gpart, c->d_mlp_lpart, nblocks, batch, grad, c->d_mlp_loss + k, master,
                                     m, v, wbf, (float)lr, 0.9f, 0.999f, 1e-8f, ++c->adam_t, s);
         c->launches += 2;
+        c->mlp_img_dirty = true;
         if (e != cudaSuccess) return HB_ERR_CUDA;
     }
     if (loss_host && steps > 0) {
@@ -979,9 +999,11 @@ hb_status hb_mlp_forward(hb_ctx* c, const float* ybar_dev, long n, float* conc_d
     if (!c->mlp_ready) return HB_ERR_STATE;
     if (n == 0) return HB_OK;
     DeviceGuard g(c->device);
-    cudaError_t e = hb::launch_mlp_forward(c->d_mlp + 3 * hb::kNParams, c->mlp_norm, ybar_dev, n,
-                                           reinterpret_cast<float2*>(conc_dev), false,
-                                           static_cast<cudaStream_t>(stream));
+    cudaError_t e = cudaSuccess;
+    const void* img = mlp_image(c, static_cast<cudaStream_t>(stream), e);
+    if (img)
+        e = hb::launch_mlp_forward(img, c->mlp_norm, ybar_dev, n, reinterpret_cast<float2*>(conc_dev), false,
+                                   static_cast<cudaStream_t>(stream));
     c->launches++;
     return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
 }

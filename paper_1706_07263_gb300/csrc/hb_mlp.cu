@@ -361,31 +361,42 @@ __global__ void mlp_adam_kernel(const float* __restrict__ gpart, const float* __
 // 16 mt + g + {0, 8} of samples 2q, 2q + 1, where GELU, the BF16 rounding of h2 and the
 // lane's share of layer 3 are applied, and shuffles over g finish layer 3.
 constexpr int kWarpsF = 8;
-struct InferSmem {
+struct __align__(16) InferSmem {
     uint4 w2f[kHid / 16][kHid / 16][32];  // W2 A fragments per (m tile, k tile, lane)
     float4 l1[kHid];                      // W1[u][0..2], b1[u]
     float4 l3[kHid];                      // b2[u], W3[0][u], W3[1][u], 0
-    float b3[kOut];
+    float4 b3;                            // b3[0], b3[1], 0, 0
 };
+static_assert(sizeof(InferSmem) % 16 == 0, "the image is copied in 16-byte words");
 
-__global__ void __launch_bounds__(32 * kWarpsF) mlp_forward_kernel(const float* __restrict__ wbf, MlpNorm nm,
-                                                                   const float* __restrict__ ybar, long n,
-                                                                   float2* __restrict__ chat) {
-    __shared__ InferSmem S;
-    // the weights do not come from the preceding kernel: stage them before waiting on it
+// The network as the inference kernel holds it in shared memory, built once per parameter
+// change (mlp_pack_kernel) so that every CTA stages it with coalesced 16-byte loads.
+__global__ void __launch_bounds__(256) mlp_pack_kernel(const float* __restrict__ wbf, InferSmem* __restrict__ img) {
     for (int i = threadIdx.x; i < (kHid / 16) * (kHid / 16) * 32; i += blockDim.x) {
         const int l = i & 31, kt = (i >> 5) % (kHid / 16), mt = i / (32 * (kHid / 16));
         const float* w0 = wbf + kOffW2 + (mt * 16 + (l >> 2)) * kHid + kt * 16 + 2 * (l & 3);
         const float* w8 = w0 + 8 * kHid;
-        S.w2f[mt][kt][l] = make_uint4(pack_bf16(w0[0], w0[1]), pack_bf16(w8[0], w8[1]), pack_bf16(w0[8], w0[9]),
-                                      pack_bf16(w8[8], w8[9]));
+        img->w2f[mt][kt][l] = make_uint4(pack_bf16(w0[0], w0[1]), pack_bf16(w8[0], w8[1]), pack_bf16(w0[8], w0[9]),
+                                         pack_bf16(w8[8], w8[9]));
     }
     for (int u = threadIdx.x; u < kHid; u += blockDim.x) {
-        S.l1[u] = make_float4(wbf[kOffW1 + u * kIn], wbf[kOffW1 + u * kIn + 1], wbf[kOffW1 + u * kIn + 2],
-                              wbf[kOffB1 + u]);
-        S.l3[u] = make_float4(wbf[kOffB2 + u], wbf[kOffW3 + u], wbf[kOffW3 + kHid + u], 0.f);
+        img->l1[u] = make_float4(wbf[kOffW1 + u * kIn], wbf[kOffW1 + u * kIn + 1], wbf[kOffW1 + u * kIn + 2],
+                                 wbf[kOffB1 + u]);
+        img->l3[u] = make_float4(wbf[kOffB2 + u], wbf[kOffW3 + u], wbf[kOffW3 + kHid + u], 0.f);
     }
-    if (threadIdx.x < kOut) S.b3[threadIdx.x] = wbf[kOffB3 + threadIdx.x];
+    if (threadIdx.x == 0) img->b3 = make_float4(wbf[kOffB3], wbf[kOffB3 + 1], 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(32 * kWarpsF) mlp_forward_kernel(const InferSmem* __restrict__ img, MlpNorm nm,
+                                                                   const float* __restrict__ ybar, long n,
+                                                                   float2* __restrict__ chat) {
+    __shared__ InferSmem S;
+    // the weights do not come from the preceding kernel: stage them before waiting on it
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(img);
+        uint4* dst = reinterpret_cast<uint4*>(&S);
+        for (int i = threadIdx.x; i < (int)(sizeof(InferSmem) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
+    }
     __syncthreads();
     // launched after the kernel that writes ybar (programmatic dependent launch, or a
     // plain launch where this returns at once)
@@ -453,8 +464,8 @@ __global__ void __launch_bounds__(32 * kWarpsF) mlp_forward_kernel(const float* 
         if (g < 2 && rs < n) {
             const float ys[3] = {ya, yb, yc};
             const float o0 = (g & 1) ? o10 : o00, o1 = (g & 1) ? o11 : o01;
-            chat[rs] = make_float2(clip_ls(nm, ys, 0) + nm.osc0 * (o0 + S.b3[0]),
-                                   clip_ls(nm, ys, 1) + nm.osc1 * (o1 + S.b3[1]));
+            chat[rs] = make_float2(clip_ls(nm, ys, 0) + nm.osc0 * (o0 + S.b3.x),
+                                   clip_ls(nm, ys, 1) + nm.osc1 * (o1 + S.b3.y));
         }
     }
 }
@@ -488,7 +499,14 @@ cudaError_t launch_mlp_adam(const float* gpart, const float* lpart, int nblocks,
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_forward(const float* wbf, const MlpNorm& nm, const float* ybar, long n, float2* chat, bool pdl,
+size_t mlp_image_bytes() { return sizeof(InferSmem); }
+
+cudaError_t launch_mlp_pack(const float* wbf, void* img, cudaStream_t s) {
+    mlp_pack_kernel<<<1, 256, 0, s>>>(wbf, static_cast<InferSmem*>(img));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_forward(const void* img, const MlpNorm& nm, const float* ybar, long n, float2* chat, bool pdl,
                                cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -507,7 +525,7 @@ cudaError_t launch_mlp_forward(const float* wbf, const MlpNorm& nm, const float*
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, mlp_forward_kernel, wbf, nm, ybar, n, chat);
+    return cudaLaunchKernelEx(&cfg, mlp_forward_kernel, static_cast<const InferSmem*>(img), nm, ybar, n, chat);
 }
 
 }  // namespace hb

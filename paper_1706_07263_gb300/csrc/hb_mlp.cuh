@@ -39,9 +39,13 @@ cudaError_t launch_mlp_train(const float* wbf, const MlpNorm& nm, const float* y
 cudaError_t launch_mlp_adam(const float* gpart, const float* lpart, int nblocks, int batch, float* grad, float* loss,
                             float* master, float* m, float* v, float* wbf, float lr, float beta1, float beta2,
                             float eps, int t, cudaStream_t s);
-// Inference for n samples; pdl: launched as a programmatic dependent of the preceding
-// kernel in the stream (the kernel waits for it before reading ybar).
-cudaError_t launch_mlp_forward(const float* wbf, const MlpNorm& nm, const float* ybar, long n, float2* chat, bool pdl,
+// The inference kernel's shared-memory image of the network (mlp_image_bytes() bytes),
+// packed from the BF16 parameters; to be rebuilt after every parameter change.
+size_t mlp_image_bytes();
+cudaError_t launch_mlp_pack(const float* wbf, void* img, cudaStream_t s);
+// Inference for n samples from a packed image; pdl: launched as a programmatic dependent of
+// the preceding kernel in the stream (the kernel waits for it before reading ybar).
+cudaError_t launch_mlp_forward(const void* img, const MlpNorm& nm, const float* ybar, long n, float2* chat, bool pdl,
                                cudaStream_t s);
 
 }  // namespace hb

@@ -286,6 +286,13 @@ hb_status hb_release(hb_server *srv, int stream_id, int slot);
  * and batches in flight finish.  Lets a caller release a burst of frames at once. */
 hb_status hb_server_pause(hb_server *srv, int paused);
 
+/* Block until every frame submitted so far has completed (is ready for hb_poll or
+ * already polled), e.g. before hb_server_destroy or before a configuration change.
+ * Waits at most timeout_ms milliseconds (0: only test) and then returns
+ * HB_ERR_TIMEOUT, leaving every frame where it is; a paused server with queued
+ * frames therefore times out.  Returns HB_ERR_CUDA if a batch failed since start. */
+hb_status hb_server_drain(hb_server *srv, int timeout_ms);
+
 /* Counters of the server so far. */
 hb_status hb_server_stats(hb_server *srv, hb_server_info *out);
 

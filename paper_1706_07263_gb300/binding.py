@@ -30,7 +30,7 @@ EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_es
             "hb_mlp_init", "hb_mlp_set_params", "hb_mlp_get_params", "hb_lowpass_pairs", "hb_mlp_train",
             "hb_mlp_gradient", "hb_mlp_forward", "hb_set_lowpass_mode", "hb_lowpass_stats",
             "hb_server_create", "hb_server_destroy", "hb_stream_open", "hb_stream_close", "hb_submit", "hb_poll",
-            "hb_release", "hb_server_pause", "hb_server_stats", "hb_posterior_mean_static")
+            "hb_release", "hb_server_pause", "hb_server_drain", "hb_server_stats", "hb_posterior_mean_static")
 HB_FULL_GRID = 1 << 2
 HB_ILLUMINATION = 1 << 5
 HB_LOWPASS_INTENSITY = 1 << 6
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH):
     lib.hb_release.argtypes = [P, I, I]
     lib.hb_server_stats.argtypes = [P, ctypes.POINTER(_ServerInfo)]
     lib.hb_server_pause.argtypes = [P, I]
+    lib.hb_server_drain.argtypes = [P, I]
     for name in EXPORTED:
         getattr(lib, name)
     _lib = lib
@@ -349,6 +350,10 @@ class Server:
 
     def pause(self, paused: bool = True):
         _check(load().hb_server_pause(self._h, int(paused)), "hb_server_pause")
+
+    def drain(self, timeout_ms: int = 10000):
+        """Wait until every submitted frame has completed; HbError (status 6) on timeout."""
+        _check(load().hb_server_drain(self._h, int(timeout_ms)), "hb_server_drain")
 
     def stats(self) -> dict:
         i = _ServerInfo()

@@ -506,6 +506,28 @@ hb_status hb_server_pause(hb_server* srv, int paused) {
     return HB_OK;
 }
 
+hb_status hb_server_drain(hb_server* srv, int timeout_ms) {
+    if (!srv || timeout_ms < 0) return HB_ERR_ARG;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto idle = [&] {
+        if (!srv->queue.empty()) return false;
+        for (int k = 0; k < srv->nbatch_slots; ++k)
+            if (srv->batches[k].busy) return false;
+        for (const Stream& st : srv->streams)
+            for (const Slot& sl : st.slots)
+                if (sl.state == QUEUED + 100) return false;  // a frame still being copied in
+        return true;
+    };
+    // a frame leaving the copy-in state notifies only the loop, so re-check at least every millisecond
+    const auto end = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    while (!idle()) {
+        const auto now = std::chrono::steady_clock::now();
+        if (now >= end) return HB_ERR_TIMEOUT;
+        srv->cv_done.wait_for(lk, std::min<std::chrono::steady_clock::duration>(end - now, std::chrono::milliseconds(1)));
+    }
+    return srv->loop_error;
+}
+
 hb_status hb_server_stats(hb_server* srv, hb_server_info* out) {
     if (!srv || !out) return HB_ERR_ARG;
     std::lock_guard<std::mutex> lk(srv->mu);

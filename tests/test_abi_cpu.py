@@ -77,4 +77,6 @@ def test_null_arguments_are_rejected(lib):
     assert lib.hb_posterior_mean(None, None, 0, None, None) == 1
     assert lib.hb_lowpass_shape(None, None, None) == 1
     assert lib.hb_launch_count(None) == 0
+    assert lib.hb_server_drain(None, 0) == 1
+    assert lib.hb_server_pause(None, 1) == 1
     lib.hb_destroy(None)

@@ -131,3 +131,27 @@ def test_sequential_mode_runs_one_frame_per_batch():
         got = _collect(srv, 6)
         st = srv.stats()
     assert len(got) == 6 and st["batches"] == 6 and st["max_batch_frames"] == 1
+
+
+def test_drain_waits_for_every_frame_and_times_out_while_held():
+    A = synth.make_mixing(7).A
+    frames = _frames(A, 200, 150, 3, 21)
+    with Server(A, GRID, LAM, max_batch=4, batch_lowpass_pixels=100_000) as srv:
+        sid = srv.open_stream(200, 150, 2, slots=4)
+        srv.drain(0)                                      # nothing submitted: idle at once
+        srv.pause(True)
+        for k, fr in enumerate(frames):
+            assert srv.submit(sid, fr, k)
+        t0 = time.time()
+        with pytest.raises(HbError) as e:
+            srv.drain(20)                                 # held frames cannot complete
+        assert e.value.status == 6                        # HB_ERR_TIMEOUT
+        assert 0.015 <= time.time() - t0 < 5.0
+        assert srv.stats()["queued"] == 3                 # the timeout left every frame queued
+        srv.pause(False)
+        srv.drain(10_000)
+        assert srv.stats()["queued"] == 0
+        got = srv.poll(8, wait_us=0)                      # all three ready without waiting
+        assert sorted(r["tag"] for r in got) == [0, 1, 2]
+        for r in got:
+            srv.release(r["stream"], r["slot"])

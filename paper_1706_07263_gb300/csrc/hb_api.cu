@@ -236,6 +236,14 @@ void prepare(hb_ctx* c, const hb_mixing* mix, const hb_grid* g, double lambda) {
         bp.sup_inv_alpha = alpha > 0.0 ? (float)(-0.5 / alpha) : 0.f;
         bp.sup_inv_aq = aq < 0.0 ? (float)(0.5 / aq) : 0.f;
         bp.sup_inv_k1 = (cq < 0.0 && aq < 0.0 && rr != 0.0 && std::isfinite(1.0 / rr)) ? (float)(-1.0 / rr) : 0.f;
+        bp.sup_cols = (bp.sup_rows && cq < 0.0 && std::isfinite(1.0 / cq) && (float)cq < 0.f &&
+                       std::isfinite((float)(alpha / cq)) && std::isfinite((float)(alpha * g->n0 * g->n0)))
+                          ? 1
+                          : 0;
+        bp.span_a2 = bp.sup_cols ? (float)(alpha / cq) : 0.f;
+        bp.span_inv_acq = bp.sup_cols ? (float)(-1.0 / cq) : 0.f;
+        bp.span_cv = bp.sup_cols ? (float)(-0.5 / cq) : 0.f;
+        bp.span_an2 = bp.sup_cols ? (float)(alpha * g->n0 * g->n0) : 0.f;
     }
     auto split = [](double v, float& hi, float& lo) {
         hi = (float)v;

@@ -25,6 +25,10 @@
 #define HB_POST_BOUNDS(cpl) __launch_bounds__(kThreads, (cpl) >= 8 ? 3 : 4)
 #define HB_PAIR_BOUNDS __launch_bounds__(kThreads, 2)
 #endif
+#ifndef HB_SPAN_MINB
+#define HB_SPAN_MINB 2
+#endif
+#define HB_SPAN_BOUNDS __launch_bounds__(kThreads, HB_SPAN_MINB)
 
 namespace hb {
 namespace {
@@ -213,6 +217,199 @@ __global__ void HB_PAIR_BOUNDS posterior_pair_kernel(BayesParams bp, const Bayes
     if (nodes_out && gl == 0 && nodes) atomicAdd(nodes_out, nodes);
 }
 
+// ---- Span kernel: only the nodes inside each row's column interval ---------------------
+//
+// The nodes of a pixel that can hold a non-zero FP32 weight fill a tilted ellipse over the
+// grid (clipped by the grid's edges): taking whole rows would enumerate about three times
+// as many.  The span kernel enumerates, in every row of the ellipse, the 16-column lattice
+// segments that meet the row's column interval (span_pixel, span_row): items of (row,
+// segment), dealt to the 16 lanes of the pixel's half-warp in order.  For the item table the
+// rows go in chunks of 80, five consecutive rows per lane: a lane finds its rows' segments,
+// a scan over the half-warp gives each lane its first item, and the lane writes its items
+// into the half-warp's table in shared memory.  Nodes outside the intervals have weights
+// that are exactly zero, so a pixel's sums equal those over the whole grid up to the order
+// of the additions.
+constexpr int kSpanRows = 5;                 // rows per lane per chunk
+constexpr int kSpanChunk = 16 * kSpanRows;   // rows per chunk
+constexpr int kSpanMaxCols = 128;            // n1 limit
+constexpr int kSpanMaxSegs = kSpanMaxCols / kSpanSeg;
+constexpr int kSpanMaxItems = kSpanChunk * kSpanMaxSegs;
+
+// One item: columns dj0 .. dj0 + 15 of row di (relative to the reference node), in pairs;
+// even and odd pairs keep separate sums.  Adds sum w to SW and sum w di to SD (packed:
+// the two halves are added at the end), sum w dj to T0/T1.
+__device__ __forceinline__ void span_item(const BayesParams& bp, const BayesRec& rec, int di, int dj0, u64& SW,
+                                          u64& SD, u64& T0, u64& T1) {
+    const float d = (float)di;
+    const float R = fmaf(2.f * bp.Bq, d, rec.V);
+    const float S = d * fmaf(bp.Aq, d, rec.U);
+    const u64 RR = pk(R, R), SS = pk(S, S), CC = pk(bp.Cq, bp.Cq), TWO = pk(2.f, 2.f);
+    const float f = (float)dj0;
+    u64 dj = pk(f, f + 1.f);
+    u64 S0 = pk(0.f, 0.f), S1 = pk(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < kSpanSeg / 2; ++q) {
+        const u64 X = fma2(CC, dj, RR);
+        const u64 t = fma2(dj, X, SS);
+        float t0, t1;
+        upk(t, t0, t1);
+        const u64 w = pk(ex2(t0), ex2(t1));
+        if (q & 1) {
+            S1 = add2(S1, w);
+            T1 = fma2(w, dj, T1);
+        } else {
+            S0 = add2(S0, w);
+            T0 = fma2(w, dj, T0);
+        }
+        dj = add2(dj, TWO);
+    }
+    const u64 Sq = add2(S0, S1);
+    SW = add2(SW, Sq);
+    SD = fma2(pk(d, d), Sq, SD);
+}
+
+// The same for a segment cut short by the grid's last column (n1 not a multiple of 16).
+__device__ __forceinline__ void span_item_short(const BayesParams& bp, const BayesRec& rec, int di, int dj0, int n,
+                                                float& sw, float& sdi, float& sdj) {
+    const float d = (float)di;
+    const float R = fmaf(2.f * bp.Bq, d, rec.V);
+    const float S = d * fmaf(bp.Aq, d, rec.U);
+    float s = 0.f;
+    for (int c = 0; c < n; ++c) {
+        const float dj = (float)(dj0 + c);
+        const float w = ex2(fmaf(dj, fmaf(bp.Cq, dj, R), S));
+        s += w;
+        sdj = fmaf(w, dj, sdj);
+    }
+    sw += s;
+    sdi = fmaf(d, s, sdi);
+}
+
+// One round of the span kernel: pixel 2r + half, its sums and its mean.  tab: the
+// half-warp's item table.  nodes: this lane's share of the enumerated-node count.
+template <bool RAGGED>
+__device__ __forceinline__ void span_round(const BayesParams& bp, const BayesRec& rec, long r, long npix, int gl,
+                                           int half, unsigned short* tab, float2* chat, float2* chat_scaled,
+                                           float scale, unsigned long long& nodes) {
+    constexpr int G = 16;
+    const long p = 2 * r + half;
+    const bool valid = p < npix;
+    const SpanPixel sp = span_pixel(bp, rec);
+    const int nseg = (bp.n1 + kSpanSeg - 1) / kSpanSeg;
+    u64 SW = pk(0.f, 0.f), SD = pk(0.f, 0.f), T0 = pk(0.f, 0.f), T1 = pk(0.f, 0.f);
+    float xw = 0.f, xdi = 0.f, xdj = 0.f;  // short segments
+    for (int c0 = sp.rlo; __any_sync(0xffffffffu, c0 < sp.rhi); c0 += kSpanChunk) {
+        int ma[kSpanRows], ns[kSpanRows], tot = 0;
+#pragma unroll
+        for (int q = 0; q < kSpanRows; ++q) {
+            const int i = c0 + kSpanRows * gl + q;
+            span_row(sp, i - rec.i0, nseg, ma[q], ns[q]);
+            if (i >= sp.rhi) ns[q] = 0;
+            tot += ns[q];
+        }
+        int inc = tot;
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, d, G);
+            if (gl >= d) inc += v;
+        }
+        const int K = __shfl_sync(0xffffffffu, inc, G - 1, G);
+        int at = inc - tot;
+#pragma unroll
+        for (int q = 0; q < kSpanRows; ++q) {
+            const unsigned v = ((unsigned)(kSpanRows * gl + q) << 8) | (unsigned)ma[q];
+#pragma unroll
+            for (int m = 0; m < kSpanMaxSegs; ++m)
+                if (m < ns[q]) tab[at + m] = (unsigned short)(v + m);
+            at += ns[q];
+        }
+        __syncwarp();
+        if (valid && gl == 0) nodes += (unsigned)K * kSpanSeg;
+        for (int k = gl; k < K; k += G) {
+            const unsigned e = tab[k];
+            const int di = c0 + (int)(e >> 8) - rec.i0;
+            const int j = (int)(e & 255u) * kSpanSeg;
+            if (RAGGED && j + kSpanSeg > bp.n1) {
+                span_item_short(bp, rec, di, j - rec.j0, bp.n1 - j, xw, xdi, xdj);
+                if (valid) nodes -= (unsigned)(j + kSpanSeg - bp.n1);
+            } else {
+                span_item(bp, rec, di, j - rec.j0, SW, SD, T0, T1);
+            }
+        }
+        __syncwarp();
+    }
+    float a, b;
+    upk(SW, a, b);
+    float sw = (a + b) + xw;
+    upk(SD, a, b);
+    float sdi = (a + b) + xdi;
+    const u64 T = add2(T0, T1);
+    upk(T, a, b);
+    float sdj = (a + b) + xdj;
+    sw = group_sum<G>(sw);
+    sdi = group_sum<G>(sdi);
+    sdj = group_sum<G>(sdj);
+    const bool bad = !usable(sw, sdi, sdj);
+    if (__any_sync(0xffffffffu, bad)) {
+        // far outside the model: the whole grid with an explicit maximum shift (the
+        // partner half-warp takes part in the shuffles and keeps its own sums)
+        const float m = group_max<G>(grid_max<1, G>(bp, rec, gl, 0, bp.n0));
+        float fw = 0.f, fdi = 0.f, fdj = 0.f;
+        grid_sums<1, G>(bp, rec, gl, 0, bp.n0, bad ? m : 0.f, fw, fdi, fdj);
+        fw = group_sum<G>(fw);
+        fdi = group_sum<G>(fdi);
+        fdj = group_sum<G>(fdj);
+        if (bad) {
+            sw = fw;
+            sdi = fdi;
+            sdj = fdj;
+            if (valid && gl == 0) nodes += 2ull * (unsigned)bp.n0 * (unsigned)bp.n1;
+        }
+    }
+    if (valid && gl == 0) write_mean(bp, rec, p, sw, sdi, sdj, chat, chat_scaled, scale);
+}
+
+// Two pixels per warp (half-warp h takes pixel 2r + h of round r), rounds dealt as in the
+// two-pixel kernel below.
+template <bool RAGGED>
+__global__ void HB_SPAN_BOUNDS posterior_span_kernel(BayesParams bp, const BayesRec* __restrict__ recs, long npix,
+                                                     float2* __restrict__ chat, float2* __restrict__ chat_scaled,
+                                                     float scale, PosteriorGate gate, unsigned long long* nodes_out) {
+    const int lane = threadIdx.x & 31, gl = lane & 15, half = lane >> 4;
+    const long rounds = (npix + 1) / 2;
+    __shared__ unsigned short tab[kThreads / 32][2][kSpanMaxItems];
+    __shared__ unsigned ticket;
+    if (threadIdx.x == 0) ticket = 0u;
+    __syncthreads();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    if (gate.run && *gate.run == 0u) return;
+    unsigned short* my = tab[threadIdx.x >> 5][half];
+    unsigned long long nodes = 0;
+    auto next_round = [&]() {
+        unsigned k = 0;
+        if (lane == 0) k = atomicAdd(&ticket, 1u);
+        return (long)blockIdx.x + (long)__shfl_sync(0xffffffffu, k, 0) * gridDim.x;
+    };
+    auto load = [&](long r) { return recs[min(2 * r + half, npix - 1)]; };
+    long r0 = next_round();
+    BayesRec rec0 = {0, 0, 0.f, 0.f};
+    if (r0 < rounds) rec0 = load(r0);
+    while (r0 < rounds) {
+        const long r1 = next_round();
+        BayesRec rec1 = {0, 0, 0.f, 0.f};
+        if (r1 < rounds) rec1 = load(r1);
+        span_round<RAGGED>(bp, rec0, r0, npix, gl, half, my, chat, chat_scaled, scale, nodes);
+        r0 = r1;
+        rec0 = rec1;
+    }
+    if (nodes_out) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nodes += __shfl_xor_sync(0xffffffffu, nodes, off);
+        if (lane == 0 && nodes) atomicAdd(nodes_out, nodes);
+    }
+}
+
 // Resident CTAs per SM for a kernel (cached per device and kernel) and the SM count.
 template <typename K>
 cudaError_t residency(K kernel, int& resident, int& sms) {
@@ -296,28 +493,73 @@ cudaError_t launch_pair(const BayesParams& bp, const BayesRec* rec, long npix, c
                               sc.nodes);
 }
 
+// The span kernel under the same rule as the pair kernel.
+template <bool RAGGED>
+cudaError_t launch_span(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
+                        float2* chat, float2* chat_scaled, float scale, bool pdl, const PosteriorGate& gate,
+                        cudaStream_t s) {
+    int resident = 0, sms = 0;
+    cudaError_t e = residency(posterior_span_kernel<RAGGED>, resident, sms);
+    if (e != cudaSuccess) return e;
+    const long warps = (long)sms * resident * (kThreads / 32);
+    if (npix < 2 * warps) return cudaErrorNotReady;
+    const long rounds = (npix + 1) / 2;
+    long blocks = (rounds + kThreads / 32 - 1) / (kThreads / 32);
+    if (blocks > (long)sms * resident) blocks = (long)sms * resident;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, posterior_span_kernel<RAGGED>, bp, rec, npix, chat, chat_scaled, scale, gate,
+                              sc.nodes);
+}
+
+bool uses_span(const BayesParams& bp) {
+#ifdef HB_POST_NO_SPAN
+    return false;
+#else
+    return bp.sup_cols && bp.n1 <= kSpanMaxCols;
+#endif
+}
+
 }  // namespace
 
 bool posterior_uses_pairs(const BayesParams& bp, long npix) {
-#ifdef HB_POST_NO_PAIRS
-    return false;
-#else
-    if (bp.n1 > 128) return false;
     int resident = 0, sms = 0;
-    cudaError_t e = bp.n1 <= 16   ? residency(posterior_pair_kernel<1>, resident, sms)
-                    : bp.n1 <= 32 ? residency(posterior_pair_kernel<2>, resident, sms)
-                    : bp.n1 <= 64 ? residency(posterior_pair_kernel<4>, resident, sms)
-                                  : residency(posterior_pair_kernel<8>, resident, sms);
-    return e == cudaSuccess && npix >= 2L * sms * resident * (kThreads / 32);
+    cudaError_t e;
+    if (uses_span(bp)) {
+        e = bp.n1 % kSpanSeg ? residency(posterior_span_kernel<true>, resident, sms)
+                             : residency(posterior_span_kernel<false>, resident, sms);
+    } else {
+#ifdef HB_POST_NO_PAIRS
+        return false;
+#else
+        if (bp.n1 > 128) return false;
+        e = bp.n1 <= 16   ? residency(posterior_pair_kernel<1>, resident, sms)
+            : bp.n1 <= 32 ? residency(posterior_pair_kernel<2>, resident, sms)
+            : bp.n1 <= 64 ? residency(posterior_pair_kernel<4>, resident, sms)
+                          : residency(posterior_pair_kernel<8>, resident, sms);
 #endif
+    }
+    return e == cudaSuccess && npix >= 2L * sms * resident * (kThreads / 32);
 }
 
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
                              float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,
                              const PosteriorGate& gate) {
     if (npix <= 0) return cudaSuccess;
+    if (uses_span(bp)) {
+        cudaError_t e = bp.n1 % kSpanSeg ? launch_span<true>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s)
+                                         : launch_span<false>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);
+        if (e != cudaErrorNotReady) return e;
+    }
 #ifndef HB_POST_NO_PAIRS
-    if (bp.n1 <= 128) {
+    else if (bp.n1 <= 128) {
         cudaError_t e = bp.n1 <= 16   ? launch_pair<1>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s)
                         : bp.n1 <= 32 ? launch_pair<2>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s)
                         : bp.n1 <= 64 ? launch_pair<4>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s)

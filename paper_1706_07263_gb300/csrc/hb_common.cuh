@@ -55,6 +55,16 @@ struct BayesParams {
     float sup_inv_alpha;      // 0.5 / (-sup_alpha)
     float sup_inv_aq;         // 0.5 / Aq
     float sup_inv_k1;         // 1 / (-sup_r) where the edge-column pieces apply, else 0
+    // Within row di the exponent is a concave quadratic in dj (Cq < 0), so the columns that
+    // can hold a non-zero weight form one interval: centre j0 + V span_cv - sup_r di,
+    // half-width sqrt(((span_a2 di + b2) di + c2)) with b2 = (U - sup_r V) span_inv_acq and
+    // c2 = (sup_c V^2 + cut) span_inv_acq (same cut).  sup_cols = 1 enumerates only those
+    // intervals (needs sup_rows and Cq < 0).
+    int sup_cols;
+    float span_a2;            // -sup_alpha / |Cq|
+    float span_inv_acq;       // 1 / |Cq|
+    float span_cv;            // -0.5 / Cq
+    float span_an2;           // sup_alpha n0^2 (size of the quadratic term, for the rounding guard)
     int illum;                // 1: A holds (I - 11^T/3) A and the set-up removes ybar's channel mean
 };
 constexpr float kSupportCut = 150.f;
@@ -101,8 +111,9 @@ struct PosteriorGate {
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
                              float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,
                              const PosteriorGate& gate = PosteriorGate{nullptr});
-// Whether launch_posterior takes npix pixels two per warp (each pixel's result then does not
-// depend on the other pixels of the launch).
+// Whether launch_posterior takes npix pixels with the kernel it uses for large launches (two
+// pixels per warp: the span kernel, or the pair kernel without column intervals); each
+// pixel's result then does not depend on the other pixels of the launch.
 bool posterior_uses_pairs(const BayesParams& bp, long npix);
 // Exact posterior of nsample pseudo-randomly drawn pixels (seeded) against another
 // estimate of them: err[k] = the larger of |d c0| inv_ext0 and |d c1| inv_ext1 for the

@@ -205,12 +205,17 @@ __device__ __forceinline__ void superlevel(float qa, float qb, float qc, float i
 // three quadratic pieces.  The rows kept are the union over the pieces of (rows where the
 // piece reaches -cut) within (rows where the piece applies, widened by one), widened by
 // one more row; the reference row (weight exactly 1) is always kept.
+// The exponent below which a node's FP32 weight is exactly zero, for the support bounds:
+// kSupportCut plus a margin for the FP32 evaluation error of t.
+__device__ __forceinline__ float support_cut(const BayesParams& bp, const BayesRec& rec) {
+    return fmaf(1e-6f, fmaf(fabsf(rec.U), (float)bp.n0, fmaf(fabsf(rec.V), (float)bp.n1, bp.sup_mg)), kSupportCut);
+}
+
 __device__ __forceinline__ void support_rows(const BayesParams& bp, const BayesRec& rec, int& lo, int& hi) {
     lo = 0;
     hi = bp.n0;
     if (!bp.sup_rows) return;
-    const float cut = fmaf(1e-6f, fmaf(fabsf(rec.U), (float)bp.n0, fmaf(fabsf(rec.V), (float)bp.n1, bp.sup_mg)),
-                           kSupportCut);
+    const float cut = support_cut(bp, rec);
     // unconstrained row maximum: -alpha di^2 + (U - r V) di + c V^2
     float rlo, rhi;
     superlevel(-bp.sup_alpha, fmaf(-bp.sup_r, rec.V, rec.U), fmaf(rec.V * rec.V, bp.sup_c, cut), bp.sup_inv_alpha,
@@ -249,6 +254,62 @@ __device__ __forceinline__ void support_rows(const BayesParams& bp, const BayesR
     const int z = rec.i0 + (int)ceilf(fminf(rhi, lim)) + 2;
     lo = min(max(a, 0), rec.i0);
     hi = max(min(z, bp.n0), rec.i0 + 1);
+}
+
+// Per-pixel constants of the column intervals (needs bp.sup_cols).  Over real dj the
+// exponent of row di peaks at column j0 + dj*(di), dj*(di) = -(V + 2 Bq di) / (2 Cq), with
+// the value t*(di) = -alpha di^2 + (U - r V) di + c V^2 (the row maximum of support_rows),
+// and stays at or above -cut within h(di) = sqrt((t*(di) + cut) / -Cq) columns of it.
+// Centre and squared half-width are evaluated directly (the two-root formula would
+// cancel).  Rows: where t*(di) >= -cut, widened by one row on each side and clipped to
+// the grid.  A pixel whose terms are large enough for their FP32 rounding to come near the
+// 24 units between the cut and the smallest exponent with a non-zero weight (only for
+// inputs far outside the model) takes every row and column.
+constexpr int kSpanSeg = 16;  // columns per lattice segment
+
+struct SpanPixel {
+    float a2, b2, c2;   // h(di)^2 = (a2 di + b2) di + c2
+    float k1, cc;       // centre column k1 di + cc
+    int rlo, rhi;       // rows [rlo, rhi)
+    bool whole;
+};
+
+__device__ __forceinline__ SpanPixel span_pixel(const BayesParams& bp, const BayesRec& rec) {
+    SpanPixel sp;
+    const float cut = support_cut(bp, rec);
+    const float beta = fmaf(-bp.sup_r, rec.V, rec.U);
+    const float gamma = bp.sup_c * rec.V * rec.V;
+    sp.a2 = bp.span_a2;
+    sp.b2 = beta * bp.span_inv_acq;
+    sp.c2 = (gamma + cut) * bp.span_inv_acq;
+    sp.k1 = -bp.sup_r;
+    sp.cc = fmaf(rec.V, bp.span_cv, (float)rec.j0);
+    float lo, hi;
+    superlevel(-bp.sup_alpha, beta, gamma + cut, bp.sup_inv_alpha, lo, hi);
+    sp.whole = !(fmaf(fabsf(beta), (float)bp.n0, gamma + bp.span_an2) <= 1e6f) || !(lo <= hi);
+    if (sp.whole) {
+        sp.rlo = 0;
+        sp.rhi = bp.n0;
+    } else {
+        const float lim = (float)bp.n0 + 2.f;
+        sp.rlo = min(max(rec.i0 + (int)floorf(fmaxf(lo, -lim)) - 1, 0), rec.i0);
+        sp.rhi = max(min(rec.i0 + (int)ceilf(fminf(hi, lim)) + 2, bp.n0), rec.i0 + 1);
+    }
+    return sp;
+}
+
+// Lattice segments [ma, ma + ns) (kSpanSeg columns each; nseg in a row) of row i0 + di that meet
+// the row's interval, widened by one column on the left and two on the right (far more than
+// the rounding of the centre, the half-width and the approximate square root).
+__device__ __forceinline__ void span_row(const SpanPixel& sp, int di, int nseg, int& ma, int& ns) {
+    const float d = (float)di;
+    const float h2 = fmaf(d, fmaf(sp.a2, d, sp.b2), sp.c2);
+    const float c = fmaf(sp.k1, d, sp.cc);
+    const float h = sqrt_approx(fmaxf(h2, 0.f));
+    const int a = max(__float2int_rd((c - h - 1.f) * (1.f / kSpanSeg)), 0);
+    const int b = min(__float2int_ru((c + h + 2.f) * (1.f / kSpanSeg)), nseg);
+    ma = sp.whole ? 0 : a;
+    ns = sp.whole ? nseg : (h2 >= 0.f ? max(b - a, 0) : 0);
 }
 
 __device__ __forceinline__ bool usable(float sw, float sdi, float sdj) {

@@ -25,10 +25,16 @@
 #define HB_POST_BOUNDS(cpl) __launch_bounds__(kThreads, (cpl) >= 8 ? 3 : 4)
 #define HB_PAIR_BOUNDS __launch_bounds__(kThreads, 2)
 #endif
-#ifndef HB_SPAN_MINB
-#define HB_SPAN_MINB 2
+// The span kernel: CTAs of 16 warps (more warps draw rounds from one shared counter, which
+// evens out the end of the launch), two per SM (64 registers).  Measured on the 1080p
+// workload against 256 threads with 2 or 3 CTAs per SM and 512 with one: equal or faster.
+#ifndef HB_SPAN_THREADS
+#define HB_SPAN_THREADS 512
 #endif
-#define HB_SPAN_BOUNDS __launch_bounds__(kThreads, HB_SPAN_MINB)
+#ifndef HB_SPAN_MINB
+#define HB_SPAN_MINB (1024 / HB_SPAN_THREADS)
+#endif
+#define HB_SPAN_BOUNDS __launch_bounds__(HB_SPAN_THREADS, HB_SPAN_MINB)
 
 namespace hb {
 namespace {
@@ -229,6 +235,7 @@ __global__ void HB_PAIR_BOUNDS posterior_pair_kernel(BayesParams bp, const Bayes
 // into the half-warp's table in shared memory.  Nodes outside the intervals have weights
 // that are exactly zero, so a pixel's sums equal those over the whole grid up to the order
 // of the additions.
+constexpr int kSpanThreads = HB_SPAN_THREADS;
 constexpr int kSpanRows = 5;                 // rows per lane per chunk
 constexpr int kSpanChunk = 16 * kSpanRows;   // rows per chunk
 constexpr int kSpanMaxCols = 128;            // n1 limit
@@ -377,7 +384,7 @@ __global__ void HB_SPAN_BOUNDS posterior_span_kernel(BayesParams bp, const Bayes
                                                      float scale, PosteriorGate gate, unsigned long long* nodes_out) {
     const int lane = threadIdx.x & 31, gl = lane & 15, half = lane >> 4;
     const long rounds = (npix + 1) / 2;
-    __shared__ unsigned short tab[kThreads / 32][2][kSpanMaxItems];
+    __shared__ unsigned short tab[kSpanThreads / 32][2][kSpanMaxItems];
     __shared__ unsigned ticket;
     if (threadIdx.x == 0) ticket = 0u;
     __syncthreads();
@@ -412,7 +419,7 @@ __global__ void HB_SPAN_BOUNDS posterior_span_kernel(BayesParams bp, const Bayes
 
 // Resident CTAs per SM for a kernel (cached per device and kernel) and the SM count.
 template <typename K>
-cudaError_t residency(K kernel, int& resident, int& sms) {
+cudaError_t residency(K kernel, int& resident, int& sms, int threads = kThreads) {
     static K cache_k[64];
     static int cache_res[64], cache_sms[64];
     int dev = 0;
@@ -421,7 +428,7 @@ cudaError_t residency(K kernel, int& resident, int& sms) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (cache_res[dev] == 0 || cache_k[dev] != kernel) {
         e = cudaDeviceGetAttribute(&cache_sms[dev], cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cache_res[dev], kernel, kThreads, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cache_res[dev], kernel, threads, 0);
         if (e != cudaSuccess) return e;
         if (cache_res[dev] < 1) cache_res[dev] = 1;
         cache_k[dev] = kernel;
@@ -499,16 +506,16 @@ cudaError_t launch_span(const BayesParams& bp, const BayesRec* rec, long npix, c
                         float2* chat, float2* chat_scaled, float scale, bool pdl, const PosteriorGate& gate,
                         cudaStream_t s) {
     int resident = 0, sms = 0;
-    cudaError_t e = residency(posterior_span_kernel<RAGGED>, resident, sms);
+    cudaError_t e = residency(posterior_span_kernel<RAGGED>, resident, sms, kSpanThreads);
     if (e != cudaSuccess) return e;
-    const long warps = (long)sms * resident * (kThreads / 32);
+    const long warps = (long)sms * resident * (kSpanThreads / 32);
     if (npix < 2 * warps) return cudaErrorNotReady;
     const long rounds = (npix + 1) / 2;
-    long blocks = (rounds + kThreads / 32 - 1) / (kThreads / 32);
+    long blocks = (rounds + kSpanThreads / 32 - 1) / (kSpanThreads / 32);
     if (blocks > (long)sms * resident) blocks = (long)sms * resident;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(kSpanThreads);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -533,8 +540,9 @@ bool posterior_uses_pairs(const BayesParams& bp, long npix) {
     int resident = 0, sms = 0;
     cudaError_t e;
     if (uses_span(bp)) {
-        e = bp.n1 % kSpanSeg ? residency(posterior_span_kernel<true>, resident, sms)
-                             : residency(posterior_span_kernel<false>, resident, sms);
+        e = bp.n1 % kSpanSeg ? residency(posterior_span_kernel<true>, resident, sms, kSpanThreads)
+                             : residency(posterior_span_kernel<false>, resident, sms, kSpanThreads);
+        return e == cudaSuccess && npix >= 2L * sms * resident * (kSpanThreads / 32);
     } else {
 #ifdef HB_POST_NO_PAIRS
         return false;

@@ -38,7 +38,7 @@ UNIT = "frames/s"
 # DRAM traffic of one posterior launch on this workload from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/posterior_kernel_frame1080p_u8_l3_g128.md),
 # valid only while the kernel's sources hash to the value recorded with it.
-POSTERIOR_TRAFFIC = {"bytes": 539648, "sources_sha256_16": "d394457348ffe1ad",
+POSTERIOR_TRAFFIC = {"bytes": 541696, "sources_sha256_16": "35c683646c193c47",
                      "sources": ("paper_1706_07263_gb300/csrc/hb_bayes.cu", "paper_1706_07263_gb300/csrc/hb_common.cuh",
                                  "paper_1706_07263_gb300/csrc/hb_device.cuh",
                                  "paper_1706_07263_gb300/csrc/hb_posterior.cuh")}
@@ -608,8 +608,9 @@ def run_ours(args):
     e2e_s, e2e_frames = replicas.aggregate(time.perf_counter() - t0, args.steps, device=dev)
 
     # roofline of the dominant kernel (grid posterior): algorithmic work = every grid node of
-    # every low-pass pixel, one ex2 each; the kernel enumerates only the rows that can hold a
-    # non-zero FP32 weight (its own counter), which changes the work and not the result
+    # every low-pass pixel, one ex2 each; the kernel enumerates only the 16-column segments of
+    # each grid row that meet the row's interval of non-zero FP32 weights (its own counter),
+    # which changes the work and not the result
     post_ms, post_n = stage["lowpass"]
     post_avg_s = post_ms / max(post_n, 1) * 1e-3
     nodes_grid = hl * wl_ * wl.grid[0] * wl.grid[1]
@@ -635,7 +636,8 @@ def run_ours(args):
                      "units": "grid nodes of every low-pass pixel (32,400 x 16,384 per frame), one ex2 each",
                      "enumerated": {"nodes_per_launch": nodes, "share_of_grid": nodes / nodes_grid,
                                     "achieved": nodes / post_avg_s / 1e12, "frac": nodes / post_avg_s / 1e12 / peak,
-                                    "note": "nodes the kernel evaluates: rows that can hold a non-zero FP32 weight"},
+                                    "note": "nodes the kernel evaluates: per grid row, the 16-column segments meeting "
+                                            "the row's interval of non-zero FP32 weights"},
                      "traffic": posterior_traffic(),
                      "timing": "CUDA events around each posterior launch, K more steps after the timed region",
                      "peak_note": "152 SMs x 32 ex2/clk/SM x 2070 MHz (unit count measured by probe)"},

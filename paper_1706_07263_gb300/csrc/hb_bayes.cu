@@ -25,14 +25,14 @@
 #define HB_POST_BOUNDS(cpl) __launch_bounds__(kThreads, (cpl) >= 8 ? 3 : 4)
 #define HB_PAIR_BOUNDS __launch_bounds__(kThreads, 2)
 #endif
-// The span kernel: CTAs of 16 warps (more warps draw rounds from one shared counter, which
-// evens out the end of the launch), two per SM (64 registers).  Measured on the 1080p
-// workload against 256 threads with 2 or 3 CTAs per SM and 512 with one: equal or faster.
+// The span kernel: CTAs of 8 warps, two per SM (98 registers).  Measured on the 1080p
+// workload against 16 warps with one or two CTAs per SM and 8 warps with three: equal or
+// faster, and it takes the fewest pixels to fill the GPU (banded host calls).
 #ifndef HB_SPAN_THREADS
-#define HB_SPAN_THREADS 512
+#define HB_SPAN_THREADS 256
 #endif
 #ifndef HB_SPAN_MINB
-#define HB_SPAN_MINB (1024 / HB_SPAN_THREADS)
+#define HB_SPAN_MINB 2
 #endif
 #define HB_SPAN_BOUNDS __launch_bounds__(HB_SPAN_THREADS, HB_SPAN_MINB)
 

@@ -2,12 +2,16 @@
 // low-pass pixel (the Bayesian estimate on the low-pass band, Section 2); the per-pixel
 // sums are in hb_posterior.cuh.
 //
-// Work split: a unit is (pixel, part); the rs parts of a pixel take contiguous ranges of
-// its support rows (rs = 1 unless there are fewer pixels than resident warps: a split
-// costs partial sums and an atomic hand-off).  Warps are persistent (one grid of resident
-// CTAs walks all units) and prefetch the next unit's record.  Warp shuffles combine
-// lanes; when a pixel is split, the last part to finish (atomic counter) adds the parts'
-// sums in a fixed order, so results do not depend on scheduling.
+// Three kernels, all with persistent warps that prefetch their next record:
+//   posterior_span_kernel  two pixels per warp; per pixel only the column interval of each
+//                          row that can hold a non-zero FP32 weight (the default);
+//   posterior_pair_kernel  two pixels per warp over whole rows (every node enumerated, or
+//                          no column intervals for this grid);
+//   posterior_kernel       one warp per unit (pixel, part) for launches with fewer pixels
+//                          than twice the resident warps: the rs parts of a pixel take
+//                          contiguous ranges of its rows, and the last part to finish
+//                          (atomic counter) adds the parts' sums in a fixed order.
+// Which warp computes a pixel never changes its result.
 #include "hb_common.cuh"
 #include "hb_device.cuh"
 #include "hb_posterior.cuh"

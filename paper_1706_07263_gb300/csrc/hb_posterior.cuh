@@ -1,5 +1,5 @@
-// hb_posterior.cuh -- the grid posterior's per-pixel sums, shared by the posterior
-// kernel and the learned stand-in's sampled check.  Internal to libhb.
+// hb_posterior.cuh -- the grid posterior's per-pixel sums and support bounds, shared by
+// the posterior kernels and the learned stand-in's sampled check.  Internal to libhb.
 //
 // For a pixel with block-mean log-attenuation ybar the posterior over grid node k is
 // proportional to exp(-|ybar - A c_k|^2 / (2 sigma^2)) (flat prior).  Expanded around
@@ -16,14 +16,16 @@
 // overflow; a pixel whose sums still come out non-finite (only possible for inputs far
 // outside the model) is recomputed with an explicit maximum pass.
 //
-// Only the grid rows that can hold a non-zero FP32 weight are enumerated (support_rows):
-// outside them every 2^t is below 2^-150 and ex2.approx.ftz returns exactly 0, so the
-// sums are the same as over the whole grid.
+// Only nodes that can hold a non-zero FP32 weight are enumerated: the grid rows of
+// support_rows (whole-row kernels) or, per row, the column interval of span_pixel /
+// span_row (span kernel).  Outside them every 2^t is below 2^-150 and ex2.approx.ftz
+// returns exactly 0, so the sums are those over the whole grid up to the order of the
+// additions.
 //
-// Lane l of a warp takes grid columns l, l+32, l+64, ... (CPL columns per lane).  Per
-// pair of grid nodes a lane issues two packed FP32x2 FMAs for the exponents, two MUFU ex2
-// and two packed instructions for the sums (sum w and sum w*di per column; sum w*dj
-// follows from the column sums).
+// Whole-row kernels: lane l of a group takes grid columns l, l+G, l+2G, ... (CPL columns
+// per lane).  Per pair of grid nodes a lane issues two packed FP32x2 FMAs for the
+// exponents, two MUFU ex2 and two packed instructions for the sums (sum w and sum w*di per
+// column; sum w*dj follows from the column sums).
 #pragma once
 
 #include "hb_common.cuh"

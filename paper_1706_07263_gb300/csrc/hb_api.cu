@@ -295,8 +295,11 @@ void prepare_constants(const hb_mixing* mix, const hb_grid* grid, double lambda,
 
 namespace {
 
-hb::PosteriorScratch post_scratch(const hb_ctx* c) {
-    return hb::PosteriorScratch{c->d_partial, c->d_count, hb::kMaxParts, c->timing ? c->d_nodes : nullptr};
+// Posterior scratch for the low-pass pixels from ll_off on (launches that may run at the same
+// time take disjoint pixel ranges, so their counters are disjoint as well).
+hb::PosteriorScratch post_scratch(const hb_ctx* c, long ll_off = 0) {
+    return hb::PosteriorScratch{c->d_partial + (size_t)3 * hb::kMaxParts * ll_off, c->d_count + ll_off, hb::kMaxParts,
+                                c->timing ? c->d_nodes : nullptr};
 }
 
 // Event bracket around one launch when timing is armed.
@@ -381,12 +384,13 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
                                                1.f / c->mlp_ext0, 1.f / c->mlp_ext1, c->d_err, c->mlp_tol, c->d_flags,
                                                pdl, s);
             if (e == cudaSuccess)
-                e = hb::launch_posterior(c->bp, rec, b.npix, post_scratch(c), chat, nullptr, scale, pdl, s,
-                                         hb::PosteriorGate{c->d_flags + 2});
+                e = hb::launch_posterior(c->bp, rec, b.npix, post_scratch(c, b.ll_off), chat, nullptr, scale, pdl,
+                                         s, hb::PosteriorGate{c->d_flags + 2});
             c->launches += 3;
             c->mlp_frames++;
         } else {
-            e = hb::launch_posterior(c->bp, rec, b.npix, post_scratch(c), chat, conc_scaled, scale, pdl, s);
+            e = hb::launch_posterior(c->bp, rec, b.npix, post_scratch(c, b.ll_off), chat, conc_scaled, scale, pdl,
+                                     s);
             c->launches++;
         }
     }

@@ -131,6 +131,20 @@ hb_status hb_estimate(hb_ctx *ctx, const void *frame_dev, size_t row_stride_byte
 hb_status hb_estimate_host(hb_ctx *ctx, const void *frame_host, size_t row_stride_bytes, float *thb_host,
                            float *so2_host, void *stream);
 
+/* hb_estimate_host without the final synchronisation, for streams of frames: the call
+ * queues the copies and kernels and returns; THb and SO2 are in the host buffers once
+ * `stream` has reached the point of the call (cudaStreamSynchronize or an event on it).
+ * Successive calls overlap: the context alternates two staging sets, so one frame's input
+ * copy and kernels run while the previous frame's results are copied back.  Nothing waits
+ * for work queued on `stream` before the call, so the host frame must be complete when the
+ * call is made, and it and the output buffers must stay untouched until the stream has
+ * passed the call.  Results equal hb_estimate_host's (the same bands and kernels).  A
+ * synchronous call on the context first waits for asynchronous calls still in flight.
+ * Returns HB_ERR_STATE while per-stage timing is armed (hb_timing_start); otherwise as
+ * hb_estimate_host. */
+hb_status hb_estimate_host_async(hb_ctx *ctx, const void *frame_host, size_t row_stride_bytes, float *thb_host,
+                                 float *so2_host, void *stream);
+
 /* Intermediate results of the same pipeline, for testing.  Any output may be NULL.
  *   ybar_dev  : hl*wl*3 doubles, low-pass band divided by 2^n (block mean of y).
  *   conc_dev  : hl*wl*2 floats, concentration low-pass coefficients 2^n * estimate.

@@ -25,7 +25,8 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_SHAPE", 3: "HB_ERR_CUDA", 4: "
           6: "HB_ERR_TIMEOUT", 7: "HB_ERR_STATE"}
 
 # Every symbol include/hb.h declares (checked by the CPU tests against the built library).
-EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_estimate_debug", "hb_posterior_mean",
+EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_estimate_host_async", "hb_estimate_debug",
+            "hb_posterior_mean",
             "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_timing_nodes", "hb_strerror",
             "hb_mlp_init", "hb_mlp_set_params", "hb_mlp_get_params", "hb_lowpass_pairs", "hb_mlp_train",
             "hb_mlp_gradient", "hb_mlp_forward", "hb_set_lowpass_mode", "hb_lowpass_stats",
@@ -85,6 +86,7 @@ def load(path: str = LIB_PATH):
     lib.hb_destroy.restype = None
     lib.hb_estimate.argtypes = [P, P, S, P, P, P]
     lib.hb_estimate_host.argtypes = [P, P, S, P, P, P]
+    lib.hb_estimate_host_async.argtypes = [P, P, S, P, P, P]
     lib.hb_estimate_debug.argtypes = [P, P, S, P, P, P, P, P]
     lib.hb_posterior_mean.argtypes = [P, P, L, P, P]
     lib.hb_lowpass_shape.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
@@ -206,6 +208,15 @@ class Context:
         stride = frame.strides[0] if isinstance(frame, np.ndarray) else frame.stride(0) * frame.element_size()
         _check(load().hb_estimate_host(self._h, hp(frame), stride, hp(thb), hp(so2), _stream(stream)),
                "hb_estimate_host")
+
+    def estimate_host_async(self, frame, thb, so2, stream=None):
+        """As estimate_host, returning before the results arrive: they are in thb/so2 once
+        `stream` has been synchronised; the buffers must stay alive and untouched until then."""
+        def hp(a):
+            return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+        stride = frame.strides[0] if isinstance(frame, np.ndarray) else frame.stride(0) * frame.element_size()
+        _check(load().hb_estimate_host_async(self._h, hp(frame), stride, hp(thb), hp(so2), _stream(stream)),
+               "hb_estimate_host_async")
 
     def estimate_debug(self, frame, ybar=None, conc=None, hbo2=None, hb=None, stream=None):
         stride = frame.stride(0) * frame.element_size()

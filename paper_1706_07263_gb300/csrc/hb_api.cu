@@ -79,6 +79,15 @@ struct hb_ctx {
     // hb_estimate_host: copy streams and per-band events (created on first use)
     cudaStream_t s_in = nullptr, s_out = nullptr, s_alt = nullptr;
     std::vector<cudaEvent_t> host_ev;
+    // hb_estimate_host_async: a second staging set (the first is d_frame, d_thb, d_so2), the
+    // compute stream of the even bands, and per set the event after its last output copy
+    void* d_frame2 = nullptr;
+    float* d_thb2 = nullptr;
+    float* d_so22 = nullptr;
+    cudaStream_t s_c0 = nullptr;
+    cudaEvent_t set_free[2] = {nullptr, nullptr};
+    int set_next = 0;
+    bool async_pending = false;
     HostKey hg_key{};                 // the buffers etc. of the last call, and its captured graph
     bool hg_seen = false;
     cudaGraphExec_t hg_exec = nullptr;
@@ -92,14 +101,23 @@ struct hb_ctx {
 
 namespace {
 
-// Row bands of the pipelined host entry point (at most).  The copies of a 1920x1080 u8
-// frame need ~95 us with both directions of the host link (~190 GB/s each) busy; a call
-// measures ~155 us with 3 to 5 bands (201 us unbanded), and the synthesis storing THb/SO2
-// straight into pinned host memory instead of the output copies measured the same.
+// Row bands of the synchronous host entry point (at most).  The copies of a 1920x1080 u8
+// frame need ~98 us with both directions of the host link (~190 GB/s each) busy; a call
+// measures ~157 us with 3 bands (201 us unbanded, more with 4 or more), and the synthesis
+// storing THb/SO2 straight into pinned host memory instead of the output copies measured
+// the same.
 #ifndef HB_HOST_BANDS
 #define HB_HOST_BANDS 3
 #endif
 constexpr int kHostBands = HB_HOST_BANDS;
+// Row bands of the asynchronous host entry point (at most).  Successive frames overlap there,
+// which keeps the host link busy without splitting a frame: a 1920x1080 u8 frame measured
+// 101 us per frame in steady state with one band, 107 us with two and 112 us with three
+// (the two copies alone need ~98 us).
+#ifndef HB_ASYNC_BANDS
+#define HB_ASYNC_BANDS 1
+#endif
+constexpr int kAsyncBands = HB_ASYNC_BANDS < HB_HOST_BANDS ? HB_ASYNC_BANDS : HB_HOST_BANDS;
 
 struct DeviceGuard {
     int prev = -1;
@@ -507,11 +525,17 @@ void hb_destroy(hb_ctx* c) {
     cudaFree(c->d_frame);
     cudaFree(c->d_thb);
     cudaFree(c->d_so2);
+    cudaFree(c->d_frame2);
+    cudaFree(c->d_thb2);
+    cudaFree(c->d_so22);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : c->host_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->set_free)
+        if (e) cudaEventDestroy(e);
     if (c->s_in) cudaStreamDestroy(c->s_in);
     if (c->s_out) cudaStreamDestroy(c->s_out);
     if (c->s_alt) cudaStreamDestroy(c->s_alt);
+    if (c->s_c0) cudaStreamDestroy(c->s_c0);
     if (c->hg_exec) cudaGraphExecDestroy(c->hg_exec);
     cudaGetLastError();
     delete c;
@@ -531,23 +555,39 @@ hb_status hb_estimate(hb_ctx* c, const void* frame_dev, size_t row_stride_bytes,
 
 namespace {
 
-// Everything of one hb_estimate_host call in stream order, ending with every side stream
-// joined back into s (so that the sequence can also be captured as a graph).
+// Staging buffers of one host call: the frame, THb and SO2 on the device.
+struct HostSet {
+    unsigned char* frame;
+    float* thb;
+    float* so2;
+};
+
+// Everything of one host call in stream order.  Synchronous calls (async = false): the side
+// streams start after the work queued earlier on s, the even bands compute on s, and every
+// side stream is joined back into s (so that the sequence can also be captured as a graph).
+// Asynchronous calls: nothing waits for s; the input copies wait until the staging set's
+// previous frame has finished its output copies (free_set), the even bands compute on s_c0,
+// and free_set is recorded after the last output copy, which s then waits for.  Band k always
+// computes on the same stream, so the low-pass records and estimates of a band, shared by
+// successive frames, are reused in stream order.
 hb_status enqueue_host_bands(hb_ctx* c, const void* frame_host, size_t row_stride_bytes, float* thb_host,
-                             float* so2_host, cudaStream_t s, const int* bounds, int nb) {
+                             float* so2_host, cudaStream_t s, const int* bounds, int nb, const HostSet& set,
+                             bool async, cudaEvent_t free_set) {
     const int TH = 1 << c->levels;
     const size_t row = (size_t)c->W * 3 * elem_size(c->fmt);
-    // the staging buffers may still be in use by work queued earlier on s
     cudaEvent_t ev_start = c->host_ev[2 * nb], ev_alt = c->host_ev[2 * nb + 1], ev_out = c->host_ev[2 * nb + 2];
-    if (cudaEventRecord(ev_start, s) != cudaSuccess || cudaStreamWaitEvent(c->s_in, ev_start, 0) ||
-        cudaStreamWaitEvent(c->s_out, ev_start, 0) || cudaStreamWaitEvent(c->s_alt, ev_start, 0))
+    if (async) {
+        if (cudaStreamWaitEvent(c->s_in, free_set, 0) != cudaSuccess) return HB_ERR_CUDA;
+    } else if (cudaEventRecord(ev_start, s) != cudaSuccess || cudaStreamWaitEvent(c->s_in, ev_start, 0) ||
+               cudaStreamWaitEvent(c->s_out, ev_start, 0) || cudaStreamWaitEvent(c->s_alt, ev_start, 0)) {
+        // the staging buffers may still be in use by work queued earlier on s
         return HB_ERR_CUDA;
+    }
     const unsigned char* fh = static_cast<const unsigned char*>(frame_host);
-    unsigned char* fd = static_cast<unsigned char*>(c->d_frame);
     for (int k = 0; k < nb; ++k) {
         const int r0 = bounds[k] * TH, r1 = std::min(c->H, bounds[k + 1] * TH);
-        if (cudaMemcpy2DAsync(fd + (size_t)r0 * row, row, fh + (size_t)r0 * row_stride_bytes, row_stride_bytes, row,
-                              r1 - r0, cudaMemcpyHostToDevice, c->s_in) != cudaSuccess ||
+        if (cudaMemcpy2DAsync(set.frame + (size_t)r0 * row, row, fh + (size_t)r0 * row_stride_bytes,
+                              row_stride_bytes, row, r1 - r0, cudaMemcpyHostToDevice, c->s_in) != cudaSuccess ||
             cudaEventRecord(c->host_ev[2 * k], c->s_in) != cudaSuccess)
             return HB_ERR_CUDA;
     }
@@ -562,15 +602,21 @@ hb_status enqueue_host_bands(hb_ctx* c, const void* frame_host, size_t row_strid
         const size_t o = (size_t)r0 * c->W, n = (size_t)(r1 - r0) * c->W;
         // alternate bands between two compute streams: neighbouring bands share no data, and
         // one band's kernels fill the ramp and tail of the other's
-        cudaStream_t cs = (k & 1) ? c->s_alt : s;
+        cudaStream_t cs = (k & 1) ? c->s_alt : (async ? c->s_c0 : s);
         if (cudaStreamWaitEvent(cs, c->host_ev[2 * k], 0) != cudaSuccess) return HB_ERR_CUDA;
-        hb_status st = run_band(c, b, fd + (size_t)r0 * row, row, nullptr, c->d_thb + o, c->d_so2 + o, nullptr, 0, cs);
+        hb_status st = run_band(c, b, set.frame + (size_t)r0 * row, row, nullptr, set.thb + o, set.so2 + o, nullptr, 0,
+                                cs);
         if (st != HB_OK) return st;
         if (cudaEventRecord(c->host_ev[2 * k + 1], cs) != cudaSuccess ||
             cudaStreamWaitEvent(c->s_out, c->host_ev[2 * k + 1], 0) != cudaSuccess ||
-            cudaMemcpyAsync(thb_host + o, c->d_thb + o, n * 4, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess ||
-            cudaMemcpyAsync(so2_host + o, c->d_so2 + o, n * 4, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess)
+            cudaMemcpyAsync(thb_host + o, set.thb + o, n * 4, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess ||
+            cudaMemcpyAsync(so2_host + o, set.so2 + o, n * 4, cudaMemcpyDeviceToHost, c->s_out) != cudaSuccess)
             return HB_ERR_CUDA;
+    }
+    if (async) {  // every band's output copy follows its kernels, so s_out's end covers all
+        if (cudaEventRecord(free_set, c->s_out) != cudaSuccess || cudaStreamWaitEvent(s, free_set, 0) != cudaSuccess)
+            return HB_ERR_CUDA;
+        return HB_OK;
     }
     // later work on s is ordered after every band and every copy
     if (cudaEventRecord(ev_alt, c->s_alt) != cudaSuccess || cudaStreamWaitEvent(s, ev_alt, 0) != cudaSuccess ||
@@ -579,51 +625,50 @@ hb_status enqueue_host_bands(hb_ctx* c, const void* frame_host, size_t row_strid
     return HB_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_bytes, float* thb_host,
-                           float* so2_host, void* stream) {
+// What both host entry points need: arguments checked, staging sets (two for asynchronous
+// calls), side streams and events created, and the band bounds.
+// Bands of whole superblock rows, pipelined: band k's frame rows go up on s_in while band
+// k-1 computes (on an even-band stream or s_alt) and band k-2's THb/SO2 rows come back on
+// s_out.  The learned low pass takes the whole frame at once (its fallback decision is per
+// frame).  Bands are used only where every band's posterior takes the two-pixel kernel, as
+// the whole frame's does: each pixel's result is then the same as in hb_estimate.  The first
+// band is kept small, so that the first output copy starts early: the fewest superblock
+// rows that still take the two-pixel posterior (or a 2*kHostBands-th of the frame without a
+// posterior); the other rows are shared evenly among the other bands, none smaller than the
+// first.
+hb_status host_prepare(hb_ctx* c, const void* frame_host, size_t row_stride_bytes, const float* thb_host,
+                       const float* so2_host, bool two_sets, int max_bands, int* bounds, int& nb, bool& mlp) {
     if (!c || !frame_host || !thb_host || !so2_host) return HB_ERR_ARG;
-    const size_t es = elem_size(c->fmt);
-    const size_t row = (size_t)c->W * 3 * es;
+    const size_t row = (size_t)c->W * 3 * elem_size(c->fmt);
     if (row_stride_bytes < row) return HB_ERR_ARG;
-    DeviceGuard g(c->device);
     const size_t npx = (size_t)c->W * c->H;
-    if (!c->d_frame) {  // staging buffers, allocated on first use
-        if (cudaMalloc(&c->d_frame, row * c->H) != cudaSuccess || cudaMalloc(&c->d_thb, npx * 4) != cudaSuccess ||
-            cudaMalloc(&c->d_so2, npx * 4) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(c->d_frame);
-            cudaFree(c->d_thb);
-            cudaFree(c->d_so2);
-            c->d_frame = nullptr;
-            c->d_thb = nullptr;
-            c->d_so2 = nullptr;
-            return HB_ERR_OOM;
-        }
-    }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // Bands of whole superblock rows, pipelined: band k's frame rows go up on s_in while
-    // band k-1 computes (on s or s_alt) and band k-2's THb/SO2 rows come back on s_out.  The
-    // learned low pass takes the whole frame at once (its fallback decision is per frame).
-    // Bands are used only where every band's posterior takes the two-pixel kernel, as the
-    // whole frame's does: each pixel's result is then the same as in hb_estimate.
-    // The first band is kept small, so that the first output copy starts early: the fewest
-    // superblock rows that still take the two-pixel posterior (or a 2*kHostBands-th of the
-    // frame without a posterior); the other rows are shared evenly among the other bands,
-    // none smaller than the first.
+    auto alloc = [&](void*& f, float*& t, float*& o) {
+        if (f) return true;
+        if (cudaMalloc(&f, row * c->H) == cudaSuccess && cudaMalloc(&t, npx * 4) == cudaSuccess &&
+            cudaMalloc(&o, npx * 4) == cudaSuccess)
+            return true;
+        cudaGetLastError();
+        cudaFree(f);
+        cudaFree(t);
+        cudaFree(o);
+        f = nullptr;
+        t = nullptr;
+        o = nullptr;
+        return false;
+    };
+    if (!alloc(c->d_frame, c->d_thb, c->d_so2) || (two_sets && !alloc(c->d_frame2, c->d_thb2, c->d_so22)))
+        return HB_ERR_OOM;
     const bool bayes = !(c->flags & HB_LOWPASS_TIKHONOV);
-    const bool mlp = bayes && c->lowpass_mode == HB_MODE_MLP;
-    int bounds[kHostBands + 1] = {0, c->hl};
-    int nb = 1;
-    if (!mlp && kHostBands > 1) {
-        int first = std::max(1, c->hl / (2 * kHostBands));
+    mlp = bayes && c->lowpass_mode == HB_MODE_MLP;
+    bounds[0] = 0;
+    bounds[1] = c->hl;
+    nb = 1;
+    if (!mlp && max_bands > 1) {
+        int first = std::max(1, c->hl / (2 * max_bands));
         if (bayes)
             while (first < c->hl && !hb::posterior_uses_pairs(c->bp, (long)first * c->wl)) ++first;
         const int rest = c->hl - first;
-        int m = std::min(kHostBands - 1, first > 0 ? rest / first : 0);
+        int m = std::min(max_bands - 1, first > 0 ? rest / first : 0);
         if (m >= 1) {
             nb = m + 1;
             bounds[1] = first;
@@ -638,11 +683,44 @@ hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_
             return HB_ERR_CUDA;
         }
     }
+    if (two_sets && !c->s_c0) {
+        if (cudaStreamCreateWithFlags(&c->s_c0, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->set_free[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->set_free[1], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return HB_ERR_CUDA;
+        }
+    }
     while ((int)c->host_ev.size() < 2 * kHostBands + 3) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return HB_ERR_CUDA;
         c->host_ev.push_back(e);
     }
+    return HB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_bytes, float* thb_host,
+                           float* so2_host, void* stream) {
+    if (!c) return HB_ERR_ARG;
+    DeviceGuard g(c->device);
+    int bounds[kHostBands + 1];
+    int nb = 1;
+    bool mlp = false;
+    hb_status pst =
+        host_prepare(c, frame_host, row_stride_bytes, thb_host, so2_host, false, kHostBands, bounds, nb, mlp);
+    if (pst != HB_OK) return pst;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (c->async_pending) {  // asynchronous calls still in flight use the same streams and buffers
+        if (cudaStreamSynchronize(c->s_in) != cudaSuccess || cudaStreamSynchronize(c->s_c0) != cudaSuccess ||
+            cudaStreamSynchronize(c->s_alt) != cudaSuccess || cudaStreamSynchronize(c->s_out) != cudaSuccess)
+            return HB_ERR_CUDA;
+        c->async_pending = false;
+    }
+    const HostSet set{static_cast<unsigned char*>(c->d_frame), c->d_thb, c->d_so2};
     // The same buffers, stream and banding twice in a row: capture the sequence as a CUDA
     // graph, then replay it (one launch instead of some twenty calls).  Not for the learned
     // low pass (whose sampled pixels change per frame), nor with stage timing armed, nor on
@@ -657,7 +735,8 @@ hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_
     if (graphable && c->hg_seen && c->hg_key == key) {
         const long before = c->launches.load();
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return HB_ERR_CUDA;
-        hb_status st = enqueue_host_bands(c, frame_host, row_stride_bytes, thb_host, so2_host, s, bounds, nb);
+        hb_status st =
+            enqueue_host_bands(c, frame_host, row_stride_bytes, thb_host, so2_host, s, bounds, nb, set, false, nullptr);
         cudaGraph_t graph = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(s, &graph);
         const long kernels = c->launches.load() - before;
@@ -685,9 +764,32 @@ hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_
         c->hg_key = key;
         c->hg_seen = graphable;
     }
-    hb_status st = enqueue_host_bands(c, frame_host, row_stride_bytes, thb_host, so2_host, s, bounds, nb);
+    hb_status st =
+        enqueue_host_bands(c, frame_host, row_stride_bytes, thb_host, so2_host, s, bounds, nb, set, false, nullptr);
     if (st != HB_OK) return st;
     return cudaStreamSynchronize(s) == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+}
+
+hb_status hb_estimate_host_async(hb_ctx* c, const void* frame_host, size_t row_stride_bytes, float* thb_host,
+                                 float* so2_host, void* stream) {
+    if (!c) return HB_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (c->timing) return HB_ERR_STATE;
+    int bounds[kHostBands + 1];
+    int nb = 1;
+    bool mlp = false;
+    hb_status pst =
+        host_prepare(c, frame_host, row_stride_bytes, thb_host, so2_host, true, kAsyncBands, bounds, nb, mlp);
+    if (pst != HB_OK) return pst;
+    const int j = c->set_next;
+    const HostSet set = j == 0 ? HostSet{static_cast<unsigned char*>(c->d_frame), c->d_thb, c->d_so2}
+                               : HostSet{static_cast<unsigned char*>(c->d_frame2), c->d_thb2, c->d_so22};
+    hb_status st = enqueue_host_bands(c, frame_host, row_stride_bytes, thb_host, so2_host,
+                                      static_cast<cudaStream_t>(stream), bounds, nb, set, true, c->set_free[j]);
+    c->async_pending = true;
+    if (st != HB_OK) return st;
+    c->set_next = j ^ 1;
+    return HB_OK;
 }
 
 hb_status hb_estimate_debug(hb_ctx* c, const void* frame_dev, size_t row_stride_bytes, double* ybar_dev,

@@ -74,6 +74,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.hb_create(None, None, 1, 1e-3, 8, 8, 1, 0, None) == 1
     assert lib.hb_estimate(None, None, 0, None, None, None) == 1
     assert lib.hb_estimate_host(None, None, 0, None, None, None) == 1
+    assert lib.hb_estimate_host_async(None, None, 0, None, None, None) == 1
     assert lib.hb_posterior_mean(None, None, 0, None, None) == 1
     assert lib.hb_lowpass_shape(None, None, None) == 1
     assert lib.hb_launch_count(None) == 0

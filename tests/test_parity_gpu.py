@@ -362,6 +362,44 @@ def test_host_entry_in_bands_matches_the_device_call(case):
         np.testing.assert_array_equal(th2.numpy(), thb.cpu().numpy())
 
 
+@pytest.mark.parametrize("case", ["hd_bayes", "small_tikhonov"])
+def test_asynchronous_host_calls_overlap_and_match(case):
+    """hb_estimate_host_async: six different frames queued back to back on one stream (two
+    staging sets in turn, so frames overlap), each into its own pinned outputs; after one
+    synchronisation every frame equals hb_estimate on it bit for bit, and a synchronous call
+    after them still does."""
+    if case == "hd_bayes":
+        wl = synth.HD_1080
+        mix = synth.make_mixing(wl.seed)
+        A, grid, levels, flags, H, W = mix.A, synth.grid_spec(wl), wl.levels, 0, wl.H, wl.W
+        frames = [synth.make_frame(700 + k, H, W, A, wl.nblobs, wl.smin, wl.smax, wl.noise, "u8").rgb
+                  for k in range(6)]
+    else:
+        A = synth.make_mixing(44).A
+        grid, levels, flags, H, W = _grid(16, 16), 2, binding.HB_LOWPASS_TIKHONOV, 300, 500
+        frames = [synth.make_frame(800 + k, H, W, A, 6, 10.0, 60.0, 0.01, "u8").rgb for k in range(6)]
+    with Context(A, grid, levels, 1e-3, W, H, "u8", flags) as ctx:
+        ref = []
+        for rgb in frames:
+            thb = torch.empty((H, W), dtype=torch.float32, device=DEV)
+            so2 = torch.empty_like(thb)
+            ctx.estimate(torch.from_numpy(rgb).to(DEV), thb, so2)
+            ref.append((thb.cpu().numpy(), so2.cpu().numpy()))
+        hf = [torch.from_numpy(rgb).pin_memory() for rgb in frames]
+        th = [torch.full((H, W), -1.0, dtype=torch.float32).pin_memory() for _ in frames]
+        sh = [torch.full((H, W), -1.0, dtype=torch.float32).pin_memory() for _ in frames]
+        stream = torch.cuda.Stream()
+        for k in range(len(frames)):
+            ctx.estimate_host_async(hf[k], th[k], sh[k], stream=stream)
+        stream.synchronize()
+        for k in range(len(frames)):
+            np.testing.assert_array_equal(th[k].numpy(), ref[k][0])
+            np.testing.assert_array_equal(sh[k].numpy(), ref[k][1])
+        th[0].zero_()
+        ctx.estimate_host(hf[3], th[0], sh[0], stream=stream)
+        np.testing.assert_array_equal(th[0].numpy(), ref[3][0])
+
+
 def test_repeated_calls_are_deterministic_and_counted():
     A, rgb = small_frame(42, 64, 64, "u8")
     grid = _grid(64, 64)

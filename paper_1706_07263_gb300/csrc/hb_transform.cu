@@ -342,52 +342,21 @@ __device__ __forceinline__ void warp_synthesis(float (&c)[2][1 << L], int lane) 
 // log-attenuation (hi, lo) and the offset-free values d = y - y_ref.  SUMS: also the
 // column's sum of floored intensities per channel (ish + isl; for 8-bit input the exact
 // integer sum of the codes, each at least 1, i.e. in units of 1/255).
-// ---- Tile staging through the TMA engine (analysis kernel) ---------------------------------
-// A CTA's frame tile (2^L rows of kThreads pixels) is copied into shared memory with one bulk
-// asynchronous copy per row (cp.async.bulk, completing on an mbarrier) when the whole tile
-// lies inside the frame and the frame's base and row stride are 16-byte multiples (the
-// copy's alignment rule; a row of the tile is 3 * kThreads samples, a multiple of 16 bytes).
-// Other tiles, the edge tiles of the frame among them (they replicate the last row and
-// column), read the frame directly, and so do 4-level frames (their warps hold 16 rows of
-// samples; the staged path would cost them a quarter of their resident CTAs in registers).
-// A tile is 24 KB at most (3 levels, float input).
-template <int L>
-struct Stage {
-    static constexpr bool on = L <= 3;
-    static constexpr int bytes = on ? (1 << L) * kThreads * 3 * 4 : 16;
-};
-// stile: the CTA's frame tile staged in shared memory (stage_issue, stage_wait; rows of kThreads pixels,
-// tile column tc = the lane's pixel within the tile), or nullptr to read the frame in global
-// memory.
 template <int L, bool SUMS = false>
 __device__ __forceinline__ void warp_load(const TransformParams& tp, const unsigned char* __restrict__ frame,
                                           size_t stride, const float2* lut, int by, int x, int lane,
                                           float (&v)[3][1 << L], float2 (&yref)[3], float* ish = nullptr,
-                                          float* isl = nullptr, const unsigned char* stile = nullptr, int tc = 0) {
+                                          float* isl = nullptr) {
     constexpr int TH = 1 << L;
     const int xs = min(x, tp.W - 1);
     const int src_lane = lane & ~(TH - 1);
     if (tp.fmt == 1) {
         int k[3][TH];
-        if constexpr (Stage<L>::on) {
-            // one (generic) load for either source: rows of the staged tile, or of the frame
-            // with the last row replicated
-            const unsigned char* base = stile ? stile + tc * 3 : frame + (size_t)by * TH * stride + (size_t)xs * 3;
-            const size_t pitch = stile ? (size_t)kThreads * 3 : stride;
-            const int rmax = stile ? TH - 1 : tp.H - 1 - by * TH;
 #pragma unroll
-            for (int r = 0; r < TH; ++r) {
-                const unsigned char* row = base + (size_t)min(r, rmax) * pitch;
+        for (int r = 0; r < TH; ++r) {
+            const unsigned char* row = frame + (size_t)min(by * TH + r, tp.H - 1) * stride + (size_t)xs * 3;
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) k[ch][r] = row[ch];
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < TH; ++r) {
-                const unsigned char* row = frame + (size_t)min(by * TH + r, tp.H - 1) * stride + (size_t)xs * 3;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) k[ch][r] = __ldg(row + ch);
-            }
+            for (int ch = 0; ch < 3; ++ch) k[ch][r] = __ldg(row + ch);
         }
         if (SUMS) {
 #pragma unroll
@@ -414,15 +383,13 @@ __device__ __forceinline__ void warp_load(const TransformParams& tp, const unsig
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) ish[ch] = isl[ch] = 0.f;
         }
-        const unsigned char* base = Stage<L>::on && stile ? stile + tc * 12 : frame + (size_t)by * TH * stride + (size_t)xs * 12;
-        const size_t pitch = Stage<L>::on && stile ? (size_t)kThreads * 12 : stride;
-        const int rmax = Stage<L>::on && stile ? TH - 1 : tp.H - 1 - by * TH;
 #pragma unroll
         for (int r = 0; r < TH; ++r) {
-            const float* row = reinterpret_cast<const float*>(base + (size_t)min(r, rmax) * pitch);
+            const float* row =
+                reinterpret_cast<const float*>(frame + (size_t)min(by * TH + r, tp.H - 1) * stride) + (size_t)xs * 3;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                const float I = fmaxf(row[ch], tp.eps);
+                const float I = fmaxf(__ldg(row + ch), tp.eps);
                 if (SUMS) detail::dd_sub(ish[ch], isl[ch], -I, 0.f);
                 v[ch][r] = -logf(I);
             }
@@ -437,58 +404,6 @@ __device__ __forceinline__ void warp_load(const TransformParams& tp, const unsig
     }
 }
 
-constexpr int kStagePolls = 1 << 16;  // bounded wait: each try_wait suspends for a short while
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-template <int L>
-__device__ __forceinline__ bool stage_fits(const TransformParams& tp, int tx, int by, int aligned) {
-    return Stage<L>::on && aligned && (tx + 1) * kThreads <= tp.W && (by + 1) * (1 << L) <= tp.H;
-}
-
-// One thread: initialise the barrier and start the row copies.
-template <int L>
-__device__ __forceinline__ void stage_issue(const TransformParams& tp, const unsigned char* frame, size_t stride,
-                                            int tx, int by, unsigned char* tile, unsigned long long* bar) {
-    constexpr int TH = 1 << L;
-    const int rowbytes = kThreads * 3 * (tp.fmt == 1 ? 1 : 4);
-    const unsigned b = smem_addr(bar);
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(TH * rowbytes) : "memory");
-#pragma unroll
-    for (int r = 0; r < TH; ++r) {
-        const unsigned char* src = frame + (size_t)(by * TH + r) * stride + (size_t)tx * rowbytes;
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         smem_addr(tile + r * rowbytes)),
-                     "l"(src), "r"(rowbytes), "r"(b)
-                     : "memory");
-    }
-}
-
-__device__ __forceinline__ bool stage_poll(unsigned b, int polls) {
-    unsigned ok = 0;
-    for (int it = 0; it < polls && !ok; ++it)
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(ok)
-            : "r"(b)
-            : "memory");
-    return ok != 0;
-}
-
-// Every thread of the CTA: wait (bounded) until the tile has landed.  True: use the tile.
-// False (the wait ran out, which a correct copy never does): the CTA reads the frame
-// directly, after waiting once more, also bounded, so that no copy is still writing into
-// shared memory that the CTA no longer expects to change.
-__device__ __forceinline__ bool stage_wait(unsigned long long* bar) {
-    const unsigned b = smem_addr(bar);
-    if (__syncthreads_and(stage_poll(b, kStagePolls) ? 1 : 0)) return true;
-    stage_poll(b, kStagePolls);
-    __syncthreads();
-    return false;
-}
-
 // Analysis of one tile (tile column tx of superblock band by): block means of the
 // tile's superblocks and their posterior records.  sb_hi / sb_lo: kThreads x 3 floats of
 // shared memory.  Called by whole CTAs.
@@ -497,8 +412,7 @@ __device__ __forceinline__ void analysis_tile(const TransformParams& tp, const B
                                               const unsigned char* __restrict__ frame, size_t stride,
                                               const float2* lut, int tx, int by, double* __restrict__ ybar,
                                               BayesRec* __restrict__ rec, float* __restrict__ ybar_f,
-                                              float (*sb_hi)[3], float (*sb_lo)[3],
-                                              const unsigned char* stile = nullptr) {
+                                              float (*sb_hi)[3], float (*sb_lo)[3]) {
     constexpr int TH = 1 << L;
     constexpr int NSB = kThreads / TH;  // superblocks per tile (kThreads columns)
     const int lane = threadIdx.x & 31;
@@ -508,7 +422,7 @@ __device__ __forceinline__ void analysis_tile(const TransformParams& tp, const B
         float v[3][TH];
         float2 yref[3];
         if (!tp.ll_intensity) {
-            warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref, nullptr, nullptr, stile, threadIdx.x);
+            warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
             warp_analysis<L, true>(v, lane);
             if ((lane & (TH - 1)) == 0) {
                 const int t = threadIdx.x / TH;
@@ -521,7 +435,7 @@ __device__ __forceinline__ void analysis_tile(const TransformParams& tp, const B
         } else {
             // Eq. 8 literally: the low pass of the intensities, then -log of its block mean
             float ish[3], isl[3];
-            warp_load<L, true>(tp, frame, stride, lut, by, x, lane, v, yref, ish, isl, stile, threadIdx.x);
+            warp_load<L, true>(tp, frame, stride, lut, by, x, lane, v, yref, ish, isl);
 #pragma unroll
             for (int s = 1; s < TH; s <<= 1)
 #pragma unroll
@@ -578,18 +492,11 @@ __global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams
                                                                  size_t stride, const float2* __restrict__ lut_g,
                                                                  double* __restrict__ ybar,
                                                                  BayesRec* __restrict__ rec,
-                                                                 float* __restrict__ ybar_f, int aligned) {
+                                                                 float* __restrict__ ybar_f) {
     __shared__ float2 lut[256];
     __shared__ float sb_hi[kThreads][3], sb_lo[kThreads][3];
-    __shared__ __align__(128) unsigned char tile[Stage<L>::bytes];
-    __shared__ unsigned long long bar;
-    // the tile's copy runs while the log table is read
-    const bool fits = stage_fits<L>(tp, blockIdx.x, blockIdx.y, aligned);
-    if (fits && threadIdx.x == 0) stage_issue<L>(tp, frame, stride, blockIdx.x, blockIdx.y, tile, &bar);
     load_lut(tp, lut_g, lut);
-    const bool staged = fits ? stage_wait(&bar) : false;
-    analysis_tile<L>(tp, bp, frame, stride, lut, blockIdx.x, blockIdx.y, ybar, rec, ybar_f, sb_hi, sb_lo,
-                     Stage<L>::on && staged ? tile : nullptr);
+    analysis_tile<L>(tp, bp, frame, stride, lut, blockIdx.x, blockIdx.y, ybar, rec, ybar_f, sb_hi, sb_lo);
     // the posterior kernel may be scheduled now; it waits for this grid before reading rec
     asm volatile("griddepcontrol.launch_dependents;");
 }
@@ -601,7 +508,7 @@ template <int L>
 __device__ __forceinline__ void synthesis_tile(const TransformParams& tp, const unsigned char* __restrict__ frame,
                                                size_t stride, const float2* lut, const float2* __restrict__ chat,
                                                float* __restrict__ out0, float* __restrict__ out1, int debug_conc,
-                                               int tx, int by, const unsigned char* stile = nullptr) {
+                                               int tx, int by) {
     constexpr int TH = 1 << L;
     const int lane = threadIdx.x & 31;
     const int x0 = (tx * (kThreads / 32) + (threadIdx.x >> 5)) * 32;
@@ -609,7 +516,7 @@ __device__ __forceinline__ void synthesis_tile(const TransformParams& tp, const 
     const int x = x0 + lane;
     float v[3][TH];
     float2 yref[3];
-    warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref, nullptr, nullptr, stile, threadIdx.x);
+    warp_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
     warp_analysis<L, false>(v, lane);
     // Tikhonov operator on every directional coefficient; the low-pass position takes 0
     // (posterior estimate added after synthesis) or M applied to it (all-Tikhonov mode).
@@ -664,9 +571,6 @@ __global__ void __launch_bounds__(kThreads) synthesis_warp_kernel(TransformParam
                                                                   const float2* __restrict__ chat,
                                                                   float* __restrict__ out0, float* __restrict__ out1,
                                                                   int debug_conc) {
-    // (the frame is read directly here: staging the tile first, as the analysis does,
-    // measured 1.1 us slower per 1080p frame -- the CTA-wide wait lengthens each CTA's
-    // critical path in this latency-bound pass)
     __shared__ float2 lut[256];
     load_lut(tp, lut_g, lut);
     synthesis_tile<L>(tp, frame, stride, lut, chat, out0, out1, debug_conc, blockIdx.x, blockIdx.y);
@@ -697,13 +601,12 @@ cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, co
     if (tp.levels <= 4) {
         const int TH = 1 << tp.levels;
         const dim3 grid((tp.wl * TH + kThreads - 1) / kThreads, tp.hl);
-        const int aligned = ((reinterpret_cast<uintptr_t>(frame) | stride) & 15) == 0;
         switch (tp.levels) {
-            case 0: analysis_warp_kernel<0><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, aligned); break;
-            case 1: analysis_warp_kernel<1><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, aligned); break;
-            case 2: analysis_warp_kernel<2><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, aligned); break;
-            case 3: analysis_warp_kernel<3><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, aligned); break;
-            default: analysis_warp_kernel<4><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, aligned); break;
+            case 0: analysis_warp_kernel<0><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
+            case 1: analysis_warp_kernel<1><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
+            case 2: analysis_warp_kernel<2><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
+            case 3: analysis_warp_kernel<3><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
+            default: analysis_warp_kernel<4><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
         }
         return cudaGetLastError();
     }

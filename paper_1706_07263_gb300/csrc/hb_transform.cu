@@ -371,10 +371,10 @@ __device__ __forceinline__ void warp_load(const TransformParams& tp, const unsig
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             const int kr = __shfl_sync(kFull, k[ch][0], src_lane);
-            yref[ch] = lut[kr];
+            yref[ch] = __ldg(lut + kr);
 #pragma unroll
             for (int r = 0; r < TH; ++r) {
-                const float2 y = lut[k[ch][r]];
+                const float2 y = __ldg(lut + k[ch][r]);
                 v[ch][r] = (y.x - yref[ch].x) + (y.y - yref[ch].y);
             }
         }
@@ -480,12 +480,6 @@ __device__ __forceinline__ void analysis_tile(const TransformParams& tp, const B
     }
 }
 
-__device__ __forceinline__ void load_lut(const TransformParams& tp, const float2* __restrict__ lut_g, float2* lut) {
-    if (tp.fmt == 1)
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = lut_g[i];
-    __syncthreads();
-}
-
 template <int L>
 __global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams tp, BayesParams bp,
                                                                  const unsigned char* __restrict__ frame,
@@ -493,10 +487,8 @@ __global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams
                                                                  double* __restrict__ ybar,
                                                                  BayesRec* __restrict__ rec,
                                                                  float* __restrict__ ybar_f) {
-    __shared__ float2 lut[256];
     __shared__ float sb_hi[kThreads][3], sb_lo[kThreads][3];
-    load_lut(tp, lut_g, lut);
-    analysis_tile<L>(tp, bp, frame, stride, lut, blockIdx.x, blockIdx.y, ybar, rec, ybar_f, sb_hi, sb_lo);
+    analysis_tile<L>(tp, bp, frame, stride, lut_g, blockIdx.x, blockIdx.y, ybar, rec, ybar_f, sb_hi, sb_lo);
     // the posterior kernel may be scheduled now; it waits for this grid before reading rec
     asm volatile("griddepcontrol.launch_dependents;");
 }
@@ -571,9 +563,7 @@ __global__ void __launch_bounds__(kThreads) synthesis_warp_kernel(TransformParam
                                                                   const float2* __restrict__ chat,
                                                                   float* __restrict__ out0, float* __restrict__ out1,
                                                                   int debug_conc) {
-    __shared__ float2 lut[256];
-    load_lut(tp, lut_g, lut);
-    synthesis_tile<L>(tp, frame, stride, lut, chat, out0, out1, debug_conc, blockIdx.x, blockIdx.y);
+    synthesis_tile<L>(tp, frame, stride, lut_g, chat, out0, out1, debug_conc, blockIdx.x, blockIdx.y);
 }
 
 template <typename K>
@@ -682,41 +672,33 @@ __device__ __forceinline__ int find_job(const FrameJob* jobs, int njobs, int blo
 __global__ void __launch_bounds__(kThreads) batch_analysis_kernel(BayesParams bp, const FrameJob* __restrict__ jobs,
                                                                   int njobs, int fmt, const float2* __restrict__ lut_g,
                                                                   BayesRec* __restrict__ rec_all) {
-    __shared__ float2 lut[256];
     __shared__ float sb_hi[kThreads][3], sb_lo[kThreads][3];
-    if (fmt == 1)
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = lut_g[i];
-    __syncthreads();
     const FrameJob& job = jobs[find_job(jobs, njobs, blockIdx.x)];
     const int local = blockIdx.x - job.tile_begin;
     const int by = local / job.tiles_x, tx = local - by * job.tiles_x;
     BayesRec* rec = rec_all + job.ll_offset;
     switch (job.tp.levels) {
-        case 0: analysis_tile<0>(job.tp, bp, job.frame, job.stride, lut, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
-        case 1: analysis_tile<1>(job.tp, bp, job.frame, job.stride, lut, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
-        case 2: analysis_tile<2>(job.tp, bp, job.frame, job.stride, lut, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
-        case 3: analysis_tile<3>(job.tp, bp, job.frame, job.stride, lut, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
-        default: analysis_tile<4>(job.tp, bp, job.frame, job.stride, lut, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+        case 0: analysis_tile<0>(job.tp, bp, job.frame, job.stride, lut_g, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+        case 1: analysis_tile<1>(job.tp, bp, job.frame, job.stride, lut_g, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+        case 2: analysis_tile<2>(job.tp, bp, job.frame, job.stride, lut_g, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+        case 3: analysis_tile<3>(job.tp, bp, job.frame, job.stride, lut_g, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+        default: analysis_tile<4>(job.tp, bp, job.frame, job.stride, lut_g, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
     }
 }
 
 __global__ void __launch_bounds__(kThreads) batch_synthesis_kernel(const FrameJob* __restrict__ jobs, int njobs, int fmt,
                                                                    const float2* __restrict__ lut_g,
                                                                    const float2* __restrict__ chat_all) {
-    __shared__ float2 lut[256];
-    if (fmt == 1)
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = lut_g[i];
-    __syncthreads();
     const FrameJob& job = jobs[find_job(jobs, njobs, blockIdx.x)];
     const int local = blockIdx.x - job.tile_begin;
     const int by = local / job.tiles_x, tx = local - by * job.tiles_x;
     const float2* chat = chat_all + job.ll_offset;
     switch (job.tp.levels) {
-        case 0: synthesis_tile<0>(job.tp, job.frame, job.stride, lut, chat, job.thb, job.so2, 0, tx, by); break;
-        case 1: synthesis_tile<1>(job.tp, job.frame, job.stride, lut, chat, job.thb, job.so2, 0, tx, by); break;
-        case 2: synthesis_tile<2>(job.tp, job.frame, job.stride, lut, chat, job.thb, job.so2, 0, tx, by); break;
-        case 3: synthesis_tile<3>(job.tp, job.frame, job.stride, lut, chat, job.thb, job.so2, 0, tx, by); break;
-        default: synthesis_tile<4>(job.tp, job.frame, job.stride, lut, chat, job.thb, job.so2, 0, tx, by); break;
+        case 0: synthesis_tile<0>(job.tp, job.frame, job.stride, lut_g, chat, job.thb, job.so2, 0, tx, by); break;
+        case 1: synthesis_tile<1>(job.tp, job.frame, job.stride, lut_g, chat, job.thb, job.so2, 0, tx, by); break;
+        case 2: synthesis_tile<2>(job.tp, job.frame, job.stride, lut_g, chat, job.thb, job.so2, 0, tx, by); break;
+        case 3: synthesis_tile<3>(job.tp, job.frame, job.stride, lut_g, chat, job.thb, job.so2, 0, tx, by); break;
+        default: synthesis_tile<4>(job.tp, job.frame, job.stride, lut_g, chat, job.thb, job.so2, 0, tx, by); break;
     }
 }
 

@@ -129,6 +129,43 @@ def test_forced_fallback_reproduces_the_exact_path(trained):
     ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
 
 
+def test_asynchronous_host_calls_in_learned_mode(trained):
+    """hb_estimate_host_async with the learned low pass (one whole-frame band per call, frames
+    overlapping): with a working network each frame equals the device call bit for bit; with a
+    corrupted one every frame falls back and equals the exact path."""
+    ctx, wl = trained["ctx"], trained["wl"]
+    frames = [_frame(trained, 910 + k) for k in range(3)]
+    ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
+    exact = [_run(ctx, f) for f in frames]
+    good = ctx.mlp_get_params()
+    hf = [f.cpu().pin_memory() for f in frames]
+    th = [torch.empty((wl.H, wl.W), dtype=torch.float32).pin_memory() for _ in frames]
+    sh = [torch.empty_like(t).pin_memory() for t in th]
+    stream = torch.cuda.Stream()
+    try:
+        ctx.set_lowpass_mode(binding.HB_MODE_MLP, float("inf"), 256)
+        device = [_run(ctx, f) for f in frames]
+        for k in range(3):
+            ctx.estimate_host_async(hf[k], th[k], sh[k], stream=stream)
+        stream.synchronize()
+        for k in range(3):
+            assert torch.equal(th[k], device[k][0].cpu()) and torch.equal(sh[k], device[k][1].cpu())
+        bad = good.copy()
+        bad[mlp.OFF_B3:] = 0.5
+        ctx.mlp_set_params(bad)
+        ctx.set_lowpass_mode(binding.HB_MODE_MLP, 1e-3, 256)
+        b0 = ctx.lowpass_stats()[1]
+        for k in range(3):
+            ctx.estimate_host_async(hf[k], th[k], sh[k], stream=stream)
+        stream.synchronize()
+        assert ctx.lowpass_stats()[1] - b0 == 3
+        for k in range(3):
+            assert torch.equal(th[k], exact[k][0].cpu()) and torch.equal(sh[k], exact[k][1].cpu())
+    finally:
+        ctx.mlp_set_params(good)
+        ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
+
+
 def test_mlp_mode_is_faster_than_the_grid_posterior(trained):
     """What the network gains: a 1920x1080 frame (3 levels, 128x128 grid) with the network,
     its sampled check and the gated fallback, against the exact grid posterior (about

@@ -123,8 +123,9 @@ hb_status hb_estimate(hb_ctx *ctx, const void *frame_dev, size_t row_stride_byte
  * hb_estimate into context-owned device buffers, copies THb and SO2
  * device->host, and synchronises `stream` before returning.  The frame is taken in
  * bands of whole 2^n-row superblock bands (a band's pixels depend on no other band), so
- * a band's input copy, its kernels on `stream` and the previous band's output copy
- * overlap; the copies use two context-owned streams.  Results equal hb_estimate's.
+ * a band's input copy, its kernels (on `stream` and a context-owned stream, alternately)
+ * and the previous band's output copy overlap; the copies use two more context-owned
+ * streams.  Results equal hb_estimate's.
  * Pinned host buffers let the copies run asynchronously.  A second call with the same
  * buffers and the same (non-default) stream captures the sequence as a CUDA graph, which
  * later calls with those buffers replay; other buffers or stage timing run it directly. */

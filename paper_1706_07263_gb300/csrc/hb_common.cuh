@@ -129,9 +129,9 @@ cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_
 size_t transform_smem_bytes(const TransformParams& tp);
 // Serving batches: one launch per stage for all jobs (levels 0..4 per job).  jobs is a
 // device array of njobs entries; total_tiles = sum of tiles_x * hl.
-cudaError_t launch_batch_analysis(const BayesParams& bp, const FrameJob* jobs, int njobs, int total_tiles, int fmt,
+cudaError_t launch_batch_analysis(const BayesParams& bp, const FrameJob* jobs, int njobs, int total_tiles,
                                   const float2* lut, BayesRec* rec_all, cudaStream_t s);
-cudaError_t launch_batch_synthesis(const FrameJob* jobs, int njobs, int total_tiles, int fmt, const float2* lut,
+cudaError_t launch_batch_synthesis(const FrameJob* jobs, int njobs, int total_tiles, const float2* lut,
                                    const float2* chat_all, cudaStream_t s);
 
 }  // namespace hb

@@ -158,11 +158,11 @@ cudaError_t run_batch(hb_server* srv, Batch& b) {
         ll += st.npix_ll;
     }
     cudaError_t e = cudaMemcpyAsync(b.d_jobs, b.h_jobs, sizeof(FrameJob) * nj, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = hb::launch_batch_analysis(srv->bp, b.d_jobs, nj, tiles, srv->fmt, srv->d_lut, b.d_rec, s);
+    if (e == cudaSuccess) e = hb::launch_batch_analysis(srv->bp, b.d_jobs, nj, tiles, srv->d_lut, b.d_rec, s);
     if (e == cudaSuccess)
         e = hb::launch_posterior(srv->bp, b.d_rec, ll, hb::PosteriorScratch{b.d_partial, b.d_count, hb::kMaxParts},
                                  b.d_chat, nullptr, 1.f, false, s);
-    if (e == cudaSuccess) e = hb::launch_batch_synthesis(b.d_jobs, nj, tiles, srv->fmt, srv->d_lut, b.d_chat, s);
+    if (e == cudaSuccess) e = hb::launch_batch_synthesis(b.d_jobs, nj, tiles, srv->d_lut, b.d_chat, s);
     for (int j = 0; e == cudaSuccess && j < nj; ++j) {
         Stream& st = srv->streams[b.members[j].first];
         Slot& sl = st.slots[b.members[j].second];

@@ -670,7 +670,7 @@ __device__ __forceinline__ int find_job(const FrameJob* jobs, int njobs, int blo
 }
 
 __global__ void __launch_bounds__(kThreads) batch_analysis_kernel(BayesParams bp, const FrameJob* __restrict__ jobs,
-                                                                  int njobs, int fmt, const float2* __restrict__ lut_g,
+                                                                  int njobs, const float2* __restrict__ lut_g,
                                                                   BayesRec* __restrict__ rec_all) {
     __shared__ float sb_hi[kThreads][3], sb_lo[kThreads][3];
     const FrameJob& job = jobs[find_job(jobs, njobs, blockIdx.x)];
@@ -686,7 +686,7 @@ __global__ void __launch_bounds__(kThreads) batch_analysis_kernel(BayesParams bp
     }
 }
 
-__global__ void __launch_bounds__(kThreads) batch_synthesis_kernel(const FrameJob* __restrict__ jobs, int njobs, int fmt,
+__global__ void __launch_bounds__(kThreads) batch_synthesis_kernel(const FrameJob* __restrict__ jobs, int njobs,
                                                                    const float2* __restrict__ lut_g,
                                                                    const float2* __restrict__ chat_all) {
     const FrameJob& job = jobs[find_job(jobs, njobs, blockIdx.x)];
@@ -704,17 +704,17 @@ __global__ void __launch_bounds__(kThreads) batch_synthesis_kernel(const FrameJo
 
 }  // namespace
 
-cudaError_t launch_batch_analysis(const BayesParams& bp, const FrameJob* jobs, int njobs, int total_tiles, int fmt,
+cudaError_t launch_batch_analysis(const BayesParams& bp, const FrameJob* jobs, int njobs, int total_tiles,
                                   const float2* lut, BayesRec* rec_all, cudaStream_t s) {
     if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
-    batch_analysis_kernel<<<total_tiles, kThreads, 0, s>>>(bp, jobs, njobs, fmt, lut, rec_all);
+    batch_analysis_kernel<<<total_tiles, kThreads, 0, s>>>(bp, jobs, njobs, lut, rec_all);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_synthesis(const FrameJob* jobs, int njobs, int total_tiles, int fmt, const float2* lut,
+cudaError_t launch_batch_synthesis(const FrameJob* jobs, int njobs, int total_tiles, const float2* lut,
                                    const float2* chat_all, cudaStream_t s) {
     if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
-    batch_synthesis_kernel<<<total_tiles, kThreads, 0, s>>>(jobs, njobs, fmt, lut, chat_all);
+    batch_synthesis_kernel<<<total_tiles, kThreads, 0, s>>>(jobs, njobs, lut, chat_all);
     return cudaGetLastError();
 }
 

@@ -38,7 +38,7 @@ UNIT = "frames/s"
 # DRAM traffic of one posterior launch on this workload from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/posterior_kernel_frame1080p_u8_l3_g128.md),
 # valid only while the kernel's sources hash to the value recorded with it.
-POSTERIOR_TRAFFIC = {"bytes": 540928, "sources_sha256_16": "afde56fd8cc6b8c3",
+POSTERIOR_TRAFFIC = {"bytes": 540928, "warp_instructions": 18746663, "sources_sha256_16": "8d01859df6b37e4c",
                      "sources": ("paper_1706_07263_gb300/csrc/hb_bayes.cu", "paper_1706_07263_gb300/csrc/hb_common.cuh",
                                  "paper_1706_07263_gb300/csrc/hb_device.cuh",
                                  "paper_1706_07263_gb300/csrc/hb_posterior.cuh")}
@@ -47,14 +47,28 @@ EX2_PER_CLK_PER_SM = 32          # MUFU ex2 lanes per clock per SM on GB300
 SM_MAX_MHZ = 2070.0
 
 
-def posterior_traffic():
-    """Bytes per posterior launch, or None if the kernel changed since the capture."""
+def posterior_traffic(key="bytes"):
+    """Bytes (or warp instructions, key="warp_instructions") per posterior launch from the ncu
+    capture, or None if the kernel changed since the capture."""
     import hashlib
     h = hashlib.sha256()
     for f in POSTERIOR_TRAFFIC["sources"]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return POSTERIOR_TRAFFIC["bytes"] if h.hexdigest()[:16] == POSTERIOR_TRAFFIC["sources_sha256_16"] else None
+    return POSTERIOR_TRAFFIC[key] if h.hexdigest()[:16] == POSTERIOR_TRAFFIC["sources_sha256_16"] else None
+
+
+def issue_roofline(launch_s):
+    """The posterior's instruction issue against the SMs' issue rate (one warp-instruction per
+    clock per scheduler, 4 schedulers per SM): the resource that binds it now that it skips
+    the nodes whose weights are zero.  Instructions per launch come from the ncu capture."""
+    inst = posterior_traffic("warp_instructions")
+    if inst is None:
+        return None
+    peak = SM_COUNT * 4 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = inst / launch_s / 1e12
+    return {"warp_instructions_per_launch": inst, "achieved": achieved, "peak": peak, "unit": "Twarp-inst/s",
+            "frac": achieved / peak, "note": "ncu smsp__inst_executed.sum of one launch over the live launch time"}
 
 
 def parse():
@@ -651,6 +665,7 @@ def run_ours(args):
                                     "note": "nodes the kernel evaluates: per grid row, the 16-column segments meeting "
                                             "the row's interval of non-zero FP32 weights"},
                      "traffic": posterior_traffic(),
+                     "issue": issue_roofline(post_avg_s),
                      "timing": "CUDA events around each posterior launch, K more steps after the timed region",
                      "peak_note": "152 SMs x 32 ex2/clk/SM x 2070 MHz (unit count measured by probe)"},
         "e2e": {"value": e2e_frames / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W * 3,

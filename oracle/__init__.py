@@ -156,7 +156,9 @@ def estimate(frame: np.ndarray, A: np.ndarray, grid: dict, levels: int, lam: flo
              intensity_lowpass: bool = False) -> dict:
     """Whole estimator on one HWC frame (uint8 codes or float32 intensities); illumination:
     with the constant (illumination) term of Eq. 8; intensity_lowpass: the low pass is -log
-    of the block mean of the intensities (Eq. 3-8 literally).
+    of the block mean of the intensities (Eq. 3-8 literally); lowpass: "bayes" (the grid
+    posterior mean, Eq. 8-11), "tikhonov" (M on every band, Eq. 5) or "ls" (least squares on
+    the low pass, Eq. 9).
 
     Returns a dict of float64 arrays: hbo2, hb, thb, so2 (H, W); ybar_ll
     (hl, wl, 3); conc_ll (hl, wl, 2)."""
@@ -172,7 +174,7 @@ def estimate(frame: np.ndarray, A: np.ndarray, grid: dict, levels: int, lam: flo
     A = _f64(A).reshape(3, 2)
     rc = _load().hbo_estimate(fr.ctypes.data, FMT[fmt], H, W, fr.strides[0], _p(A), float(lam), int(relative),
                               grid["n0"], grid["n1"], grid["lo0"], grid["hi0"], grid["lo1"], grid["hi1"],
-                              grid["sigma_l"], levels, 0 if lowpass == "bayes" else 1, int(illumination),
+                              grid["sigma_l"], levels, {"bayes": 0, "tikhonov": 1, "ls": 2}[lowpass], int(illumination),
                               int(intensity_lowpass), nthreads,
                               _p(out["hbo2"]), _p(out["hb"]), _p(out["thb"]), _p(out["so2"]),
                               _p(out["ybar_ll"]), _p(out["conc_ll"]))

@@ -305,8 +305,9 @@ int hbo_estimate(const void *frame, int fmt, int H, int W, long row_stride_bytes
                  double sigma, int levels, int lowpass_mode, int illum, int ll_intensity, int nthreads,
                  double *hbo2, double *hb, double *thb, double *so2, double *ybar_ll, double *conc_ll) {
     if (H <= 0 || W <= 0 || levels < 0 || levels > 6 || n0 < 1 || n1 < 1 || sigma <= 0) return -1;
-    if (levels == 0 && lowpass_mode != 0) return -1;
-    if (ll_intensity && lowpass_mode != 0) return -1;
+    if (lowpass_mode < 0 || lowpass_mode > 2) return -1;
+    if (levels == 0 && lowpass_mode == 1) return -1;
+    if (ll_intensity && lowpass_mode == 1) return -1;
     const double eps = fmt == HBO_FMT_U8 ? 1.0 / 255.0 : 1e-6;
     const int blk = 1 << levels;
     const int Hp = (H + blk - 1) / blk * blk, Wp = (W + blk - 1) / blk * blk;
@@ -398,10 +399,22 @@ int hbo_estimate(const void *frame, int fmt, int H, int W, long row_stride_bytes
         if (lowpass_mode == 0) {
             hbo_posterior_mean_many(yb, (long)hl * wl, A, n0, n1, lo0, hi0, lo1, hi1, sigma, illum, nthreads, cll);
         } else {
+            /* 1: the Tikhonov operator M on the low pass too (Eq. 5 on every band);
+             * 2: least squares on the low pass (the fit of Section 2's maximisation step,
+             *    Eq. 9 read as the ordinary least-squares solution over xi = A, or [A | 1]
+             *    with the illumination term): the same operator with no regularisation */
+            double L[6];
+            if (lowpass_mode == 2) {
+                if (illum)
+                    hbo_tikhonov_operator_illum(A, 0.0, 0, L);
+                else
+                    hbo_tikhonov_operator(A, 0.0, 0, L);
+            }
+            const double *Op = lowpass_mode == 2 ? L : M;
             for (size_t p = 0; p < (size_t)hl * wl; ++p)
                 for (int j = 0; j < 2; ++j) {
                     double s = 0.0;
-                    for (int c = 0; c < 3; ++c) s += M[j * 3 + c] * yb[p * 3 + c];
+                    for (int c = 0; c < 3; ++c) s += Op[j * 3 + c] * yb[p * 3 + c];
                     cll[p * 2 + j] = s;
                 }
         }

@@ -84,10 +84,17 @@ enum {
                                       operator solves over xi = [A | 1] and keeps the HbO2 and Hb rows;
                                       the posterior integrates a per-pixel offset kappa (1,1,1) out
                                       under a flat prior.  Not with the learned low pass. */
-    HB_LOWPASS_INTENSITY = 1u << 6 /* Eq. 3-8 literally for the low pass: the posterior sees
+    HB_LOWPASS_INTENSITY = 1u << 6, /* Eq. 3-8 literally for the low pass: the posterior sees
                                       -log(block mean of the intensities) instead of the block mean of
                                       -log I (directional bands unchanged).  Levels 0..4; not with
                                       HB_LOWPASS_TIKHONOV nor the learned low pass. */
+    HB_LOWPASS_LS = 1u << 7         /* the low pass by least squares instead of the posterior: the fit
+                                      of the maximisation step in Section 2 (Eq. 9, read as the ordinary
+                                      least-squares solution), c = (xi^T xi)^-1 xi^T ybar with xi = A, or
+                                      [A | 1] with HB_ILLUMINATION, on the low pass of -log I or, with
+                                      HB_LOWPASS_INTENSITY, -log of the block mean of I; directional
+                                      bands through M as always.  Not with HB_LOWPASS_TIKHONOV nor the
+                                      learned low pass. */
 };
 
 /* Per-stage timing slots reported by hb_timing_read. */

@@ -35,6 +35,7 @@ EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_es
 HB_FULL_GRID = 1 << 2
 HB_ILLUMINATION = 1 << 5
 HB_LOWPASS_INTENSITY = 1 << 6
+HB_LOWPASS_LS = 1 << 7
 HB_SERVE_SEQUENTIAL = 1 << 4
 MLP_NPARAMS = 4546
 HB_MODE_BAYES = 0

@@ -140,15 +140,19 @@ void prepare(hb_ctx* c, const hb_mixing* mix, const hb_grid* g, double lambda) {
     for (int j = 0; j < 2; ++j)
         for (int k = 0; k < 2; ++k) G[j][k] = Ain[0][j] * Ain[0][k] + Ain[1][j] * Ain[1][k] + Ain[2][j] * Ain[2][k];
     c->gamma = (c->flags & HB_LAMBDA_ABSOLUTE) ? lambda : lambda * (G[0][0] + G[1][1]) / 2.0;
-    if (!(c->flags & HB_ILLUMINATION)) {
-        const double R00 = G[0][0] + c->gamma, R11 = G[1][1] + c->gamma, R01 = G[0][1];
-        const double det = R00 * R11 - R01 * R01;
-        for (int ch = 0; ch < 3; ++ch) {
-            c->tp.M[0 * 3 + ch] = (float)((R11 * Ain[ch][0] - R01 * Ain[ch][1]) / det);
-            c->tp.M[1 * 3 + ch] = (float)((-R01 * Ain[ch][0] + R00 * Ain[ch][1]) / det);
+    // The 2x3 operator (A^T A + gamma I)^-1 A^T (Eq. 5), or with the illumination term the
+    // HbO2 and Hb rows of (xi^T xi + gamma I)^-1 xi^T for xi = [A | 1] (Eq. 8's constant term).
+    // gamma = 0 gives the least-squares fit of the maximisation step (Eq. 9).
+    auto operator_2x3 = [&](double gamma, float (&out)[6]) {
+        if (!(c->flags & HB_ILLUMINATION)) {
+            const double R00 = G[0][0] + gamma, R11 = G[1][1] + gamma, R01 = G[0][1];
+            const double det = R00 * R11 - R01 * R01;
+            for (int ch = 0; ch < 3; ++ch) {
+                out[0 * 3 + ch] = (float)((R11 * Ain[ch][0] - R01 * Ain[ch][1]) / det);
+                out[1 * 3 + ch] = (float)((-R01 * Ain[ch][0] + R00 * Ain[ch][1]) / det);
+            }
+            return;
         }
-    } else {
-        // xi = [A | 1]: the HbO2 and Hb rows of (xi^T xi + gamma I)^-1 xi^T (Eq. 8's constant term)
         double xi[3][3], R[3][3], Ri[3][3];
         for (int ch = 0; ch < 3; ++ch) {
             xi[ch][0] = Ain[ch][0];
@@ -157,7 +161,7 @@ void prepare(hb_ctx* c, const hb_mixing* mix, const hb_grid* g, double lambda) {
         }
         for (int j = 0; j < 3; ++j)
             for (int k = 0; k < 3; ++k)
-                R[j][k] = xi[0][j] * xi[0][k] + xi[1][j] * xi[1][k] + xi[2][j] * xi[2][k] + (j == k ? c->gamma : 0.0);
+                R[j][k] = xi[0][j] * xi[0][k] + xi[1][j] * xi[1][k] + xi[2][j] * xi[2][k] + (j == k ? gamma : 0.0);
         const double det = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) -
                            R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
                            R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
@@ -168,8 +172,10 @@ void prepare(hb_ctx* c, const hb_mixing* mix, const hb_grid* g, double lambda) {
             }
         for (int j = 0; j < 2; ++j)
             for (int ch = 0; ch < 3; ++ch)
-                c->tp.M[j * 3 + ch] = (float)(Ri[j][0] * xi[ch][0] + Ri[j][1] * xi[ch][1] + Ri[j][2] * xi[ch][2]);
-    }
+                out[j * 3 + ch] = (float)(Ri[j][0] * xi[ch][0] + Ri[j][1] * xi[ch][1] + Ri[j][2] * xi[ch][2]);
+    };
+    operator_2x3(c->gamma, c->tp.M);
+    operator_2x3(0.0, c->tp.ls_L);
     // The posterior's mixing matrix.  With the illumination term the likelihood after
     // integrating kappa out is that of P (ybar - A c), P = I - (1,1,1)(1,1,1)^T / 3; using
     // P A in place of A gives it exactly, since the part of ybar along (1,1,1) is the same
@@ -376,21 +382,33 @@ Band whole_frame(const hb_ctx* c) { return Band{c->tp, 0, c->npix_ll}; }
 hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, double* ybar, float* out0, float* out1,
                    float2* conc_scaled, int debug, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
-    const bool bayes = !(c->flags & HB_LOWPASS_TIKHONOV);
+    // the low pass: the grid posterior (possibly through the learned stand-in), least squares
+    // (written by the analysis itself), or nothing separate (Tikhonov on every band)
+    const bool lowpass = !(c->flags & HB_LOWPASS_TIKHONOV);
+    const bool ls = lowpass && (c->flags & HB_LOWPASS_LS);
+    const bool bayes = lowpass && !ls;
     const bool pdl = !c->timing;
     const bool mlp = bayes && c->lowpass_mode == HB_MODE_MLP;
     BayesRec* rec = c->d_rec + b.ll_off;
     float2* chat = c->d_chat + b.ll_off;
-    if (bayes) {
+    const float scale = (float)(1 << c->levels);
+    if (lowpass) {
         {
             StageTimer t(c, s, HB_STAGE_ANALYSIS);
+            hb::LsOut lso;
+            if (ls) {
+                lso.c = chat;
+                lso.c_scaled = conc_scaled;
+                lso.scale = scale;
+            }
             e = hb::launch_analysis(b.tp, c->bp, frame, stride, c->d_lut, ybar, rec, s,
-                                    mlp ? c->d_ybar_f + 3 * b.ll_off : nullptr);
+                                    mlp ? c->d_ybar_f + 3 * b.ll_off : nullptr, lso);
             c->launches++;
         }
         if (e != cudaSuccess) return HB_ERR_CUDA;
+    }
+    if (bayes) {
         StageTimer t(c, s, HB_STAGE_LOWPASS);
-        const float scale = (float)(1 << c->levels);
         if (mlp) {
             // network estimate, sampled exact check, exact recomputation only if the check
             // failed; each kernel waits for its predecessor in-kernel (PDL)
@@ -415,7 +433,7 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
     if (e != cudaSuccess) return HB_ERR_CUDA;
     if (out0 || out1) {
         StageTimer t(c, s, HB_STAGE_SYNTHESIS);
-        e = hb::launch_synthesis(b.tp, frame, stride, c->d_lut, chat, out0, out1, debug, bayes && pdl, s);
+        e = hb::launch_synthesis(b.tp, frame, stride, c->d_lut, chat, out0, out1, debug, lowpass && pdl, s);
         c->launches++;
     }
     return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
@@ -437,9 +455,10 @@ hb_status hb_create(const hb_mixing* mix, const hb_grid* grid, int levels, doubl
     if (!mix || !grid) return HB_ERR_ARG;
     if (in_format != HB_IN_F32_HWC && in_format != HB_IN_U8_HWC) return HB_ERR_ARG;
     if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_LOWPASS_TIKHONOV | HB_FULL_GRID | HB_ILLUMINATION |
-                            HB_LOWPASS_INTENSITY))
+                            HB_LOWPASS_INTENSITY | HB_LOWPASS_LS))
         return HB_ERR_ARG;
     if ((flags & HB_LOWPASS_INTENSITY) && ((flags & HB_LOWPASS_TIKHONOV) || levels > 4)) return HB_ERR_ARG;
+    if ((flags & HB_LOWPASS_LS) && (flags & HB_LOWPASS_TIKHONOV)) return HB_ERR_ARG;
     if (width <= 0 || height <= 0 || levels < 0 || levels > hb::kMaxLevels) return HB_ERR_SHAPE;
     if (grid->n0 < 1 || grid->n1 < 1 || !(grid->hi0 >= grid->lo0) || !(grid->hi1 >= grid->lo1) ||
         !(grid->sigma_l > 0.0))
@@ -658,7 +677,7 @@ hb_status host_prepare(hb_ctx* c, const void* frame_host, size_t row_stride_byte
     };
     if (!alloc(c->d_frame, c->d_thb, c->d_so2) || (two_sets && !alloc(c->d_frame2, c->d_thb2, c->d_so22)))
         return HB_ERR_OOM;
-    const bool bayes = !(c->flags & HB_LOWPASS_TIKHONOV);
+    const bool bayes = !(c->flags & (HB_LOWPASS_TIKHONOV | HB_LOWPASS_LS));
     mlp = bayes && c->lowpass_mode == HB_MODE_MLP;
     bounds[0] = 0;
     bounds[1] = c->hl;
@@ -1128,7 +1147,8 @@ hb_status hb_set_lowpass_mode(hb_ctx* c, int mode, double tol, int nsample) {
     if (mode == HB_MODE_MLP) {
         if (!(tol >= 0.0) || nsample < 1) return HB_ERR_ARG;
         if (!c->mlp_ready) return HB_ERR_STATE;
-        if (c->flags & (HB_LOWPASS_TIKHONOV | HB_ILLUMINATION | HB_LOWPASS_INTENSITY)) return HB_ERR_STATE;
+        if (c->flags & (HB_LOWPASS_TIKHONOV | HB_LOWPASS_LS | HB_ILLUMINATION | HB_LOWPASS_INTENSITY))
+            return HB_ERR_STATE;
         if (nsample > c->mlp_err_cap) {
             DeviceGuard g(c->device);
             cudaFree(c->d_err);

@@ -21,6 +21,7 @@ struct TransformParams {
     int tikhonov_lowpass;     // 1: low pass through M as well
     int ll_intensity;         // 1: ybar = -log(block mean of intensity), Eq. 8 (analysis, levels <= 4)
     float M[6];               // M[j*3 + c], j = HbO2/Hb, c = R/G/B
+    float ls_L[6];            // least-squares low pass (HB_LOWPASS_LS): c = ls_L ybar, same layout
 };
 
 // Constants of the grid posterior, prepared in FP64 on the host.
@@ -67,6 +68,14 @@ struct BayesParams {
     float span_an2;           // sup_alpha n0^2 (size of the quadratic term, for the rounding guard)
     int illum;                // 1: A holds (I - 11^T/3) A and the set-up removes ybar's channel mean
 };
+
+// Where the analysis writes the least-squares low-pass estimates (c = nullptr: it writes the
+// posterior records instead): c per low-pass pixel, and optionally 2^n c.
+struct LsOut {
+    float2* c = nullptr;
+    float2* c_scaled = nullptr;
+    float scale = 1.f;
+};
 constexpr float kSupportCut = 150.f;
 
 // Per low-pass pixel record written by the analysis kernel for the posterior kernel.
@@ -101,7 +110,8 @@ constexpr int kMaxBatchJobs = 64;
 
 // Launch wrappers (defined in the .cu files).  All return the launch status.
 cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
-                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f = nullptr);
+                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f = nullptr,
+                            const LsOut& ls = LsOut{});
 cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s);
 // Optional gate of the posterior launch: when run is set the kernel does nothing unless
 // *run is non-zero (the decision launch_posterior_check leaves behind).

@@ -102,4 +102,28 @@ __device__ __forceinline__ BayesRec bayes_setup(const float yhi_in[3], const flo
     return rec;
 }
 
+// The low-pass output of one superblock o from its block mean yhi + ylo: the posterior
+// record, or with a least-squares low pass the estimate itself (the 2x3 operator applied to
+// the float pair).  With the illumination term the operator annihilates (1,1,1) only in
+// exact arithmetic: ybar's channel mean is removed first, in double-float, so that the
+// rounding of the FP32 operator does not meet it (it can be large against the concentrations
+// when the system [A | 1] is ill-conditioned).
+__device__ __forceinline__ void low_pass_out(const float yhi[3], const float ylo[3], const TransformParams& tp,
+                                             const BayesParams& bp, size_t o, BayesRec* rec, const LsOut& ls) {
+    if (ls.c) {
+        float h[3] = {yhi[0], yhi[1], yhi[2]}, l[3] = {ylo[0], ylo[1], ylo[2]};
+        if (bp.illum) detail::dd_remove_mean(h, l);
+        float c[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float* L = tp.ls_L + 3 * j;
+            c[j] = fmaf(L[0], h[0], fmaf(L[1], h[1], L[2] * h[2])) + fmaf(L[0], l[0], fmaf(L[1], l[1], L[2] * l[2]));
+        }
+        ls.c[o] = make_float2(c[0], c[1]);
+        if (ls.c_scaled) ls.c_scaled[o] = make_float2(c[0] * ls.scale, c[1] * ls.scale);
+    } else {
+        rec[o] = bayes_setup(yhi, ylo, bp);
+    }
+}
+
 }  // namespace hb

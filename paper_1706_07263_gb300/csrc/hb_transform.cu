@@ -161,7 +161,8 @@ namespace {
 __global__ void __launch_bounds__(kThreads) analysis_kernel(TransformParams tp, BayesParams bp,
                                                             const unsigned char* __restrict__ frame, size_t stride,
                                                             const float2* __restrict__ lut, double* __restrict__ ybar,
-                                                            BayesRec* __restrict__ rec, float* __restrict__ ybar_f) {
+                                                            BayesRec* __restrict__ rec, float* __restrict__ ybar_f,
+                                                            LsOut ls) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int TH = 1 << tp.levels, TW = tp.tile_w;
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) analysis_kernel(TransformParams tp, 
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) ybar_f[o * 3 + ch] = yhi[ch] + ylo[ch];
         }
-        rec[o] = bayes_setup(yhi, ylo, bp);
+        low_pass_out(yhi, ylo, tp, bp, o, rec, ls);
     }
 }
 
@@ -412,7 +413,7 @@ __device__ __forceinline__ void analysis_tile(const TransformParams& tp, const B
                                               const unsigned char* __restrict__ frame, size_t stride,
                                               const float2* lut, int tx, int by, double* __restrict__ ybar,
                                               BayesRec* __restrict__ rec, float* __restrict__ ybar_f,
-                                              float (*sb_hi)[3], float (*sb_lo)[3]) {
+                                              float (*sb_hi)[3], float (*sb_lo)[3], const LsOut& ls = LsOut{}) {
     constexpr int TH = 1 << L;
     constexpr int NSB = kThreads / TH;  // superblocks per tile (kThreads columns)
     const int lane = threadIdx.x & 31;
@@ -476,7 +477,7 @@ __device__ __forceinline__ void analysis_tile(const TransformParams& tp, const B
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) ybar_f[o * 3 + ch] = yhi[ch] + ylo[ch];
         }
-        rec[o] = bayes_setup(yhi, ylo, bp);
+        low_pass_out(yhi, ylo, tp, bp, o, rec, ls);
     }
 }
 
@@ -486,9 +487,9 @@ __global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams
                                                                  size_t stride, const float2* __restrict__ lut_g,
                                                                  double* __restrict__ ybar,
                                                                  BayesRec* __restrict__ rec,
-                                                                 float* __restrict__ ybar_f) {
+                                                                 float* __restrict__ ybar_f, LsOut ls) {
     __shared__ float sb_hi[kThreads][3], sb_lo[kThreads][3];
-    analysis_tile<L>(tp, bp, frame, stride, lut_g, blockIdx.x, blockIdx.y, ybar, rec, ybar_f, sb_hi, sb_lo);
+    analysis_tile<L>(tp, bp, frame, stride, lut_g, blockIdx.x, blockIdx.y, ybar, rec, ybar_f, sb_hi, sb_lo, ls);
     // the posterior kernel may be scheduled now; it waits for this grid before reading rec
     asm volatile("griddepcontrol.launch_dependents;");
 }
@@ -586,24 +587,25 @@ static dim3 tile_grid(const TransformParams& tp) {
 }
 
 cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
-                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f) {
+                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f,
+                            const LsOut& ls) {
     const unsigned char* f = static_cast<const unsigned char*>(frame);
     if (tp.levels <= 4) {
         const int TH = 1 << tp.levels;
         const dim3 grid((tp.wl * TH + kThreads - 1) / kThreads, tp.hl);
         switch (tp.levels) {
-            case 0: analysis_warp_kernel<0><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
-            case 1: analysis_warp_kernel<1><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
-            case 2: analysis_warp_kernel<2><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
-            case 3: analysis_warp_kernel<3><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
-            default: analysis_warp_kernel<4><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f); break;
+            case 0: analysis_warp_kernel<0><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls); break;
+            case 1: analysis_warp_kernel<1><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls); break;
+            case 2: analysis_warp_kernel<2><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls); break;
+            case 3: analysis_warp_kernel<3><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls); break;
+            default: analysis_warp_kernel<4><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls); break;
         }
         return cudaGetLastError();
     }
     const size_t sm = transform_smem_bytes(tp);
     cudaError_t e = set_smem(analysis_kernel, sm);
     if (e != cudaSuccess) return e;
-    analysis_kernel<<<tile_grid(tp), kThreads, sm, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f);
+    analysis_kernel<<<tile_grid(tp), kThreads, sm, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls);
     return cudaGetLastError();
 }
 

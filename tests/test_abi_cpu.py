@@ -63,6 +63,8 @@ def _create(lib, **kw):
     (dict(grid=dict(n0=0)), 2), (dict(grid=dict(sigma_l=0.0)), 2), (dict(grid=dict(hi0=-1.0)), 2),
     (dict(fmt=5), 1), (dict(flags=1 << 9), 1), (dict(lam=-1.0), 1), (dict(lam=float("nan")), 1),
     (dict(levels=0, flags=binding.HB_LOWPASS_TIKHONOV), 1),
+    (dict(flags=binding.HB_LOWPASS_LS | binding.HB_LOWPASS_TIKHONOV), 1),
+    (dict(levels=5, flags=binding.HB_LOWPASS_LS | binding.HB_LOWPASS_INTENSITY), 1),
 ])
 def test_create_rejects_bad_arguments_without_a_device(lib, kw, status):
     rc, h = _create(lib, **kw)

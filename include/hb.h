@@ -146,8 +146,10 @@ hb_status hb_estimate_host(hb_ctx *ctx, const void *frame_host, size_t row_strid
  * copy and kernels run while the previous frame's results are copied back.  Nothing waits
  * for work queued on `stream` before the call, so the host frame must be complete when the
  * call is made, and it and the output buffers must stay untouched until the stream has
- * passed the call.  Results equal hb_estimate_host's (the same bands and kernels).  A
- * synchronous call on the context first waits for asynchronous calls still in flight.
+ * passed the call.  Results equal hb_estimate_host's (the same bands and kernels).  Every
+ * other call on the context that launches work or reads its device state (hb_estimate*,
+ * hb_posterior_mean, hb_lowpass_*, hb_mlp_* except get_params, hb_set_lowpass_mode,
+ * hb_timing_start) first waits for asynchronous calls still in flight.
  * Returns HB_ERR_STATE while per-stage timing is armed (hb_timing_start); otherwise as
  * hb_estimate_host. */
 hb_status hb_estimate_host_async(hb_ctx *ctx, const void *frame_host, size_t row_stride_bytes, float *thb_host,

@@ -319,6 +319,17 @@ void prepare_constants(const hb_mixing* mix, const hb_grid* grid, double lambda,
 
 namespace {
 
+// Asynchronous host calls still in flight run on the context's own streams and share its
+// low-pass arrays (and, in learned mode, its network and flags) with every other call: wait
+// for them first.
+hb_status settle_async(hb_ctx* c) {
+    if (!c->async_pending) return HB_OK;
+    for (cudaStream_t st : {c->s_in, c->s_c0, c->s_alt, c->s_out})
+        if (st && cudaStreamSynchronize(st) != cudaSuccess) return HB_ERR_CUDA;
+    c->async_pending = false;
+    return HB_OK;
+}
+
 // Posterior scratch for the low-pass pixels from ll_off on (launches that may run at the same
 // time take disjoint pixel ranges, so their counters are disjoint as well).
 hb::PosteriorScratch post_scratch(const hb_ctx* c, long ll_off = 0) {
@@ -566,6 +577,7 @@ hb_status hb_estimate(hb_ctx* c, const void* frame_dev, size_t row_stride_bytes,
     hb_status st = check_frame_args(c, frame_dev, row_stride_bytes);
     if (st != HB_OK) return st;
     DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     return run_frame(c, frame_dev, row_stride_bytes, nullptr, thb_dev, so2_dev, nullptr, 0,
                      static_cast<cudaStream_t>(stream));
 }
@@ -733,12 +745,7 @@ hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_
         host_prepare(c, frame_host, row_stride_bytes, thb_host, so2_host, false, kHostBands, bounds, nb, mlp);
     if (pst != HB_OK) return pst;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (c->async_pending) {  // asynchronous calls still in flight use the same streams and buffers
-        if (cudaStreamSynchronize(c->s_in) != cudaSuccess || cudaStreamSynchronize(c->s_c0) != cudaSuccess ||
-            cudaStreamSynchronize(c->s_alt) != cudaSuccess || cudaStreamSynchronize(c->s_out) != cudaSuccess)
-            return HB_ERR_CUDA;
-        c->async_pending = false;
-    }
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     const HostSet set{static_cast<unsigned char*>(c->d_frame), c->d_thb, c->d_so2};
     // The same buffers, stream and banding twice in a row: capture the sequence as a CUDA
     // graph, then replay it (one launch instead of some twenty calls).  Not for the learned
@@ -819,6 +826,7 @@ hb_status hb_estimate_debug(hb_ctx* c, const void* frame_dev, size_t row_stride_
     hb_status st = check_frame_args(c, frame_dev, row_stride_bytes);
     if (st != HB_OK) return st;
     DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     return run_frame(c, frame_dev, row_stride_bytes, ybar_dev, hbo2_dev, hb_dev, reinterpret_cast<float2*>(conc_dev),
                      1, static_cast<cudaStream_t>(stream));
 }
@@ -830,6 +838,7 @@ hb_status hb_posterior_mean(hb_ctx* c, const double* ybar_dev, long npix, float*
         (reinterpret_cast<uintptr_t>(ybar_dev) & 7))
         return HB_ERR_ARG;
     DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (npix > c->rec_cap) {
         if (cudaStreamSynchronize(s) != cudaSuccess) return HB_ERR_CUDA;
@@ -858,6 +867,7 @@ long hb_launch_count(const hb_ctx* c) { return c ? c->launches.load() : 0; }
 hb_status hb_timing_start(hb_ctx* c, int max_launches) {
     if (!c || max_launches <= 0) return HB_ERR_ARG;
     DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     while ((int)c->ev.size() < 2 * max_launches) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return HB_ERR_CUDA;
@@ -1015,6 +1025,7 @@ hb_status put_params(hb_ctx* c, const float* host) {
 hb_status hb_mlp_init(hb_ctx* c, unsigned seed) {
     if (!c) return HB_ERR_ARG;
     DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     hb_status st = ensure_mlp(c);
     if (st != HB_OK) return st;
     std::vector<float> p(hb::kNParams, 0.f);
@@ -1037,6 +1048,7 @@ hb_status hb_mlp_set_params(hb_ctx* c, const float* params_host) {
     for (int i = 0; i < hb::kNParams; ++i)
         if (!std::isfinite(params_host[i])) return HB_ERR_ARG;
     DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     hb_status st = ensure_mlp(c);
     if (st != HB_OK) return st;
     return put_params(c, params_host);
@@ -1057,6 +1069,7 @@ hb_status hb_lowpass_pairs(hb_ctx* c, const void* frame_dev, size_t row_stride_b
     hb_status st = check_frame_args(c, frame_dev, row_stride_bytes);
     if (st != HB_OK) return st;
     DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = hb::launch_analysis(c->tp, c->bp, frame_dev, row_stride_bytes, c->d_lut, nullptr, c->d_rec, s,
                                         ybar_dev);
@@ -1074,6 +1087,7 @@ hb_status hb_mlp_train(hb_ctx* c, const float* ybar_dev, const float* target_dev
     if (batch > kMlpMaxBlocks * hb::kMlpTrainSamples) return HB_ERR_SHAPE;
     if (!c->mlp_ready) return HB_ERR_STATE;
     DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (steps > c->mlp_loss_cap) {
         if (cudaStreamSynchronize(s) != cudaSuccess) return HB_ERR_CUDA;
@@ -1115,6 +1129,7 @@ hb_status hb_mlp_gradient(hb_ctx* c, const float* ybar_dev, const float* target_
     if (n > (long)kMlpMaxBlocks * hb::kMlpTrainSamples) return HB_ERR_SHAPE;
     if (!c->mlp_ready) return HB_ERR_STATE;
     DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t np = hb::kNParams;
     const int nblocks = (int)((n + hb::kMlpTrainSamples - 1) / hb::kMlpTrainSamples);
@@ -1132,6 +1147,7 @@ hb_status hb_mlp_forward(hb_ctx* c, const float* ybar_dev, long n, float* conc_d
     if (!c->mlp_ready) return HB_ERR_STATE;
     if (n == 0) return HB_OK;
     DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     cudaError_t e = cudaSuccess;
     const void* img = mlp_image(c, static_cast<cudaStream_t>(stream), e);
     if (img)
@@ -1144,6 +1160,10 @@ hb_status hb_mlp_forward(hb_ctx* c, const float* ybar_dev, long n, float* conc_d
 hb_status hb_set_lowpass_mode(hb_ctx* c, int mode, double tol, int nsample) {
     if (!c) return HB_ERR_ARG;
     if (mode != HB_MODE_BAYES && mode != HB_MODE_MLP) return HB_ERR_ARG;
+    {
+        DeviceGuard g(c->device);
+        if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
+    }
     if (mode == HB_MODE_MLP) {
         if (!(tol >= 0.0) || nsample < 1) return HB_ERR_ARG;
         if (!c->mlp_ready) return HB_ERR_STATE;
@@ -1170,6 +1190,7 @@ hb_status hb_set_lowpass_mode(hb_ctx* c, int mode, double tol, int nsample) {
 hb_status hb_lowpass_stats(hb_ctx* c, long* mlp_frames, long* fallbacks) {
     if (!c || !mlp_frames || !fallbacks) return HB_ERR_ARG;
     DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     unsigned fb = 0;
     if (c->d_flags && cudaMemcpy(&fb, c->d_flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
         return HB_ERR_CUDA;

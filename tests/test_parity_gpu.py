@@ -366,8 +366,8 @@ def test_host_entry_in_bands_matches_the_device_call(case):
 def test_asynchronous_host_calls_overlap_and_match(case):
     """hb_estimate_host_async: six different frames queued back to back on one stream (two
     staging sets in turn, so frames overlap), each into its own pinned outputs; after one
-    synchronisation every frame equals hb_estimate on it bit for bit, and a synchronous call
-    after them still does."""
+    synchronisation every frame equals hb_estimate on it bit for bit, as does a device call made
+    while they are in flight and a synchronous call after them."""
     if case == "hd_bayes":
         wl = synth.HD_1080
         mix = synth.make_mixing(wl.seed)
@@ -391,6 +391,13 @@ def test_asynchronous_host_calls_overlap_and_match(case):
         stream = torch.cuda.Stream()
         for k in range(len(frames)):
             ctx.estimate_host_async(hf[k], th[k], sh[k], stream=stream)
+        # a device call while they are in flight: it waits for them (they share the context's
+        # low-pass arrays), and neither disturbs the other
+        thb = torch.empty((H, W), dtype=torch.float32, device=DEV)
+        so2 = torch.empty_like(thb)
+        ctx.estimate(torch.from_numpy(frames[2]).to(DEV), thb, so2)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(thb.cpu().numpy(), ref[2][0])
         stream.synchronize()
         for k in range(len(frames)):
             np.testing.assert_array_equal(th[k].numpy(), ref[k][0])

@@ -380,8 +380,8 @@ __device__ __forceinline__ void span_round(const BayesParams& bp, const BayesRec
     if (valid && gl == 0) write_mean(bp, rec, p, sw, sdi, sdj, chat, chat_scaled, scale);
 }
 
-// Two pixels per warp (half-warp h takes pixel 2r + h of round r), rounds dealt as in the
-// two-pixel kernel below.
+// Two pixels per warp (half-warp h takes pixel 2r + h of round r), rounds dealt as in
+// posterior_pair_kernel above.
 template <bool RAGGED>
 __global__ void HB_SPAN_BOUNDS posterior_span_kernel(BayesParams bp, const BayesRec* __restrict__ recs, long npix,
                                                      float2* __restrict__ chat, float2* __restrict__ chat_scaled,

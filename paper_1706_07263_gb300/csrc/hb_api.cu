@@ -264,6 +264,7 @@ void prepare(hb_ctx* c, const hb_mixing* mix, const hb_grid* g, double lambda) {
                        std::isfinite((float)(alpha / cq)) && std::isfinite((float)(alpha * g->n0 * g->n0)))
                           ? 1
                           : 0;
+        bp.span_cut = (float)std::min((double)hb::kSupportCut, 30.0 + std::log2((double)g->n0 * (double)g->n1));
         bp.span_a2 = bp.sup_cols ? (float)(alpha / cq) : 0.f;
         bp.span_inv_acq = bp.sup_cols ? (float)(-1.0 / cq) : 0.f;
         bp.span_cv = bp.sup_cols ? (float)(-0.5 / cq) : 0.f;

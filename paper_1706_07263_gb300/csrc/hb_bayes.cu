@@ -229,18 +229,17 @@ __global__ void HB_PAIR_BOUNDS posterior_pair_kernel(BayesParams bp, const Bayes
 
 // ---- Span kernel: only the nodes inside each row's column interval ---------------------
 //
-// The nodes of a pixel that can hold a non-zero FP32 weight fill a tilted ellipse over the
-// grid (clipped by the grid's edges): taking whole rows would enumerate about three times
-// as many.  The span kernel enumerates, in every row of the ellipse, the 16-column lattice
-// segments that meet the row's column interval (span_pixel, span_row): items of (row,
-// segment), dealt to the 16 lanes of the pixel's half-warp in order.  For the item table the
-// rows go in chunks of 80, five consecutive rows per lane: a lane finds its rows' segments,
-// a scan over the half-warp gives each lane its first item, and the lane writes its items
-// into the half-warp's table in shared memory.  Nodes outside the intervals have weights
-// that are exactly zero, so a pixel's sums equal those over the whole grid up to the order
-// of the additions.
+// The nodes of a pixel whose weights matter fill a tilted ellipse over the grid (clipped by
+// the grid's edges): taking whole rows would enumerate several times as many.  The span
+// kernel enumerates, in every row of the ellipse, the 16-column lattice segments that meet
+// the row's column interval (span_pixel, span_row): items of (row, segment), dealt to the 16
+// lanes of the pixel's half-warp in order.  For the item table the rows go in chunks of 48,
+// three consecutive rows per lane: a lane finds its rows' segments, a scan over the
+// half-warp gives each lane its first item, and the lane writes its items into the
+// half-warp's table in shared memory.  The nodes outside the intervals carry together less
+// than 2^-30 of the posterior mass (BayesParams::span_cut).
 constexpr int kSpanThreads = HB_SPAN_THREADS;
-constexpr int kSpanRows = 5;                 // rows per lane per chunk
+constexpr int kSpanRows = 3;                 // rows per lane per chunk
 constexpr int kSpanChunk = 16 * kSpanRows;   // rows per chunk
 constexpr int kSpanMaxCols = 128;            // n1 limit
 constexpr int kSpanMaxSegs = kSpanMaxCols / kSpanSeg;

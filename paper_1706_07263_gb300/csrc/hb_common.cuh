@@ -62,6 +62,11 @@ struct BayesParams {
     // c2 = (sup_c V^2 + cut) span_inv_acq (same cut).  sup_cols = 1 enumerates only those
     // intervals (needs sup_rows and Cq < 0).
     int sup_cols;
+    // Cut of the column intervals: nodes below 2^-span_cut of the reference node's weight
+    // (exactly 1, and at most the total) are left out; with span_cut = 30 + log2(n0 n1) they
+    // carry together less than 2^-30 of the posterior mass, far below the FP32 rounding of
+    // the sums (at most kSupportCut: beyond it FP32 weights are zero anyway).
+    float span_cut;
     float span_a2;            // -sup_alpha / |Cq|
     float span_inv_acq;       // 1 / |Cq|
     float span_cv;            // -0.5 / Cq

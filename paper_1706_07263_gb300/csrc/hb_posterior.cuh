@@ -16,11 +16,11 @@
 // overflow; a pixel whose sums still come out non-finite (only possible for inputs far
 // outside the model) is recomputed with an explicit maximum pass.
 //
-// Only nodes that can hold a non-zero FP32 weight are enumerated: the grid rows of
-// support_rows (whole-row kernels) or, per row, the column interval of span_pixel /
-// span_row (span kernel).  Outside them every 2^t is below 2^-150 and ex2.approx.ftz
-// returns exactly 0, so the sums are those over the whole grid up to the order of the
-// additions.
+// Whole-row kernels enumerate only the grid rows that can hold a non-zero FP32 weight
+// (support_rows): outside them every 2^t is below 2^-150 and ex2.approx.ftz returns
+// exactly 0, so the sums are those over the whole grid up to the order of the additions.
+// The span kernel enumerates, per row, the column interval of span_pixel / span_row, whose
+// cut leaves out only nodes carrying together less than 2^-30 of the posterior mass.
 //
 // Whole-row kernels: lane l of a group takes grid columns l, l+G, l+2G, ... (CPL columns
 // per lane).  Per pair of grid nodes a lane issues two packed FP32x2 FMAs for the
@@ -262,11 +262,13 @@ __device__ __forceinline__ void support_rows(const BayesParams& bp, const BayesR
 // exponent of row di peaks at column j0 + dj*(di), dj*(di) = -(V + 2 Bq di) / (2 Cq), with
 // the value t*(di) = -alpha di^2 + (U - r V) di + c V^2 (the row maximum of support_rows),
 // and stays at or above -cut within h(di) = sqrt((t*(di) + cut) / -Cq) columns of it.
-// Centre and squared half-width are evaluated directly (the two-root formula would
-// cancel).  Rows: where t*(di) >= -cut, widened by one row on each side and clipped to
-// the grid.  A pixel whose terms are large enough for their FP32 rounding to come near the
-// 24 units between the cut and the smallest exponent with a non-zero weight (only for
-// inputs far outside the model) takes every row and column.
+// cut = bp.span_cut plus a margin for the FP32 evaluation of t (as in support_cut): the
+// nodes left out weigh less than 2^-span_cut each against the reference node, together
+// less than 2^-30 of the posterior mass.  Centre and squared half-width are evaluated
+// directly (the two-root formula would cancel).  Rows: where t*(di) >= -cut, widened by one
+// row on each side and clipped to the grid.  A pixel whose terms are so large that their
+// FP32 rounding could move the bounds by whole columns (only for inputs far outside the
+// model) takes every row and column.
 constexpr int kSpanSeg = 16;  // columns per lattice segment
 
 struct SpanPixel {
@@ -278,7 +280,8 @@ struct SpanPixel {
 
 __device__ __forceinline__ SpanPixel span_pixel(const BayesParams& bp, const BayesRec& rec) {
     SpanPixel sp;
-    const float cut = support_cut(bp, rec);
+    const float cut =
+        fmaf(1e-6f, fmaf(fabsf(rec.U), (float)bp.n0, fmaf(fabsf(rec.V), (float)bp.n1, bp.sup_mg)), bp.span_cut);
     const float beta = fmaf(-bp.sup_r, rec.V, rec.U);
     const float gamma = bp.sup_c * rec.V * rec.V;
     sp.a2 = bp.span_a2;

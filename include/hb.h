@@ -77,9 +77,10 @@ enum {
 enum {
     HB_LAMBDA_ABSOLUTE = 1u << 0,  /* gamma = lambda; default gamma = lambda * trace(A^T A) / 2 */
     HB_LOWPASS_TIKHONOV = 1u << 1, /* low pass through M as well (the all-Tikhonov comparison) */
-    HB_FULL_GRID = 1u << 2,        /* posterior enumerates every grid node; by default the rows whose
-                                      every weight is exactly zero in FP32 (below 2^-150 relative to
-                                      the reference node) are skipped, which leaves the sums unchanged */
+    HB_FULL_GRID = 1u << 2,        /* posterior enumerates every grid node; by default, per low-pass
+                                      pixel, only the nodes within 2^-(30 + log2(n0 n1)) of the reference
+                                      node's weight (which is exactly 1) are, so that the nodes left out
+                                      carry together less than 2^-30 of the posterior mass */
     HB_ILLUMINATION = 1u << 5,     /* the constant term of Eq. 8 (global illumination): the Tikhonov
                                       operator solves over xi = [A | 1] and keeps the HbO2 and Hb rows;
                                       the posterior integrates a per-pixel offset kappa (1,1,1) out

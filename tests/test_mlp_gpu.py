@@ -166,31 +166,36 @@ def test_asynchronous_host_calls_in_learned_mode(trained):
         ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
 
 
-def test_mlp_mode_is_faster_than_the_grid_posterior(trained):
-    """What the network gains: a 1920x1080 frame (3 levels, 128x128 grid) with the network,
-    its sampled check and the gated fallback, against the exact grid posterior (about
-    0.77x the time on a GB300, 35 us against 45 us back to back: the transforms, common to
-    both, are about 30 us of it)."""
+def test_mlp_mode_is_faster_than_the_grid_search(trained):
+    """What the network replaces: the grid search of every node (HB_FULL_GRID, the method as
+    the paper describes it).  A 1920x1080 frame (3 levels, 128x128 grid) with the network, its
+    sampled check and the gated fallback takes well under half that time.  (Against the exact
+    path with its support bounds, which skips the nodes whose weights do not matter, the
+    network now gains only a few percent; the bench reports that ratio.)"""
     wl, mix = synth.HD_1080, trained["mix"]
     fr = synth.make_frame(902, wl.H, wl.W, mix.A, wl.nblobs, wl.smin, wl.smax, wl.noise, wl.fmt)
     frame = torch.from_numpy(fr.rgb).to(DEV)
     thb = torch.empty((wl.H, wl.W), dtype=torch.float32, device=DEV)
     so2 = torch.empty_like(thb)
-    times = {}
+
+    def frame_ms(ctx):
+        for _ in range(3):
+            ctx.estimate(frame, thb, so2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(20):
+            ctx.estimate(frame, thb, so2)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 20
+
+    with Context(mix.A, GRID, wl.levels, wl.lam, wl.W, wl.H, wl.fmt, binding.HB_FULL_GRID) as ctx:
+        grid_ms = frame_ms(ctx)
     with Context(mix.A, GRID, wl.levels, wl.lam, wl.W, wl.H, wl.fmt) as ctx:
         ctx.mlp_set_params(trained["ctx"].mlp_get_params())
-        for mode, tol in ((binding.HB_MODE_BAYES, 0.0), (binding.HB_MODE_MLP, float("inf"))):
-            ctx.set_lowpass_mode(mode, tol, 256)
-            for _ in range(3):
-                ctx.estimate(frame, thb, so2)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            for _ in range(20):
-                ctx.estimate(frame, thb, so2)
-            b.record()
-            torch.cuda.synchronize()
-            times[mode] = a.elapsed_time(b) / 20
-    assert times[binding.HB_MODE_MLP] < 0.9 * times[binding.HB_MODE_BAYES], times
+        ctx.set_lowpass_mode(binding.HB_MODE_MLP, float("inf"), 256)
+        mlp_ms = frame_ms(ctx)
+    assert mlp_ms < 0.5 * grid_ms, (mlp_ms, grid_ms)
 
 
 def test_mode_requires_a_network():

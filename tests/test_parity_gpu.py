@@ -362,7 +362,7 @@ def test_host_entry_in_bands_matches_the_device_call(case):
         np.testing.assert_array_equal(th2.numpy(), thb.cpu().numpy())
 
 
-@pytest.mark.parametrize("case", ["hd_bayes", "small_tikhonov"])
+@pytest.mark.parametrize("case", ["hd_bayes", "small_tikhonov", "small_bayes", "f32_bayes"])
 def test_asynchronous_host_calls_overlap_and_match(case):
     """hb_estimate_host_async: six different frames queued back to back on one stream (two
     staging sets in turn, so frames overlap), each into its own pinned outputs; after one
@@ -374,11 +374,20 @@ def test_asynchronous_host_calls_overlap_and_match(case):
         A, grid, levels, flags, H, W = mix.A, synth.grid_spec(wl), wl.levels, 0, wl.H, wl.W
         frames = [synth.make_frame(700 + k, H, W, A, wl.nblobs, wl.smin, wl.smax, wl.noise, "u8").rgb
                   for k in range(6)]
-    else:
+    elif case == "small_tikhonov":
         A = synth.make_mixing(44).A
         grid, levels, flags, H, W = _grid(16, 16), 2, binding.HB_LOWPASS_TIKHONOV, 300, 500
         frames = [synth.make_frame(800 + k, H, W, A, 6, 10.0, 60.0, 0.01, "u8").rgb for k in range(6)]
-    with Context(A, grid, levels, 1e-3, W, H, "u8", flags) as ctx:
+    elif case == "small_bayes":                   # 300 low-pass pixels: the one-pixel-per-unit kernel
+        A = synth.make_mixing(45).A
+        grid, levels, flags, H, W = _grid(64, 64), 3, 0, 120, 160
+        frames = [synth.make_frame(850 + k, H, W, A, 4, 5.0, 30.0, 0.01, "u8").rgb for k in range(6)]
+    else:                                         # float frames, 2 levels, a ragged size
+        A = synth.make_mixing(46).A
+        grid, levels, flags, H, W = _grid(128, 96), 2, 0, 602, 998
+        frames = [synth.make_frame(870 + k, H, W, A, 8, 10.0, 80.0, 0.005, "f32").rgb for k in range(6)]
+    fmt = "u8" if frames[0].dtype == np.uint8 else "f32"
+    with Context(A, grid, levels, 1e-3, W, H, fmt, flags) as ctx:
         ref = []
         for rgb in frames:
             thb = torch.empty((H, W), dtype=torch.float32, device=DEV)

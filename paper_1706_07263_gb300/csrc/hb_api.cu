@@ -422,19 +422,19 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
     if (bayes) {
         StageTimer t(c, s, HB_STAGE_LOWPASS);
         if (mlp) {
-            // network estimate, sampled exact check, exact recomputation only if the check
-            // failed; each kernel waits for its predecessor in-kernel (PDL)
+            // network estimate together with the sampled exact check (one launch), then the
+            // exact recomputation only if the check failed; each kernel waits for its
+            // predecessor in-kernel (PDL)
             const void* img = mlp_image(c, s, e);
+            hb::MlpCheck ck{c->mlp_nsample, 0, c->frame_seq++, 1.f / c->mlp_ext0, 1.f / c->mlp_ext1, c->mlp_tol,
+                            c->d_err, c->d_flags};
             if (img)
-                e = hb::launch_mlp_forward(img, c->mlp_norm, c->d_ybar_f + 3 * b.ll_off, b.npix, chat, pdl, s);
+                e = hb::launch_mlp_forward_check(img, c->mlp_norm, c->d_ybar_f + 3 * b.ll_off, b.npix, chat,
+                                                 conc_scaled, scale, c->bp, rec, ck, pdl, s);
             if (e == cudaSuccess)
-                e = hb::launch_posterior_check(c->bp, rec, b.npix, c->mlp_nsample, c->frame_seq++, chat,
-                                               1.f / c->mlp_ext0, 1.f / c->mlp_ext1, c->d_err, c->mlp_tol, c->d_flags,
-                                               pdl, s);
-            if (e == cudaSuccess)
-                e = hb::launch_posterior(c->bp, rec, b.npix, post_scratch(c, b.ll_off), chat, nullptr, scale, pdl,
+                e = hb::launch_posterior(c->bp, rec, b.npix, post_scratch(c, b.ll_off), chat, conc_scaled, scale, pdl,
                                          s, hb::PosteriorGate{c->d_flags + 2});
-            c->launches += 3;
+            c->launches += 2;
             c->mlp_frames++;
         } else {
             e = hb::launch_posterior(c->bp, rec, b.npix, post_scratch(c, b.ll_off), chat, conc_scaled, scale, pdl,

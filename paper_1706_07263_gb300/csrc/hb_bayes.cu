@@ -584,85 +584,4 @@ cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long np
     return launch_cpl<8>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);
 }
 
-namespace {
-
-// The learned stand-in's sampled check: one sampled pixel per CTA (cta_posterior_mean
-// shares its support rows out over the CTA's warps; the check is latency-bound: few
-// pixels, each wanted quickly).  err[k] = the larger of the two axes' errors of est
-// relative to the box extents (NaN if either is).  The last CTA to arrive adds all the
-// errors in index order and leaves the decision in sync[2].
-template <int CPL>
-__global__ void __launch_bounds__(kThreads) posterior_check_kernel(BayesParams bp, const BayesRec* __restrict__ recs,
-                                                                   long npix, int nsample, unsigned seed,
-                                                                   const float2* __restrict__ est, float inv_ext0,
-                                                                   float inv_ext1, float* err, float tol,
-                                                                   unsigned* sync) {
-    __shared__ float part[kThreads / 32][3];
-    __shared__ unsigned last;
-    __shared__ float red[kThreads];
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;");
-    for (int k = blockIdx.x; k < nsample; k += gridDim.x) {
-        const long p = sample_pixel(seed, k, npix);
-        const float2 c = cta_posterior_mean<CPL>(bp, recs[p], part);
-        if (threadIdx.x == 0) {
-            const float2 e = est[p];
-            const float dx = fabsf(e.x - c.x) * inv_ext0, dy = fabsf(e.y - c.y) * inv_ext1;
-            err[k] = isnan(dx) || isnan(dy) ? NAN : fmaxf(dx, dy);
-            __threadfence();
-        }
-    }
-    if (threadIdx.x == 0) last = atomicAdd(&sync[0], 1u) == gridDim.x - 1 ? 1u : 0u;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    const volatile float* ev = err;
-    float e = 0.f;
-    for (int k = threadIdx.x; k < nsample; k += kThreads) e += ev[k];
-    red[threadIdx.x] = e;
-    __syncthreads();
-#pragma unroll
-    for (int h = kThreads / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const bool run = !(red[0] / (float)nsample <= tol);
-        sync[2] = run ? 1u : 0u;
-        if (run) sync[1] += 1u;
-        sync[0] = 0u;
-    }
-}
-
-template <int CPL>
-cudaError_t launch_check_cpl(const BayesParams& bp, const BayesRec* rec, long npix, int nsample, unsigned seed,
-                             const float2* est, float inv_ext0, float inv_ext1, float* err, float tol, unsigned* sync,
-                             bool pdl, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(nsample < 4096 ? nsample : 4096));
-    cfg.blockDim = dim3(kThreads);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, posterior_check_kernel<CPL>, bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1,
-                              err, tol, sync);
-}
-
-}  // namespace
-
-cudaError_t launch_posterior_check(const BayesParams& bp, const BayesRec* rec, long npix, int nsample, unsigned seed,
-                                   const float2* est, float inv_ext0, float inv_ext1, float* err, float tol,
-                                   unsigned* sync, bool pdl, cudaStream_t s) {
-    if (npix <= 0 || nsample <= 0) return cudaSuccess;
-#define HB_CHECK_ARGS bp, rec, npix, nsample, seed, est, inv_ext0, inv_ext1, err, tol, sync, pdl, s
-    if (bp.n1 <= 32) return launch_check_cpl<1>(HB_CHECK_ARGS);
-    if (bp.n1 <= 64) return launch_check_cpl<2>(HB_CHECK_ARGS);
-    if (bp.n1 <= 128) return launch_check_cpl<4>(HB_CHECK_ARGS);
-    return launch_check_cpl<8>(HB_CHECK_ARGS);
-#undef HB_CHECK_ARGS
-}
-
 }  // namespace hb

@@ -119,7 +119,7 @@ cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, co
                             const LsOut& ls = LsOut{});
 cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s);
 // Optional gate of the posterior launch: when run is set the kernel does nothing unless
-// *run is non-zero (the decision launch_posterior_check leaves behind).
+// *run is non-zero (the decision the learned stand-in's sampled check leaves behind).
 struct PosteriorGate {
     const unsigned* run;
 };
@@ -130,15 +130,6 @@ cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long np
 // pixels per warp: the span kernel, or the pair kernel without column intervals); each
 // pixel's result then does not depend on the other pixels of the launch.
 bool posterior_uses_pairs(const BayesParams& bp, long npix);
-// Exact posterior of nsample pseudo-randomly drawn pixels (seeded) against another
-// estimate of them: err[k] = the larger of |d c0| inv_ext0 and |d c1| inv_ext1 for the
-// k-th drawn pixel (NaN if either is).  The last CTA to finish adds the errors in index
-// order and sets sync[2] = 1 when their mean exceeds tol or is NaN (then also sync[1] += 1),
-// else 0; sync[0] is its arrival counter (zero before and after).  pdl as for
-// launch_posterior.
-cudaError_t launch_posterior_check(const BayesParams& bp, const BayesRec* rec, long npix, int nsample, unsigned seed,
-                                   const float2* est, float inv_ext0, float inv_ext1, float* err, float tol,
-                                   unsigned* sync, bool pdl, cudaStream_t s);
 cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_t stride, const float2* lut,
                              const float2* chat, float* out0, float* out1, int debug_conc, bool pdl, cudaStream_t s);
 size_t transform_smem_bytes(const TransformParams& tp);

@@ -19,13 +19,16 @@
 // (mma.sync m16n8k16, BF16 in, FP32 accumulate), the 3- and 2-wide layers on the FP32
 // pipes.  mlp_adam_kernel adds the partials in a fixed order (deterministic) and applies
 // Adam to the FP32 master weights, refreshing the BF16 copies.  mlp_forward_kernel:
-// inference, 8 samples per warp held in tensor-core fragments.  Weights are BF16;
+// inference, 8 samples per warp held in tensor-core fragments.  mlp_forward_check_kernel:
+// the same inference with the per-frame sampled exact check in extra CTAs of the launch,
+// so that the check runs beside the inference instead of after it.  Weights are BF16;
 // activations are rounded to BF16 at h1 and h2, and so is the gradient dz2 fed to the
 // tensor cores; erf is evaluated to FP32 accuracy (see gelu); the input x
 // stays FP32 (the correction varies fast near the box edges, so the input needs more
 // resolution than BF16's 8 bits); accumulation is FP32 throughout.
 #include "hb_common.cuh"
 #include "hb_mlp.cuh"
+#include "hb_posterior.cuh"
 
 #include <cuda_bf16.h>
 #include <math.h>
@@ -361,6 +364,19 @@ __global__ void mlp_adam_kernel(const float* __restrict__ gpart, const float* __
 // 16 mt + g + {0, 8} of samples 2q, 2q + 1, where GELU, the BF16 rounding of h2 and the
 // lane's share of layer 3 are applied, and shuffles over g finish layer 3.
 constexpr int kWarpsF = 8;
+constexpr int kMlpCheckPerCta = kWarpsF / 2;  // drawn pixels a check CTA takes at a time
+static_assert(kMlpCheckPerCta == 4, "pair_barrier names one barrier per pair of warps");
+
+// Barrier of the two warps 2 pair, 2 pair + 1 (named barriers 1 .. 4; 0 is __syncthreads).
+// The identifiers are literals so that the kernel reserves only the barriers it uses.
+__device__ __forceinline__ void pair_barrier(int pair) {
+    switch (pair) {
+        case 0: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+        case 1: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+        case 2: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+        default: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
+    }
+}
 struct __align__(16) InferSmem {
     uint4 w2f[kHid / 16][kHid / 16][32];  // W2 A fragments per (m tile, k tile, lane)
     float4 l1[kHid];                      // W1[u][0..2], b1[u]
@@ -387,86 +403,203 @@ __global__ void __launch_bounds__(256) mlp_pack_kernel(const float* __restrict__
     if (threadIdx.x == 0) img->b3 = make_float4(wbf[kOffB3], wbf[kOffB3 + 1], 0.f, 0.f);
 }
 
+// One 8-sample tile (samples 8 tile .. 8 tile + 7) through the network in one warp.  The
+// lanes with g < 2 end up holding sample 2q + g: they return its index and leave its
+// estimate in val; the other lanes, and samples past n, return -1.
+__device__ __forceinline__ long infer_tile(const InferSmem& S, const MlpNorm& nm, const float* __restrict__ ybar,
+                                           long n, long tile, int lane, float2& val) {
+    const int g = lane >> 2, q = lane & 3;
+    const long r = tile * 8 + g;
+    float y[3], x[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = r < n ? ybar[r * 3 + c] : 0.f;
+#pragma unroll
+    for (int c = 0; c < kIn; ++c)
+        x[c] = nm.T[c * 3] * y[0] + nm.T[c * 3 + 1] * y[1] + nm.T[c * 3 + 2] * y[2] + nm.t0[c];
+    // layer 1 into the B fragments of layer 2 (k = unit, n = sample g)
+    unsigned bfr[kHid / 16][2];
+#pragma unroll
+    for (int kt = 0; kt < kHid / 16; ++kt) {
+        float h[4];  // units 16 kt + 2q + {0, 1, 8, 9}
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float4 w = S.l1[kt * 16 + 2 * q + (v & 1) + 8 * (v >> 1)];
+            float z = w.w;
+            z = fmaf(w.x, x[0], z);
+            z = fmaf(w.y, x[1], z);
+            z = fmaf(w.z, x[2], z);
+            h[v] = gelu(z);
+        }
+        bfr[kt][0] = pack_bf16(h[0], h[1]);
+        bfr[kt][1] = pack_bf16(h[2], h[3]);
+    }
+    // layer 2 on the tensor cores, layer 3 from the accumulators
+    float o00 = 0.f, o01 = 0.f, o10 = 0.f, o11 = 0.f;  // (sample 2q / 2q + 1, output 0 / 1)
+#pragma unroll
+    for (int mt = 0; mt < kHid / 16; ++mt) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < kHid / 16; ++kt) {
+            const uint4 aw = S.w2f[mt][kt][lane];
+            const unsigned af[4] = {aw.x, aw.y, aw.z, aw.w};
+            mma16816(d, af, bfr[kt]);
+        }
+        // d: (unit mt*16 + g, samples 2q, 2q+1), (unit mt*16 + g + 8, samples 2q, 2q+1)
+        const float4 la = S.l3[mt * 16 + g], lb = S.l3[mt * 16 + g + 8];
+        const float h00 = bf(gelu(d[0] + la.x)), h01 = bf(gelu(d[1] + la.x));
+        const float h10 = bf(gelu(d[2] + lb.x)), h11 = bf(gelu(d[3] + lb.x));
+        o00 = fmaf(la.y, h00, fmaf(lb.y, h10, o00));
+        o01 = fmaf(la.z, h00, fmaf(lb.z, h10, o01));
+        o10 = fmaf(la.y, h01, fmaf(lb.y, h11, o10));
+        o11 = fmaf(la.z, h01, fmaf(lb.z, h11, o11));
+    }
+#pragma unroll
+    for (int off = 4; off <= 16; off <<= 1) {
+        o00 += __shfl_xor_sync(0xffffffffu, o00, off);
+        o01 += __shfl_xor_sync(0xffffffffu, o01, off);
+        o10 += __shfl_xor_sync(0xffffffffu, o10, off);
+        o11 += __shfl_xor_sync(0xffffffffu, o11, off);
+    }
+    // lanes g = 0 and g = 1 hold samples 2q and 2q + 1; they need those samples' ybar
+    const int s = 2 * q + (g & 1);
+    const long rs = tile * 8 + s;
+    const float ya = __shfl_sync(0xffffffffu, y[0], 4 * s), yb = __shfl_sync(0xffffffffu, y[1], 4 * s),
+                yc = __shfl_sync(0xffffffffu, y[2], 4 * s);
+    if (g >= 2 || rs >= n) return -1;
+    const float ys[3] = {ya, yb, yc};
+    const float o0 = (g & 1) ? o10 : o00, o1 = (g & 1) ? o11 : o01;
+    val = make_float2(clip_ls(nm, ys, 0) + nm.osc0 * (o0 + S.b3.x), clip_ls(nm, ys, 1) + nm.osc1 * (o1 + S.b3.y));
+    return rs;
+}
+
+// Every CTA stages the network image before waiting on the kernel that writes ybar (the
+// weights do not come from it); then the launch's dependents may start.
+__device__ __forceinline__ void stage_image(InferSmem& S, const InferSmem* __restrict__ img) {
+    const uint4* src = reinterpret_cast<const uint4*>(img);
+    uint4* dst = reinterpret_cast<uint4*>(&S);
+    for (int i = threadIdx.x; i < (int)(sizeof(InferSmem) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    // programmatic dependent launch: returns at once after a plain launch
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
 __global__ void __launch_bounds__(32 * kWarpsF) mlp_forward_kernel(const InferSmem* __restrict__ img, MlpNorm nm,
                                                                    const float* __restrict__ ybar, long n,
                                                                    float2* __restrict__ chat) {
     __shared__ InferSmem S;
-    // the weights do not come from the preceding kernel: stage them before waiting on it
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(img);
-        uint4* dst = reinterpret_cast<uint4*>(&S);
-        for (int i = threadIdx.x; i < (int)(sizeof(InferSmem) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
-    }
-    __syncthreads();
-    // launched after the kernel that writes ybar (programmatic dependent launch, or a
-    // plain launch where this returns at once)
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;");
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    stage_image(S, img);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long ntile = (n + 7) / 8;
     for (long tile = (long)blockIdx.x * kWarpsF + warp; tile < ntile; tile += (long)gridDim.x * kWarpsF) {
-        const long r = tile * 8 + g;
-        float y[3], x[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) y[c] = r < n ? ybar[r * 3 + c] : 0.f;
-#pragma unroll
-        for (int c = 0; c < kIn; ++c)
-            x[c] = nm.T[c * 3] * y[0] + nm.T[c * 3 + 1] * y[1] + nm.T[c * 3 + 2] * y[2] + nm.t0[c];
-        // layer 1 into the B fragments of layer 2 (k = unit, n = sample g)
-        unsigned bfr[kHid / 16][2];
-#pragma unroll
-        for (int kt = 0; kt < kHid / 16; ++kt) {
-            float h[4];  // units 16 kt + 2q + {0, 1, 8, 9}
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const float4 w = S.l1[kt * 16 + 2 * q + (v & 1) + 8 * (v >> 1)];
-                float z = w.w;
-                z = fmaf(w.x, x[0], z);
-                z = fmaf(w.y, x[1], z);
-                z = fmaf(w.z, x[2], z);
-                h[v] = gelu(z);
+        float2 v;
+        const long rs = infer_tile(S, nm, ybar, n, tile, lane, v);
+        if (rs >= 0) chat[rs] = v;
+    }
+}
+
+// Exact posterior mean of one pixel computed by one warp (its support rows, CPL grid
+// columns per lane); the same sums as the posterior kernels up to the order of the
+// additions, valid in every lane.
+template <int CPL>
+__device__ float2 warp_posterior_mean(const BayesParams& bp, const BayesRec& rec, int lane) {
+    int lo, hi;
+    support_rows(bp, rec, lo, hi);
+    float sw = 0.f, sdi = 0.f, sdj = 0.f;
+    grid_sums<CPL>(bp, rec, lane, lo, hi, 0.f, sw, sdi, sdj);
+    sw = warp_sum(sw);
+    sdi = warp_sum(sdi);
+    sdj = warp_sum(sdj);
+    if (!usable(sw, sdi, sdj)) {  // far outside the model: all rows, explicit maximum shift
+        const float shift = warp_max(grid_max<CPL>(bp, rec, lane, 0, bp.n0));
+        sw = sdi = sdj = 0.f;
+        grid_sums<CPL>(bp, rec, lane, 0, bp.n0, shift, sw, sdi, sdj);
+        sw = warp_sum(sw);
+        sdi = warp_sum(sdi);
+        sdj = warp_sum(sdj);
+    }
+    return make_float2(fmaf(bp.h0f, sdi / sw, fmaf((float)rec.i0, bp.h0f, bp.lo0f)),
+                       fmaf(bp.h1f, sdj / sw, fmaf((float)rec.j0, bp.h1f, bp.lo1f)));
+}
+
+// Inference and the sampled exact check in one launch.  CTAs 0 .. ck.nctas - 1 check
+// kMlpCheckPerCta drawn pixels at a time, one per pair of warps: the even warp computes the
+// pixel's exact posterior mean (warp_posterior_mean) while the odd warp runs the pixel's
+// 8-sample tile through the same code as the inference CTAs; then err[k] = the larger of
+// the two axes' errors relative to the box extents (NaN if either is).  The last check
+// CTA to arrive adds the errors in index order and leaves the decision in sync[2]
+// (sync[1] counts the failed frames, sync[0] is the arrival counter).  The remaining CTAs
+// run inference exactly as mlp_forward_kernel and, if chat_scaled is set, also write the
+// estimates times scale there.
+template <int CPL>
+__global__ void __launch_bounds__(32 * kWarpsF, 4)
+    mlp_forward_check_kernel(const InferSmem* __restrict__ img, MlpNorm nm, const float* __restrict__ ybar, long n,
+                             float2* __restrict__ chat, float2* __restrict__ chat_scaled, float scale,
+                             BayesParams bp, const BayesRec* __restrict__ recs, MlpCheck ck) {
+    __shared__ InferSmem S;
+    __shared__ float2 est[kMlpCheckPerCta];
+    __shared__ float red[32 * kWarpsF];
+    __shared__ unsigned last;
+    stage_image(S, img);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if ((int)blockIdx.x >= ck.nctas) {
+        const long ntile = (n + 7) / 8, nblk = (long)gridDim.x - ck.nctas;
+        for (long tile = ((long)blockIdx.x - ck.nctas) * kWarpsF + warp; tile < ntile; tile += nblk * kWarpsF) {
+            float2 v;
+            const long rs = infer_tile(S, nm, ybar, n, tile, lane, v);
+            if (rs >= 0) {
+                chat[rs] = v;
+                if (chat_scaled) chat_scaled[rs] = make_float2(scale * v.x, scale * v.y);
             }
-            bfr[kt][0] = pack_bf16(h[0], h[1]);
-            bfr[kt][1] = pack_bf16(h[2], h[3]);
         }
-        // layer 2 on the tensor cores, layer 3 from the accumulators
-        float o00 = 0.f, o01 = 0.f, o10 = 0.f, o11 = 0.f;  // (sample 2q / 2q + 1, output 0 / 1)
+        return;
+    }
+    const int pair = warp >> 1;
+    for (int k0 = blockIdx.x * kMlpCheckPerCta; k0 < ck.nsample; k0 += ck.nctas * kMlpCheckPerCta) {
+        const int k = k0 + pair;
+        const bool on = k < ck.nsample;  // the same for both warps of the pair
+        const long p = on ? sample_pixel(ck.seed, k, n) : 0;
+        float2 c = make_float2(0.f, 0.f);
+        if (on && (warp & 1)) {
+            float2 v = make_float2(0.f, 0.f);
+            const long rs = infer_tile(S, nm, ybar, n, p >> 3, lane, v);
+            const int src = __ffs(__ballot_sync(0xffffffffu, rs == p)) - 1;  // the one lane holding p
+            const float ex = __shfl_sync(0xffffffffu, v.x, src), ey = __shfl_sync(0xffffffffu, v.y, src);
+            if (lane == 0) est[pair] = make_float2(ex, ey);
+        } else if (on) {
+            c = warp_posterior_mean<CPL>(bp, recs[p], lane);
+        }
+        pair_barrier(pair);  // the even warp reads what the odd one wrote
+        if (on && !(warp & 1) && lane == 0) {
+            const float2 e = est[pair];
+            const float dx = fabsf(e.x - c.x) * ck.inv_ext0, dy = fabsf(e.y - c.y) * ck.inv_ext1;
+            ck.err[k] = isnan(dx) || isnan(dy) ? NAN : fmaxf(dx, dy);
+        }
+        pair_barrier(pair);  // est[pair] free again
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();  // the CTA's errors (ordered before by the barrier) before the arrival
+        last = atomicAdd(&ck.sync[0], 1u) == (unsigned)ck.nctas - 1u ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const volatile float* ev = ck.err;
+    float e = 0.f;
+    for (int k = threadIdx.x; k < ck.nsample; k += blockDim.x) e += ev[k];
+    red[threadIdx.x] = e;
+    __syncthreads();
 #pragma unroll
-        for (int mt = 0; mt < kHid / 16; ++mt) {
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int kt = 0; kt < kHid / 16; ++kt) {
-                const uint4 aw = S.w2f[mt][kt][lane];
-                const unsigned af[4] = {aw.x, aw.y, aw.z, aw.w};
-                mma16816(d, af, bfr[kt]);
-            }
-            // d: (unit mt*16 + g, samples 2q, 2q+1), (unit mt*16 + g + 8, samples 2q, 2q+1)
-            const float4 la = S.l3[mt * 16 + g], lb = S.l3[mt * 16 + g + 8];
-            const float h00 = bf(gelu(d[0] + la.x)), h01 = bf(gelu(d[1] + la.x));
-            const float h10 = bf(gelu(d[2] + lb.x)), h11 = bf(gelu(d[3] + lb.x));
-            o00 = fmaf(la.y, h00, fmaf(lb.y, h10, o00));
-            o01 = fmaf(la.z, h00, fmaf(lb.z, h10, o01));
-            o10 = fmaf(la.y, h01, fmaf(lb.y, h11, o10));
-            o11 = fmaf(la.z, h01, fmaf(lb.z, h11, o11));
-        }
-#pragma unroll
-        for (int off = 4; off <= 16; off <<= 1) {
-            o00 += __shfl_xor_sync(0xffffffffu, o00, off);
-            o01 += __shfl_xor_sync(0xffffffffu, o01, off);
-            o10 += __shfl_xor_sync(0xffffffffu, o10, off);
-            o11 += __shfl_xor_sync(0xffffffffu, o11, off);
-        }
-        // lanes g = 0 and g = 1 hold samples 2q and 2q + 1; they need those samples' ybar
-        const int s = 2 * q + (g & 1);
-        const long rs = tile * 8 + s;
-        const float ya = __shfl_sync(0xffffffffu, y[0], 4 * s), yb = __shfl_sync(0xffffffffu, y[1], 4 * s),
-                    yc = __shfl_sync(0xffffffffu, y[2], 4 * s);
-        if (g < 2 && rs < n) {
-            const float ys[3] = {ya, yb, yc};
-            const float o0 = (g & 1) ? o10 : o00, o1 = (g & 1) ? o11 : o01;
-            chat[rs] = make_float2(clip_ls(nm, ys, 0) + nm.osc0 * (o0 + S.b3.x),
-                                   clip_ls(nm, ys, 1) + nm.osc1 * (o1 + S.b3.y));
-        }
+    for (int h = 32 * kWarpsF / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const bool run = !(red[0] / (float)ck.nsample <= ck.tol);
+        ck.sync[2] = run ? 1u : 0u;
+        if (run) ck.sync[1] += 1u;
+        ck.sync[0] = 0u;
     }
 }
 
@@ -526,6 +659,53 @@ cudaError_t launch_mlp_forward(const void* img, const MlpNorm& nm, const float* 
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, mlp_forward_kernel, static_cast<const InferSmem*>(img), nm, ybar, n, chat);
+}
+
+namespace {
+
+template <int CPL>
+cudaError_t launch_forward_check_cpl(const void* img, const MlpNorm& nm, const float* ybar, long n, float2* chat,
+                                     float2* chat_scaled, float scale, const BayesParams& bp, const BayesRec* rec,
+                                     const MlpCheck& ck, unsigned blocks, bool pdl, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(32 * kWarpsF);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, mlp_forward_check_kernel<CPL>, static_cast<const InferSmem*>(img), nm, ybar, n,
+                              chat, chat_scaled, scale, bp, rec, ck);
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_forward_check(const void* img, const MlpNorm& nm, const float* ybar, long n, float2* chat,
+                                     float2* chat_scaled, float scale, const BayesParams& bp, const BayesRec* rec,
+                                     MlpCheck ck, bool pdl, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (ck.nsample <= 0) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // check CTAs first (dispatched first), kMlpCheckPerCta drawn pixels each while 4096 CTAs
+    // suffice
+    const long need = (ck.nsample + kMlpCheckPerCta - 1) / kMlpCheckPerCta;
+    ck.nctas = (int)(need < 4096 ? need : 4096);
+    const long tiles = (n + 7) / 8;
+    long blocks = (tiles + kWarpsF - 1) / kWarpsF;  // one tile per warp while that fits
+    if (blocks > 8L * sms) blocks = 8L * sms;
+    if (blocks < 1) blocks = 1;
+    blocks += ck.nctas;
+#define HB_FC_ARGS img, nm, ybar, n, chat, chat_scaled, scale, bp, rec, ck, (unsigned)blocks, pdl, s
+    if (bp.n1 <= 32) return launch_forward_check_cpl<1>(HB_FC_ARGS);
+    if (bp.n1 <= 64) return launch_forward_check_cpl<2>(HB_FC_ARGS);
+    if (bp.n1 <= 128) return launch_forward_check_cpl<4>(HB_FC_ARGS);
+    return launch_forward_check_cpl<8>(HB_FC_ARGS);
+#undef HB_FC_ARGS
 }
 
 }  // namespace hb

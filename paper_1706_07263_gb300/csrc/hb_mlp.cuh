@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include "hb_common.cuh"
+
 namespace hb {
 
 constexpr int kIn = 3, kHid = 64, kOut = 2;
@@ -47,5 +49,26 @@ cudaError_t launch_mlp_pack(const float* wbf, void* img, cudaStream_t s);
 // the preceding kernel in the stream (the kernel waits for it before reading ybar).
 cudaError_t launch_mlp_forward(const void* img, const MlpNorm& nm, const float* ybar, long n, float2* chat, bool pdl,
                                cudaStream_t s);
+
+// The learned stand-in's sampled check, run by extra CTAs of the inference launch: the
+// exact posterior of nsample pseudo-randomly drawn pixels (seeded) against the network's
+// estimate of them.  err[k] = the larger of |d c0| inv_ext0 and |d c1| inv_ext1 for the
+// k-th drawn pixel (NaN if either is); the last check CTA to finish adds the errors in
+// index order and sets sync[2] = 1 when their mean exceeds tol or is NaN (then also
+// sync[1] += 1), else 0; sync[0] is its arrival counter (zero before and after).
+struct MlpCheck {
+    int nsample;
+    int nctas;  // check CTAs (set by the launch)
+    unsigned seed;
+    float inv_ext0, inv_ext1, tol;
+    float* err;
+    unsigned* sync;
+};
+// Inference for the n samples of a band (the rows of rec) and the sampled check of it in
+// one launch; chat_scaled (optional) also receives the estimates times scale; pdl as for
+// launch_mlp_forward.  nsample must be positive; n = 0 launches nothing.
+cudaError_t launch_mlp_forward_check(const void* img, const MlpNorm& nm, const float* ybar, long n, float2* chat,
+                                     float2* chat_scaled, float scale, const BayesParams& bp, const BayesRec* rec,
+                                     MlpCheck ck, bool pdl, cudaStream_t s);
 
 }  // namespace hb

@@ -129,6 +129,72 @@ def test_forced_fallback_reproduces_the_exact_path(trained):
     ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
 
 
+def _debug(ctx, frame):
+    hl, wl = ctx.lowpass_shape()
+    ybar = torch.empty((hl, wl, 3), dtype=torch.float64, device=DEV)
+    conc = torch.empty((hl, wl, 2), dtype=torch.float32, device=DEV)
+    ctx.estimate_debug(frame, ybar, conc, None, None)
+    torch.cuda.synchronize()
+    return ybar, conc
+
+
+@pytest.mark.parametrize("nsample", [1, 5, 256, 3001])
+def test_check_size_leaves_the_estimate_unchanged(trained, nsample):
+    """The sampled check runs in extra CTAs of the inference launch (a few drawn pixels per
+    CTA): however many pixels it draws, the network's estimate is the same bit for bit, and a
+    corrupted network still falls back to the exact path."""
+    ctx = trained["ctx"]
+    frame = _frame(trained, 920)
+    good = ctx.mlp_get_params()
+    try:
+        ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
+        exact = _run(ctx, frame)
+        ctx.set_lowpass_mode(binding.HB_MODE_MLP, float("inf"), 256)
+        ref = _run(ctx, frame)
+        ctx.set_lowpass_mode(binding.HB_MODE_MLP, float("inf"), nsample)
+        b0 = ctx.lowpass_stats()[1]
+        got = _run(ctx, frame)
+        assert ctx.lowpass_stats()[1] == b0
+        assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
+        bad = good.copy()
+        bad[mlp.OFF_B3:] = 0.5
+        ctx.mlp_set_params(bad)
+        ctx.set_lowpass_mode(binding.HB_MODE_MLP, 1e-3, nsample)
+        got = _run(ctx, frame)
+        assert ctx.lowpass_stats()[1] == b0 + 1
+        assert torch.equal(got[0], exact[0]) and torch.equal(got[1], exact[1])
+    finally:
+        ctx.mlp_set_params(good)
+        ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
+
+
+def test_learned_low_pass_in_the_debug_output(trained):
+    """hb_estimate_debug in learned mode: the low-pass coefficients are 2^levels times the
+    network's estimate for the frame's block means (hb_mlp_forward on the same inputs, bit for
+    bit), or, after a failed check, those of the exact path."""
+    ctx, wl = trained["ctx"], trained["wl"]
+    frame = _frame(trained, 921)
+    good = ctx.mlp_get_params()
+    try:
+        ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
+        _, exact = _debug(ctx, frame)
+        ctx.set_lowpass_mode(binding.HB_MODE_MLP, float("inf"), 256)
+        ybar, conc = _debug(ctx, frame)
+        out = torch.empty((ybar.shape[0] * ybar.shape[1], 2), dtype=torch.float32, device=DEV)
+        ctx.mlp_forward(ybar.reshape(-1, 3).float().contiguous(), out)
+        torch.cuda.synchronize()
+        assert torch.equal(conc.reshape(-1, 2), out * float(1 << wl.levels))
+        bad = good.copy()
+        bad[mlp.OFF_B3:] = 0.5
+        ctx.mlp_set_params(bad)
+        ctx.set_lowpass_mode(binding.HB_MODE_MLP, 1e-3, 256)
+        _, conc = _debug(ctx, frame)
+        assert torch.equal(conc, exact)
+    finally:
+        ctx.mlp_set_params(good)
+        ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
+
+
 def test_asynchronous_host_calls_in_learned_mode(trained):
     """hb_estimate_host_async with the learned low pass (one whole-frame band per call, frames
     overlapping): with a working network each frame equals the device call bit for bit; with a
@@ -171,7 +237,7 @@ def test_mlp_mode_is_faster_than_the_grid_search(trained):
     the paper describes it).  A 1920x1080 frame (3 levels, 128x128 grid) with the network, its
     sampled check and the gated fallback takes well under half that time.  (Against the exact
     path with its support bounds, which skips the nodes whose weights do not matter, the
-    network now gains only a few percent; the bench reports that ratio.)"""
+    network gains far less; the bench reports that ratio.)"""
     wl, mix = synth.HD_1080, trained["mix"]
     fr = synth.make_frame(902, wl.H, wl.W, mix.A, wl.nblobs, wl.smin, wl.smax, wl.noise, wl.fmt)
     frame = torch.from_numpy(fr.rgb).to(DEV)

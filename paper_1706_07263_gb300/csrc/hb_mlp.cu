@@ -498,13 +498,20 @@ __global__ void __launch_bounds__(32 * kWarpsF) mlp_forward_kernel(const InferSm
     }
 }
 
-// Exact posterior mean of one pixel computed by one warp (its support rows, CPL grid
-// columns per lane); the same sums as the posterior kernels up to the order of the
-// additions, valid in every lane.
+// Posterior mean of one pixel computed by one warp (CPL grid columns per lane), valid in
+// every lane.  Rows: those of the span kernel's cut where it applies (every node left out
+// weighs under 2^-span_cut of the reference node, together under 2^-30 of the posterior
+// mass), else the rows of non-zero FP32 weight; each row is summed whole.
 template <int CPL>
 __device__ float2 warp_posterior_mean(const BayesParams& bp, const BayesRec& rec, int lane) {
     int lo, hi;
-    support_rows(bp, rec, lo, hi);
+    if (bp.sup_cols) {
+        const SpanPixel sp = span_pixel(bp, rec);
+        lo = sp.rlo;
+        hi = sp.rhi;
+    } else {
+        support_rows(bp, rec, lo, hi);
+    }
     float sw = 0.f, sdi = 0.f, sdj = 0.f;
     grid_sums<CPL>(bp, rec, lane, lo, hi, 0.f, sw, sdi, sdj);
     sw = warp_sum(sw);
@@ -527,7 +534,7 @@ __device__ float2 warp_posterior_mean(const BayesParams& bp, const BayesRec& rec
 // pixel's exact posterior mean (warp_posterior_mean) while the odd warp runs the pixel's
 // 8-sample tile through the same code as the inference CTAs; then err[k] = the larger of
 // the two axes' errors relative to the box extents (NaN if either is).  The last check
-// CTA to arrive adds the errors in index order and leaves the decision in sync[2]
+// CTA to arrive adds the errors in a fixed order and leaves the decision in sync[2]
 // (sync[1] counts the failed frames, sync[0] is the arrival counter).  The remaining CTAs
 // run inference exactly as mlp_forward_kernel and, if chat_scaled is set, also write the
 // estimates times scale there.
@@ -538,7 +545,7 @@ __global__ void __launch_bounds__(32 * kWarpsF, 4)
                              BayesParams bp, const BayesRec* __restrict__ recs, MlpCheck ck) {
     __shared__ InferSmem S;
     __shared__ float2 est[kMlpCheckPerCta];
-    __shared__ float red[32 * kWarpsF];
+    __shared__ float red[kWarpsF];
     __shared__ unsigned last;
     stage_image(S, img);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -588,15 +595,13 @@ __global__ void __launch_bounds__(32 * kWarpsF, 4)
     const volatile float* ev = ck.err;
     float e = 0.f;
     for (int k = threadIdx.x; k < ck.nsample; k += blockDim.x) e += ev[k];
-    red[threadIdx.x] = e;
+    e = warp_sum(e);
+    if (lane == 0) red[warp] = e;
     __syncthreads();
-#pragma unroll
-    for (int h = 32 * kWarpsF / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
-        const bool run = !(red[0] / (float)ck.nsample <= ck.tol);
+        float t = 0.f;
+        for (int w = 0; w < kWarpsF; ++w) t += red[w];
+        const bool run = !(t / (float)ck.nsample <= ck.tol);
         ck.sync[2] = run ? 1u : 0u;
         if (run) ck.sync[1] += 1u;
         ck.sync[0] = 0u;

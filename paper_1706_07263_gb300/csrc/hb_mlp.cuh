@@ -54,7 +54,7 @@ cudaError_t launch_mlp_forward(const void* img, const MlpNorm& nm, const float* 
 // exact posterior of nsample pseudo-randomly drawn pixels (seeded) against the network's
 // estimate of them.  err[k] = the larger of |d c0| inv_ext0 and |d c1| inv_ext1 for the
 // k-th drawn pixel (NaN if either is); the last check CTA to finish adds the errors in
-// index order and sets sync[2] = 1 when their mean exceeds tol or is NaN (then also
+// a fixed order and sets sync[2] = 1 when their mean exceeds tol or is NaN (then also
 // sync[1] += 1), else 0; sync[0] is its arrival counter (zero before and after).
 struct MlpCheck {
     int nsample;

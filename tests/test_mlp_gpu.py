@@ -168,12 +168,22 @@ def test_check_size_leaves_the_estimate_unchanged(trained, nsample):
         ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
 
 
-def test_learned_low_pass_in_the_debug_output(trained):
+@pytest.mark.parametrize("shape", [None, (100, 150), (41, 67)])
+def test_learned_low_pass_in_the_debug_output(trained, shape):
     """hb_estimate_debug in learned mode: the low-pass coefficients are 2^levels times the
     network's estimate for the frame's block means (hb_mlp_forward on the same inputs, bit for
-    bit), or, after a failed check, those of the exact path."""
-    ctx, wl = trained["ctx"], trained["wl"]
-    frame = _frame(trained, 921)
+    bit), or, after a failed check, those of the exact path.  Besides the training frame size
+    (4,096 low-pass samples), two frames whose 247 and 54 samples end in a partial 8-sample
+    tile."""
+    wl = trained["wl"]
+    if shape is None:
+        ctx, frame = trained["ctx"], _frame(trained, 921)
+    else:
+        H, W = shape
+        fr = synth.make_frame(922, H, W, trained["mix"].A, 4, 3.0, 20.0, 0.01, "u8")
+        frame = torch.from_numpy(fr.rgb).to(DEV)
+        ctx = Context(trained["mix"].A, GRID, wl.levels, wl.lam, W, H, "u8")
+        ctx.mlp_set_params(trained["ctx"].mlp_get_params())
     good = ctx.mlp_get_params()
     try:
         ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
@@ -193,6 +203,8 @@ def test_learned_low_pass_in_the_debug_output(trained):
     finally:
         ctx.mlp_set_params(good)
         ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
+        if shape is not None:
+            ctx.close()
 
 
 def test_asynchronous_host_calls_in_learned_mode(trained):

@@ -47,7 +47,8 @@ typedef enum {
     HB_ERR_OOM = 4,     /* device or pinned-host allocation failed */
     HB_ERR_BUDGET = 5,  /* admission refused: the request does not fit the memory budget */
     HB_ERR_TIMEOUT = 6, /* a bounded wait ran out */
-    HB_ERR_STATE = 7    /* call not valid in the object's current state */
+    HB_ERR_STATE = 7,   /* call not valid in the object's current state */
+    HB_ERR_IO = 8       /* a file could not be read or written, or is not of the expected kind */
 } hb_status;
 
 /* Mixing model: A[c][j] is the attenuation of colour channel c (R, G, B) per
@@ -210,6 +211,22 @@ hb_status hb_mlp_init(hb_ctx *ctx, unsigned seed);
  * set_params also refreshes the BF16 copies and zeroes the Adam state. */
 hb_status hb_mlp_set_params(hb_ctx *ctx, const float *params_host);
 hb_status hb_mlp_get_params(hb_ctx *ctx, float *params_host);
+
+/* Save the network to a file: the FP32 master parameters (not the Adam state) and the
+ * model they were trained for -- the mixing matrix, the grid box and sigma_l, which fix
+ * the network's input transform, least-squares baseline and output scale.  Layout, all
+ * little-endian: 8 bytes "HBMLPv1\n"; uint32 HB_MLP_NPARAMS; uint32 0; 11 doubles A[0][0],
+ * A[0][1], A[1][0], ..., A[2][1], lo0, hi0, lo1, hi1, sigma_l; HB_MLP_NPARAMS floats in the
+ * order of hb_mlp_set_params; uint32 FNV-1a hash of every preceding byte (18,292 bytes in
+ * all).  HB_ERR_STATE if the context has no network; HB_ERR_IO if the file cannot be
+ * written completely. */
+hb_status hb_mlp_save(hb_ctx *ctx, const char *path);
+
+/* Load a network written by hb_mlp_save, as hb_mlp_set_params would.  HB_ERR_IO if the
+ * file cannot be read or is not such a file (length, header, parameter count, hash, or a
+ * non-finite value); HB_ERR_STATE if it was trained for another mixing matrix, grid box
+ * or sigma_l than the context's (compared exactly); the context is then unchanged. */
+hb_status hb_mlp_load(hb_ctx *ctx, const char *path);
 
 /* Training pairs from one frame: the block means of the low-pass band (npix x 3
  * floats) and the posterior means the exact step gives for them (npix x 2 floats, uM),

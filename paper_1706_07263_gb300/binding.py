@@ -22,13 +22,13 @@ HB_LOWPASS_TIKHONOV = 1 << 1
 STAGES = ("analysis", "lowpass", "synthesis")
 
 STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_SHAPE", 3: "HB_ERR_CUDA", 4: "HB_ERR_OOM", 5: "HB_ERR_BUDGET",
-          6: "HB_ERR_TIMEOUT", 7: "HB_ERR_STATE"}
+          6: "HB_ERR_TIMEOUT", 7: "HB_ERR_STATE", 8: "HB_ERR_IO"}
 
 # Every symbol include/hb.h declares (checked by the CPU tests against the built library).
 EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_estimate_host_async", "hb_estimate_debug",
             "hb_posterior_mean",
             "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_timing_nodes", "hb_strerror",
-            "hb_mlp_init", "hb_mlp_set_params", "hb_mlp_get_params", "hb_lowpass_pairs", "hb_mlp_train",
+            "hb_mlp_init", "hb_mlp_set_params", "hb_mlp_get_params", "hb_mlp_save", "hb_mlp_load", "hb_lowpass_pairs", "hb_mlp_train",
             "hb_mlp_gradient", "hb_mlp_forward", "hb_set_lowpass_mode", "hb_lowpass_stats",
             "hb_server_create", "hb_server_destroy", "hb_stream_open", "hb_stream_close", "hb_submit", "hb_poll",
             "hb_release", "hb_server_pause", "hb_server_drain", "hb_server_stats", "hb_posterior_mean_static")
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
     lib.hb_mlp_init.argtypes = [P, ctypes.c_uint]
     lib.hb_mlp_set_params.argtypes = [P, F]
     lib.hb_mlp_get_params.argtypes = [P, F]
+    lib.hb_mlp_save.argtypes = [P, ctypes.c_char_p]
+    lib.hb_mlp_load.argtypes = [P, ctypes.c_char_p]
     lib.hb_lowpass_pairs.argtypes = [P, P, S, P, P, P]
     lib.hb_mlp_train.argtypes = [P, P, P, L, I, I, D, ctypes.c_uint, F, P]
     lib.hb_mlp_gradient.argtypes = [P, P, P, L, P, P, P]
@@ -246,6 +248,15 @@ class Context:
         _check(load().hb_mlp_get_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
                "hb_mlp_get_params")
         return p
+
+    def mlp_save(self, path):
+        """Write the network and the model it was trained for to a file (hb_mlp_save)."""
+        _check(load().hb_mlp_save(self._h, os.fsencode(path)), "hb_mlp_save")
+
+    def mlp_load(self, path):
+        """Read a network written by mlp_save (hb_mlp_load); raises HbError with HB_ERR_IO for
+        a file that is not one, HB_ERR_STATE for a network of another model."""
+        _check(load().hb_mlp_load(self._h, os.fsencode(path)), "hb_mlp_load")
 
     def lowpass_pairs(self, frame, ybar, conc, stream=None):
         stride = frame.stride(0) * frame.element_size()

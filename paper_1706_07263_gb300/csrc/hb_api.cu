@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -1003,6 +1004,37 @@ hb_status ensure_mlp(hb_ctx* c) {
     return HB_OK;
 }
 
+// Network files (hb_mlp_save / hb_mlp_load): header, model, parameters, hash.
+constexpr unsigned char kMlpMagic[8] = {'H', 'B', 'M', 'L', 'P', 'v', '1', '\n'};
+constexpr int kMlpModelValues = 11;  // A (6), lo0, hi0, lo1, hi1, sigma_l
+constexpr size_t kMlpFileBytes = 16 + 8 * kMlpModelValues + 4 * (size_t)hb::kNParams + 4;
+
+// The model a network is trained for, in file order.
+void mlp_model(const hb_ctx* c, double (&m)[kMlpModelValues]) {
+    for (int k = 0; k < 6; ++k) m[k] = c->bp.A[k];
+    m[6] = c->bp.lo0;
+    m[7] = c->bp.hi0;
+    m[8] = c->bp.lo1;
+    m[9] = c->bp.hi1;
+    m[10] = c->sigma_l;
+}
+
+void put_le(std::vector<unsigned char>& b, uint64_t v, int bytes) {
+    for (int k = 0; k < bytes; ++k) b.push_back((unsigned char)(v >> (8 * k)));
+}
+
+uint64_t get_le(const unsigned char* q, int bytes) {
+    uint64_t v = 0;
+    for (int k = 0; k < bytes; ++k) v |= (uint64_t)q[k] << (8 * k);
+    return v;
+}
+
+uint32_t fnv1a(const unsigned char* q, size_t n) {  // 32-bit FNV-1a (Fowler, Noll, Vo)
+    uint32_t h = 2166136261u;
+    for (size_t k = 0; k < n; ++k) h = (h ^ q[k]) * 16777619u;
+    return h;
+}
+
 // Upload masters, refresh the BF16 copies, zero the Adam state.
 hb_status put_params(hb_ctx* c, const float* host) {
     const size_t np = hb::kNParams;
@@ -1062,6 +1094,65 @@ hb_status hb_mlp_get_params(hb_ctx* c, float* params_host) {
     return cudaMemcpy(params_host, c->d_mlp, sizeof(float) * hb::kNParams, cudaMemcpyDeviceToHost) == cudaSuccess
                ? HB_OK
                : HB_ERR_CUDA;
+}
+
+hb_status hb_mlp_save(hb_ctx* c, const char* path) {
+    if (!c || !path) return HB_ERR_ARG;
+    if (!c->mlp_ready) return HB_ERR_STATE;
+    std::vector<float> p(hb::kNParams);
+    hb_status st = hb_mlp_get_params(c, p.data());
+    if (st != HB_OK) return st;
+    std::vector<unsigned char> buf;
+    buf.reserve(kMlpFileBytes);
+    buf.insert(buf.end(), kMlpMagic, kMlpMagic + 8);
+    put_le(buf, (uint64_t)hb::kNParams, 4);
+    put_le(buf, 0, 4);
+    double model[kMlpModelValues];
+    mlp_model(c, model);
+    for (double v : model) {
+        uint64_t u;
+        std::memcpy(&u, &v, 8);
+        put_le(buf, u, 8);
+    }
+    for (float v : p) {
+        uint32_t u;
+        std::memcpy(&u, &v, 4);
+        put_le(buf, u, 4);
+    }
+    put_le(buf, fnv1a(buf.data(), buf.size()), 4);
+    std::FILE* f = std::fopen(path, "wb");
+    if (!f) return HB_ERR_IO;
+    const bool ok = std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    return (std::fclose(f) == 0 && ok) ? HB_OK : HB_ERR_IO;
+}
+
+hb_status hb_mlp_load(hb_ctx* c, const char* path) {
+    if (!c || !path) return HB_ERR_ARG;
+    std::FILE* f = std::fopen(path, "rb");
+    if (!f) return HB_ERR_IO;
+    std::vector<unsigned char> buf(kMlpFileBytes + 1);
+    const size_t got = std::fread(buf.data(), 1, buf.size(), f);
+    std::fclose(f);
+    if (got != kMlpFileBytes) return HB_ERR_IO;  // shorter, or longer than a network file
+    const unsigned char* q = buf.data();
+    if (std::memcmp(q, kMlpMagic, 8) != 0 || get_le(q + 8, 4) != (uint64_t)hb::kNParams || get_le(q + 12, 4) != 0 ||
+        get_le(q + kMlpFileBytes - 4, 4) != fnv1a(q, kMlpFileBytes - 4))
+        return HB_ERR_IO;
+    double model[kMlpModelValues];
+    mlp_model(c, model);
+    for (int k = 0; k < kMlpModelValues; ++k) {
+        const uint64_t u = get_le(q + 16 + 8 * k, 8);
+        double v;
+        std::memcpy(&v, &u, 8);
+        if (!(v == model[k])) return HB_ERR_STATE;
+    }
+    std::vector<float> p(hb::kNParams);
+    for (int i = 0; i < hb::kNParams; ++i) {
+        const uint32_t u = (uint32_t)get_le(q + 16 + 8 * kMlpModelValues + 4 * i, 4);
+        std::memcpy(&p[i], &u, 4);
+        if (!std::isfinite(p[i])) return HB_ERR_IO;
+    }
+    return hb_mlp_set_params(c, p.data());
 }
 
 hb_status hb_lowpass_pairs(hb_ctx* c, const void* frame_dev, size_t row_stride_bytes, float* ybar_dev,
@@ -1288,6 +1379,7 @@ const char* hb_strerror(hb_status s) {
         case HB_ERR_BUDGET: return "memory budget exceeded";
         case HB_ERR_TIMEOUT: return "timed out";
         case HB_ERR_STATE: return "invalid state";
+        case HB_ERR_IO: return "file error";
     }
     return "unknown status";
 }

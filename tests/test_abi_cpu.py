@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_strerror_names_every_status(lib):
-    for code in range(8):
+    for code in range(9):
         msg = lib.hb_strerror(code).decode()
         assert msg and msg != "unknown status"
     assert lib.hb_strerror(99).decode() == "unknown status"
@@ -82,4 +82,6 @@ def test_null_arguments_are_rejected(lib):
     assert lib.hb_launch_count(None) == 0
     assert lib.hb_server_drain(None, 0) == 1
     assert lib.hb_server_pause(None, 1) == 1
+    assert lib.hb_mlp_save(None, b"net.bin") == 1
+    assert lib.hb_mlp_load(None, b"net.bin") == 1
     lib.hb_destroy(None)

@@ -207,6 +207,66 @@ def test_learned_low_pass_in_the_debug_output(trained, shape):
             ctx.close()
 
 
+def _fnv1a(data: bytes) -> int:
+    h = 2166136261
+    for b in data:
+        h = ((h ^ b) * 16777619) & 0xFFFFFFFF
+    return h
+
+
+def test_network_file_round_trip(trained, tmp_path):
+    """hb_mlp_save / hb_mlp_load: the file has the documented layout (header, the model, the
+    parameters, an FNV-1a hash); loaded into a new context of the same model it gives the same
+    parameters and the same learned-mode frame, bit for bit.  A file cut short, one byte too
+    long, with one byte altered or with another header is refused with HB_ERR_IO and leaves
+    the network as it was; a network of another model (sigma_l) is refused with HB_ERR_STATE."""
+    ctx, wl, mix = trained["ctx"], trained["wl"], trained["mix"]
+    path = tmp_path / "net.hbmlp"
+    ctx.mlp_save(path)
+    raw = path.read_bytes()
+    n = binding.MLP_NPARAMS
+    assert len(raw) == 16 + 88 + 4 * n + 4 and raw[:8] == b"HBMLPv1\n"
+    assert int.from_bytes(raw[8:12], "little") == n and int.from_bytes(raw[12:16], "little") == 0
+    model = np.frombuffer(raw[16:104], dtype="<f8")
+    expect = list(np.asarray(mix.A, dtype=np.float64).reshape(-1)) + [GRID["lo0"], GRID["hi0"], GRID["lo1"],
+                                                                      GRID["hi1"], GRID["sigma_l"]]
+    np.testing.assert_array_equal(model, np.array(expect))
+    np.testing.assert_array_equal(np.frombuffer(raw[104:104 + 4 * n], dtype="<f4"), ctx.mlp_get_params())
+    assert int.from_bytes(raw[-4:], "little") == _fnv1a(raw[:-4])
+    frame = _frame(trained, 930)
+    with Context(mix.A, GRID, wl.levels, wl.lam, wl.W, wl.H, wl.fmt) as other:
+        with pytest.raises(HbError) as e:
+            other.mlp_save(tmp_path / "none.hbmlp")      # no network yet
+        assert e.value.status == 7
+        other.mlp_load(path)
+        np.testing.assert_array_equal(other.mlp_get_params(), ctx.mlp_get_params())
+        try:
+            for c in (ctx, other):
+                c.set_lowpass_mode(binding.HB_MODE_MLP, float("inf"), 256)
+            a, b = _run(ctx, frame), _run(other, frame)
+        finally:
+            ctx.set_lowpass_mode(binding.HB_MODE_BAYES)
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+        before = other.mlp_get_params()
+        flipped = bytearray(raw)
+        flipped[200] ^= 0x10
+        bad = {"short": raw[:-1], "long": raw + b"\0", "flipped": bytes(flipped), "header": b"X" + raw[1:]}
+        for name, data in bad.items():
+            q = tmp_path / f"{name}.hbmlp"
+            q.write_bytes(data)
+            with pytest.raises(HbError) as e:
+                other.mlp_load(q)
+            assert e.value.status == 8, name
+        with pytest.raises(HbError) as e:
+            other.mlp_load(tmp_path / "missing.hbmlp")
+        assert e.value.status == 8
+        np.testing.assert_array_equal(other.mlp_get_params(), before)
+    with Context(mix.A, dict(GRID, sigma_l=0.03), wl.levels, wl.lam, wl.W, wl.H, wl.fmt) as third:
+        with pytest.raises(HbError) as e:
+            third.mlp_load(path)
+        assert e.value.status == 7
+
+
 def test_asynchronous_host_calls_in_learned_mode(trained):
     """hb_estimate_host_async with the learned low pass (one whole-frame band per call, frames
     overlapping): with a working network each frame equals the device call bit for bit; with a

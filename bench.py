@@ -181,9 +181,18 @@ def cpu_oracle_sample(budget_s: float, keep=None):
             break
     if keep is not None:
         keep["thb"], keep["so2"] = out["thb"], out["so2"]
+    # one thread, on a band of whole superblock rows (independent of the rest of the frame,
+    # so its time scales with its share of the rows)
+    rows = min(wl.H, 16 << wl.levels)
+    t1 = time.perf_counter()
+    oracle.estimate(np.ascontiguousarray(fr.rgb[:rows]), mix.A, grid, wl.levels, wl.lam, nthreads=1)
+    el1 = time.perf_counter() - t1
     return {"value": frames / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{frames} whole {wl.W}x{wl.H} u8 frame(s) in {el:.1f} s, FP64 C oracle, "
-                      f"{cores} threads over low-pass pixels"}
+                      f"{cores} threads over low-pass pixels",
+            "single_thread": {"value": rows / wl.H / el1, "unit": UNIT, "cores": 1,
+                              "sample": f"rows 0-{rows - 1} of the frame ({rows >> wl.levels} superblock rows) in "
+                                        f"{el1:.2f} s on one thread, scaled by {wl.H}/{rows}"}}
 
 
 def errors(thb, so2, ref_thb, ref_so2):

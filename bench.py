@@ -38,7 +38,7 @@ UNIT = "frames/s"
 # DRAM traffic of one posterior launch on this workload from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/posterior_kernel_frame1080p_u8_l3_g128.md),
 # valid only while the kernel's sources hash to the value recorded with it.
-POSTERIOR_TRAFFIC = {"bytes": 539392, "warp_instructions": 12425078, "sources_sha256_16": "e7df03eeedd52cbb",
+POSTERIOR_TRAFFIC = {"bytes": 539392, "warp_instructions": 12425078, "sources_sha256_16": "4b7a3e5a88a7e6c9",
                      "sources": ("paper_1706_07263_gb300/csrc/hb_bayes.cu", "paper_1706_07263_gb300/csrc/hb_common.cuh",
                                  "paper_1706_07263_gb300/csrc/hb_device.cuh",
                                  "paper_1706_07263_gb300/csrc/hb_posterior.cuh")}

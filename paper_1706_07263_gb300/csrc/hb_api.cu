@@ -392,8 +392,11 @@ struct Band {
 
 Band whole_frame(const hb_ctx* c) { return Band{c->tp, 0, c->npix_ll}; }
 
+// chain: the frame is already on the device and the analysis may be launched as a
+// programmatic dependent of whatever kernel precedes it on the stream (it waits for that
+// kernel before reading); host bands, whose analysis follows a copy, pass false.
 hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, double* ybar, float* out0, float* out1,
-                   float2* conc_scaled, int debug, cudaStream_t s) {
+                   float2* conc_scaled, int debug, cudaStream_t s, bool chain = false) {
     cudaError_t e = cudaSuccess;
     // the low pass: the grid posterior (possibly through the learned stand-in), least squares
     // (written by the analysis itself), or nothing separate (Tikhonov on every band)
@@ -415,7 +418,7 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
                 lso.scale = scale;
             }
             e = hb::launch_analysis(b.tp, c->bp, frame, stride, c->d_lut, ybar, rec, s,
-                                    mlp ? c->d_ybar_f + 3 * b.ll_off : nullptr, lso);
+                                    mlp ? c->d_ybar_f + 3 * b.ll_off : nullptr, lso, pdl && chain);
             c->launches++;
         }
         if (e != cudaSuccess) return HB_ERR_CUDA;
@@ -454,7 +457,7 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
 
 hb_status run_frame(hb_ctx* c, const void* frame, size_t stride, double* ybar, float* out0, float* out1,
                     float2* conc_scaled, int debug, cudaStream_t s) {
-    return run_band(c, whole_frame(c), frame, stride, ybar, out0, out1, conc_scaled, debug, s);
+    return run_band(c, whole_frame(c), frame, stride, ybar, out0, out1, conc_scaled, debug, s, true);
 }
 
 }  // namespace

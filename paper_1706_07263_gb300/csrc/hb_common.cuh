@@ -113,10 +113,10 @@ struct FrameJob {
 };
 constexpr int kMaxBatchJobs = 64;
 
-// Launch wrappers (defined in the .cu files).  All return the launch status.
+// Launch wrappers (defined in the .cu files).  All return the launch status; pdl: PDL launch.
 cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
                             const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f = nullptr,
-                            const LsOut& ls = LsOut{});
+                            const LsOut& ls = LsOut{}, bool pdl = false);
 cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s);
 // Optional gate of the posterior launch: when run is set the kernel does nothing unless
 // *run is non-zero (the decision the learned stand-in's sampled check leaves behind).

@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(kThreads) analysis_kernel(TransformParams tp, 
     const int TH = 1 << tp.levels, TW = tp.tile_w;
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
     TileSmem sm = carve(smem, TH, TW, tp.fmt);
+    asm volatile("griddepcontrol.wait;" ::: "memory");  // as in analysis_warp_kernel
     load_tile(tp, frame, stride, ty0, tx0, TH, TW, lut, sm);
     __syncthreads();
     offset_log(tp, sm, TH, TW);
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(kThreads) synthesis_kernel(TransformParams tp,
                                                              size_t stride, const float2* __restrict__ lut,
                                                              const float2* __restrict__ chat, float* __restrict__ out0,
                                                              float* __restrict__ out1, int debug_conc) {
+    asm volatile("griddepcontrol.launch_dependents;");  // as in synthesis_warp_kernel
     extern __shared__ __align__(16) unsigned char smem[];
     const int TH = 1 << tp.levels, TW = tp.tile_w;
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
@@ -489,6 +491,9 @@ __global__ void __launch_bounds__(kThreads) analysis_warp_kernel(TransformParams
                                                                  BayesRec* __restrict__ rec,
                                                                  float* __restrict__ ybar_f, LsOut ls) {
     __shared__ float sb_hi[kThreads][3], sb_lo[kThreads][3];
+    // launched as a programmatic dependent of the preceding kernel (the previous frame's
+    // synthesis, or whatever wrote the frame): wait for it before reading anything
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     analysis_tile<L>(tp, bp, frame, stride, lut_g, blockIdx.x, blockIdx.y, ybar, rec, ybar_f, sb_hi, sb_lo, ls);
     // the posterior kernel may be scheduled now; it waits for this grid before reading rec
     asm volatile("griddepcontrol.launch_dependents;");
@@ -564,6 +569,9 @@ __global__ void __launch_bounds__(kThreads) synthesis_warp_kernel(TransformParam
                                                                   const float2* __restrict__ chat,
                                                                   float* __restrict__ out0, float* __restrict__ out1,
                                                                   int debug_conc) {
+    // the next frame's analysis may be scheduled as CTAs of this grid retire; it waits for
+    // this grid before reading anything
+    asm volatile("griddepcontrol.launch_dependents;");
     synthesis_tile<L>(tp, frame, stride, lut_g, chat, out0, out1, debug_conc, blockIdx.x, blockIdx.y);
 }
 
@@ -586,38 +594,10 @@ static dim3 tile_grid(const TransformParams& tp) {
     return dim3((Wp + tp.tile_w - 1) / tp.tile_w, tp.hl);
 }
 
-cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
-                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f,
-                            const LsOut& ls) {
-    const unsigned char* f = static_cast<const unsigned char*>(frame);
-    if (tp.levels <= 4) {
-        const int TH = 1 << tp.levels;
-        const dim3 grid((tp.wl * TH + kThreads - 1) / kThreads, tp.hl);
-        switch (tp.levels) {
-            case 0: analysis_warp_kernel<0><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls); break;
-            case 1: analysis_warp_kernel<1><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls); break;
-            case 2: analysis_warp_kernel<2><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls); break;
-            case 3: analysis_warp_kernel<3><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls); break;
-            default: analysis_warp_kernel<4><<<grid, kThreads, 0, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls); break;
-        }
-        return cudaGetLastError();
-    }
-    const size_t sm = transform_smem_bytes(tp);
-    cudaError_t e = set_smem(analysis_kernel, sm);
-    if (e != cudaSuccess) return e;
-    analysis_kernel<<<tile_grid(tp), kThreads, sm, s>>>(tp, bp, f, stride, lut, ybar, rec, ybar_f, ls);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s) {
-    if (npix <= 0) return cudaSuccess;
-    setup_kernel<<<(unsigned)((npix + kThreads - 1) / kThreads), kThreads, 0, s>>>(bp, ybar, npix, rec);
-    return cudaGetLastError();
-}
-
 // Launch with or without programmatic dependent launch (PDL): with it, CTAs of this
-// kernel may start while the preceding kernel on the stream is still running; they do
-// all posterior-independent work and then wait (griddepcontrol.wait) for that kernel.
+// kernel may start once every CTA of the preceding kernel on the stream has started (or
+// asked for it, griddepcontrol.launch_dependents); they wait (griddepcontrol.wait) for that
+// kernel to finish before touching what it wrote.
 template <typename... Args>
 static cudaError_t launch_maybe_pdl(void (*kernel)(Args...), dim3 grid, size_t smem, cudaStream_t s, bool pdl,
                                     Args... args) {
@@ -632,6 +612,35 @@ static cudaError_t launch_maybe_pdl(void (*kernel)(Args...), dim3 grid, size_t s
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
+                            const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f,
+                            const LsOut& ls, bool pdl) {
+    const unsigned char* f = static_cast<const unsigned char*>(frame);
+    if (tp.levels <= 4) {
+        const int TH = 1 << tp.levels;
+        const dim3 grid((tp.wl * TH + kThreads - 1) / kThreads, tp.hl);
+#define HB_AN_ARGS grid, 0, s, pdl, tp, bp, f, stride, lut, ybar, rec, ybar_f, ls
+        switch (tp.levels) {
+            case 0: return launch_maybe_pdl(analysis_warp_kernel<0>, HB_AN_ARGS);
+            case 1: return launch_maybe_pdl(analysis_warp_kernel<1>, HB_AN_ARGS);
+            case 2: return launch_maybe_pdl(analysis_warp_kernel<2>, HB_AN_ARGS);
+            case 3: return launch_maybe_pdl(analysis_warp_kernel<3>, HB_AN_ARGS);
+            default: return launch_maybe_pdl(analysis_warp_kernel<4>, HB_AN_ARGS);
+        }
+#undef HB_AN_ARGS
+    }
+    const size_t sm = transform_smem_bytes(tp);
+    cudaError_t e = set_smem(analysis_kernel, sm);
+    if (e != cudaSuccess) return e;
+    return launch_maybe_pdl(analysis_kernel, tile_grid(tp), sm, s, pdl, tp, bp, f, stride, lut, ybar, rec, ybar_f, ls);
+}
+
+cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s) {
+    if (npix <= 0) return cudaSuccess;
+    setup_kernel<<<(unsigned)((npix + kThreads - 1) / kThreads), kThreads, 0, s>>>(bp, ybar, npix, rec);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_t stride, const float2* lut,

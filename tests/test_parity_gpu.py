@@ -445,3 +445,36 @@ def test_bad_stride_and_cpu_tensor_are_rejected():
             ctx.estimate(frame, thb, thb.clone(), row_stride_bytes=16 * 3 * 4 - 4)
         with pytest.raises(ValueError):
             ctx.estimate(torch.from_numpy(rgb), thb, thb.clone())
+
+
+@pytest.mark.parametrize("mode", ["bayes", "ls", "mlp", "tikhonov"])
+def test_frames_back_to_back_match_single_calls(mode):
+    """Frames enqueued back to back on one stream -- each written into the same input buffer
+    by a torch kernel just before the call, each frame's analysis launched as a programmatic
+    dependent of the kernel before it -- give the THb/SO2 of one synchronised call per frame,
+    bit for bit, in every low-pass mode."""
+    mix = synth.make_mixing(3)
+    H, W = 270, 480
+    frames = [torch.from_numpy(synth.make_frame(300 + k, H, W, mix.A, 8, 5.0, 40.0, 0.01, "u8").rgb).to(DEV)
+              for k in range(4)]
+    flags = {"bayes": 0, "ls": binding.HB_LOWPASS_LS, "mlp": 0, "tikhonov": binding.HB_LOWPASS_TIKHONOV}[mode]
+    with Context(mix.A, _grid(128, 128), 3, 1e-3, W, H, "u8", flags) as ctx:
+        if mode == "mlp":
+            ctx.mlp_init(1)
+            ctx.set_lowpass_mode(binding.HB_MODE_MLP, float("inf"), 64)
+        ref = []
+        for f in frames:
+            thb = torch.empty((H, W), dtype=torch.float32, device=DEV)
+            so2 = torch.empty_like(thb)
+            ctx.estimate(f, thb, so2)
+            torch.cuda.synchronize()
+            ref.append((thb, so2))
+        buf = torch.empty_like(frames[0])
+        outs = [(torch.empty((H, W), dtype=torch.float32, device=DEV),
+                 torch.empty((H, W), dtype=torch.float32, device=DEV)) for _ in range(8)]
+        for r in range(8):
+            torch.add(frames[r % 4], 0, out=buf)   # a kernel writes the next frame in place
+            ctx.estimate(buf, *outs[r])
+        torch.cuda.synchronize()
+        for r in range(8):
+            assert torch.equal(outs[r][0], ref[r % 4][0]) and torch.equal(outs[r][1], ref[r % 4][1]), r

@@ -253,7 +253,7 @@ hb_status hb_mlp_forward(hb_ctx *ctx, const float *ybar_dev, long n, float *conc
 
 /* Low-pass mode of hb_estimate.  HB_MODE_MLP: the network replaces the posterior; on
  * every frame the exact posterior is also evaluated on nsample seeded low-pass pixels
- * (nsample >= 1), and if the mean of their errors exceeds tol -- a pixel's error being
+ * (1 <= nsample <= 2^24, else HB_ERR_ARG), and if the mean of their errors exceeds tol -- a pixel's error being
  * the larger of |dHbO2| / (hi0 - lo0) and |dHb| / (hi1 - lo1) -- the whole low pass of
  * that frame is recomputed exactly (all on the device, no host round trip). */
 hb_status hb_set_lowpass_mode(hb_ctx *ctx, int mode, double tol, int nsample);

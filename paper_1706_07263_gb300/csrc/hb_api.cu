@@ -1007,6 +1007,8 @@ hb_status ensure_mlp(hb_ctx* c) {
     return HB_OK;
 }
 
+constexpr int kMlpMaxSample = 1 << 24;  // drawn pixels per frame of the learned mode's check
+
 // Network files (hb_mlp_save / hb_mlp_load): header, model, parameters, hash.
 constexpr unsigned char kMlpMagic[8] = {'H', 'B', 'M', 'L', 'P', 'v', '1', '\n'};
 constexpr int kMlpModelValues = 11;  // A (6), lo0, hi0, lo1, hi1, sigma_l
@@ -1260,7 +1262,7 @@ hb_status hb_set_lowpass_mode(hb_ctx* c, int mode, double tol, int nsample) {
         if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     }
     if (mode == HB_MODE_MLP) {
-        if (!(tol >= 0.0) || nsample < 1) return HB_ERR_ARG;
+        if (!(tol >= 0.0) || nsample < 1 || nsample > kMlpMaxSample) return HB_ERR_ARG;
         if (!c->mlp_ready) return HB_ERR_STATE;
         if (c->flags & (HB_LOWPASS_TIKHONOV | HB_LOWPASS_LS | HB_ILLUMINATION | HB_LOWPASS_INTENSITY))
             return HB_ERR_STATE;

@@ -341,3 +341,9 @@ def test_mode_requires_a_network():
     with Context(A, GRID, 3, 1e-3, 64, 64, "u8") as ctx:
         with pytest.raises(HbError):
             ctx.set_lowpass_mode(binding.HB_MODE_MLP, 1e-3, 16)
+        ctx.mlp_init(1)
+        for tol, nsample in ((1e-3, 0), (1e-3, (1 << 24) + 1), (-1.0, 16), (float("nan"), 16)):
+            with pytest.raises(HbError) as e:
+                ctx.set_lowpass_mode(binding.HB_MODE_MLP, tol, nsample)
+            assert e.value.status == 1, (tol, nsample)
+        ctx.set_lowpass_mode(binding.HB_MODE_MLP, 1e-3, 1 << 24)

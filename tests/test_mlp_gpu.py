@@ -1,7 +1,5 @@
 """The learned low-pass stand-in on the GPU: forward and gradient parity with the FP64
 reference (oracle/mlp.py), training, and the per-frame fallback to the exact posterior."""
-import time
-
 import numpy as np
 import pytest
 

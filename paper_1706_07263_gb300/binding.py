@@ -144,6 +144,16 @@ def _dev_ptr(t, what):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _host_ptr(a):
+    """Address of a host buffer: a CPU tensor (pinned for speed) or a NumPy array."""
+    return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+
+
+def _host_row_stride(frame) -> int:
+    """Bytes between rows of an HWC host frame (NumPy array or CPU tensor)."""
+    return frame.strides[0] if isinstance(frame, np.ndarray) else frame.stride(0) * frame.element_size()
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -206,20 +216,14 @@ class Context:
 
     def estimate_host(self, frame: np.ndarray, thb: np.ndarray, so2: np.ndarray, stream=None):
         """Host buffers in and out (NumPy or pinned CPU tensors)."""
-        def hp(a):
-            return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
-        stride = frame.strides[0] if isinstance(frame, np.ndarray) else frame.stride(0) * frame.element_size()
-        _check(load().hb_estimate_host(self._h, hp(frame), stride, hp(thb), hp(so2), _stream(stream)),
-               "hb_estimate_host")
+        _check(load().hb_estimate_host(self._h, _host_ptr(frame), _host_row_stride(frame), _host_ptr(thb),
+                                       _host_ptr(so2), _stream(stream)), "hb_estimate_host")
 
     def estimate_host_async(self, frame, thb, so2, stream=None):
         """As estimate_host, returning before the results arrive: they are in thb/so2 once
         `stream` has been synchronised; the buffers must stay alive and untouched until then."""
-        def hp(a):
-            return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
-        stride = frame.strides[0] if isinstance(frame, np.ndarray) else frame.stride(0) * frame.element_size()
-        _check(load().hb_estimate_host_async(self._h, hp(frame), stride, hp(thb), hp(so2), _stream(stream)),
-               "hb_estimate_host_async")
+        _check(load().hb_estimate_host_async(self._h, _host_ptr(frame), _host_row_stride(frame), _host_ptr(thb),
+                                             _host_ptr(so2), _stream(stream)), "hb_estimate_host_async")
 
     def estimate_debug(self, frame, ybar=None, conc=None, hbo2=None, hb=None, stream=None):
         stride = frame.stride(0) * frame.element_size()

@@ -85,3 +85,18 @@ def test_null_arguments_are_rejected(lib):
     assert lib.hb_mlp_save(None, b"net.bin") == 1
     assert lib.hb_mlp_load(None, b"net.bin") == 1
     lib.hb_destroy(None)
+
+
+def test_host_buffer_helpers():
+    """Addresses and row strides of host frames as the host entry points pass them: NumPy
+    arrays and CPU tensors, contiguous or a row slice of a wider frame."""
+    torch = pytest.importorskip("torch")
+    a = np.zeros((6, 10, 3), dtype=np.uint8)
+    assert binding._host_ptr(a).value == a.ctypes.data
+    assert binding._host_row_stride(a) == 30
+    sub = a[:, 2:7]
+    assert binding._host_row_stride(sub) == 30 and binding._host_ptr(sub).value == a.ctypes.data + 6
+    t = torch.zeros((4, 5, 3), dtype=torch.float32)
+    assert binding._host_ptr(t).value == t.data_ptr()
+    assert binding._host_row_stride(t) == 5 * 3 * 4
+    assert binding._host_row_stride(t[:, 1:4]) == 60

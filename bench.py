@@ -35,16 +35,23 @@ import numpy as np  # noqa: E402
 
 METRIC = "1080p frames/s and p99 frame latency (THb+SO2) vs plain pipeline, same GB300, <=1e-4 rel err"
 UNIT = "frames/s"
-# DRAM traffic of one posterior launch on this workload from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/posterior_kernel_frame1080p_u8_l3_g128.md),
-# valid only while the kernel's sources hash to the value recorded with it.
+# DRAM traffic and warp instructions of one posterior launch on this workload, from an ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, smsp__inst_executed.sum); valid only
+# while the kernel's sources hash to the value recorded with them.
 POSTERIOR_TRAFFIC = {"bytes": 539392, "warp_instructions": 12425078, "sources_sha256_16": "4b7a3e5a88a7e6c9",
                      "sources": ("paper_1706_07263_gb300/csrc/hb_bayes.cu", "paper_1706_07263_gb300/csrc/hb_common.cuh",
                                  "paper_1706_07263_gb300/csrc/hb_device.cuh",
                                  "paper_1706_07263_gb300/csrc/hb_posterior.cuh")}
-SM_COUNT = 152
-EX2_PER_CLK_PER_SM = 32          # MUFU ex2 lanes per clock per SM on GB300
-SM_MAX_MHZ = 2070.0
+SCHEDULERS_PER_SM = 4            # warp schedulers per SM, one instruction issued per clock each
+
+
+def measured_peaks():
+    """The driver's measured peaks of this machine (copy bandwidth, bf16 GEMM, clocks), if present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def posterior_traffic(key="bytes"):
@@ -58,14 +65,14 @@ def posterior_traffic(key="bytes"):
     return POSTERIOR_TRAFFIC[key] if h.hexdigest()[:16] == POSTERIOR_TRAFFIC["sources_sha256_16"] else None
 
 
-def issue_roofline(launch_s):
+def issue_roofline(launch_s, sms, sm_mhz):
     """The posterior's instruction issue against the SMs' issue rate (one warp-instruction per
-    clock per scheduler, 4 schedulers per SM): the resource that binds it now that it skips
-    the nodes whose weights are zero.  Instructions per launch come from the ncu capture."""
+    clock per scheduler, 4 schedulers per SM).  Instructions per launch come from the ncu
+    capture."""
     inst = posterior_traffic("warp_instructions")
     if inst is None:
         return None
-    peak = SM_COUNT * 4 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = sms * SCHEDULERS_PER_SM * sm_mhz * 1e6 / 1e12
     achieved = inst / launch_s / 1e12
     return {"warp_instructions_per_launch": inst, "achieved": achieved, "peak": peak, "unit": "Twarp-inst/s",
             "frac": achieved / peak, "note": "ncu smsp__inst_executed.sum of one launch over the live launch time"}
@@ -87,6 +94,7 @@ def parse():
     ap.add_argument("--stereo-frames", type=int, default=300)
     ap.add_argument("--stereo-pool", type=int, default=6)
     ap.add_argument("--pulse-frames", type=int, default=300)
+    ap.add_argument("--latency-frames", type=int, default=2000, help="single-frame calls of the latency leg")
     return ap.parse_args()
 
 
@@ -534,6 +542,35 @@ def measure_stereo(args, dev):
             "synthesis_pass_gb_per_s": (fbytes + wl.H * wl.W * 8) / (s_ms * 1e-3) / 1e9}
 
 
+def bench_config(wl, world, l2):
+    """The `config` object of both arms' JSON lines (same keys and values)."""
+    return {"workload": wl.name, "width": wl.W, "height": wl.H, "levels": wl.levels, "grid": list(wl.grid),
+            "sigma_l": wl.sigma_l, "lambda": wl.lam, "input": "u8 HWC", "frames_per_rank_per_step": 1,
+            "l2": l2, "parallelism": f"replicas x{world}"}
+
+
+def measure_latency(ctx, frame, thb, so2, flush, stream, n):
+    """Per-frame latency of the plain path: n single-frame calls, each after the L2 flush,
+    bracketed by CUDA events on the launch stream.  Quantiles over all n, and the spread of
+    the per-block medians over 4 blocks of n/4 frames (run-to-run noise)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        ctx.estimate(frame, thb, so2, stream=stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = np.array([a.elapsed_time(b) for a, b in ev])
+    v = np.sort(ms)
+    q = lambda f: float(v[min(v.size - 1, int(round(f * (v.size - 1))))])  # noqa: E731
+    blocks = [float(np.median(x)) for x in np.array_split(ms, 4)]
+    return {"frames": int(n), "p50": q(0.5), "p99": q(0.99), "p99_9": q(0.999), "max": float(v[-1]),
+            "mean": float(ms.mean()),
+            "noise": {"block_medians_ms": blocks, "spread_rel": (max(blocks) - min(blocks)) / float(np.median(ms))},
+            "how": f"{n} single-frame calls, 256 MiB L2 flush before each, CUDA events on the launch stream"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -544,8 +581,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": wl.name, "width": wl.W, "height": wl.H, "levels": wl.levels,
-                       "grid": list(wl.grid), "input": wl.fmt, "l2": "n/a (host)"},
+            "config": bench_config(wl, 1, "n/a (host)"),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -554,7 +590,7 @@ def run_reference(args):
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_1706_07263_gb300 import Context, build, replicas, synth
+    from paper_1706_07263_gb300 import Context, binding, build, replicas, synth
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -642,41 +678,55 @@ def run_ours(args):
     barrier()
     e2e_s, e2e_frames = replicas.aggregate(time.perf_counter() - t0, args.steps, device=dev)
 
-    # roofline of the dominant kernel (grid posterior): algorithmic work = every grid node of
-    # every low-pass pixel, one ex2 each; the kernel enumerates only the 16-column segments of
-    # each grid row that meet the row's interval of non-zero FP32 weights (its own counter),
-    # which changes the work and not the result
+    # roofline of the dominant kernel (grid posterior), bound by the MUFU ex2 pipe and issue:
+    # achieved = the grid nodes the kernel evaluates (its own counter), one ex2 each, over its
+    # launch time; peak = SMs x the ex2 rate per SM clock measured in this process x the SM
+    # clock limit.  The kernel leaves out the nodes below 2^-cut of the reference weight (less
+    # than 2^-30 of the posterior mass together); the whole grid's count is reported beside
+    # the fraction as a grid-equivalent throughput.
     post_ms, post_n = stage["lowpass"]
     post_avg_s = post_ms / max(post_n, 1) * 1e-3
     nodes_grid = hl * wl_ * wl.grid[0] * wl.grid[1]
     nodes = nodes_enumerated / max(post_n, 1)
-    achieved = nodes_grid / post_avg_s / 1e12
-    peak = SM_COUNT * EX2_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    stages = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1]} for k, v in stage.items()
-              if v[1]}
-    q = sorted(step_ms)
+    ex2_clk, sms = binding.measure_ex2_rate()
+    sm_mhz = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    peak = sms * ex2_clk * sm_mhz * 1e6 / 1e12
+    achieved = nodes / post_avg_s / 1e12
+    hbm = measured_peaks().get("hbm_gbs")
+    npix_ll = hl * wl_
+    stage_bytes = {"analysis": H * W * 3 + npix_ll * 16, "lowpass": npix_ll * (16 + 8),
+                   "synthesis": H * W * 3 + npix_ll * 8 + H * W * 8}
+    stages = {}
+    for k, v in stage.items():
+        if not v[1]:
+            continue
+        t = v[0] / v[1]
+        stages[k] = {"ms_per_launch": t, "launches": v[1], "algorithmic_bytes": stage_bytes[k],
+                     "gb_per_s": stage_bytes[k] / (t * 1e-3) / 1e9}
+        if hbm:
+            stages[k]["frac_of_hbm"] = stages[k]["gb_per_s"] / hbm
+    latency = measure_latency(ctx, frame, thb, so2, flush, stream, args.latency_frames)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl.name, "width": W, "height": H, "levels": wl.levels, "grid": list(wl.grid),
-                   "sigma_l": wl.sigma_l, "lambda": wl.lam, "input": "u8 HWC", "frames_per_rank_per_step": 1,
-                   "l2": "256 MiB buffer rewritten between timed steps", "parallelism": f"replicas x{world}"},
-        "latency_ms": {"p50": q[len(q) // 2], "p99": q[min(len(q) - 1, int(round(0.99 * (len(q) - 1))))],
-                       "max": q[-1]},
+        "config": bench_config(wl, world, "256 MiB buffer rewritten between timed steps"),
+        "latency_ms": latency,
         "megapixels_per_s": value * W * H / 1e6,
         "stages": stages,
-        "roofline": {"bound": "alu", "kernel": "posterior (grid posterior mean, one MUFU ex2 per grid node)",
-                     "achieved": achieved, "peak": peak, "unit": "Texp/s", "frac": achieved / peak,
-                     "units": "grid nodes of every low-pass pixel (32,400 x 16,384 per frame), one ex2 each",
-                     "enumerated": {"nodes_per_launch": nodes, "share_of_grid": nodes / nodes_grid,
-                                    "achieved": nodes / post_avg_s / 1e12, "frac": nodes / post_avg_s / 1e12 / peak,
-                                    "note": "nodes the kernel evaluates: per grid row, the 16-column segments meeting "
-                                            "the row's interval of non-zero FP32 weights"},
+        "roofline": {"bound": "alu", "kernel": "posterior (grid posterior mean, one MUFU ex2 per evaluated node)",
+                     "achieved": achieved, "peak": peak, "unit": "Tex2/s", "frac": achieved / peak,
+                     "units": f"grid nodes the kernel evaluates per launch ({nodes:.4g}: per grid row the "
+                              "16-column segments meeting the row's interval above the cut), one ex2 each",
                      "traffic": posterior_traffic(),
-                     "issue": issue_roofline(post_avg_s),
+                     "issue": issue_roofline(post_avg_s, sms, sm_mhz),
+                     "peak_method": f"{sms} SMs (device attribute) x {ex2_clk:.2f} ex2/clk/SM (hb_measure_ex2_rate, "
+                                    f"this process) x {sm_mhz:.0f} MHz (SM clock limit)",
                      "timing": "CUDA events around each posterior launch, K more steps after the timed region",
-                     "peak_note": "152 SMs x 32 ex2/clk/SM x 2070 MHz (unit count measured by probe)"},
+                     "grid_equivalent": {"nodes_per_launch": nodes_grid, "evaluated_share": nodes / nodes_grid,
+                                         "throughput": nodes_grid / post_avg_s / 1e12, "unit": "Tnode/s",
+                                         "note": "every node of the 128x128 grid for every low-pass pixel over the "
+                                                 "same launch time: a throughput, not a fraction of any peak"}},
         "e2e": {"value": e2e_frames / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W * 3,
                 "d2h_bytes_per_step": 2 * H * W * 4,
                 "api": "hb_estimate_host_async, K frames queued back to back, one synchronisation",

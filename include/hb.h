@@ -338,6 +338,14 @@ hb_status hb_server_drain(hb_server *srv, int timeout_ms);
 /* Counters of the server so far. */
 hb_status hb_server_stats(hb_server *srv, hb_server_info *out);
 
+/* Measurement helper (the paper has no counterpart): the MUFU ex2 throughput of the
+ * current device, the denominator of the grid posterior's roofline (one ex2 per grid node
+ * it evaluates).  A throughput kernel fills every SM with independent ex2 chains and reads
+ * the SMs' cycle counters around its loop, so the figure is in ex2 results per SM clock
+ * per SM, independent of the clock frequency.  Synchronous (about a millisecond of GPU
+ * time); allocates and frees a few KB of device memory.  Writes the SM count too. */
+hb_status hb_measure_ex2_rate(double *ex2_per_clock_per_sm, int *sm_count);
+
 /* Largest npix that hb_posterior_mean_static accepts. */
 #define HB_STATIC_MAX_PIXELS 65536
 
@@ -348,16 +356,21 @@ hb_status hb_server_stats(hb_server *srv, hb_server_info *out);
  * whose host application owns all device memory through its own pool, and
  * embedded deployments that must know their whole device footprint up front.
  *
- * Computes the same result as hb_posterior_mean (posterior mean of (HbO2, Hb) for
- * each of npix rows of ybar_dev, 3 doubles each, written as 2 floats each to
- * conc_dev), but takes the mixing model and grid directly instead of a context
- * and keeps its working memory in one fixed array compiled into libhb.so
- * (about 4.3 MiB per GPU, held from library load until process exit).
+ * Computes what hb_posterior_mean computes for a context created with flags 0 (any
+ * lambda: the posterior does not use it) -- the posterior mean of (HbO2, Hb) for each
+ * of npix rows of ybar_dev, 3 doubles each, written as 2 floats each to conc_dev --
+ * up to the order of FP32 additions, but takes the mixing model and grid directly
+ * instead of a context.  The flags that change the posterior (HB_ILLUMINATION,
+ * HB_FULL_GRID) have no counterpart here.  Its working memory is one fixed array
+ * compiled into libhb.so (about 4.3 MiB per GPU, held from library load until process
+ * exit).
  *   - npix > HB_STATIC_MAX_PIXELS returns HB_ERR_SHAPE and launches nothing;
  *     npix == 0 returns HB_OK; ybar_dev and conc_dev must be 8-byte aligned.
  *   - The first call on each device looks up that array's device address
  *     (cudaGetSymbolAddress, with the device current); make that first call
- *     before any stream capture starts.
+ *     before any stream capture starts.  The address is kept for the life of the
+ *     process: after a cudaDeviceReset of a device this entry point must not be
+ *     called on that device again.
  *   - Every call on a device shares the one array and leaves its contents
  *     behind; the call clears the part it needs before use.  Calls whose work
  *     overlaps on the GPU (different streams, or threads without ordering)

@@ -31,7 +31,8 @@ EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_es
             "hb_mlp_init", "hb_mlp_set_params", "hb_mlp_get_params", "hb_mlp_save", "hb_mlp_load", "hb_lowpass_pairs", "hb_mlp_train",
             "hb_mlp_gradient", "hb_mlp_forward", "hb_set_lowpass_mode", "hb_lowpass_stats",
             "hb_server_create", "hb_server_destroy", "hb_stream_open", "hb_stream_close", "hb_submit", "hb_poll",
-            "hb_release", "hb_server_pause", "hb_server_drain", "hb_server_stats", "hb_posterior_mean_static")
+            "hb_release", "hb_server_pause", "hb_server_drain", "hb_server_stats", "hb_posterior_mean_static",
+            "hb_measure_ex2_rate")
 HB_FULL_GRID = 1 << 2
 HB_ILLUMINATION = 1 << 5
 HB_LOWPASS_INTENSITY = 1 << 6
@@ -123,6 +124,7 @@ def load(path: str = LIB_PATH):
     lib.hb_server_stats.argtypes = [P, ctypes.POINTER(_ServerInfo)]
     lib.hb_server_pause.argtypes = [P, I]
     lib.hb_server_drain.argtypes = [P, I]
+    lib.hb_measure_ex2_rate.argtypes = [ctypes.POINTER(D), ctypes.POINTER(I)]
     for name in EXPORTED:
         getattr(lib, name)
     _lib = lib
@@ -134,18 +136,53 @@ def _check(rc: int, what: str):
         raise HbError(rc, what)
 
 
-def _dev_ptr(t, what):
+def _dev_ptr(t, what, dtype=None, min_numel=None, multiple=None, device=None):
+    """Device pointer of a tensor, after checking what the C side assumes of it.
+
+    dtype: the element type the entry point reads or writes ("float32", "float64", "uint8");
+    min_numel: the fewest elements it touches; multiple: the element count must divide by it;
+    device: the CUDA device index the call runs on ("current": the current device).  Violations raise ValueError before
+    anything is launched, so no kernel is ever given a buffer shorter than it assumes."""
     if t is None:
         return None
+    if dtype is not None and str(getattr(t, "dtype", "")).replace("torch.", "") != dtype:
+        raise ValueError(f"{what} must have dtype {dtype}, not {getattr(t, 'dtype', type(t).__name__)}")
+    n = int(t.numel())
+    if multiple is not None and n % multiple:
+        raise ValueError(f"{what} must hold a multiple of {multiple} elements, not {n}")
+    if min_numel is not None and n < min_numel:
+        raise ValueError(f"{what} must hold at least {min_numel} elements, not {n}")
     if not getattr(t, "is_cuda", False):
         raise ValueError(f"{what} must be a CUDA tensor")
+    if device == "current":
+        device = _current_device()
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{what} is on cuda:{t.device.index}, but the call runs on cuda:{device}")
     if not t.is_contiguous():
         raise ValueError(f"{what} must be contiguous")
     return ctypes.c_void_p(t.data_ptr())
 
 
-def _host_ptr(a):
-    """Address of a host buffer: a CPU tensor (pinned for speed) or a NumPy array."""
+def _current_device():
+    import torch
+    return torch.cuda.current_device()
+
+
+def _frame_dtype(fmt):
+    return "uint8" if fmt == "u8" else "float32"
+
+
+def _host_ptr(a, what="buffer", dtype=None, min_numel=None):
+    """Address of a host buffer: a CPU tensor (pinned for speed) or a NumPy array, after
+    checking its element type and that it holds at least min_numel elements."""
+    if getattr(a, "is_cuda", False):
+        raise ValueError(f"{what} must be in host memory")
+    if dtype is not None and str(getattr(a, "dtype", "")).replace("torch.", "") != dtype:
+        raise ValueError(f"{what} must have dtype {dtype}, not {getattr(a, 'dtype', type(a).__name__)}")
+    if min_numel is not None:
+        n = int(a.numel() if hasattr(a, "numel") and callable(a.numel) else np.asarray(a).size)
+        if n < min_numel:
+            raise ValueError(f"{what} must hold at least {min_numel} elements, not {n}")
     return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
 
 
@@ -182,6 +219,22 @@ class Context:
         _check(lib.hb_create(ctypes.byref(mix), ctypes.byref(g), levels, float(lam), width, height,
                              HB_IN_U8_HWC if fmt == "u8" else HB_IN_F32_HWC, flags, ctypes.byref(self._h)),
                "hb_create")
+        # hb_create binds the context to the current device; its calls run there
+        self.device = _current_device()
+        b = 1 << levels
+        self.npix_ll = ((height + b - 1) // b) * ((width + b - 1) // b)
+
+    def _frame(self, frame, stride, what="frame"):
+        """Pointer of a device frame after checking its type, device and extent for `stride`."""
+        es = 1 if self.fmt == "u8" else 4
+        if stride < self.width * 3 * es:
+            raise ValueError(f"row stride {stride} B is shorter than a row of {self.width} RGB pixels")
+        need = ((self.height - 1) * stride + self.width * 3 * es + es - 1) // es
+        return _dev_ptr(frame, what, _frame_dtype(self.fmt), need, device=self.device)
+
+    def _map(self, t, what):
+        """Pointer of an H x W float32 output map on the context's device."""
+        return _dev_ptr(t, what, "float32", self.width * self.height, device=self.device)
 
     @property
     def handle(self):
@@ -211,30 +264,53 @@ class Context:
 
     def estimate(self, frame, thb, so2, stream=None, row_stride_bytes=None):
         stride = row_stride_bytes if row_stride_bytes is not None else frame.stride(0) * frame.element_size()
-        _check(load().hb_estimate(self._h, _dev_ptr(frame, "frame"), stride, _dev_ptr(thb, "thb"),
-                                  _dev_ptr(so2, "so2"), _stream(stream)), "hb_estimate")
+        _check(load().hb_estimate(self._h, self._frame(frame, stride), stride, self._map(thb, "thb"),
+                                  self._map(so2, "so2"), _stream(stream)), "hb_estimate")
 
     def estimate_host(self, frame: np.ndarray, thb: np.ndarray, so2: np.ndarray, stream=None):
         """Host buffers in and out (NumPy or pinned CPU tensors)."""
-        _check(load().hb_estimate_host(self._h, _host_ptr(frame), _host_row_stride(frame), _host_ptr(thb),
-                                       _host_ptr(so2), _stream(stream)), "hb_estimate_host")
+        _check(load().hb_estimate_host(self._h, self._host_frame(frame), _host_row_stride(frame),
+                                       self._host_map(thb, "thb"), self._host_map(so2, "so2"), _stream(stream)),
+               "hb_estimate_host")
 
     def estimate_host_async(self, frame, thb, so2, stream=None):
         """As estimate_host, returning before the results arrive: they are in thb/so2 once
         `stream` has been synchronised; the buffers must stay alive and untouched until then."""
-        _check(load().hb_estimate_host_async(self._h, _host_ptr(frame), _host_row_stride(frame), _host_ptr(thb),
-                                             _host_ptr(so2), _stream(stream)), "hb_estimate_host_async")
+        _check(load().hb_estimate_host_async(self._h, self._host_frame(frame), _host_row_stride(frame),
+                                             self._host_map(thb, "thb"), self._host_map(so2, "so2"),
+                                             _stream(stream)), "hb_estimate_host_async")
+
+    def _host_frame(self, frame):
+        """Address of a host HWC frame after checking its type and the pixels within a row."""
+        p = _host_ptr(frame, "frame", _frame_dtype(self.fmt))
+        row = frame[0] if len(frame.shape) > 1 else frame
+        contiguous = row.flags["C_CONTIGUOUS"] if isinstance(row, np.ndarray) else row.is_contiguous()
+        if frame.shape[0] != self.height or not contiguous or int(np.prod(frame.shape[1:])) < 3 * self.width:
+            raise ValueError(f"frame must have {self.height} rows of at least {self.width} contiguous RGB pixels "
+                             f"(e.g. shape ({self.height}, {self.width}, 3)), not shape {tuple(frame.shape)}")
+        return p
+
+    def _host_map(self, a, what):
+        if isinstance(a, np.ndarray) and not a.flags["C_CONTIGUOUS"] or hasattr(a, "is_contiguous") and \
+                not a.is_contiguous():
+            raise ValueError(f"{what} must be contiguous")
+        return _host_ptr(a, what, "float32", self.width * self.height)
 
     def estimate_debug(self, frame, ybar=None, conc=None, hbo2=None, hb=None, stream=None):
         stride = frame.stride(0) * frame.element_size()
-        _check(load().hb_estimate_debug(self._h, _dev_ptr(frame, "frame"), stride, _dev_ptr(ybar, "ybar"),
-                                        _dev_ptr(conc, "conc"), _dev_ptr(hbo2, "hbo2"), _dev_ptr(hb, "hb"),
+        n = self.npix_ll
+        _check(load().hb_estimate_debug(self._h, self._frame(frame, stride), stride,
+                                        _dev_ptr(ybar, "ybar", "float64", 3 * n, device=self.device),
+                                        _dev_ptr(conc, "conc", "float32", 2 * n, device=self.device),
+                                        self._map(hbo2, "hbo2"), self._map(hb, "hb"),
                                         _stream(stream)), "hb_estimate_debug")
 
     def posterior_mean(self, ybar, conc, stream=None):
+        """ybar: float64 (npix, 3) block means; conc: float32, at least npix x 2 values."""
+        p_y = _dev_ptr(ybar, "ybar", "float64", multiple=3, device=self.device)
         npix = ybar.numel() // 3
-        _check(load().hb_posterior_mean(self._h, _dev_ptr(ybar, "ybar"), npix, _dev_ptr(conc, "conc"),
-                                        _stream(stream)), "hb_posterior_mean")
+        p_c = _dev_ptr(conc, "conc", "float32", 2 * npix, device=self.device)
+        _check(load().hb_posterior_mean(self._h, p_y, npix, p_c, _stream(stream)), "hb_posterior_mean")
 
     # -------------------------------------------------------------- learned stand-in
     def mlp_init(self, seed: int = 0):
@@ -264,25 +340,35 @@ class Context:
 
     def lowpass_pairs(self, frame, ybar, conc, stream=None):
         stride = frame.stride(0) * frame.element_size()
-        _check(load().hb_lowpass_pairs(self._h, _dev_ptr(frame, "frame"), stride, _dev_ptr(ybar, "ybar"),
-                                       _dev_ptr(conc, "conc"), _stream(stream)), "hb_lowpass_pairs")
+        n = self.npix_ll
+        _check(load().hb_lowpass_pairs(self._h, self._frame(frame, stride), stride,
+                                       _dev_ptr(ybar, "ybar", "float32", 3 * n, device=self.device),
+                                       _dev_ptr(conc, "conc", "float32", 2 * n, device=self.device),
+                                       _stream(stream)), "hb_lowpass_pairs")
 
     def mlp_train(self, ybar, target, steps: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
                   stream=None) -> np.ndarray:
         losses = np.empty(max(steps, 1), dtype=np.float32)
-        _check(load().hb_mlp_train(self._h, _dev_ptr(ybar, "ybar"), _dev_ptr(target, "target"), ybar.numel() // 3,
-                                   steps, batch, float(lr), seed,
+        p_y = _dev_ptr(ybar, "ybar", "float32", multiple=3, device=self.device)
+        n = ybar.numel() // 3
+        p_t = _dev_ptr(target, "target", "float32", 2 * n, device=self.device)
+        _check(load().hb_mlp_train(self._h, p_y, p_t, n, steps, batch, float(lr), seed,
                                    losses.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream(stream)),
                "hb_mlp_train")
         return losses[:steps]
 
     def mlp_gradient(self, ybar, target, grad, loss, stream=None):
-        _check(load().hb_mlp_gradient(self._h, _dev_ptr(ybar, "ybar"), _dev_ptr(target, "target"),
-                                      ybar.numel() // 3, _dev_ptr(grad, "grad"), _dev_ptr(loss, "loss"),
+        p_y = _dev_ptr(ybar, "ybar", "float32", multiple=3, device=self.device)
+        n = ybar.numel() // 3
+        _check(load().hb_mlp_gradient(self._h, p_y, _dev_ptr(target, "target", "float32", 2 * n, device=self.device),
+                                      n, _dev_ptr(grad, "grad", "float32", MLP_NPARAMS, device=self.device),
+                                      _dev_ptr(loss, "loss", "float32", 1, device=self.device),
                                       _stream(stream)), "hb_mlp_gradient")
 
     def mlp_forward(self, ybar, conc, stream=None):
-        _check(load().hb_mlp_forward(self._h, _dev_ptr(ybar, "ybar"), ybar.numel() // 3, _dev_ptr(conc, "conc"),
+        p_y = _dev_ptr(ybar, "ybar", "float32", multiple=3, device=self.device)
+        n = ybar.numel() // 3
+        _check(load().hb_mlp_forward(self._h, p_y, n, _dev_ptr(conc, "conc", "float32", 2 * n, device=self.device),
                                      _stream(stream)), "hb_mlp_forward")
 
     def set_lowpass_mode(self, mode: int, tol: float = 1e-3, nsample: int = 256):
@@ -352,6 +438,9 @@ class Server:
     def submit(self, sid: int, frame: np.ndarray, tag: int = 0) -> bool:
         """Queue a frame; False when every slot of the stream is busy."""
         fr = np.ascontiguousarray(frame)
+        h, w = self.shapes.get(sid, fr.shape[:2])  # an unknown stream is the library's to refuse
+        if fr.shape != (h, w, 3) or fr.dtype != (np.uint8 if self.fmt == "u8" else np.float32):
+            raise ValueError(f"stream {sid} takes ({h}, {w}, 3) {self.fmt} frames, not {fr.shape} {fr.dtype}")
         rc = load().hb_submit(self._h, sid, ctypes.c_void_p(fr.ctypes.data), fr.strides[0], tag)
         if rc == 7:
             return False
@@ -405,6 +494,13 @@ class Server:
         self.close()
 
 
+def measure_ex2_rate():
+    """(ex2 results per SM clock per SM, SM count) of the current device (hb_measure_ex2_rate)."""
+    r, n = ctypes.c_double(), ctypes.c_int()
+    _check(load().hb_measure_ex2_rate(ctypes.byref(r), ctypes.byref(n)), "hb_measure_ex2_rate")
+    return r.value, n.value
+
+
 def strerror(status: int) -> str:
     return load().hb_strerror(status).decode()
 
@@ -426,6 +522,8 @@ def posterior_mean_static(A, grid: dict, ybar, conc, stream=None):
             mix.A[c][j] = float(A[c, j])
     g = _Grid(int(grid["n0"]), int(grid["n1"]), float(grid["lo0"]), float(grid["hi0"]), float(grid["lo1"]),
               float(grid["hi1"]), float(grid["sigma_l"]))
+    p_y = _dev_ptr(ybar, "ybar", "float64", multiple=3, device="current")
     npix = ybar.numel() // 3
-    _check(lib.hb_posterior_mean_static(ctypes.byref(mix), ctypes.byref(g), _dev_ptr(ybar, "ybar"), npix,
-                                        _dev_ptr(conc, "conc"), _stream(stream)), "hb_posterior_mean_static")
+    p_c = _dev_ptr(conc, "conc", "float32", 2 * npix, device="current")
+    _check(lib.hb_posterior_mean_static(ctypes.byref(mix), ctypes.byref(g), p_y, npix, p_c, _stream(stream)),
+           "hb_posterior_mean_static")

@@ -6,6 +6,7 @@ Tolerances (the arithmetic behind them is in the design notes):
   * block means ybar: |d| <= 2e-7 (float32 log table / logf against FP64 -log);
   * posterior means: |d| <= 2e-4 uM + 2e-6 * |c| (FP32 sums of up to 2^14 weights).
 """
+import ctypes
 import os
 
 import numpy as np
@@ -16,7 +17,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import oracle  # noqa: E402
-from paper_1706_07263_gb300 import Context, HbError, build, synth  # noqa: E402
+from paper_1706_07263_gb300 import Context, build, synth  # noqa: E402
 from paper_1706_07263_gb300 import binding  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -441,8 +442,13 @@ def test_bad_stride_and_cpu_tensor_are_rejected():
     with Context(A, _grid(8, 8), 1, 1e-3, 16, 16, "f32") as ctx:
         frame = torch.from_numpy(rgb).to(DEV)
         thb = torch.empty((16, 16), dtype=torch.float32, device=DEV)
-        with pytest.raises(HbError):
+        with pytest.raises(ValueError):   # the binding refuses it before the call
             ctx.estimate(frame, thb, thb.clone(), row_stride_bytes=16 * 3 * 4 - 4)
+        # and the library itself, called directly through the C ABI
+        so2 = thb.clone()
+        rc = binding.load().hb_estimate(ctx.handle, ctypes.c_void_p(frame.data_ptr()), 16 * 3 * 4 - 4,
+                                        ctypes.c_void_p(thb.data_ptr()), ctypes.c_void_p(so2.data_ptr()), None)
+        assert rc == 1
         with pytest.raises(ValueError):
             ctx.estimate(torch.from_numpy(rgb), thb, thb.clone())
 

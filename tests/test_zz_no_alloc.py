@@ -46,6 +46,29 @@ def test_static_posterior_matches_context_path_twice():
             assert np.all(np.abs(g - r) <= tol), f"call npix={npix}: max diff {np.abs(g - r).max():.3e}"
 
 
+@pytest.mark.parametrize("shape,npix", [((128, 128), 300), ((96, 200), 20000), ((96, 200), 250)])
+def test_static_posterior_split_pixels_and_wide_grids_match_twice(shape, npix):
+    """The kernels that use the array's partial-sum and arrival-counter regions: a few hundred
+    pixels (fewer than the resident warps, so each pixel's rows are split into parts whose
+    last arrival adds them up) and a grid wider than the two-pixel kernels take (one pixel
+    per warp).  Two calls in a row, each against the context path."""
+    build.build()
+    A = synth.make_mixing(19).A
+    grid = dict(n0=shape[0], n1=shape[1], lo0=0.0, hi0=150.0, lo1=0.0, hi1=100.0, sigma_l=0.02)
+    with Context(A, grid, 3, 1e-3, 64, 64, "u8") as ctx:
+        for seed in (3, 4):
+            yb = torch.from_numpy(_inputs(seed + npix, npix, A)).to(DEV)
+            ref = torch.empty((npix, 2), dtype=torch.float32, device=DEV)
+            got = torch.full((npix, 2), float("nan"), dtype=torch.float32, device=DEV)
+            ctx.posterior_mean(yb, ref)
+            binding.posterior_mean_static(A, grid, yb, got)
+            torch.cuda.synchronize()
+            r = ref.cpu().numpy().astype(np.float64)
+            g = got.cpu().numpy().astype(np.float64)
+            tol = 2e-4 + 2e-6 * np.abs(r)
+            assert np.all(np.abs(g - r) <= tol), f"seed {seed}: max diff {np.abs(g - r).max():.3e}"
+
+
 def test_static_posterior_refuses_oversize_and_launches_nothing():
     A = synth.make_mixing(18).A
     grid = dict(n0=16, n1=16, lo0=0.0, hi0=150.0, lo1=0.0, hi1=100.0, sigma_l=0.02)

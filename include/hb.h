@@ -193,14 +193,17 @@ const char *hb_strerror(hb_status s);
 /* ------------------------------------------------------------------------------------
  * Learned stand-in for the low-pass posterior (not part of the paper's method).
  * A 3 -> 64 -> 64 -> 2 multilayer perceptron with exact GELU, BF16 weights and hidden
- * activations (FP32 input) and FP32 accumulation maps a low-pass pixel's block-mean log-attenuation
- * to a correction of the box-clipped least-squares concentration (normalised by the
- * box extents); it is trained on the GPU on pairs produced by the posterior step.
+ * activations (FP32 input) and FP32 accumulation maps a low-pass pixel's block-mean
+ * log-attenuation to a correction, in posterior standard deviations, of a baseline: the
+ * least-squares concentration moved by each edge of the grid box as the mean of the
+ * Gaussian likelihood cut by that edge alone (inverse Mills ratio); it is trained on the
+ * GPU on pairs produced by the posterior step.  The grid needs at least 2 nodes and an
+ * extent on both axes (else hb_mlp_init and hb_mlp_set_params return HB_ERR_STATE).
  * Parameters (FP32 masters, HB_MLP_NPARAMS floats): W1[64][3], b1[64], W2[64][64]
  * (row = output unit), b2[64], W3[2][64], b3[2].
  * ------------------------------------------------------------------------------------ */
 #define HB_MLP_NPARAMS 4546
-enum { HB_MODE_BAYES = 0, HB_MODE_MLP = 1 };
+enum { HB_MODE_BAYES = 0, HB_MODE_MLP = 1, HB_MODE_MLP_MEAN_GATE = 2 };
 
 /* Random initialisation (Glorot-uniform from a seeded splitmix64 stream, biases 0)
  * and zeroed Adam state.  The input normalisation and the least-squares baseline are
@@ -253,14 +256,32 @@ hb_status hb_mlp_forward(hb_ctx *ctx, const float *ybar_dev, long n, float *conc
 
 /* Low-pass mode of hb_estimate.  HB_MODE_MLP: the network replaces the posterior; on
  * every frame the exact posterior is also evaluated on nsample seeded low-pass pixels
- * (1 <= nsample <= 2^24, else HB_ERR_ARG), and if the mean of their errors exceeds tol -- a pixel's error being
- * the larger of |dHbO2| / (hi0 - lo0) and |dHb| / (hi1 - lo1) -- the whole low pass of
- * that frame is recomputed exactly (all on the device, no host round trip). */
+ * (1 <= nsample <= 2^24, else HB_ERR_ARG), and if the largest of their errors exceeds tol
+ * -- a pixel's error being the larger of |dHbO2| / (hi0 - lo0) and |dHb| / (hi1 - lo1) --
+ * or any is NaN, the whole low pass of that frame is recomputed exactly (all on the
+ * device, no host round trip).  HB_MODE_MLP_MEAN_GATE: the same with the mean of the
+ * sampled errors in place of the largest (a weaker guard, kept for comparison).  After
+ * hb_mlp_certify, the pixels of cells the certification did not trust are computed by the
+ * exact posterior in every frame (and count as error 0 in the check). */
 hb_status hb_set_lowpass_mode(hb_ctx *ctx, int mode, double tol, int nsample);
 
-/* Frames estimated in HB_MODE_MLP and how many of them fell back to the exact
- * posterior (synchronises the context's device work). */
-hb_status hb_lowpass_stats(hb_ctx *ctx, long *mlp_frames, long *fallbacks);
+/* Frames estimated in a learned mode, how many of them fell back to the exact posterior,
+ * and (routed_pixels, may be NULL) how many low-pass pixels of the others the
+ * certification's route sent to the exact posterior (synchronises the context's work). */
+hb_status hb_lowpass_stats(hb_ctx *ctx, long *mlp_frames, long *fallbacks, long *routed_pixels);
+
+/* Certify the current network against the exact posterior.  Over a 128 x 128 map of cells
+ * of least-squares concentrations covering the grid box widened by 3 posterior standard
+ * deviations on every side, the network and the exact posterior step are evaluated at
+ * every cell corner and centre, each for three values (-1.5, 0, 1.5 sigma_l) of the
+ * component of ybar outside the range of A; a cell is trusted when every one of its points
+ * is within tol (error as in hb_set_lowpass_mode).  From then on the learned modes send
+ * the low-pass pixels whose least-squares point falls in an untrusted cell, or outside the
+ * map, to the exact posterior (one gated launch per frame).  Any change of the parameters
+ * (init, set, load, train) ends the certification.  trusted_fraction (may be NULL)
+ * receives the share of trusted cells.  Synchronises `stream`; allocates and frees
+ * temporary device memory (a few MB). */
+hb_status hb_mlp_certify(hb_ctx *ctx, double tol, double *trusted_fraction, void *stream);
 
 /* ------------------------------------------------------------------------------------
  * Serving: continuous batching of frames from many concurrent streams (an extension; the

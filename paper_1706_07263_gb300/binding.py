@@ -29,7 +29,7 @@ EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_es
             "hb_posterior_mean",
             "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_timing_nodes", "hb_strerror",
             "hb_mlp_init", "hb_mlp_set_params", "hb_mlp_get_params", "hb_mlp_save", "hb_mlp_load", "hb_lowpass_pairs", "hb_mlp_train",
-            "hb_mlp_gradient", "hb_mlp_forward", "hb_set_lowpass_mode", "hb_lowpass_stats",
+            "hb_mlp_gradient", "hb_mlp_forward", "hb_set_lowpass_mode", "hb_lowpass_stats", "hb_mlp_certify",
             "hb_server_create", "hb_server_destroy", "hb_stream_open", "hb_stream_close", "hb_submit", "hb_poll",
             "hb_release", "hb_server_pause", "hb_server_drain", "hb_server_stats", "hb_posterior_mean_static",
             "hb_measure_ex2_rate")
@@ -41,6 +41,7 @@ HB_SERVE_SEQUENTIAL = 1 << 4
 MLP_NPARAMS = 4546
 HB_MODE_BAYES = 0
 HB_MODE_MLP = 1
+HB_MODE_MLP_MEAN_GATE = 2
 STATIC_MAX_PIXELS = 65536
 
 
@@ -111,7 +112,8 @@ def load(path: str = LIB_PATH):
     lib.hb_mlp_gradient.argtypes = [P, P, P, L, P, P, P]
     lib.hb_mlp_forward.argtypes = [P, P, L, P, P]
     lib.hb_set_lowpass_mode.argtypes = [P, I, D, I]
-    lib.hb_lowpass_stats.argtypes = [P, ctypes.POINTER(L), ctypes.POINTER(L)]
+    lib.hb_lowpass_stats.argtypes = [P, ctypes.POINTER(L), ctypes.POINTER(L), ctypes.POINTER(L)]
+    lib.hb_mlp_certify.argtypes = [P, D, ctypes.POINTER(D), P]
     lib.hb_server_create.argtypes = [ctypes.POINTER(_Mixing), ctypes.POINTER(_Grid), D, ctypes.c_uint, I, S, I, L,
                                      ctypes.POINTER(P)]
     lib.hb_server_destroy.argtypes = [P]
@@ -375,9 +377,19 @@ class Context:
         _check(load().hb_set_lowpass_mode(self._h, mode, float(tol), nsample), "hb_set_lowpass_mode")
 
     def lowpass_stats(self):
-        f, b = ctypes.c_long(), ctypes.c_long()
-        _check(load().hb_lowpass_stats(self._h, ctypes.byref(f), ctypes.byref(b)), "hb_lowpass_stats")
-        return f.value, b.value
+        """(frames in a learned mode, frames that fell back, low-pass pixels the route sent to
+        the exact posterior in the others)."""
+        f, b, r = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
+        _check(load().hb_lowpass_stats(self._h, ctypes.byref(f), ctypes.byref(b), ctypes.byref(r)),
+               "hb_lowpass_stats")
+        return f.value, b.value, r.value
+
+    def mlp_certify(self, tol: float, stream=None) -> float:
+        """hb_mlp_certify: trust map of the current network at tolerance tol; returns the share
+        of trusted cells."""
+        frac = ctypes.c_double()
+        _check(load().hb_mlp_certify(self._h, float(tol), ctypes.byref(frac), _stream(stream)), "hb_mlp_certify")
+        return frac.value
 
     def launch_count(self) -> int:
         return int(load().hb_launch_count(self._h))

@@ -71,7 +71,12 @@ struct hb_ctx {
     float mlp_tol = 1e-3f;
     int mlp_nsample = 256;
     float* d_ybar_f = nullptr;    // block means for the network (npix_ll x 3)
-    unsigned* d_flags = nullptr;  // [0] check arrivals, [1] fallback count, [2] run the exact posterior
+    // [0] check arrivals, [1] fallback count, [2] run the exact posterior on every pixel,
+    // [4 + (frame & 1)] pixels the route listed, [6, 7] listed pixels taken (64-bit total)
+    unsigned* d_flags = nullptr;
+    int* d_route = nullptr;       // the route's list (npix_ll)
+    unsigned char* d_trust = nullptr;  // certification map (trust_k0 x trust_k1)
+    hb::MlpRoute route{};         // trust set while a certification holds for the parameters
     float* d_err = nullptr;       // per sampled pixel error of the stand-in (mlp_err_cap)
     int mlp_err_cap = 0;
     unsigned long long* d_nodes = nullptr;  // grid nodes enumerated by timed posterior launches
@@ -404,7 +409,7 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
     const bool ls = lowpass && (c->flags & HB_LOWPASS_LS);
     const bool bayes = lowpass && !ls;
     const bool pdl = !c->timing;
-    const bool mlp = bayes && c->lowpass_mode == HB_MODE_MLP;
+    const bool mlp = bayes && c->lowpass_mode != HB_MODE_BAYES;
     BayesRec* rec = c->d_rec + b.ll_off;
     float2* chat = c->d_chat + b.ll_off;
     const float scale = (float)(1 << c->levels);
@@ -430,14 +435,28 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
             // exact recomputation only if the check failed; each kernel waits for its
             // predecessor in-kernel (PDL)
             const void* img = mlp_image(c, s, e);
-            hb::MlpCheck ck{c->mlp_nsample, 0, c->frame_seq++, 1.f / c->mlp_ext0, 1.f / c->mlp_ext1, c->mlp_tol,
-                            c->d_err, c->d_flags};
+            const unsigned seq = c->frame_seq++;
+            hb::MlpCheck ck{c->mlp_nsample, 0, seq, 1.f / c->mlp_ext0, 1.f / c->mlp_ext1, c->mlp_tol,
+                            c->lowpass_mode == HB_MODE_MLP ? 1 : 0, c->d_err, c->d_flags};
+            // with a certification, the pixels of untrusted cells go to the exact posterior
+            hb::MlpRoute rt = c->route;
+            hb::PosteriorGate gate{c->d_flags + 2};
+            // every learned frame clears the next frame's counter, routed or not, so that
+            // each frame starts its list from zero
+            rt.next_count = c->d_flags + 4 + ((seq + 1u) & 1u);
+            if (rt.trust) {
+                rt.list = c->d_route + b.ll_off;
+                rt.count = c->d_flags + 4 + (seq & 1u);
+                gate.list = rt.list;
+                gate.count = rt.count;
+                gate.listed_total = reinterpret_cast<unsigned long long*>(c->d_flags + 6);
+            }
             if (img)
                 e = hb::launch_mlp_forward_check(img, c->mlp_norm, c->d_ybar_f + 3 * b.ll_off, b.npix, chat,
-                                                 conc_scaled, scale, c->bp, rec, ck, pdl, s);
+                                                 conc_scaled, scale, c->bp, rec, ck, rt, pdl, s);
             if (e == cudaSuccess)
                 e = hb::launch_posterior(c->bp, rec, b.npix, post_scratch(c, b.ll_off), chat, conc_scaled, scale, pdl,
-                                         s, hb::PosteriorGate{c->d_flags + 2});
+                                         s, gate);
             c->launches += 2;
             c->mlp_frames++;
         } else {
@@ -556,6 +575,8 @@ void hb_destroy(hb_ctx* c) {
     cudaFree(c->d_ybar_f);
     cudaFree(c->d_flags);
     cudaFree(c->d_err);
+    cudaFree(c->d_route);
+    cudaFree(c->d_trust);
     cudaFree(c->d_nodes);
     cudaFree(c->d_frame);
     cudaFree(c->d_thb);
@@ -695,7 +716,7 @@ hb_status host_prepare(hb_ctx* c, const void* frame_host, size_t row_stride_byte
     if (!alloc(c->d_frame, c->d_thb, c->d_so2) || (two_sets && !alloc(c->d_frame2, c->d_thb2, c->d_so22)))
         return HB_ERR_OOM;
     const bool bayes = !(c->flags & (HB_LOWPASS_TIKHONOV | HB_LOWPASS_LS));
-    mlp = bayes && c->lowpass_mode == HB_MODE_MLP;
+    mlp = bayes && c->lowpass_mode != HB_MODE_BAYES;
     bounds[0] = 0;
     bounds[1] = c->hl;
     nb = 1;
@@ -950,20 +971,25 @@ uint64_t splitmix64(uint64_t& x) {  // Steele, Lea and Flood's SplitMix64 output
     return z ^ (z >> 31);
 }
 
+constexpr int kMlpFlags = 8;
+
 hb_status ensure_mlp(hb_ctx* c) {
     if (c->d_mlp) return HB_OK;
+    // the baseline needs a box with an extent on both axes
+    if (c->bp.n0 < 2 || c->bp.n1 < 2 || !(c->bp.hi0 > c->bp.lo0) || !(c->bp.hi1 > c->bp.lo1)) return HB_ERR_STATE;
     const size_t np = hb::kNParams;
     if (cudaMalloc(&c->d_mlp, sizeof(float) * 5 * np) != cudaSuccess ||
         cudaMalloc(&c->d_mlp_img, hb::mlp_image_bytes()) != cudaSuccess ||
         cudaMalloc(&c->d_mlp_gpart, sizeof(float) * kMlpMaxBlocks * np) != cudaSuccess ||
         cudaMalloc(&c->d_mlp_lpart, sizeof(float) * kMlpMaxBlocks) != cudaSuccess ||
         cudaMalloc(&c->d_ybar_f, sizeof(float) * 3 * c->npix_ll) != cudaSuccess ||
-        cudaMalloc(&c->d_flags, sizeof(unsigned) * 4) != cudaSuccess) {
+        cudaMalloc(&c->d_flags, sizeof(unsigned) * kMlpFlags) != cudaSuccess ||
+        cudaMalloc(&c->d_route, sizeof(int) * c->npix_ll) != cudaSuccess) {
         cudaGetLastError();
         return HB_ERR_OOM;
     }
     if (cudaMemset(c->d_mlp, 0, sizeof(float) * 5 * np) != cudaSuccess ||
-        cudaMemset(c->d_flags, 0, sizeof(unsigned) * 4) != cudaSuccess)
+        cudaMemset(c->d_flags, 0, sizeof(unsigned) * kMlpFlags) != cudaSuccess)
         return HB_ERR_CUDA;
     // least-squares baseline, input transform and output scale (FP64 here)
     const double* A = c->bp.A;
@@ -1002,12 +1028,25 @@ hb_status ensure_mlp(hb_ctx* c) {
     nm.hi1 = (float)hi[1];
     nm.osc0 = (float)(sl * std::sqrt(Gi[0][0]));
     nm.osc1 = (float)(sl * std::sqrt(Gi[1][1]));
+    // the baseline's four edges (see MlpNorm): S = sl^2 Gi, v_e = sgn_e S[:, axis] / s_axis
+    for (int e = 0; e < 4; ++e) {
+        const int ax = e / 2;
+        const double sgn = (e & 1) ? -1.0 : 1.0, pos = (e & 1) ? -hi[ax] : lo[ax];
+        const double sa = sl * std::sqrt(Gi[ax][ax]);
+        nm.edge_sgn[e] = (float)sgn;
+        nm.edge_pos[e] = (float)pos;
+        nm.edge_inv_s[e] = (float)(1.0 / sa);
+        nm.edge_v0[e] = (float)(sgn * sl * sl * Gi[0][ax] / sa);
+        nm.edge_v1[e] = (float)(sgn * sl * sl * Gi[1][ax] / sa);
+    }
     c->mlp_ext0 = hi[0] > lo[0] ? (float)(hi[0] - lo[0]) : 1.f;
     c->mlp_ext1 = hi[1] > lo[1] ? (float)(hi[1] - lo[1]) : 1.f;
     return HB_OK;
 }
 
 constexpr int kMlpMaxSample = 1 << 24;  // drawn pixels per frame of the learned mode's check
+constexpr int kTrustCells = 128;        // certification map: cells per axis
+constexpr double kTrustPad = 3.0;       // ... over the box widened by 3 standard deviations
 
 // Network files (hb_mlp_save / hb_mlp_load): header, model, parameters, hash.
 constexpr unsigned char kMlpMagic[8] = {'H', 'B', 'M', 'L', 'P', 'v', '1', '\n'};
@@ -1053,6 +1092,7 @@ hb_status put_params(hb_ctx* c, const float* host) {
     c->adam_t = 0;
     c->mlp_ready = true;
     c->mlp_img_dirty = true;
+    c->route.trust = nullptr;  // a certification holds only for the parameters it checked
     return HB_OK;
 }
 
@@ -1209,6 +1249,7 @@ hb_status hb_mlp_train(hb_ctx* c, const float* ybar_dev, const float* target_dev
                                     m, v, wbf, (float)lr, 0.9f, 0.999f, 1e-8f, ++c->adam_t, s);
         c->launches += 2;
         c->mlp_img_dirty = true;
+        c->route.trust = nullptr;
         if (e != cudaSuccess) return HB_ERR_CUDA;
     }
     if (loss_host && steps > 0) {
@@ -1256,12 +1297,12 @@ hb_status hb_mlp_forward(hb_ctx* c, const float* ybar_dev, long n, float* conc_d
 
 hb_status hb_set_lowpass_mode(hb_ctx* c, int mode, double tol, int nsample) {
     if (!c) return HB_ERR_ARG;
-    if (mode != HB_MODE_BAYES && mode != HB_MODE_MLP) return HB_ERR_ARG;
+    if (mode != HB_MODE_BAYES && mode != HB_MODE_MLP && mode != HB_MODE_MLP_MEAN_GATE) return HB_ERR_ARG;
     {
         DeviceGuard g(c->device);
         if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     }
-    if (mode == HB_MODE_MLP) {
+    if (mode != HB_MODE_BAYES) {
         if (!(tol >= 0.0) || nsample < 1 || nsample > kMlpMaxSample) return HB_ERR_ARG;
         if (!c->mlp_ready) return HB_ERR_STATE;
         if (c->flags & (HB_LOWPASS_TIKHONOV | HB_LOWPASS_LS | HB_ILLUMINATION | HB_LOWPASS_INTENSITY))
@@ -1284,15 +1325,141 @@ hb_status hb_set_lowpass_mode(hb_ctx* c, int mode, double tol, int nsample) {
     return HB_OK;
 }
 
-hb_status hb_lowpass_stats(hb_ctx* c, long* mlp_frames, long* fallbacks) {
+hb_status hb_lowpass_stats(hb_ctx* c, long* mlp_frames, long* fallbacks, long* routed_pixels) {
     if (!c || !mlp_frames || !fallbacks) return HB_ERR_ARG;
     DeviceGuard g(c->device);
     if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
-    unsigned fb = 0;
-    if (c->d_flags && cudaMemcpy(&fb, c->d_flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return HB_ERR_CUDA;
+    unsigned f[kMlpFlags] = {0};
+    if (c->d_flags && cudaMemcpy(f, c->d_flags, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess) return HB_ERR_CUDA;
+    unsigned long long routed = 0;
+    std::memcpy(&routed, f + 6, sizeof(routed));
     *mlp_frames = c->mlp_frames;
-    *fallbacks = fb;
+    *fallbacks = f[1];
+    if (routed_pixels) *routed_pixels = (long)routed;
+    return HB_OK;
+}
+
+hb_status hb_mlp_certify(hb_ctx* c, double tol, double* trusted_fraction, void* stream) {
+    if (!c || !(tol >= 0.0)) return HB_ERR_ARG;
+    if (!c->mlp_ready) return HB_ERR_STATE;
+    DeviceGuard g(c->device);
+    if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The lattice: kTrustCells^2 cells over the box widened by kTrustPad standard deviations on
+    // every side; points at every cell corner and centre, each with three values of the
+    // component of ybar outside the range of A (-1.5, 0, 1.5 sigma_l), to which the exact
+    // posterior is blind and the network should be.
+    constexpr int K = kTrustCells;
+    const hb::MlpNorm& nm = c->mlp_norm;
+    const double sl = c->sigma_l;
+    const double osc[2] = {nm.osc0, nm.osc1};
+    const double lo[2] = {c->bp.lo0 - kTrustPad * osc[0], c->bp.lo1 - kTrustPad * osc[1]};
+    const double hi[2] = {c->bp.hi0 + kTrustPad * osc[0], c->bp.hi1 + kTrustPad * osc[1]};
+    const double cell[2] = {(hi[0] - lo[0]) / K, (hi[1] - lo[1]) / K};
+    const double* A = c->bp.A;
+    const double nx = A[2] * A[5] - A[4] * A[3], ny = A[4] * A[1] - A[0] * A[5], nz = A[0] * A[3] - A[2] * A[1];
+    const double nn = std::sqrt(nx * nx + ny * ny + nz * nz);
+    const double nrm[3] = {nx / nn, ny / nn, nz / nn};
+    const double offs[3] = {-1.5, 0.0, 1.5};
+    const long ncorner = (long)(K + 1) * (K + 1), ncentre = (long)K * K, npt = 3 * (ncorner + ncentre);
+    std::vector<double> yd(3 * npt);
+    std::vector<float> yf(3 * npt);
+    for (int o = 0; o < 3; ++o)
+        for (long q = 0; q < ncorner + ncentre; ++q) {
+            double c0, c1;
+            if (q < ncorner) {
+                c0 = lo[0] + cell[0] * (double)(q / (K + 1));
+                c1 = lo[1] + cell[1] * (double)(q % (K + 1));
+            } else {
+                const long r = q - ncorner;
+                c0 = lo[0] + cell[0] * ((double)(r / K) + 0.5);
+                c1 = lo[1] + cell[1] * ((double)(r % K) + 0.5);
+            }
+            const long i = (long)o * (ncorner + ncentre) + q;
+            for (int ch = 0; ch < 3; ++ch) {
+                yd[3 * i + ch] = A[ch * 2] * c0 + A[ch * 2 + 1] * c1 + offs[o] * sl * nrm[ch];
+                yf[3 * i + ch] = (float)yd[3 * i + ch];
+            }
+        }
+    double* d_yd = nullptr;
+    float* d_yf = nullptr;
+    float2 *d_exact = nullptr, *d_net = nullptr;
+    BayesRec* d_rec = nullptr;
+    float* d_part = nullptr;
+    unsigned* d_cnt = nullptr;
+    hb_status st = HB_OK;
+    if (cudaMalloc(&d_yd, sizeof(double) * 3 * npt) != cudaSuccess ||
+        cudaMalloc(&d_yf, sizeof(float) * 3 * npt) != cudaSuccess ||
+        cudaMalloc(&d_exact, sizeof(float2) * npt) != cudaSuccess ||
+        cudaMalloc(&d_net, sizeof(float2) * npt) != cudaSuccess ||
+        cudaMalloc(&d_rec, sizeof(BayesRec) * npt) != cudaSuccess ||
+        cudaMalloc(&d_part, sizeof(float) * 3 * hb::kMaxParts * npt) != cudaSuccess ||
+        cudaMalloc(&d_cnt, sizeof(unsigned) * npt) != cudaSuccess || (!c->d_trust &&
+        cudaMalloc(&c->d_trust, (size_t)K * K) != cudaSuccess))
+        st = HB_ERR_OOM;
+    std::vector<float2> ex(npt), net(npt);
+    cudaError_t e = cudaSuccess;
+    if (st == HB_OK) {
+        e = cudaMemcpyAsync(d_yd, yd.data(), sizeof(double) * 3 * npt, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_yf, yf.data(), sizeof(float) * 3 * npt, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned) * npt, s);
+        if (e == cudaSuccess) e = hb::launch_setup(c->bp, d_yd, npt, d_rec, s);
+        if (e == cudaSuccess)
+            e = hb::launch_posterior(c->bp, d_rec, npt, hb::PosteriorScratch{d_part, d_cnt, hb::kMaxParts}, d_exact,
+                                     nullptr, 1.f, false, s);
+        const void* img = e == cudaSuccess ? mlp_image(c, s, e) : nullptr;
+        if (img) e = hb::launch_mlp_forward(img, c->mlp_norm, d_yf, npt, d_net, false, s);
+        c->launches += 3;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ex.data(), d_exact, sizeof(float2) * npt, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(net.data(), d_net, sizeof(float2) * npt, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = HB_ERR_CUDA;
+    }
+    std::vector<unsigned char> map((size_t)K * K, 0);
+    long trusted = 0;
+    if (st == HB_OK) {
+        // error of one point relative to the box extents (NaN counts as out of tolerance)
+        auto ok = [&](long q) {
+            for (int o = 0; o < 3; ++o) {
+                const long i = (long)o * (ncorner + ncentre) + q;
+                const double d0 = std::fabs((double)net[i].x - ex[i].x) / c->mlp_ext0;
+                const double d1 = std::fabs((double)net[i].y - ex[i].y) / c->mlp_ext1;
+                if (!(d0 <= tol && d1 <= tol)) return false;
+            }
+            return true;
+        };
+        for (int i = 0; i < K; ++i)
+            for (int j = 0; j < K; ++j) {
+                const bool t = ok((long)i * (K + 1) + j) && ok((long)(i + 1) * (K + 1) + j) &&
+                               ok((long)i * (K + 1) + j + 1) && ok((long)(i + 1) * (K + 1) + j + 1) &&
+                               ok(ncorner + (long)i * K + j);
+                map[(size_t)i * K + j] = t ? 1 : 0;
+                trusted += t;
+            }
+        if (cudaMemcpyAsync(c->d_trust, map.data(), map.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            st = HB_ERR_CUDA;
+    }
+    cudaFree(d_yd);
+    cudaFree(d_yf);
+    cudaFree(d_exact);
+    cudaFree(d_net);
+    cudaFree(d_rec);
+    cudaFree(d_part);
+    cudaFree(d_cnt);
+    if (st != HB_OK) {
+        cudaGetLastError();
+        c->route.trust = nullptr;
+        return st;
+    }
+    c->route.trust = c->d_trust;
+    c->route.k0 = K;
+    c->route.k1 = K;
+    c->route.org0 = (float)lo[0];
+    c->route.org1 = (float)lo[1];
+    c->route.inv0 = (float)(1.0 / cell[0]);
+    c->route.inv1 = (float)(1.0 / cell[1]);
+    if (trusted_fraction) *trusted_fraction = (double)trusted / ((double)K * K);
     return HB_OK;
 }
 

@@ -43,6 +43,24 @@
 namespace hb {
 namespace {
 
+// The pixels a launch takes: all npix, or -- under a gate that did not fire -- the ones the
+// gate lists (none without a list); the k-th of them is pixel at(k).  Read after the
+// kernel's griddepcontrol.wait.
+struct Pixels {
+    long n;
+    const int* list;
+    __device__ __forceinline__ long at(long k) const { return list ? (long)list[k] : k; }
+};
+
+__device__ __forceinline__ Pixels gated_pixels(const PosteriorGate& g, long npix) {
+    if (!g.run || *g.run != 0u) return Pixels{npix, nullptr};
+    if (!g.list) return Pixels{0, nullptr};
+    const long c = (long)*g.count;
+    const Pixels px{c < npix ? c : npix, g.list};
+    if (g.listed_total && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(g.listed_total, (unsigned long long)px.n);
+    return px;
+}
+
 // Posterior mean from the sums, in FP32 (the output is FP32): c = c_ref + h * (sum w d / sum w).
 __device__ __forceinline__ void write_mean(const BayesParams& bp, const BayesRec& rec, long p, float sw, float sdi,
                                            float sdj, float2* chat, float2* chat_scaled, float scale) {
@@ -59,8 +77,8 @@ __device__ __forceinline__ void write_mean(const BayesParams& bp, const BayesRec
 // outside the model) is summed again over all rows with an explicit maximum shift.
 // grid_sums has a single call site so that the rare path costs the loop no registers.
 template <int CPL>
-__device__ __forceinline__ void run_unit(const BayesParams& bp, const BayesRec& rec, long p, int part, int rs,
-                                         int lane, float* partial, unsigned* count, float2* chat,
+__device__ __forceinline__ void run_unit(const BayesParams& bp, const BayesRec& rec, long p, long out, int part,
+                                         int rs, int lane, float* partial, unsigned* count, float2* chat,
                                          float2* chat_scaled, float scale, unsigned long long& nodes) {
     int lo, hi;
     support_rows(bp, rec, lo, hi);
@@ -107,7 +125,7 @@ __device__ __forceinline__ void run_unit(const BayesParams& bp, const BayesRec& 
             whole = true;
         }
         if (usable(sw, sdi, sdj) || shift != 0.f) {
-            if (lane == 0) write_mean(bp, rec, p, sw, sdi, sdj, chat, chat_scaled, scale);
+            if (lane == 0) write_mean(bp, rec, out, sw, sdi, sdj, chat, chat_scaled, scale);
             return;
         }
         rb = 0;
@@ -126,38 +144,38 @@ __global__ void HB_POST_BOUNDS(CPL) posterior_kernel(BayesParams bp, const Bayes
                                                 unsigned long long* nodes_out) {
     const int lane = threadIdx.x & 31;
     const long nw = (long)gridDim.x * (kThreads / 32);
-    const long units = npix * rs;
     long u = (long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     // launched with PDL after the kernel that writes the records (or the gate's errors):
     // wait for it, then let the next kernel be scheduled
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
-    // gated launch (fallback of the learned stand-in): run only when the sampled check
-    // before this kernel decided so
-    if (gate.run && *gate.run == 0u) return;
-    // (rs == 1 unless there are few pixels: the unit index is then the pixel index, and
-    // the 64-bit divisions below are skipped)
+    // gated launch (the learned stand-in's exact posterior): every pixel when its sampled
+    // check failed, else the pixels its route listed
+    const Pixels px = gated_pixels(gate, npix);
+    const long units = px.n * rs;
+    // (rs == 1 unless there are few pixels: the unit index is then the pixel's position, and
+    // the 64-bit divisions below are skipped; the scratch slots follow the position)
     BayesRec next = {0, 0, 0.f, 0.f};
-    if (u < units) next = recs[rs == 1 ? u : u / rs];
+    if (u < units) next = recs[px.at(rs == 1 ? u : u / rs)];
     unsigned long long nodes = 0;
     for (; u < units; u += nw) {
         const long p = rs == 1 ? u : u / rs;
         const BayesRec rec = next;
-        if (u + nw < units) next = recs[rs == 1 ? u + nw : (u + nw) / rs];
-        run_unit<CPL>(bp, rec, p, rs == 1 ? 0 : (int)(u - p * rs), rs, lane, partial, count, chat, chat_scaled, scale,
-                      nodes);
+        if (u + nw < units) next = recs[px.at(rs == 1 ? u + nw : (u + nw) / rs)];
+        run_unit<CPL>(bp, rec, p, px.at(p), rs == 1 ? 0 : (int)(u - p * rs), rs, lane, partial, count, chat,
+                      chat_scaled, scale, nodes);
     }
     if (nodes_out && lane == 0 && nodes) atomicAdd(nodes_out, nodes);
 }
 
 // One round of the two-pixel kernel below: pixel 2r + half, its sums and its mean.
 template <int CPL>
-__device__ __forceinline__ void pair_round(const BayesParams& bp, const BayesRec& rec, long r, long npix, int gl,
-                                           int half, float2* chat, float2* chat_scaled, float scale,
+__device__ __forceinline__ void pair_round(const BayesParams& bp, const BayesRec& rec, long r, const Pixels& px,
+                                           int gl, int half, float2* chat, float2* chat_scaled, float scale,
                                            unsigned long long& nodes) {
     constexpr int G = 16;
-    const long p = 2 * r + half;
-    const bool valid = p < npix;
+    const long k = 2 * r + half;
+    const bool valid = k < px.n;
     int lo, hi;
     support_rows(bp, rec, lo, hi);
     int rb = __reduce_min_sync(0xffffffffu, lo), re = __reduce_max_sync(0xffffffffu, hi);
@@ -177,7 +195,7 @@ __device__ __forceinline__ void pair_round(const BayesParams& bp, const BayesRec
         re = bp.n0;
         if (valid && bad) nodes += 2ull * (unsigned)bp.n0 * (unsigned)bp.n1;
     }
-    if (valid && gl == 0) write_mean(bp, rec, p, sw, sdi, sdj, chat, chat_scaled, scale);
+    if (valid && gl == 0) write_mean(bp, rec, px.at(k), sw, sdi, sdj, chat, chat_scaled, scale);
 }
 
 // Two pixels per warp: half-warp h (lanes 16h .. 16h+15) takes pixel 2r + h of round r, CPL
@@ -199,20 +217,20 @@ __global__ void HB_PAIR_BOUNDS posterior_pair_kernel(BayesParams bp, const Bayes
                                                      float2* __restrict__ chat, float2* __restrict__ chat_scaled,
                                                      float scale, PosteriorGate gate, unsigned long long* nodes_out) {
     const int lane = threadIdx.x & 31, gl = lane & 15, half = lane >> 4;
-    const long rounds = (npix + 1) / 2;
     __shared__ unsigned ticket;
     if (threadIdx.x == 0) ticket = 0u;
     __syncthreads();
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
-    if (gate.run && *gate.run == 0u) return;
+    const Pixels px = gated_pixels(gate, npix);
+    const long rounds = (px.n + 1) / 2;
     unsigned long long nodes = 0;
     auto next_round = [&]() {
         unsigned k = 0;
         if (lane == 0) k = atomicAdd(&ticket, 1u);
         return (long)blockIdx.x + (long)__shfl_sync(0xffffffffu, k, 0) * gridDim.x;
     };
-    auto load = [&](long r) { return recs[min(2 * r + half, npix - 1)]; };
+    auto load = [&](long r) { return recs[px.at(min(2 * r + half, px.n - 1))]; };
     long r0 = next_round();
     BayesRec rec0 = {0, 0, 0.f, 0.f};
     if (r0 < rounds) rec0 = load(r0);
@@ -220,7 +238,7 @@ __global__ void HB_PAIR_BOUNDS posterior_pair_kernel(BayesParams bp, const Bayes
         const long r1 = next_round();
         BayesRec rec1 = {0, 0, 0.f, 0.f};
         if (r1 < rounds) rec1 = load(r1);
-        pair_round<CPL>(bp, rec0, r0, npix, gl, half, chat, chat_scaled, scale, nodes);
+        pair_round<CPL>(bp, rec0, r0, px, gl, half, chat, chat_scaled, scale, nodes);
         r0 = r1;
         rec0 = rec1;
     }
@@ -298,12 +316,12 @@ __device__ __forceinline__ void span_item_short(const BayesParams& bp, const Bay
 // One round of the span kernel: pixel 2r + half, its sums and its mean.  tab: the
 // half-warp's item table.  nodes: this lane's share of the enumerated-node count.
 template <bool RAGGED>
-__device__ __forceinline__ void span_round(const BayesParams& bp, const BayesRec& rec, long r, long npix, int gl,
-                                           int half, unsigned short* tab, float2* chat, float2* chat_scaled,
+__device__ __forceinline__ void span_round(const BayesParams& bp, const BayesRec& rec, long r, const Pixels& px,
+                                           int gl, int half, unsigned short* tab, float2* chat, float2* chat_scaled,
                                            float scale, unsigned long long& nodes) {
     constexpr int G = 16;
-    const long p = 2 * r + half;
-    const bool valid = p < npix;
+    const long k = 2 * r + half;
+    const bool valid = k < px.n;
     const SpanPixel sp = span_pixel(bp, rec);
     const int nseg = (bp.n1 + kSpanSeg - 1) / kSpanSeg;
     u64 SW = pk(0.f, 0.f), SD = pk(0.f, 0.f), T0 = pk(0.f, 0.f), T1 = pk(0.f, 0.f);
@@ -376,7 +394,7 @@ __device__ __forceinline__ void span_round(const BayesParams& bp, const BayesRec
             if (valid && gl == 0) nodes += 2ull * (unsigned)bp.n0 * (unsigned)bp.n1;
         }
     }
-    if (valid && gl == 0) write_mean(bp, rec, p, sw, sdi, sdj, chat, chat_scaled, scale);
+    if (valid && gl == 0) write_mean(bp, rec, px.at(k), sw, sdi, sdj, chat, chat_scaled, scale);
 }
 
 // Two pixels per warp (half-warp h takes pixel 2r + h of round r), rounds dealt as in
@@ -386,14 +404,14 @@ __global__ void HB_SPAN_BOUNDS posterior_span_kernel(BayesParams bp, const Bayes
                                                      float2* __restrict__ chat, float2* __restrict__ chat_scaled,
                                                      float scale, PosteriorGate gate, unsigned long long* nodes_out) {
     const int lane = threadIdx.x & 31, gl = lane & 15, half = lane >> 4;
-    const long rounds = (npix + 1) / 2;
     __shared__ unsigned short tab[kSpanThreads / 32][2][kSpanMaxItems];
     __shared__ unsigned ticket;
     if (threadIdx.x == 0) ticket = 0u;
     __syncthreads();
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
-    if (gate.run && *gate.run == 0u) return;
+    const Pixels px = gated_pixels(gate, npix);
+    const long rounds = (px.n + 1) / 2;
     unsigned short* my = tab[threadIdx.x >> 5][half];
     unsigned long long nodes = 0;
     auto next_round = [&]() {
@@ -401,7 +419,7 @@ __global__ void HB_SPAN_BOUNDS posterior_span_kernel(BayesParams bp, const Bayes
         if (lane == 0) k = atomicAdd(&ticket, 1u);
         return (long)blockIdx.x + (long)__shfl_sync(0xffffffffu, k, 0) * gridDim.x;
     };
-    auto load = [&](long r) { return recs[min(2 * r + half, npix - 1)]; };
+    auto load = [&](long r) { return recs[px.at(min(2 * r + half, px.n - 1))]; };
     long r0 = next_round();
     BayesRec rec0 = {0, 0, 0.f, 0.f};
     if (r0 < rounds) rec0 = load(r0);
@@ -409,7 +427,7 @@ __global__ void HB_SPAN_BOUNDS posterior_span_kernel(BayesParams bp, const Bayes
         const long r1 = next_round();
         BayesRec rec1 = {0, 0, 0.f, 0.f};
         if (r1 < rounds) rec1 = load(r1);
-        span_round<RAGGED>(bp, rec0, r0, npix, gl, half, my, chat, chat_scaled, scale, nodes);
+        span_round<RAGGED>(bp, rec0, r0, px, gl, half, my, chat, chat_scaled, scale, nodes);
         r0 = r1;
         rec0 = rec1;
     }

@@ -118,10 +118,15 @@ cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, co
                             const float2* lut, double* ybar, BayesRec* rec, cudaStream_t s, float* ybar_f = nullptr,
                             const LsOut& ls = LsOut{}, bool pdl = false);
 cudaError_t launch_setup(const BayesParams& bp, const double* ybar, long npix, BayesRec* rec, cudaStream_t s);
-// Optional gate of the posterior launch: when run is set the kernel does nothing unless
-// *run is non-zero (the decision the learned stand-in's sampled check leaves behind).
+// Optional gate of the posterior launch: when run is set the kernel takes every pixel if
+// *run is non-zero (the decision the learned stand-in's sampled check leaves behind), and
+// otherwise only the *count pixels of list (none without a list: the pixels the learned
+// stand-in's route sends to the exact posterior), adding how many to *listed_total.
 struct PosteriorGate {
     const unsigned* run;
+    const int* list = nullptr;
+    const unsigned* count = nullptr;
+    unsigned long long* listed_total = nullptr;
 };
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
                              float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,

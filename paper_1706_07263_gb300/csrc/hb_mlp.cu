@@ -6,12 +6,12 @@
 //
 // Model.  x = T ybar + t0;  z1 = W1 x + b1;  h1 = bf16(gelu(z1));
 //         z2 = W2 h1 + b2;  h2 = bf16(gelu(z2));  o = W3 h2 + b3;
-//         c = clip(A+ ybar, box) + osc * o          (A+ = pseudo-inverse of A)
-// so the network learns the residual of the posterior mean on the clipped
-// least-squares estimate (non-zero near the box edges, where the prior truncates the
-// likelihood), in units of the posterior standard deviation osc; its input is ybar in
-// least-squares coordinates (see MlpNorm).  Loss: mean over samples and both outputs
-// of (o - t)^2, t = (c_target - clip(A+ ybar)) / osc.
+//         c = b(ybar) + osc * o
+// where b is the least-squares point moved by each box edge as if that edge alone cut the
+// Gaussian likelihood (MlpNorm); the network learns what b leaves of the posterior mean
+// (the corners, where two edges act together, and the grid's discreteness), in units of
+// the posterior standard deviation osc; its input is ybar in least-squares coordinates.
+// Loss: mean over samples and both outputs of (o - t)^2, t = (c_target - b(ybar)) / osc.
 //
 // Kernels.  mlp_train_kernel: a CTA of 4 warps takes 64 samples of a minibatch (16 per
 // warp), runs the forward pass, the loss gradient and the backward pass, and writes its
@@ -123,9 +123,35 @@ __device__ void load_params(SmemParams& P, const float* __restrict__ wbf) {
     }
 }
 
-__device__ __forceinline__ float clip_ls(const MlpNorm& nm, const float y[3], int j) {
-    const float c = nm.Ap[j * 3] * y[0] + nm.Ap[j * 3 + 1] * y[1] + nm.Ap[j * 3 + 2] * y[2];
-    return j == 0 ? fminf(fmaxf(c, nm.lo0), nm.hi0) : fminf(fmaxf(c, nm.lo1), nm.hi1);
+__device__ __forceinline__ float2 least_squares(const MlpNorm& nm, const float y[3]) {
+    return make_float2(fmaf(nm.Ap[0], y[0], fmaf(nm.Ap[1], y[1], nm.Ap[2] * y[2])),
+                       fmaf(nm.Ap[3], y[0], fmaf(nm.Ap[4], y[1], nm.Ap[5] * y[2])));
+}
+
+// The baseline b from the least-squares point (see MlpNorm): lambda(d) = phi(d) / Phi(d) as
+// sqrt(2/pi) / erfcx(-d / sqrt 2), finite on both sides of the edge (erfcx overflows to
+// infinity only far inside, where lambda is 0).
+__device__ __forceinline__ float2 baseline(const MlpNorm& nm, float2 c) {
+    constexpr float kSqrt2OverPi = 0.79788456080286535588f;
+    float b0 = c.x, b1 = c.y;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float d = (nm.edge_sgn[e] * (e < 2 ? c.x : c.y) - nm.edge_pos[e]) * nm.edge_inv_s[e];
+        const float lam = kSqrt2OverPi / erfcxf(-d * kInvSqrt2);
+        b0 = fmaf(lam, nm.edge_v0[e], b0);
+        b1 = fmaf(lam, nm.edge_v1[e], b1);
+    }
+    return make_float2(b0, b1);
+}
+
+// Whether the route sends the pixel with least-squares point c to the network (true) or
+// lists it for the exact posterior.
+__device__ __forceinline__ bool trusted(const MlpRoute& rt, float2 c) {
+    if (!rt.trust) return true;
+    const float u = (c.x - rt.org0) * rt.inv0, v = (c.y - rt.org1) * rt.inv1;
+    if (!(u >= 0.f && v >= 0.f && u < (float)rt.k0 && v < (float)rt.k1)) return false;  // NaN too
+    const int i = min((int)u, rt.k0 - 1), j = min((int)v, rt.k1 - 1);
+    return rt.trust[i * rt.k1 + j] != 0;
 }
 
 // Per-warp forward for 16 samples whose inputs are ys[s][3].  TRAIN keeps z1 and z2
@@ -246,7 +272,8 @@ __global__ void __launch_bounds__(32 * kWarpsT) mlp_train_kernel(const float* __
         const long b = (long)blockIdx.x * kSamplesT + s0 + s;
         const float* y = S.ys[s0 + s];
         const float osc = j == 0 ? nm.osc0 : nm.osc1;
-        const float t = (tgt_local[(s0 + s) * kOut + j] - clip_ls(nm, y, j)) / osc;
+        const float2 bl = baseline(nm, least_squares(nm, y));
+        const float t = (tgt_local[(s0 + s) * kOut + j] - (j == 0 ? bl.x : bl.y)) / osc;
         const float err = b < batch ? B.o[s][j] - t : 0.f;
         sq = err * err;
         S.do_[s0 + s][j] = err * (2.f / ((float)batch * kOut));
@@ -405,9 +432,12 @@ __global__ void __launch_bounds__(256) mlp_pack_kernel(const float* __restrict__
 
 // One 8-sample tile (samples 8 tile .. 8 tile + 7) through the network in one warp.  The
 // lanes with g < 2 end up holding sample 2q + g: they return its index and leave its
-// estimate in val; the other lanes, and samples past n, return -1.
+// estimate in val; the other lanes, and samples past n, return -1.  With a route, the
+// samples of untrusted cells are appended to its list (their estimates are still written;
+// the exact posterior replaces them).
 __device__ __forceinline__ long infer_tile(const InferSmem& S, const MlpNorm& nm, const float* __restrict__ ybar,
-                                           long n, long tile, int lane, float2& val) {
+                                           long n, long tile, int lane, float2& val,
+                                           const MlpRoute& rt = MlpRoute{}) {
     const int g = lane >> 2, q = lane & 3;
     const long r = tile * 8 + g;
     float y[3], x[3];
@@ -465,10 +495,25 @@ __device__ __forceinline__ long infer_tile(const InferSmem& S, const MlpNorm& nm
     const long rs = tile * 8 + s;
     const float ya = __shfl_sync(0xffffffffu, y[0], 4 * s), yb = __shfl_sync(0xffffffffu, y[1], 4 * s),
                 yc = __shfl_sync(0xffffffffu, y[2], 4 * s);
-    if (g >= 2 || rs >= n) return -1;
+    const bool mine = g < 2 && rs < n;
     const float ys[3] = {ya, yb, yc};
+    const float2 cls = least_squares(nm, ys);
+    if (rt.trust) {
+        // warp-aggregated append of the untrusted samples
+        const bool out = mine && !trusted(rt, cls);
+        const unsigned m = __ballot_sync(0xffffffffu, out);
+        if (m) {
+            unsigned base = 0;
+            if (lane == __ffs(m) - 1) base = atomicAdd(rt.count, (unsigned)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+            const unsigned at = base + __popc(m & ((1u << lane) - 1u));
+            if (out && at < (unsigned long)n) rt.list[at] = (int)rs;  // at most n are ever listed
+        }
+    }
+    if (!mine) return -1;
     const float o0 = (g & 1) ? o10 : o00, o1 = (g & 1) ? o11 : o01;
-    val = make_float2(clip_ls(nm, ys, 0) + nm.osc0 * (o0 + S.b3.x), clip_ls(nm, ys, 1) + nm.osc1 * (o1 + S.b3.y));
+    const float2 bl = baseline(nm, cls);
+    val = make_float2(fmaf(nm.osc0, o0 + S.b3.x, bl.x), fmaf(nm.osc1, o1 + S.b3.y, bl.y));
     return rs;
 }
 
@@ -542,18 +587,22 @@ template <int CPL>
 __global__ void __launch_bounds__(32 * kWarpsF, 4)
     mlp_forward_check_kernel(const InferSmem* __restrict__ img, MlpNorm nm, const float* __restrict__ ybar, long n,
                              float2* __restrict__ chat, float2* __restrict__ chat_scaled, float scale,
-                             BayesParams bp, const BayesRec* __restrict__ recs, MlpCheck ck) {
+                             BayesParams bp, const BayesRec* __restrict__ recs, MlpCheck ck, MlpRoute rt) {
     __shared__ InferSmem S;
     __shared__ float2 est[kMlpCheckPerCta];
     __shared__ float red[kWarpsF];
+    __shared__ unsigned redbad[kWarpsF];
     __shared__ unsigned last;
     stage_image(S, img);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // every kernel before this one in the stream has completed (the wait in stage_image), so
+    // the previous frame's exact posterior has read its counter: clear it for the next frame
+    if (rt.next_count && blockIdx.x == 0 && threadIdx.x == 0) *rt.next_count = 0u;
     if ((int)blockIdx.x >= ck.nctas) {
         const long ntile = (n + 7) / 8, nblk = (long)gridDim.x - ck.nctas;
         for (long tile = ((long)blockIdx.x - ck.nctas) * kWarpsF + warp; tile < ntile; tile += nblk * kWarpsF) {
             float2 v;
-            const long rs = infer_tile(S, nm, ybar, n, tile, lane, v);
+            const long rs = infer_tile(S, nm, ybar, n, tile, lane, v, rt);
             if (rs >= 0) {
                 chat[rs] = v;
                 if (chat_scaled) chat_scaled[rs] = make_float2(scale * v.x, scale * v.y);
@@ -580,7 +629,12 @@ __global__ void __launch_bounds__(32 * kWarpsF, 4)
         if (on && !(warp & 1) && lane == 0) {
             const float2 e = est[pair];
             const float dx = fabsf(e.x - c.x) * ck.inv_ext0, dy = fabsf(e.y - c.y) * ck.inv_ext1;
-            ck.err[k] = isnan(dx) || isnan(dy) ? NAN : fmaxf(dx, dy);
+            float err = isnan(dx) || isnan(dy) ? NAN : fmaxf(dx, dy);
+            if (rt.trust) {  // a listed pixel gets the exact posterior: nothing to check
+                const float yp[3] = {ybar[p * 3], ybar[p * 3 + 1], ybar[p * 3 + 2]};
+                if (!trusted(rt, least_squares(nm, yp))) err = 0.f;
+            }
+            ck.err[k] = err;
         }
         pair_barrier(pair);  // est[pair] free again
     }
@@ -592,16 +646,30 @@ __global__ void __launch_bounds__(32 * kWarpsF, 4)
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // the decision: the largest sampled error (or their mean) against tol; a NaN fails
     const volatile float* ev = ck.err;
     float e = 0.f;
-    for (int k = threadIdx.x; k < ck.nsample; k += blockDim.x) e += ev[k];
-    e = warp_sum(e);
-    if (lane == 0) red[warp] = e;
+    unsigned bad = 0u;
+    for (int k = threadIdx.x; k < ck.nsample; k += blockDim.x) {
+        const float v = ev[k];
+        bad |= isnan(v) ? 1u : 0u;
+        e = ck.use_max ? fmaxf(e, v) : e + v;
+    }
+    e = ck.use_max ? warp_max(e) : warp_sum(e);
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        red[warp] = e;
+        redbad[warp] = bad;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         float t = 0.f;
-        for (int w = 0; w < kWarpsF; ++w) t += red[w];
-        const bool run = !(t / (float)ck.nsample <= ck.tol);
+        for (int w = 0; w < kWarpsF; ++w) {
+            t = ck.use_max ? fmaxf(t, red[w]) : t + red[w];
+            bad |= redbad[w];
+        }
+        const float stat = ck.use_max ? t : t / (float)ck.nsample;
+        const bool run = bad || !(stat <= ck.tol);
         ck.sync[2] = run ? 1u : 0u;
         if (run) ck.sync[1] += 1u;
         ck.sync[0] = 0u;
@@ -671,7 +739,8 @@ namespace {
 template <int CPL>
 cudaError_t launch_forward_check_cpl(const void* img, const MlpNorm& nm, const float* ybar, long n, float2* chat,
                                      float2* chat_scaled, float scale, const BayesParams& bp, const BayesRec* rec,
-                                     const MlpCheck& ck, unsigned blocks, bool pdl, cudaStream_t s) {
+                                     const MlpCheck& ck, const MlpRoute& rt, unsigned blocks, bool pdl,
+                                     cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(32 * kWarpsF);
@@ -682,14 +751,14 @@ cudaError_t launch_forward_check_cpl(const void* img, const MlpNorm& nm, const f
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, mlp_forward_check_kernel<CPL>, static_cast<const InferSmem*>(img), nm, ybar, n,
-                              chat, chat_scaled, scale, bp, rec, ck);
+                              chat, chat_scaled, scale, bp, rec, ck, rt);
 }
 
 }  // namespace
 
 cudaError_t launch_mlp_forward_check(const void* img, const MlpNorm& nm, const float* ybar, long n, float2* chat,
                                      float2* chat_scaled, float scale, const BayesParams& bp, const BayesRec* rec,
-                                     MlpCheck ck, bool pdl, cudaStream_t s) {
+                                     MlpCheck ck, const MlpRoute& rt, bool pdl, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (ck.nsample <= 0) return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
@@ -705,7 +774,7 @@ cudaError_t launch_mlp_forward_check(const void* img, const MlpNorm& nm, const f
     if (blocks > 8L * sms) blocks = 8L * sms;
     if (blocks < 1) blocks = 1;
     blocks += ck.nctas;
-#define HB_FC_ARGS img, nm, ybar, n, chat, chat_scaled, scale, bp, rec, ck, (unsigned)blocks, pdl, s
+#define HB_FC_ARGS img, nm, ybar, n, chat, chat_scaled, scale, bp, rec, ck, rt, (unsigned)blocks, pdl, s
     if (bp.n1 <= 32) return launch_forward_check_cpl<1>(HB_FC_ARGS);
     if (bp.n1 <= 64) return launch_forward_check_cpl<2>(HB_FC_ARGS);
     if (bp.n1 <= 128) return launch_forward_check_cpl<4>(HB_FC_ARGS);

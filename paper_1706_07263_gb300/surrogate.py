@@ -2,8 +2,10 @@
 
 The network replaces the grid posterior on the low-pass band; it is trained on pairs
 (block-mean log-attenuation -> posterior mean) that the exact posterior kernel
-produces on seeded synthetic frames, and at run time the exact posterior stays its
-per-frame fallback (see ``Context.set_lowpass_mode``).  Everything here is
+produces on seeded synthetic frames, then certified against the exact posterior over
+the whole range of inputs (``Context.mlp_certify``): the pixels where it was not found
+within tolerance go to the exact posterior, and at run time the exact posterior stays
+its per-frame fallback (see ``Context.set_lowpass_mode``).  Everything here is
 orchestration: frames are rendered by ``synth``, every numeric step runs on the GPU
 through the C ABI, and parameters are saved as ``.npz`` files.
 """
@@ -57,6 +59,39 @@ def train_phases(ctx: binding.Context, ybar, conc, phases=DEFAULT_PHASES, batch:
     out = [ctx.mlp_train(ybar, conc, steps, batch=batch, lr=lr, seed=seed + 7919 * k)
            for k, (lr, steps) in enumerate(phases)]
     return np.concatenate(out)
+
+
+def density_resampled(ybar, conc, A, grid: dict, alpha: float = 0.25, cells: int = 48, seed: int = 0):
+    """The pairs drawn again (with replacement, as many as there are) with probability
+    proportional to count^-alpha of their least-squares point's cell in a cells x cells map
+    over the box widened by a tenth: the frames are smooth fields, so the rare regions (the
+    corners of the box, where two edges cut the likelihood together) get more of the
+    minibatches than their share of the pixels.  alpha = 0 keeps the frames' distribution."""
+    import torch
+    A = np.asarray(A, dtype=np.float64)
+    P = torch.tensor(np.linalg.pinv(A), dtype=torch.float32, device=ybar.device)
+    c = ybar @ P.T
+    lo = torch.tensor([grid["lo0"], grid["lo1"]], dtype=torch.float32, device=ybar.device)
+    hi = torch.tensor([grid["hi0"], grid["hi1"]], dtype=torch.float32, device=ybar.device)
+    pad = 0.1 * (hi - lo)
+    u = ((c - (lo - pad)) / (hi - lo + 2 * pad) * cells).floor().clamp(0, cells - 1).long()
+    cell = u[:, 0] * cells + u[:, 1]
+    cnt = torch.bincount(cell, minlength=cells * cells).double()
+    w = cnt[cell].pow(-alpha)
+    g = torch.Generator(device=ybar.device).manual_seed(seed)
+    idx = torch.multinomial(w / w.sum(), ybar.shape[0], replacement=True, generator=g)
+    return ybar[idx].contiguous(), conc[idx].contiguous()
+
+
+def train_certified(ctx: binding.Context, ybar, conc, A, grid: dict, cert_tol: float, alpha: float = 0.25,
+                    phases=DEFAULT_PHASES, batch: int = 4096, seed: int = 0, init_seed: int = 0):
+    """The default recipe: density-resampled pairs, phased training, then the certification
+    of the trained network at cert_tol (hb_mlp_certify).  Returns (losses, trusted share of
+    the certification map)."""
+    ys, cs = density_resampled(ybar, conc, A, grid, alpha, seed=seed)
+    losses = train_phases(ctx, ys, cs, phases=phases, batch=batch, seed=seed, init_seed=init_seed)
+    del ys, cs
+    return losses, ctx.mlp_certify(cert_tol)
 
 
 def edge_weighted(ybar, conc, A, grid: dict, sigmas: float = 4.0, repeat: int = 8):

@@ -74,3 +74,53 @@ def test_output_bias_only_network_has_closed_form_loss_and_gradient():
     assert loss == pytest.approx(np.mean(e * e), rel=1e-14)
     np.testing.assert_allclose(g[mlp.OFF_B3:], 2 * e.sum(axis=0) / e.size, rtol=1e-13)
     np.testing.assert_array_equal(g[:mlp.OFF_W3], 0.0)   # zero weights: nothing flows back
+
+
+def _edge_setup():
+    A = synth.make_mixing(3).A
+    grid = dict(n0=128, n1=128, lo0=0.0, hi0=150.0, lo1=0.0, hi1=100.0, sigma_l=0.02)
+    return A, grid, mlp.norm_for(A, grid)
+
+
+@pytest.mark.parametrize("c,axis,side", [([75.0, 2.0], 1, "lo"), ([75.0, -8.0], 1, "lo"), ([75.0, 97.0], 1, "hi"),
+                                         ([146.0, 50.0], 0, "hi"), ([3.0, 50.0], 0, "lo"),
+                                         ([-12.0, 50.0], 0, "lo")])
+def test_baseline_is_the_mean_of_a_gaussian_cut_by_one_edge(c, axis, side):
+    """Near one edge (the others many standard deviations away) the baseline is the mean of
+    N(c_ls, S) truncated to that edge's side: the marginal along the edge's axis is a
+    truncated normal (scipy.stats.truncnorm), and the other coordinate follows it through the
+    regression S_01 / S_aa -- inside, at and outside the edge."""
+    from scipy.stats import truncnorm
+    A, grid, nm = _edge_setup()
+    c = np.array(c)
+    S = nm["S"]
+    s = np.sqrt(S[axis, axis])
+    lo, hi = (nm["lo"][axis], np.inf) if side == "lo" else (-np.inf, nm["hi"][axis])
+    m = truncnorm.mean((lo - c[axis]) / s, (hi - c[axis]) / s, loc=c[axis], scale=s)
+    want = c + S[:, axis] / S[axis, axis] * (m - c[axis])
+    got = mlp.baseline(nm, (A @ c)[None])[0]
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-8)
+
+
+def test_baseline_is_the_least_squares_point_deep_inside():
+    A, grid, nm = _edge_setup()
+    c = np.array([[75.0, 50.0], [60.0, 45.0], [90.0, 55.0]])
+    np.testing.assert_allclose(mlp.baseline(nm, c @ A.T), c, rtol=0, atol=1e-10)
+
+
+def test_baseline_is_the_fine_grid_limit_of_the_posterior_near_one_edge():
+    """The grid posterior (the oracle's, FP64) near one edge converges to the baseline as the
+    grid is refined: halving the node spacing halves the difference (the edge node's weight
+    is an O(h) term), and on the finer grid it is a small fraction of a standard deviation.
+    A wrong sign or scale of an edge's shift would not converge."""
+    import oracle
+    A, _, nm = _edge_setup()
+    for c in ([75.0, 2.0], [75.0, -8.0], [146.0, 50.0]):
+        y = (A @ np.array(c))[None]
+        diffs = []
+        for n0, n1 in ((601, 401), (1201, 801)):
+            grid = dict(n0=n0, n1=n1, lo0=0.0, hi0=150.0, lo1=0.0, hi1=100.0, sigma_l=0.02)
+            diffs.append(np.abs(mlp.baseline(nm, y)[0] - oracle.posterior_mean(y, A, grid)[0]))
+        ratio = diffs[0] / diffs[1]
+        assert np.all((ratio > 1.8) & (ratio < 2.2)), (c, ratio)
+        assert np.all(diffs[1] < 0.05 * nm["osc"]), (c, diffs[1])

@@ -80,6 +80,7 @@ struct hb_ctx {
     float* d_err = nullptr;       // per sampled pixel error of the stand-in (mlp_err_cap)
     int mlp_err_cap = 0;
     unsigned long long* d_nodes = nullptr;  // grid nodes enumerated by timed posterior launches
+    unsigned* d_lpwork = nullptr;  // fused low pass: a pair of counters per band index
     long mlp_frames = 0;
     unsigned frame_seq = 0;
     // hb_estimate_host: copy streams and per-band events (created on first use)
@@ -275,6 +276,11 @@ void prepare(hb_ctx* c, const hb_mixing* mix, const hb_grid* g, double lambda) {
         bp.span_inv_acq = bp.sup_cols ? (float)(-1.0 / cq) : 0.f;
         bp.span_cv = bp.sup_cols ? (float)(-0.5 / cq) : 0.f;
         bp.span_an2 = bp.sup_cols ? (float)(alpha * g->n0 * g->n0) : 0.f;
+        const double q8 = std::exp2(8.0 * (double)bp.Cq);
+        bp.row_q = (float)q8;
+        // (steeper rows, |Cq| > 2, have a few nodes each and go to the span kernel: there the
+        // widened ends of a row can lie so far below the cut that the chains' range would not do)
+        bp.rows_ok = (bp.sup_cols && bp.Cq < 0.f && bp.Cq >= -2.f && q8 <= 1.0) ? 1 : 0;
     }
     auto split = [](double v, float& hi, float& lo) {
         hi = (float)v;
@@ -393,9 +399,11 @@ struct Band {
     TransformParams tp;
     long ll_off;
     long npix;
+    int index;  // bands that may run at the same time have different indices (< kMaxBands)
 };
+constexpr int kMaxBands = 8;
 
-Band whole_frame(const hb_ctx* c) { return Band{c->tp, 0, c->npix_ll}; }
+Band whole_frame(const hb_ctx* c) { return Band{c->tp, 0, c->npix_ll, 0}; }
 
 // chain: the frame is already on the device and the analysis may be launched as a
 // programmatic dependent of whatever kernel precedes it on the stream (it waits for that
@@ -413,7 +421,14 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
     BayesRec* rec = c->d_rec + b.ll_off;
     float2* chat = c->d_chat + b.ll_off;
     const float scale = (float)(1 << c->levels);
-    if (lowpass) {
+    if (bayes && !mlp && !ybar && hb::lowpass_fused_ok(b.tp, c->bp)) {
+        // block means, records and posterior means in one launch
+        StageTimer t(c, s, HB_STAGE_LOWPASS);
+        e = hb::launch_lowpass_fused(b.tp, c->bp, frame, stride, c->d_lut, chat, conc_scaled, scale,
+                                     c->d_lpwork + 2 * b.index, c->timing ? c->d_nodes : nullptr, pdl && chain, s);
+        c->launches++;
+        if (e != cudaSuccess) return HB_ERR_CUDA;
+    } else if (lowpass) {
         {
             StageTimer t(c, s, HB_STAGE_ANALYSIS);
             hb::LsOut lso;
@@ -428,7 +443,7 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
         }
         if (e != cudaSuccess) return HB_ERR_CUDA;
     }
-    if (bayes) {
+    if (bayes && (mlp || ybar || !hb::lowpass_fused_ok(b.tp, c->bp))) {
         StageTimer t(c, s, HB_STAGE_LOWPASS);
         if (mlp) {
             // network estimate together with the sampled exact check (one launch), then the
@@ -549,6 +564,9 @@ hb_status hb_create(const hb_mixing* mix, const hb_grid* grid, int levels, doubl
     if (cudaMalloc(&c->d_lut, sizeof(lut)) != cudaSuccess) st = HB_ERR_OOM;
     if (st == HB_OK && cudaMemcpy(c->d_lut, lut, sizeof(lut), cudaMemcpyHostToDevice) != cudaSuccess) st = HB_ERR_CUDA;
     if (st == HB_OK) st = ensure_rec(c, c->npix_ll);
+    if (st == HB_OK && (cudaMalloc(&c->d_lpwork, sizeof(unsigned) * 2 * kMaxBands) != cudaSuccess ||
+                        cudaMemset(c->d_lpwork, 0, sizeof(unsigned) * 2 * kMaxBands) != cudaSuccess))
+        st = HB_ERR_OOM;
     if (st != HB_OK) {
         cudaGetLastError();
         hb_destroy(c);
@@ -578,6 +596,7 @@ void hb_destroy(hb_ctx* c) {
     cudaFree(c->d_route);
     cudaFree(c->d_trust);
     cudaFree(c->d_nodes);
+    cudaFree(c->d_lpwork);
     cudaFree(c->d_frame);
     cudaFree(c->d_thb);
     cudaFree(c->d_so2);
@@ -656,6 +675,7 @@ hb_status enqueue_host_bands(hb_ctx* c, const void* frame_host, size_t row_strid
         b.tp.hl = b1 - b0;
         b.ll_off = (long)b0 * c->wl;
         b.npix = (long)(b1 - b0) * c->wl;
+        b.index = k;
         const size_t o = (size_t)r0 * c->W, n = (size_t)(r1 - r0) * c->W;
         // alternate bands between two compute streams: neighbouring bands share no data, and
         // one band's kernels fill the ramp and tail of the other's

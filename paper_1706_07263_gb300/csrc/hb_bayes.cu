@@ -15,6 +15,7 @@
 #include "hb_common.cuh"
 #include "hb_device.cuh"
 #include "hb_posterior.cuh"
+#include "hb_strip.cuh"
 
 #include <math.h>
 
@@ -438,6 +439,276 @@ __global__ void HB_SPAN_BOUNDS posterior_span_kernel(BayesParams bp, const Bayes
     }
 }
 
+// ---- Row kernel: the span kernel's cut, exact column intervals, weights by recurrence ----
+//
+// Per pixel (a half-warp of 16 lanes) the rows of span_pixel are dealt to the lanes in
+// slots of 16 (lane g takes rows rlo + g, rlo + g + 16, ...), and each lane sums its row
+// over the row's column interval (row_span: the span kernel's cut without rounding to
+// segments).  Along a row the base-2 log weight is the quadratic t(j) = Cq j^2 + R j + S in
+// the column offset j, so the weights of every second column satisfy w(j + 2) = w(j) r(j)
+// with r(j + 2) = r(j) row_q, row_q = 2^(8 Cq): the lane evaluates 2^t with ex2 only at the
+// first two columns (and their ratios), then advances the two chains (even and odd
+// columns from the start) together in FP32x2 -- two multiplies and two adds per pair of
+// nodes, no MUFU.  The sums are accumulated as A = sum w and B = sum of the running A, from
+// which sum w k = m A - B over the m steps of a chain.
+//
+// Every lane of the warp runs the same number of steps (the warp's longest row), so the
+// loop needs no per-lane test: a chain starts at the row's end that the grid cuts off (or at
+// the left end), and the steps beyond its interval continue the same Gaussian into the
+// row's tail, where every weight is below 2^-cut of the reference node's -- nodes the cut
+// would leave out anyway, on or beyond the grid's edge alike (together far below the FP32
+// rounding of the sums).  Only a row cut off by the grid at both ends (a posterior wider
+// than the grid) must stop at the grid's edge; a warp holding one takes a loop with a
+// per-lane test.  Pixels whose bounds take every row and column (span_pixel's guard for
+// inputs far outside the model), and pixels whose sums come out not finite, are summed over
+// the whole grid with an explicit maximum shift.
+constexpr int kRowThreads = 256;
+#ifndef HB_ROWS_CTAS_PER_SM
+#define HB_ROWS_CTAS_PER_SM 3
+#endif
+constexpr int kRowCtasPerSm = HB_ROWS_CTAS_PER_SM;
+
+// The cut's column interval [na, nb) of row i0 + di (grid column indices), not clipped to the
+// grid (widened by one column on the left and two on the right, as span_row); na >= nb when
+// the row holds none.
+__device__ __forceinline__ void row_span(const SpanPixel& sp, int di, int& na, int& nb) {
+    const float d = (float)di;
+    const float h2 = fmaf(d, fmaf(sp.a2, d, sp.b2), sp.c2);
+    const float c = fmaf(sp.k1, d, sp.cc);
+    const float h = sqrt_approx(fmaxf(h2, 0.f));
+    na = __float2int_ru(c - h - 1.f);
+    nb = __float2int_rd(c + h + 2.f) + 1;
+    if (!(h2 >= 0.f) || nb < na) nb = na;
+}
+
+// The posterior mean of the half-warp's pixel (record rec) into chat[out] (and chat_scaled)
+// when valid; both half-warps of the warp call it together.
+__device__ __forceinline__ void rows_pixel(const BayesParams& bp, const BayesRec& rec, bool valid, long out, int gl,
+                                           float2* chat, float2* chat_scaled, float scale,
+                                           unsigned long long& nodes) {
+    constexpr int G = 16;
+    const SpanPixel sp = span_pixel(bp, rec);
+    const bool direct = sp.whole;  // summed over the whole grid below instead
+    const int nslots = __reduce_max_sync(0xffffffffu, direct ? 0 : (sp.rhi - sp.rlo + G - 1) / G);
+    const u64 QQ = pk(bp.row_q, bp.row_q), CC = pk(bp.Cq, bp.Cq);
+    float sw = 0.f, sdi = 0.f, sdj = 0.f;
+    unsigned cnt = 0;
+    for (int slot = 0; slot < nslots; ++slot) {
+        const int i = sp.rlo + slot * G + gl;
+        int na = 0, nb = 0;
+        if (!direct && i < sp.rhi) row_span(sp, i - rec.i0, na, nb);
+        const int ja = max(na, 0), jb = min(nb, bp.n1);  // clipped to the grid
+        const bool live = jb > ja;
+        const bool lclip = na < 0, rclip = nb > bp.n1;
+        const bool full = live && lclip && rclip;
+        const bool back = live && rclip && !lclip;  // start at the right end, walk left
+        const bool any_full = __any_sync(0xffffffffu, full);
+        // steps: the warp's longest row; a lane with a full row takes only its own, and the
+        // grid's last column on its own when the row has an odd number of columns
+        const int len = live ? jb - ja : 0;
+        const int own = full ? (len >> 1) : ((len + 1) >> 1);
+        const int steps = __reduce_max_sync(0xffffffffu, own);
+        const bool extra = full && (len & 1);
+        const float d = (float)(i - rec.i0);
+        const float R = fmaf(2.f * bp.Bq, d, rec.V);
+        const float S = d * fmaf(bp.Aq, d, rec.U);
+        const float dir = back ? -1.f : 1.f;
+        const float s0 = (float)((back ? jb - 1 : ja) - rec.j0);  // the first chain's first column
+        const u64 J = pk(s0, s0 + dir);
+        const u64 T = fma2(J, fma2(CC, J, pk(R, R)), pk(S, S));
+        // t(j + 2 dir) - t(j) = Cq (4 dir j + 4) + 2 dir R
+        const u64 D = fma2(CC, fma2(pk(4.f * dir, 4.f * dir), J, pk(4.f, 4.f)), pk(2.f * dir * R, 2.f * dir * R));
+        float t0, t1, d0, d1;
+        upk(T, t0, t1);
+        upk(D, d0, d1);
+        // a chain whose first weight would be below 2^-100 starts 2^sh higher and its sums are
+        // scaled back (a weight flushed to zero would stop the recurrence)
+        const float sh = live ? fmaxf(0.f, -100.f - fminf(t0, t1)) : 0.f;
+        u64 w = live ? pk(ex2(t0 + sh), ex2(t1 + sh)) : pk(0.f, 0.f);
+        u64 q = live ? pk(ex2(d0), ex2(d1)) : pk(0.f, 0.f);
+        u64 A = pk(0.f, 0.f), B = pk(0.f, 0.f);
+        if (!any_full) {
+#pragma unroll 4
+            for (int st = 0; st < steps; ++st) {
+                A = add2(A, w);
+                B = add2(B, A);
+                w = mul2(w, q);
+                q = mul2(q, QQ);
+            }
+        } else {
+            for (int st = 0; st < steps; ++st) {
+                if (st < own) {
+                    A = add2(A, w);
+                    B = add2(B, A);
+                    w = mul2(w, q);
+                    q = mul2(q, QQ);
+                }
+            }
+        }
+        if (sh > 0.f) {
+            const float u = ex2(-sh);
+            A = mul2(A, pk(u, u));
+            B = mul2(B, pk(u, u));
+        }
+        const int m = any_full ? own : steps;  // the steps this lane summed
+        float a0, a1, b0, b1;
+        upk(A, a0, a1);
+        upk(B, b0, b1);
+        const float fm = (float)m;
+        float rs = a0 + a1;
+        // chain c: sum w (j - j0) = (its first column) A + 2 dir (m A - B)
+        float rm = fmaf(s0, a0, fmaf(s0 + dir, a1, 2.f * dir * (fmaf(fm, a0, -b0) + fmaf(fm, a1, -b1))));
+        if (extra) {  // the grid's last column of an odd full row
+            const float jx = (float)(bp.n1 - 1 - rec.j0);
+            const float wx = ex2(fmaf(jx, fmaf(bp.Cq, jx, R), S));
+            rs += wx;
+            rm = fmaf(wx, jx, rm);
+        }
+        sw += rs;
+        sdj += rm;
+        sdi = fmaf(d, rs, sdi);
+        if (live) cnt += 2u * (unsigned)m + (extra ? 1u : 0u);
+    }
+    sw = group_sum<G>(sw);
+    sdi = group_sum<G>(sdi);
+    sdj = group_sum<G>(sdj);
+    if (valid) nodes += cnt;
+    const bool bad = direct || !usable(sw, sdi, sdj);
+    if (__any_sync(0xffffffffu, bad)) {
+        // the whole grid with an explicit maximum shift (the partner half-warp takes part in
+        // the shuffles and keeps its own sums)
+        const float mx = group_max<G>(grid_max<1, G>(bp, rec, gl, 0, bp.n0));
+        float fw = 0.f, fdi = 0.f, fdj = 0.f;
+        grid_sums<1, G>(bp, rec, gl, 0, bp.n0, bad ? mx : 0.f, fw, fdi, fdj);
+        fw = group_sum<G>(fw);
+        fdi = group_sum<G>(fdi);
+        fdj = group_sum<G>(fdj);
+        if (bad) {
+            sw = fw;
+            sdi = fdi;
+            sdj = fdj;
+            if (valid && gl == 0) nodes += (unsigned long long)bp.n0 * (unsigned)bp.n1 * 2ull;
+        }
+    }
+    if (valid && gl == 0) write_mean(bp, rec, out, sw, sdi, sdj, chat, chat_scaled, scale);
+}
+
+// Two pixels per warp (half-warp h takes pixel 2r + h of round r), rounds dealt as in
+// posterior_pair_kernel.
+__global__ void __launch_bounds__(kRowThreads, 3) posterior_rows_kernel(BayesParams bp,
+                                                                       const BayesRec* __restrict__ recs, long npix,
+                                                                       float2* __restrict__ chat,
+                                                                       float2* __restrict__ chat_scaled, float scale,
+                                                                       PosteriorGate gate,
+                                                                       unsigned long long* nodes_out) {
+    const int lane = threadIdx.x & 31, gl = lane & 15, half = lane >> 4;
+    __shared__ unsigned ticket;
+    if (threadIdx.x == 0) ticket = 0u;
+    __syncthreads();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const Pixels px = gated_pixels(gate, npix);
+    const long rounds = (px.n + 1) / 2;
+    unsigned long long nodes = 0;
+    auto next_round = [&]() {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(&ticket, 1u);
+        return (long)blockIdx.x + (long)__shfl_sync(0xffffffffu, t, 0) * gridDim.x;
+    };
+    auto load = [&](long rr) { return recs[px.at(min(2 * rr + half, px.n - 1))]; };
+    long r0 = next_round();
+    BayesRec rec0 = {0, 0, 0.f, 0.f};
+    if (r0 < rounds) rec0 = load(r0);
+    while (r0 < rounds) {
+        const long r1 = next_round();
+        BayesRec rec1 = {0, 0, 0.f, 0.f};
+        if (r1 < rounds) rec1 = load(r1);
+        const long k = 2 * r0 + half;
+        rows_pixel(bp, rec0, k < px.n, k < px.n ? px.at(k) : 0, gl, chat, chat_scaled, scale, nodes);
+        r0 = r1;
+        rec0 = rec1;
+    }
+    if (nodes_out) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nodes += __shfl_xor_sync(0xffffffffu, nodes, off);
+        if (lane == 0 && nodes) atomicAdd(nodes_out, nodes);
+    }
+}
+
+// ---- Fused low pass: block means, posterior records and posterior means in one kernel ----
+//
+// For 1..3 levels with the row kernel's bounds.  A unit is one warp's strip of the frame:
+// 64 pixel columns of one superblock band (64 / 2^n superblocks).  Warps take units from a
+// counter; for each, the warp forms the superblocks' block means by the strip analysis (the
+// same code as the analysis kernel), computes their posterior records on lanes 0 .. 64/2^n
+// - 1 (bayes_setup), and then the posterior means two superblocks at a time (rows_pixel),
+// so a superblock's record never leaves the warp and the frame's loads overlap other warps'
+// posterior sums.  work[0] counts the units taken and work[1] the CTAs that are done; the
+// last CTA to finish sets both back to zero for the next launch (which, on the same stream,
+// starts after this one has completed).
+constexpr int kFusedThreads = 256;
+
+template <int L>
+__global__ void __launch_bounds__(kFusedThreads, 3)
+    lowpass_fused_kernel(TransformParams tp, BayesParams bp, const unsigned char* __restrict__ frame, size_t stride,
+                         const float2* __restrict__ lut, float2* __restrict__ chat, float2* __restrict__ chat_scaled,
+                         float scale, unsigned* __restrict__ work, unsigned long long* nodes_out) {
+    constexpr int TH = 1 << L, NSB = 64 / TH;
+    const int lane = threadIdx.x & 31, gl = lane & 15, half = lane >> 4;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int ux = (tp.wl * TH + 63) / 64;  // units per superblock band
+    const unsigned nunits = (unsigned)ux * (unsigned)tp.hl;
+    unsigned long long nodes = 0;
+    for (;;) {
+        unsigned u = 0;
+        if (lane == 0) u = atomicAdd(&work[0], 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= nunits) break;
+        const int by = (int)(u / (unsigned)ux), x0w = (int)(u % (unsigned)ux) * 64;
+        float v[3][TH][2];
+        float2 yref[3];
+        strip_load<L>(tp, frame, stride, lut, by, x0w + 2 * lane, lane, v, yref);
+        strip_analysis<L, 3, true>(v, lane);
+        // superblock t's sum sits in lane t * 2^(n-1): lane t < NSB gathers it
+        const int src = (lane * (TH / 2)) & 31;
+        float yhi[3], ylo[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float sum = __shfl_sync(0xffffffffu, v[ch][0][0], src);
+            yhi[ch] = __shfl_sync(0xffffffffu, yref[ch].x, src);
+            ylo[ch] = fmaf(sum, 1.f / (float)(TH * TH), __shfl_sync(0xffffffffu, yref[ch].y, src));
+        }
+        const int sb0 = x0w / TH, nsb = min(NSB, tp.wl - sb0);  // superblocks of this unit
+        BayesRec rec = {0, 0, 0.f, 0.f};
+        if (lane < nsb) rec = bayes_setup(yhi, ylo, bp);
+        for (int k = 0; 2 * k < nsb; ++k) {
+            const int t = 2 * k + half;
+            BayesRec rr;
+            rr.i0 = __shfl_sync(0xffffffffu, rec.i0, t);
+            rr.j0 = __shfl_sync(0xffffffffu, rec.j0, t);
+            rr.U = __shfl_sync(0xffffffffu, rec.U, t);
+            rr.V = __shfl_sync(0xffffffffu, rec.V, t);
+            rows_pixel(bp, rr, t < nsb, (long)by * tp.wl + sb0 + t, gl, chat, chat_scaled, scale, nodes);
+        }
+    }
+    if (nodes_out) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nodes += __shfl_xor_sync(0xffffffffu, nodes, off);
+        if (lane == 0 && nodes) atomicAdd(nodes_out, nodes);
+    }
+    // every warp of the CTA has seen the counter run out; the last CTA clears it
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&work[1], 1u) == gridDim.x - 1u) {
+            __threadfence();
+            work[0] = 0u;
+            work[1] = 0u;
+        }
+    }
+}
+
 // Resident CTAs per SM for a kernel (cached per device and kernel) and the SM count.
 template <typename K>
 cudaError_t residency(K kernel, int& resident, int& sms, int threads = kThreads) {
@@ -547,6 +818,42 @@ cudaError_t launch_span(const BayesParams& bp, const BayesRec* rec, long npix, c
                               sc.nodes);
 }
 
+// The row kernel under the same rule as the pair kernel.
+cudaError_t launch_rows(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
+                        float2* chat, float2* chat_scaled, float scale, bool pdl, const PosteriorGate& gate,
+                        cudaStream_t s) {
+    int resident = 0, sms = 0;
+    cudaError_t e = residency(posterior_rows_kernel, resident, sms, kRowThreads);
+    if (e != cudaSuccess) return e;
+    if (resident > kRowCtasPerSm) resident = kRowCtasPerSm;
+    const long warps = (long)sms * resident * (kRowThreads / 32);
+    if (npix < 2 * warps) return cudaErrorNotReady;
+    const long rounds = (npix + 1) / 2;
+    long blocks = (rounds + kRowThreads / 32 - 1) / (kRowThreads / 32);
+    // at most kRowCtasPerSm CTAs per SM (resident above), leaving room beside them for CTAs
+    // of the synthesis launched as its programmatic dependent (its transform runs before it
+    // waits for the posterior)
+    if (blocks > (long)sms * resident) blocks = (long)sms * resident;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kRowThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, posterior_rows_kernel, bp, rec, npix, chat, chat_scaled, scale, gate, sc.nodes);
+}
+
+bool uses_rows(const BayesParams& bp) {
+#ifdef HB_POST_NO_ROWS
+    return false;
+#else
+    return bp.rows_ok != 0;
+#endif
+}
+
 bool uses_span(const BayesParams& bp) {
 #ifdef HB_POST_NO_SPAN
     return false;
@@ -560,6 +867,11 @@ bool uses_span(const BayesParams& bp) {
 bool posterior_uses_pairs(const BayesParams& bp, long npix) {
     int resident = 0, sms = 0;
     cudaError_t e;
+    if (uses_rows(bp)) {
+        e = residency(posterior_rows_kernel, resident, sms, kRowThreads);
+        if (resident > kRowCtasPerSm) resident = kRowCtasPerSm;
+        return e == cudaSuccess && npix >= 2L * sms * resident * (kRowThreads / 32);
+    }
     if (uses_span(bp)) {
         e = bp.n1 % kSpanSeg ? residency(posterior_span_kernel<true>, resident, sms, kSpanThreads)
                              : residency(posterior_span_kernel<false>, resident, sms, kSpanThreads);
@@ -578,11 +890,56 @@ bool posterior_uses_pairs(const BayesParams& bp, long npix) {
     return e == cudaSuccess && npix >= 2L * sms * resident * (kThreads / 32);
 }
 
+bool lowpass_fused_ok(const TransformParams& tp, const BayesParams& bp) {
+#ifdef HB_NO_FUSED_LOWPASS
+    return false;
+#else
+    // where the separate posterior launch would take the row kernel too, so that each pixel's
+    // result is the same either way (the learned stand-in's fallback runs the separate launch)
+    return tp.levels >= 1 && tp.levels <= 3 && !tp.ll_intensity && uses_rows(bp) &&
+           posterior_uses_pairs(bp, (long)tp.hl * tp.wl);
+#endif
+}
+
+cudaError_t launch_lowpass_fused(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
+                                 const float2* lut, float2* chat, float2* chat_scaled, float scale, unsigned* work,
+                                 unsigned long long* nodes, bool pdl, cudaStream_t s) {
+    int resident = 0, sms = 0;
+    cudaError_t e;
+    switch (tp.levels) {
+        case 1: e = residency(lowpass_fused_kernel<1>, resident, sms, kFusedThreads); break;
+        case 2: e = residency(lowpass_fused_kernel<2>, resident, sms, kFusedThreads); break;
+        default: e = residency(lowpass_fused_kernel<3>, resident, sms, kFusedThreads); break;
+    }
+    if (e != cudaSuccess) return e;
+    const long units = (long)((tp.wl * (1 << tp.levels) + 63) / 64) * tp.hl;
+    long blocks = (units + kFusedThreads / 32 - 1) / (kFusedThreads / 32);
+    if (blocks > (long)sms * resident) blocks = (long)sms * resident;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kFusedThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const unsigned char* f = static_cast<const unsigned char*>(frame);
+    switch (tp.levels) {
+        case 1: return cudaLaunchKernelEx(&cfg, lowpass_fused_kernel<1>, tp, bp, f, stride, lut, chat, chat_scaled, scale, work, nodes);
+        case 2: return cudaLaunchKernelEx(&cfg, lowpass_fused_kernel<2>, tp, bp, f, stride, lut, chat, chat_scaled, scale, work, nodes);
+        default: return cudaLaunchKernelEx(&cfg, lowpass_fused_kernel<3>, tp, bp, f, stride, lut, chat, chat_scaled, scale, work, nodes);
+    }
+}
+
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
                              float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,
                              const PosteriorGate& gate) {
     if (npix <= 0) return cudaSuccess;
-    if (uses_span(bp)) {
+    if (uses_rows(bp)) {
+        cudaError_t e = launch_rows(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);
+        if (e != cudaErrorNotReady) return e;
+    } else if (uses_span(bp)) {
         cudaError_t e = bp.n1 % kSpanSeg ? launch_span<true>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s)
                                          : launch_span<false>(bp, rec, npix, sc, chat, chat_scaled, scale, pdl, gate, s);
         if (e != cudaErrorNotReady) return e;

@@ -9,6 +9,13 @@ namespace hb {
 
 constexpr int kThreads = 256;       // threads per CTA of every kernel here
 constexpr int kMaxLevels = 6;
+constexpr int kStripCols = 512;     // pixel columns per CTA of the two-column-per-lane transforms
+
+// Pixel columns per CTA of the register transforms for 0..4 levels: two per lane for 1..3
+// levels (the strip kernels), one per lane otherwise and for the intensity low pass.
+__host__ __device__ constexpr int tile_cols(int levels, int ll_intensity) {
+    return (levels >= 1 && levels <= 3 && !ll_intensity) ? kStripCols : kThreads;
+}
 
 // Frame geometry and the per-coefficient Tikhonov operator (Eq. 5).
 struct TransformParams {
@@ -71,6 +78,12 @@ struct BayesParams {
     float span_inv_acq;       // 1 / |Cq|
     float span_cv;            // -0.5 / Cq
     float span_an2;           // sup_alpha n0^2 (size of the quadratic term, for the rounding guard)
+    // Row kernel: along a grid row the weights of every second column form a sequence whose
+    // consecutive ratios grow by the constant factor row_q = 2^(8 Cq) (the weights are a
+    // Gaussian in the column index).  rows_ok = 1 when the column intervals apply and
+    // -2 <= Cq < 0 (row_q >= 2^-16).
+    float row_q;
+    int rows_ok;
     int illum;                // 1: A holds (I - 11^T/3) A and the set-up removes ybar's channel mean
 };
 
@@ -131,6 +144,14 @@ struct PosteriorGate {
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,
                              float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,
                              const PosteriorGate& gate = PosteriorGate{nullptr});
+// The fused low pass (block means, posterior records and posterior means in one launch, for
+// the plain grid posterior at 1..3 levels): whether it applies, and its launch.  work: two
+// counters, zero before the launch and left at zero by it; launches that may run at the
+// same time need their own.
+bool lowpass_fused_ok(const TransformParams& tp, const BayesParams& bp);
+cudaError_t launch_lowpass_fused(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
+                                 const float2* lut, float2* chat, float2* chat_scaled, float scale, unsigned* work,
+                                 unsigned long long* nodes, bool pdl, cudaStream_t s);
 // Whether launch_posterior takes npix pixels with the kernel it uses for large launches (two
 // pixels per warp: the span kernel, or the pair kernel without column intervals); each
 // pixel's result then does not depend on the other pixels of the launch.

@@ -58,6 +58,11 @@ __device__ __forceinline__ u64 add2(u64 a, u64 b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 __device__ __forceinline__ float ex2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -315,6 +320,26 @@ __device__ __forceinline__ void span_row(const SpanPixel& sp, int di, int nseg, 
     const int b = min(__float2int_ru((c + h + 2.f) * (1.f / kSpanSeg)), nseg);
     ma = sp.whole ? 0 : a;
     ns = sp.whole ? nseg : (h2 >= 0.f ? max(b - a, 0) : 0);
+}
+
+// Columns [ja, jb) of row i0 + di: those of the row's interval widened by one column on the
+// left and two on the right (the same cut as span_row, without rounding to segments),
+// clipped to the grid; ja >= jb when the row holds none.
+__device__ __forceinline__ void row_cols(const SpanPixel& sp, const BayesRec& rec, int di, int n1, int& ja,
+                                         int& jb) {
+    if (sp.whole) {
+        ja = 0;
+        jb = n1;
+        return;
+    }
+    const float d = (float)di;
+    const float h2 = fmaf(d, fmaf(sp.a2, d, sp.b2), sp.c2);
+    const float c = fmaf(sp.k1, d, sp.cc);
+    const float h = sqrt_approx(fmaxf(h2, 0.f));
+    ja = max(__float2int_ru(c - h - 1.f), 0);
+    jb = min(__float2int_rd(c + h + 2.f) + 1, n1);
+    if (!(h2 >= 0.f) || jb < ja) jb = ja;
+    (void)rec;
 }
 
 __device__ __forceinline__ bool usable(float sw, float sdi, float sdj) {

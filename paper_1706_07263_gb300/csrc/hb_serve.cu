@@ -364,7 +364,8 @@ hb_status hb_stream_open(hb_server* srv, int width, int height, int levels, int 
     tp.ll_intensity = srv->ll_intensity;
     for (int k = 0; k < 6; ++k) tp.M[k] = srv->M[k];
     st.npix_ll = (long)tp.hl * tp.wl;
-    st.tiles_x = (tp.wl * B + hb::kThreads - 1) / hb::kThreads;
+    const int cols = hb::tile_cols(levels, tp.ll_intensity);
+    st.tiles_x = (tp.wl * B + cols - 1) / cols;
     if (st.npix_ll > srv->cap_ll) return HB_ERR_SHAPE;
     const size_t px = (size_t)width * height;
     st.dev_bytes = (size_t)slots * (st.row * height + 2 * px * 4);

@@ -1,0 +1,178 @@
+// hb_strip.cuh -- the register Haar transforms of the strip kernels (two pixel columns
+// per lane, 1..3 levels), shared by the transform kernels and the fused low-pass kernel.
+// Internal to libhb (header-only, so that they inline without relocatable device code).
+#pragma once
+
+#include "hb_common.cuh"
+
+#include <math.h>
+
+namespace hb {
+namespace {
+
+constexpr unsigned kStripFull = 0xffffffffu;
+
+// ------------------------------------------------------------------------------------
+// Strip variants for 1..3 levels: lane l of a warp owns the two pixel columns
+// x = 2 (32 w + l) + {0, 1} of one superblock band (2^n rows), so the first level's 2x2
+// windows lie inside the lane and a superblock spans 2^(n-1) neighbouring lanes.  Every
+// level is computed as unscaled butterflies (sums and differences, i.e. 2 H per level):
+// the first level inside the lane; level l >= 2 as a butterfly across lanes (lane ^
+// 2^(l-2)) on the slots holding level-(l-1) low passes, then one across those slots' rows
+// inside the lane.  The lanes taking part in level l are those with lane % 2^(l-2) == 0;
+// a slot that a level leaves as a directional coefficient is not touched again.  With the
+// unscaled forward the level-l coefficients are 2^l times Eq. 2's; the inverse (Eq. 4,
+// H = H*) run as the same unscaled butterflies reproduces the pixels when it is fed the
+// level-l coefficients times 4^-l -- the Tikhonov operator is applied as M 4^-l -- and the
+// low pass as the block mean.  All these factors are powers of two.
+// ------------------------------------------------------------------------------------
+template <int L>
+__device__ __forceinline__ void strip_load(const TransformParams& tp, const unsigned char* __restrict__ frame,
+                                           size_t stride, const float2* lut, int by, int x0, int lane,
+                                           float (&v)[3][1 << L][2], float2 (&yref)[3]) {
+    constexpr int TH = 1 << L;
+    const int xa = min(x0, tp.W - 1), xb = min(x0 + 1, tp.W - 1);
+    const int src_lane = lane & ~((TH >> 1) - 1);  // the superblock's first lane
+    if (tp.fmt == 1) {
+        int k[3][TH][2];
+#pragma unroll
+        for (int r = 0; r < TH; ++r) {
+            const unsigned char* row = frame + (size_t)min(by * TH + r, tp.H - 1) * stride;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                k[ch][r][0] = __ldg(row + (size_t)xa * 3 + ch);
+                k[ch][r][1] = __ldg(row + (size_t)xb * 3 + ch);
+            }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const int kr = __shfl_sync(kStripFull, k[ch][0][0], src_lane);
+            yref[ch] = __ldg(lut + kr);
+#pragma unroll
+            for (int r = 0; r < TH; ++r)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const float2 y = __ldg(lut + k[ch][r][c]);
+                    v[ch][r][c] = (y.x - yref[ch].x) + (y.y - yref[ch].y);
+                }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < TH; ++r) {
+            const float* row = reinterpret_cast<const float*>(frame + (size_t)min(by * TH + r, tp.H - 1) * stride);
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                v[ch][r][0] = -logf(fmaxf(__ldg(row + (size_t)xa * 3 + ch), tp.eps));
+                v[ch][r][1] = -logf(fmaxf(__ldg(row + (size_t)xb * 3 + ch), tp.eps));
+            }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float yr = __shfl_sync(kStripFull, v[ch][0][0], src_lane);
+            yref[ch] = make_float2(yr, 0.f);
+#pragma unroll
+            for (int r = 0; r < TH; ++r) {
+                v[ch][r][0] -= yr;
+                v[ch][r][1] -= yr;
+            }
+        }
+    }
+}
+
+// The unscaled forward levels in place.  LL_ONLY: only the low passes are formed (the
+// block sum of each superblock), in slot (0, 0) of the superblock's first lane.
+template <int L, int NCH, bool LL_ONLY>
+__device__ __forceinline__ void strip_analysis(float (&v)[NCH][1 << L][2], int lane) {
+    constexpr int TH = 1 << L;
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch)
+#pragma unroll
+        for (int r = 0; r < TH; r += 2) {
+            const float a = v[ch][r][0], b = v[ch][r][1], c = v[ch][r + 1][0], d = v[ch][r + 1][1];
+            const float s1 = a + b, s2 = c + d;
+            v[ch][r][0] = s1 + s2;                 // low pass
+            if (!LL_ONLY) {
+                const float d1 = a - b, d2 = c - d;
+                v[ch][r][1] = s1 - s2;             // rows differ
+                v[ch][r + 1][0] = d1 - d2;         // diagonal
+                v[ch][r + 1][1] = d1 + d2;         // columns differ
+            }
+        }
+#pragma unroll
+    for (int l = 2; l <= L; ++l) {
+        const int s = 1 << (l - 2), rs = 1 << (l - 1);
+        const bool active = (lane & (s - 1)) == 0;
+        const float sgn = (lane & s) ? -1.f : 1.f;  // left lane: own + partner; right: partner - own
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch)
+#pragma unroll
+            for (int r = 0; r < TH; r += rs) {
+                const float x = v[ch][r][0];
+                const float q = fmaf(sgn, x, __shfl_xor_sync(kStripFull, x, s));
+                if (active) v[ch][r][0] = q;
+            }
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch)
+#pragma unroll
+            for (int r = 0; r < TH; r += 2 * rs)
+                if (active) {
+                    const float a = v[ch][r][0], b = v[ch][r + rs][0];
+                    v[ch][r][0] = a + b;
+                    if (!LL_ONLY) v[ch][r + rs][0] = a - b;
+                }
+    }
+}
+
+// The unscaled inverse levels in place (the forward's steps undone in reverse order).
+template <int L>
+__device__ __forceinline__ void strip_synthesis(float (&c)[2][1 << L][2], int lane) {
+    constexpr int TH = 1 << L;
+#pragma unroll
+    for (int l = L; l >= 2; --l) {
+        const int s = 1 << (l - 2), rs = 1 << (l - 1);
+        const bool active = (lane & (s - 1)) == 0;
+        const float sgn = (lane & s) ? -1.f : 1.f;
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+            for (int r = 0; r < TH; r += 2 * rs)
+                if (active) {
+                    const float a = c[ch][r][0], b = c[ch][r + rs][0];
+                    c[ch][r][0] = a + b;
+                    c[ch][r + rs][0] = a - b;
+                }
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+            for (int r = 0; r < TH; r += rs) {
+                const float x = c[ch][r][0];
+                const float q = fmaf(sgn, x, __shfl_xor_sync(kStripFull, x, s));
+                if (active) c[ch][r][0] = q;
+            }
+    }
+#pragma unroll
+    for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+        for (int r = 0; r < TH; r += 2) {
+            const float ll = c[ch][r][0], dr = c[ch][r][1], dd = c[ch][r + 1][0], dc = c[ch][r + 1][1];
+            const float s1 = ll + dr, s2 = ll - dr, d1 = dc + dd, d2 = dc - dd;
+            c[ch][r][0] = s1 + d1;
+            c[ch][r][1] = s1 - d1;
+            c[ch][r + 1][0] = s2 + d2;
+            c[ch][r + 1][1] = s2 - d2;
+        }
+}
+
+// Level of the coefficient left in slot (r, 0), r even, of lane `lane` after the forward
+// levels (0: the superblock's low pass).  Level l >= 2 turns a slot into a directional
+// coefficient by its butterfly across lanes (lane bit l-2) or across rows (row bit l-1).
+__device__ __forceinline__ int strip_slot_level(int r, int lane, int L) {
+    for (int l = 2; l <= L; ++l) {
+        if ((lane >> (l - 2)) & 1) return l;
+        if ((r >> (l - 1)) & 1) return l;
+    }
+    return 0;
+}
+
+}  // namespace
+}  // namespace hb

@@ -25,8 +25,13 @@
 // float hi + float lo.
 #include "hb_common.cuh"
 #include "hb_device.cuh"
+#include "hb_strip.cuh"
 
 #include <math.h>
+
+#ifndef HB_AN_EARLY_DEPENDENTS
+#define HB_AN_EARLY_DEPENDENTS 0
+#endif
 
 namespace hb {
 
@@ -575,6 +580,186 @@ __global__ void __launch_bounds__(kThreads) synthesis_warp_kernel(TransformParam
     synthesis_tile<L>(tp, frame, stride, lut_g, chat, out0, out1, debug_conc, blockIdx.x, blockIdx.y);
 }
 
+static_assert(kStripCols == 64 * (kThreads / 32), "two columns per lane");
+
+// Analysis of one strip tile (tile column tx of superblock band by): block means of the
+// tile's superblocks and their posterior records.  sb_hi / sb_lo: kThreads x 3 floats of
+// shared memory (kStripCols / 2^L <= kThreads superblocks).  Called by whole CTAs.
+template <int L>
+__device__ __forceinline__ void analysis_strip_tile(const TransformParams& tp, const BayesParams& bp,
+                                                    const unsigned char* __restrict__ frame, size_t stride,
+                                                    const float2* lut, int tx, int by, double* __restrict__ ybar,
+                                                    BayesRec* __restrict__ rec, float* __restrict__ ybar_f,
+                                                    float (*sb_hi)[3], float (*sb_lo)[3], const LsOut& ls = LsOut{}) {
+    constexpr int TH = 1 << L;
+    constexpr int NSB = kStripCols / TH;  // superblocks per tile
+    const int lane = threadIdx.x & 31;
+    const int x0w = tx * kStripCols + (threadIdx.x >> 5) * 64;  // the warp's first column
+    if (x0w < tp.wl * TH) {  // whole warps right of the padded frame skip the transform
+        float v[3][TH][2];
+        float2 yref[3];
+        strip_load<L>(tp, frame, stride, lut, by, x0w + 2 * lane, lane, v, yref);
+        strip_analysis<L, 3, true>(v, lane);
+        if ((lane & ((TH >> 1) - 1)) == 0) {
+            const int t = (threadIdx.x * 2) / TH;  // superblock within the tile
+            constexpr float inv = 1.f / (float)(TH * TH);
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                sb_hi[t][ch] = yref[ch].x;
+                sb_lo[t][ch] = fmaf(v[ch][0][0], inv, yref[ch].y);
+            }
+        }
+    }
+    __syncthreads();
+    // one superblock per thread for the posterior set-up, so whole warps do it together
+    for (int t = threadIdx.x; t < NSB; t += blockDim.x) {
+        const int gx = (tx * kStripCols) / TH + t;
+        if (gx >= tp.wl) continue;
+        float yhi[3], ylo[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            yhi[ch] = sb_hi[t][ch];
+            ylo[ch] = sb_lo[t][ch];
+        }
+        const size_t o = (size_t)by * tp.wl + gx;
+        if (ybar) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) ybar[o * 3 + ch] = (double)yhi[ch] + (double)ylo[ch];
+        }
+        if (ybar_f) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) ybar_f[o * 3 + ch] = yhi[ch] + ylo[ch];
+        }
+        low_pass_out(yhi, ylo, tp, bp, o, rec, ls);
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads, 4) analysis_strip_kernel(TransformParams tp, BayesParams bp,
+                                                                  const unsigned char* __restrict__ frame,
+                                                                  size_t stride, const float2* __restrict__ lut_g,
+                                                                  double* __restrict__ ybar,
+                                                                  BayesRec* __restrict__ rec,
+                                                                  float* __restrict__ ybar_f, LsOut ls) {
+    __shared__ float sb_hi[kThreads][3], sb_lo[kThreads][3];
+    // launched as a programmatic dependent of the preceding kernel (the previous frame's
+    // synthesis, or whatever wrote the frame): wait for it before reading anything
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#if HB_AN_EARLY_DEPENDENTS
+    // the posterior kernel may be scheduled as SMs free up; it waits for this whole grid
+    // before reading rec
+    asm volatile("griddepcontrol.launch_dependents;");
+#endif
+    analysis_strip_tile<L>(tp, bp, frame, stride, lut_g, blockIdx.x, blockIdx.y, ybar, rec, ybar_f, sb_hi, sb_lo,
+                           ls);
+#if !HB_AN_EARLY_DEPENDENTS
+    // the posterior kernel may be scheduled now; it waits for this grid before reading rec
+    asm volatile("griddepcontrol.launch_dependents;");
+#endif
+}
+
+// Synthesis of one strip tile: analysis, Tikhonov operator on the directional
+// coefficients (M 4^-l at level l), inverse transform, THb and SO2 (or HbO2 and Hb when
+// debug_conc).  Whole warps return early, so it must be called last in a kernel.
+template <int L>
+__device__ __forceinline__ void synthesis_strip_tile(const TransformParams& tp,
+                                                     const unsigned char* __restrict__ frame, size_t stride,
+                                                     const float2* lut, const float2* __restrict__ chat,
+                                                     float* __restrict__ out0, float* __restrict__ out1,
+                                                     int debug_conc, int tx, int by) {
+    constexpr int TH = 1 << L;
+    const int lane = threadIdx.x & 31;
+    const int x0w = tx * kStripCols + (threadIdx.x >> 5) * 64;
+    if (x0w >= tp.wl * TH) return;
+    const int x = x0w + 2 * lane;
+    float v[3][TH][2];
+    float2 yref[3];
+    strip_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
+    strip_analysis<L, 3, false>(v, lane);
+    // Tikhonov operator: level-1 coefficients (odd rows, second column) with M / 4; the
+    // first column's even rows by their level (the low pass: 0, or M 4^-L in the
+    // all-Tikhonov mode)
+    float c[2][TH][2];
+    const float* M = tp.M;
+#pragma unroll
+    for (int r = 0; r < TH; ++r)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float v0 = v[0][r][k], v1 = v[1][r][k], v2 = v[2][r][k];
+            float sc = 0.25f;
+            if (k == 0 && (r & 1) == 0) {
+                const int lv = strip_slot_level(r, lane, L);
+                // 4^-lv exactly; the low pass (lv = 0) keeps 4^-L only in the all-Tikhonov mode
+                sc = lv ? __int_as_float((127 - 2 * lv) << 23)
+                        : (tp.tikhonov_lowpass ? 1.f / (float)(TH * TH) : 0.f);
+            }
+            c[0][r][k] = sc * fmaf(M[0], v0, fmaf(M[1], v1, M[2] * v2));
+            c[1][r][k] = sc * fmaf(M[3], v0, fmaf(M[4], v1, M[5] * v2));
+        }
+    strip_synthesis<L>(c, lane);
+    float off0, off1;
+    if (tp.tikhonov_lowpass) {
+        off0 = (M[0] * yref[0].x + M[1] * yref[1].x + M[2] * yref[2].x) +
+               (M[0] * yref[0].y + M[1] * yref[1].y + M[2] * yref[2].y);
+        off1 = (M[3] * yref[0].x + M[4] * yref[1].x + M[5] * yref[2].x) +
+               (M[3] * yref[0].y + M[4] * yref[1].y + M[5] * yref[2].y);
+    } else {
+        // everything above is independent of the posterior step; wait for it here
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        const float2 ch = chat[(size_t)by * tp.wl + min(x >> L, tp.wl - 1)];
+        off0 = ch.x;
+        off1 = ch.y;
+    }
+    if (x >= tp.W) return;
+    const bool pair = x + 1 < tp.W;
+    const bool vec = pair && ((tp.W & 1) == 0);  // 8-byte aligned pairs of outputs
+#pragma unroll
+    for (int r = 0; r < TH; ++r) {
+        const int gy = by * TH + r;
+        if (gy >= tp.H) break;
+        float a0, a1, b0, b1;
+        const float h0 = c[0][r][0] + off0, h1 = c[0][r][1] + off0;  // HbO2
+        const float g0 = c[1][r][0] + off1, g1 = c[1][r][1] + off1;  // Hb
+        if (debug_conc) {
+            a0 = h0;
+            a1 = h1;
+            b0 = g0;
+            b1 = g1;
+        } else {
+            a0 = h0 + g0;
+            a1 = h1 + g1;
+            // SO2 needs 1e-3 absolute: the fast reciprocal-based division (2 ulp) is plenty
+            b0 = a0 >= 1.17549435e-38f ? __fdividef(h0, a0) : (a0 > 0.f ? h0 / a0 : 0.f);
+            b1 = a1 >= 1.17549435e-38f ? __fdividef(h1, a1) : (a1 > 0.f ? h1 / a1 : 0.f);
+        }
+        const size_t o = (size_t)gy * tp.W + x;
+        if (vec) {
+            *reinterpret_cast<float2*>(out0 + o) = make_float2(a0, a1);
+            *reinterpret_cast<float2*>(out1 + o) = make_float2(b0, b1);
+        } else {
+            out0[o] = a0;
+            out1[o] = b0;
+            if (pair) {
+                out0[o + 1] = a1;
+                out1[o + 1] = b1;
+            }
+        }
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads, 4) synthesis_strip_kernel(TransformParams tp,
+                                                                   const unsigned char* __restrict__ frame,
+                                                                   size_t stride, const float2* __restrict__ lut_g,
+                                                                   const float2* __restrict__ chat,
+                                                                   float* __restrict__ out0, float* __restrict__ out1,
+                                                                   int debug_conc) {
+    // the next frame's analysis may be scheduled as CTAs of this grid retire; it waits for
+    // this grid before reading anything
+    asm volatile("griddepcontrol.launch_dependents;");
+    synthesis_strip_tile<L>(tp, frame, stride, lut_g, chat, out0, out1, debug_conc, blockIdx.x, blockIdx.y);
+}
+
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
@@ -619,9 +804,14 @@ cudaError_t launch_analysis(const TransformParams& tp, const BayesParams& bp, co
                             const LsOut& ls, bool pdl) {
     const unsigned char* f = static_cast<const unsigned char*>(frame);
     if (tp.levels <= 4) {
-        const int TH = 1 << tp.levels;
-        const dim3 grid((tp.wl * TH + kThreads - 1) / kThreads, tp.hl);
+        const int TH = 1 << tp.levels, cols = tile_cols(tp.levels, tp.ll_intensity);
+        const dim3 grid((tp.wl * TH + cols - 1) / cols, tp.hl);
 #define HB_AN_ARGS grid, 0, s, pdl, tp, bp, f, stride, lut, ybar, rec, ybar_f, ls
+        if (cols == kStripCols) switch (tp.levels) {
+                case 1: return launch_maybe_pdl(analysis_strip_kernel<1>, HB_AN_ARGS);
+                case 2: return launch_maybe_pdl(analysis_strip_kernel<2>, HB_AN_ARGS);
+                default: return launch_maybe_pdl(analysis_strip_kernel<3>, HB_AN_ARGS);
+            }
         switch (tp.levels) {
             case 0: return launch_maybe_pdl(analysis_warp_kernel<0>, HB_AN_ARGS);
             case 1: return launch_maybe_pdl(analysis_warp_kernel<1>, HB_AN_ARGS);
@@ -647,8 +837,13 @@ cudaError_t launch_synthesis(const TransformParams& tp, const void* frame, size_
                              const float2* chat, float* out0, float* out1, int debug_conc, bool pdl, cudaStream_t s) {
     const unsigned char* f = static_cast<const unsigned char*>(frame);
     if (tp.levels <= 4) {
-        const int TH = 1 << tp.levels;
-        const dim3 grid((tp.wl * TH + kThreads - 1) / kThreads, tp.hl);
+        const int TH = 1 << tp.levels, cols = tile_cols(tp.levels, tp.ll_intensity);
+        const dim3 grid((tp.wl * TH + cols - 1) / cols, tp.hl);
+        if (cols == kStripCols) switch (tp.levels) {
+                case 1: return launch_maybe_pdl(synthesis_strip_kernel<1>, grid, 0, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
+                case 2: return launch_maybe_pdl(synthesis_strip_kernel<2>, grid, 0, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
+                default: return launch_maybe_pdl(synthesis_strip_kernel<3>, grid, 0, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
+            }
         switch (tp.levels) {
             case 0: return launch_maybe_pdl(synthesis_warp_kernel<0>, grid, 0, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
             case 1: return launch_maybe_pdl(synthesis_warp_kernel<1>, grid, 0, s, pdl, tp, f, stride, lut, chat, out0, out1, debug_conc);
@@ -688,6 +883,14 @@ __global__ void __launch_bounds__(kThreads) batch_analysis_kernel(BayesParams bp
     const int local = blockIdx.x - job.tile_begin;
     const int by = local / job.tiles_x, tx = local - by * job.tiles_x;
     BayesRec* rec = rec_all + job.ll_offset;
+    if (tile_cols(job.tp.levels, job.tp.ll_intensity) == kStripCols) {
+        switch (job.tp.levels) {
+            case 1: analysis_strip_tile<1>(job.tp, bp, job.frame, job.stride, lut_g, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+            case 2: analysis_strip_tile<2>(job.tp, bp, job.frame, job.stride, lut_g, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+            default: analysis_strip_tile<3>(job.tp, bp, job.frame, job.stride, lut_g, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
+        }
+        return;
+    }
     switch (job.tp.levels) {
         case 0: analysis_tile<0>(job.tp, bp, job.frame, job.stride, lut_g, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
         case 1: analysis_tile<1>(job.tp, bp, job.frame, job.stride, lut_g, tx, by, nullptr, rec, nullptr, sb_hi, sb_lo); break;
@@ -704,6 +907,14 @@ __global__ void __launch_bounds__(kThreads) batch_synthesis_kernel(const FrameJo
     const int local = blockIdx.x - job.tile_begin;
     const int by = local / job.tiles_x, tx = local - by * job.tiles_x;
     const float2* chat = chat_all + job.ll_offset;
+    if (tile_cols(job.tp.levels, job.tp.ll_intensity) == kStripCols) {
+        switch (job.tp.levels) {
+            case 1: synthesis_strip_tile<1>(job.tp, job.frame, job.stride, lut_g, chat, job.thb, job.so2, 0, tx, by); break;
+            case 2: synthesis_strip_tile<2>(job.tp, job.frame, job.stride, lut_g, chat, job.thb, job.so2, 0, tx, by); break;
+            default: synthesis_strip_tile<3>(job.tp, job.frame, job.stride, lut_g, chat, job.thb, job.so2, 0, tx, by); break;
+        }
+        return;
+    }
     switch (job.tp.levels) {
         case 0: synthesis_tile<0>(job.tp, job.frame, job.stride, lut_g, chat, job.thb, job.so2, 0, tx, by); break;
         case 1: synthesis_tile<1>(job.tp, job.frame, job.stride, lut_g, chat, job.thb, job.so2, 0, tx, by); break;

@@ -173,12 +173,16 @@ def test_hd_1080_u8_frame():
 
 
 def _close_to_every_node(got_thb, got_so2, full_thb, full_so2):
-    """Nodes carrying all but 2^-30 of the posterior mass, sums added in another order: outputs
-    agree to a few FP32 roundings of the low-pass sums."""
+    """Nodes carrying all but 2^-30 of the posterior mass, sums added in another order, and
+    along each row the weights advanced by the FP32 ratio recurrence (the first ratio carries
+    the rounding of its exponent, a few 1e-6 in log2, and each step one more rounding: a
+    drift of at most about 1e-4 relative over the 23 steps of the longest row, which tilts a
+    low-pass mean by a few 1e-5 uM): outputs agree to 2e-5 relative in THb and 5e-5 in SO2
+    where THb >= 1 uM."""
     d = np.abs(got_thb - full_thb) / np.maximum(np.abs(full_thb), 1.0)
-    assert d.max() <= 1e-5, d.max()
+    assert d.max() <= 2e-5, d.max()
     mask = np.abs(full_thb) >= 1.0
-    assert np.abs(got_so2 - full_so2)[mask].max(initial=0.0) <= 1e-5
+    assert np.abs(got_so2 - full_so2)[mask].max(initial=0.0) <= 5e-5
 
 
 def test_support_bounds_leave_the_result_unchanged():

@@ -35,14 +35,15 @@ import numpy as np  # noqa: E402
 
 METRIC = "1080p frames/s and p99 frame latency (THb+SO2) vs plain pipeline, same GB300, <=1e-4 rel err"
 UNIT = "frames/s"
-# DRAM traffic and warp instructions of one posterior launch on this workload, from an ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum, smsp__inst_executed.sum); valid only
-# while the kernel's sources hash to the value recorded with them.
-POSTERIOR_TRAFFIC = {"bytes": 539392, "warp_instructions": 12425078, "sources_sha256_16": "4b7a3e5a88a7e6c9",
-                     "sources": ("paper_1706_07263_gb300/csrc/hb_bayes.cu", "paper_1706_07263_gb300/csrc/hb_common.cuh",
-                                 "paper_1706_07263_gb300/csrc/hb_device.cuh",
-                                 "paper_1706_07263_gb300/csrc/hb_posterior.cuh")}
+# DRAM traffic and warp instructions of one launch of the dominant kernel (the fused low-pass
+# kernel) on this workload, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# smsp__inst_executed.sum); valid only while the kernel's sources hash to the value recorded
+# with them.
+KERNEL_COUNTERS = {"bytes": 6278656, "warp_instructions": 14840533, "sources_sha256_16": "e0389f526d5107f5",
+                   "sources": ('paper_1706_07263_gb300/csrc/hb_bayes.cu', 'paper_1706_07263_gb300/csrc/hb_common.cuh', 'paper_1706_07263_gb300/csrc/hb_device.cuh', 'paper_1706_07263_gb300/csrc/hb_posterior.cuh', 'paper_1706_07263_gb300/csrc/hb_strip.cuh')}
 SCHEDULERS_PER_SM = 4            # warp schedulers per SM, one instruction issued per clock each
+FP32_LANES_PER_SM = 128          # FP32 operations per clock per SM (a packed f32x2 op counts as two)
+FP32_OPS_PER_NODE = 4            # the posterior's weight recurrence and sums per evaluated grid node
 
 
 def measured_peaks():
@@ -54,22 +55,31 @@ def measured_peaks():
         return {}
 
 
-def posterior_traffic(key="bytes"):
-    """Bytes (or warp instructions, key="warp_instructions") per posterior launch from the ncu
-    capture, or None if the kernel changed since the capture."""
+def kernel_counters(key="bytes"):
+    """Bytes (or warp instructions, key="warp_instructions") per launch of the dominant kernel
+    from the ncu capture, or None if the kernel changed since the capture."""
+    return KERNEL_COUNTERS[key] if sources_digest() == KERNEL_COUNTERS["sources_sha256_16"] else None
+
+
+def sources_digest(sources=None):
+    """SHA-256 (first 16 hex digits) of the dominant kernel's sources with comments and
+    blank lines removed, so that a comment edit keeps the capture's counters valid."""
     import hashlib
+    import re
     h = hashlib.sha256()
-    for f in POSTERIOR_TRAFFIC["sources"]:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    return POSTERIOR_TRAFFIC[key] if h.hexdigest()[:16] == POSTERIOR_TRAFFIC["sources_sha256_16"] else None
+    for f in sources or KERNEL_COUNTERS["sources"]:
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines())
+        h.update("\n".join(ln for ln in lines if ln).encode())
+    return h.hexdigest()[:16]
 
 
 def issue_roofline(launch_s, sms, sm_mhz):
-    """The posterior's instruction issue against the SMs' issue rate (one warp-instruction per
-    clock per scheduler, 4 schedulers per SM).  Instructions per launch come from the ncu
-    capture."""
-    inst = posterior_traffic("warp_instructions")
+    """The dominant kernel's instruction issue against the SMs' issue rate (one
+    warp-instruction per clock per scheduler, 4 schedulers per SM).  Instructions per launch
+    come from the ncu capture."""
+    inst = kernel_counters("warp_instructions")
     if inst is None:
         return None
     peak = sms * SCHEDULERS_PER_SM * sm_mhz * 1e6 / 1e12
@@ -91,8 +101,7 @@ def parse():
     ap.add_argument("--mlp-eval-frames", type=int, default=8)
     ap.add_argument("--mlp-tol", type=float, default=1e-3)
     ap.add_argument("--serve-seconds", type=float, default=8.0)
-    ap.add_argument("--stereo-frames", type=int, default=300)
-    ap.add_argument("--stereo-pool", type=int, default=6)
+    ap.add_argument("--stereo-frames", type=int, default=300, help="frames per view of the stereo leg")
     ap.add_argument("--pulse-frames", type=int, default=300)
     ap.add_argument("--latency-frames", type=int, default=2000, help="single-frame calls of the latency leg")
     return ap.parse_args()
@@ -508,67 +517,75 @@ def measure_pulse(args, dev):
 
 
 def measure_stereo(args, dev):
-    """Stereo video: two 1920x1080 float streams; each frame copied host->device on a copy
-    stream while the previous frame is estimated on the compute stream."""
+    """Stereo video: two views of a drifting 1920x1080 scene (8-bit, blobs moving 0-3 px per
+    frame with seeded velocities, the right view shifted by a seeded disparity), N frames
+    per view rendered ahead into a pinned host ring by host threads; each frame is copied
+    host->device on a copy stream while the previous one is estimated on the compute stream
+    (tests/test_parity_gpu.py compares streamed frames of this video with the FP64 oracle)."""
+    import concurrent.futures as cf
     import torch
     from paper_1706_07263_gb300 import Context, synth
     wl = synth.HD_1080
     mix = synth.make_mixing(2)
     grid = synth.grid_spec(wl)
-    rng = np.random.default_rng(2)
-    pool = []
-    base = rng.integers(0, 1 << 30)
-    for eye in range(2):
-        for k in range(args.stereo_pool):
-            fr = synth.make_frame(int(base) + 100 * eye + k, wl.H, wl.W, mix.A, wl.nblobs, wl.smin, wl.smax, wl.noise,
-                                  "f32")
-            pool.append(torch.from_numpy(fr.rgb).pin_memory())
-    ctx = Context(mix.A, grid, wl.levels, wl.lam, wl.W, wl.H, "f32")
+    n = args.stereo_frames
+    video = synth.drift_video(2, wl.H, wl.W, mix.A, wl.nblobs, wl.smin, wl.smax, 3.0, wl.noise, "u8")
+    t0 = time.perf_counter()
+
+    def render(i):  # stream order: left 0, right 0, left 1, ...
+        return torch.from_numpy(video.frame(i // 2, i & 1)).pin_memory()
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        ring = list(ex.map(render, range(2 * n)))
+    gen_s = time.perf_counter() - t0
+    ctx = Context(mix.A, grid, wl.levels, wl.lam, wl.W, wl.H, "u8")
     copy_s, comp_s = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-    dbuf = [torch.empty((wl.H, wl.W, 3), dtype=torch.float32, device=dev) for _ in range(2)]
+    dbuf = [torch.empty((wl.H, wl.W, 3), dtype=torch.uint8, device=dev) for _ in range(2)]
     thb = [torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev) for _ in range(2)]
     so2 = [torch.empty_like(t) for t in thb]
     copied = [torch.cuda.Event() for _ in range(2)]
     freed = [torch.cuda.Event() for _ in range(2)]
     for e in freed:
         e.record(comp_s)
-    total = 2 * args.stereo_frames
 
-    def run(n):
-        for i in range(n):
+    def run(frames):
+        for i in frames:
             b = i & 1
-            eye = i & 1
-            src = pool[eye * args.stereo_pool + (i // 2) % args.stereo_pool]
             with torch.cuda.stream(copy_s):
                 copy_s.wait_event(freed[b])
-                dbuf[b].copy_(src, non_blocking=True)
+                dbuf[b].copy_(ring[i], non_blocking=True)
                 copied[b].record(copy_s)
             with torch.cuda.stream(comp_s):
                 comp_s.wait_event(copied[b])
-                ctx.estimate(dbuf[b], thb[eye], so2[eye], stream=comp_s)
+                ctx.estimate(dbuf[b], thb[b], so2[b], stream=comp_s)
                 freed[b].record(comp_s)
 
-    run(8)
+    run(range(8))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    run(total)
+    run(range(2 * n))
     torch.cuda.synchronize(dev)
     el = time.perf_counter() - t0
-    # per-pass HBM rates from per-kernel timing of a few frames
+    out = {"workload": f"2 views x {n} frames of 1920x1080 u8, blobs drifting 0-3 px/frame, 3 levels, "
+                       "128x128 grid, rendered ahead into pinned host buffers by host threads",
+           "frames_per_s": 2 * n / el, "h2d_gb_per_s": 2 * n * wl.H * wl.W * 3 / el / 1e9,
+           "render_s": gen_s}
+    # per-pass rates from per-kernel timing of a few frames
     ctx.timing_start(64)
     for k in range(8):
         ctx.estimate(dbuf[k & 1], thb[0], so2[0])
     torch.cuda.synchronize(dev)
     st = ctx.timing_read()
+    px = wl.H * wl.W
+    passes = {}
+    for name, (ms, cnt) in st.items():
+        if cnt:
+            nbytes = {"analysis": px * 3, "lowpass": px * 3, "synthesis": px * 3 + px * 8}[name]
+            passes[name] = {"ms": ms / cnt, "gb_per_s": nbytes / (ms / cnt * 1e-3) / 1e9}
+    out["passes"] = passes
     ctx.close()
-    fbytes = wl.H * wl.W * 12
-    a_ms = st["analysis"][0] / max(st["analysis"][1], 1)
-    s_ms = st["synthesis"][0] / max(st["synthesis"][1], 1)
-    return {"workload": f"2 eyes x {args.stereo_frames} frames of 1920x1080 f32, 3 levels, 128x128 grid "
-                        f"({args.stereo_pool} distinct frames per eye cycled)",
-            "frames_per_s": total / el, "h2d_gb_per_s": total * fbytes / el / 1e9,
-            "analysis_pass_gb_per_s": fbytes / (a_ms * 1e-3) / 1e9,
-            "synthesis_pass_gb_per_s": (fbytes + wl.H * wl.W * 8) / (s_ms * 1e-3) / 1e9}
+    del ring
+    return out
 
 
 def bench_config(wl, world, l2):
@@ -713,23 +730,27 @@ def run_ours(args):
     barrier()
     e2e_s, e2e_frames = replicas.aggregate(time.perf_counter() - t0, args.steps, device=dev)
 
-    # roofline of the dominant kernel (grid posterior), bound by the MUFU ex2 pipe and issue:
-    # achieved = the grid nodes the kernel evaluates (its own counter), one ex2 each, over its
-    # launch time; peak = SMs x the ex2 rate per SM clock measured in this process x the SM
-    # clock limit.  The kernel leaves out the nodes below 2^-cut of the reference weight (less
-    # than 2^-30 of the posterior mass together); the whole grid's count is reported beside
-    # the fraction as a grid-equivalent throughput.
+    # roofline of the dominant kernel: the low-pass launch (the fused kernel: block means,
+    # posterior records and the grid posterior).  Its work is the grid nodes it evaluates (its
+    # own counter): along a row the weights follow the exact ratio recurrence, two FP32
+    # multiplies and two FP32 adds per node (ex2 only at each row's start), so the binding
+    # pipe is the FP32 one: peak = SMs x 128 FP32 lanes per clock x the SM clock limit / 4
+    # operations per node.  The kernel leaves out the nodes below 2^-cut of the reference
+    # weight (less than 2^-30 of the posterior mass together); the whole grid's count is
+    # reported beside the fraction as a grid-equivalent throughput.
     post_ms, post_n = stage["lowpass"]
     post_avg_s = post_ms / max(post_n, 1) * 1e-3
     nodes_grid = hl * wl_ * wl.grid[0] * wl.grid[1]
     nodes = nodes_enumerated / max(post_n, 1)
     ex2_clk, sms = binding.measure_ex2_rate()
     sm_mhz = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
-    peak = sms * ex2_clk * sm_mhz * 1e6 / 1e12
+    peak = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / FP32_OPS_PER_NODE / 1e12
     achieved = nodes / post_avg_s / 1e12
     hbm = measured_peaks().get("hbm_gbs")
     npix_ll = hl * wl_
-    stage_bytes = {"analysis": H * W * 3 + npix_ll * 16, "lowpass": npix_ll * (16 + 8),
+    fused = not stage.get("analysis", (0, 0))[1]   # no separate analysis launch
+    stage_bytes = {"analysis": H * W * 3 + npix_ll * 16,
+                   "lowpass": (H * W * 3 + npix_ll * 8) if fused else npix_ll * (16 + 8),
                    "synthesis": H * W * 3 + npix_ll * 8 + H * W * 8}
     stages = {}
     for k, v in stage.items():
@@ -749,15 +770,20 @@ def run_ours(args):
         "latency_ms": latency,
         "megapixels_per_s": value * W * H / 1e6,
         "stages": stages,
-        "roofline": {"bound": "alu", "kernel": "posterior (grid posterior mean, one MUFU ex2 per evaluated node)",
-                     "achieved": achieved, "peak": peak, "unit": "Tex2/s", "frac": achieved / peak,
-                     "units": f"grid nodes the kernel evaluates per launch ({nodes:.4g}: per grid row the "
-                              "16-column segments meeting the row's interval above the cut), one ex2 each",
-                     "traffic": posterior_traffic(),
+        "roofline": {"bound": "alu", "kernel": "lowpass_fused_kernel<3> (block means, posterior records, grid "
+                                               "posterior mean)" if fused else "posterior_rows_kernel",
+                     "achieved": achieved, "peak": peak, "unit": "Tnode/s", "frac": achieved / peak,
+                     "units": f"grid nodes the kernel evaluates per launch ({nodes:.4g}: in each row of the cut "
+                              "ellipse its column interval, continued to the warp's longest row), "
+                              f"{FP32_OPS_PER_NODE} FP32 operations each",
+                     "traffic": kernel_counters(),
                      "issue": issue_roofline(post_avg_s, sms, sm_mhz),
-                     "peak_method": f"{sms} SMs (device attribute) x {ex2_clk:.2f} ex2/clk/SM (hb_measure_ex2_rate, "
-                                    f"this process) x {sm_mhz:.0f} MHz (SM clock limit)",
-                     "timing": "CUDA events around each posterior launch, K more steps after the timed region",
+                     "peak_method": f"{sms} SMs (device attribute) x {FP32_LANES_PER_SM} FP32 lanes/clk x "
+                                    f"{sm_mhz:.0f} MHz (SM clock limit) / {FP32_OPS_PER_NODE} FP32 ops per node",
+                     "ex2": {"per_clk_per_sm": ex2_clk, "peak_tex2_per_s": sms * ex2_clk * sm_mhz * 1e6 / 1e12,
+                             "note": "measured in this process (hb_measure_ex2_rate); the kernel takes ex2 only at "
+                                     "row starts, so the MUFU pipe does not bind it"},
+                     "timing": "CUDA events around each low-pass launch, K more steps after the timed region",
                      "grid_equivalent": {"nodes_per_launch": nodes_grid, "evaluated_share": nodes / nodes_grid,
                                          "throughput": nodes_grid / post_avg_s / 1e12, "unit": "Tnode/s",
                                          "note": "every node of the 128x128 grid for every low-pass pixel over the "

@@ -287,7 +287,7 @@ hb_status hb_mlp_certify(hb_ctx *ctx, double tol, double *trusted_fraction, void
  * Serving: continuous batching of frames from many concurrent streams (an extension; the
  * paper processes single frames).  A request-loop thread inside the library packs the
  * frames waiting from all streams -- any mix of sizes and of 0..4 levels -- into batches
- * that run as one launch per stage, two batches in flight on separate CUDA streams;
+ * that run as one launch per stage, four batches in flight on separate CUDA streams;
  * frames that arrive while a batch runs join the next one.  Each stream owns `slots`
  * frame slots (pinned host + device buffers) admitted against the server's budget.
  * The mixing model, grid and lambda are shared by all streams.
@@ -316,7 +316,7 @@ enum { HB_SERVE_SEQUENTIAL = 1u << 4 }; /* one frame at a time, one batch in fli
 
 /* Create a server.  flags: HB_LAMBDA_ABSOLUTE, HB_FULL_GRID, HB_ILLUMINATION, HB_LOWPASS_INTENSITY,
  * HB_SERVE_SEQUENTIAL.  budget_bytes bounds
- * the device memory of all stream slots plus the two batches' scratch (sized for
+ * the device memory of all stream slots plus the four batches' scratch (sized for
  * batch_lowpass_pixels low-pass pixels each); max_batch (1..64) bounds frames per batch.
  * HB_ERR_BUDGET if the scratch alone exceeds the budget.  Starts the request loop. */
 hb_status hb_server_create(const hb_mixing *mix, const hb_grid *grid, double lambda, unsigned flags, int in_format,

@@ -2,9 +2,15 @@
 // low-pass pixel (the Bayesian estimate on the low-pass band, Section 2); the per-pixel
 // sums are in hb_posterior.cuh.
 //
-// Three kernels, all with persistent warps that prefetch their next record:
-//   posterior_span_kernel  two pixels per warp; per pixel only the column interval of each
-//                          row that can hold a non-zero FP32 weight (the default);
+// Five kernels, all with persistent warps:
+//   lowpass_fused_kernel   block means, posterior records and posterior means in one launch
+//                          (1..3 levels where the row kernel applies: the default path);
+//   posterior_rows_kernel  two pixels per warp over precomputed records; per pixel the rows
+//                          of the cut, each over its exact column interval, weights by a
+//                          ratio recurrence (the default when the records are given);
+//   posterior_span_kernel  two pixels per warp; per pixel the 16-column segments of each
+//                          row that meet the row's column interval (grids the recurrence
+//                          does not suit);
 //   posterior_pair_kernel  two pixels per warp over whole rows (every node enumerated, or
 //                          no column intervals for this grid);
 //   posterior_kernel       one warp per unit (pixel, part) for launches with fewer pixels
@@ -643,28 +649,59 @@ __global__ void __launch_bounds__(kRowThreads, 3) posterior_rows_kernel(BayesPar
 // same code as the analysis kernel), computes their posterior records on lanes 0 .. 64/2^n
 // - 1 (bayes_setup), and then the posterior means two superblocks at a time (rows_pixel),
 // so a superblock's record never leaves the warp and the frame's loads overlap other warps'
-// posterior sums.  work[0] counts the units taken and work[1] the CTAs that are done; the
+// posterior sums.  work[0] counts the tickets taken and work[1] the CTAs that are done; the
 // last CTA to finish sets both back to zero for the next launch (which, on the same stream,
 // starts after this one has completed).
+//
+// Tail.  With U units over W warps, U mod W units are left once every warp has taken its
+// share of whole units; dealt whole, they would keep that many warps busy for a whole unit
+// while the others idle.  Those tail units are instead dealt in P pieces each (P a power of
+// two up to the unit's rounds, with P x tail <= W / 2): a piece redoes its unit's analysis
+// and records and takes 1/P of its rounds.  Each superblock is still computed by exactly
+// one warp with the same code, so the results do not depend on the split.
 constexpr int kFusedThreads = 256;
+
+struct FusedTickets {
+    unsigned full, per_unit, total;  // whole units first, then per_unit pieces per tail unit
+};
+
+__device__ __forceinline__ FusedTickets fused_tickets(unsigned nunits, unsigned warps, unsigned rounds) {
+    const unsigned tail = nunits % warps;
+    unsigned p = 1;
+#ifndef HB_FUSED_WHOLE_UNITS
+    while (2 * p <= rounds && tail > 0 && 4ull * p * tail <= warps) p *= 2;
+#endif
+    if (p == 1) return FusedTickets{nunits, 1, nunits};
+    return FusedTickets{nunits - tail, p, nunits - tail + tail * p};
+}
 
 template <int L>
 __global__ void __launch_bounds__(kFusedThreads, 3)
     lowpass_fused_kernel(TransformParams tp, BayesParams bp, const unsigned char* __restrict__ frame, size_t stride,
                          const float2* __restrict__ lut, float2* __restrict__ chat, float2* __restrict__ chat_scaled,
                          float scale, unsigned* __restrict__ work, unsigned long long* nodes_out) {
-    constexpr int TH = 1 << L, NSB = 64 / TH;
+    constexpr int TH = 1 << L, NSB = 64 / TH, NR = NSB / 2;
     const int lane = threadIdx.x & 31, gl = lane & 15, half = lane >> 4;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     const int ux = (tp.wl * TH + 63) / 64;  // units per superblock band
     const unsigned nunits = (unsigned)ux * (unsigned)tp.hl;
+    const FusedTickets tk = fused_tickets(nunits, gridDim.x * (kFusedThreads / 32), NR);
     unsigned long long nodes = 0;
     for (;;) {
-        unsigned u = 0;
-        if (lane == 0) u = atomicAdd(&work[0], 1u);
-        u = __shfl_sync(0xffffffffu, u, 0);
-        if (u >= nunits) break;
+        unsigned tix = 0;
+        if (lane == 0) tix = atomicAdd(&work[0], 1u);
+        tix = __shfl_sync(0xffffffffu, tix, 0);
+        if (tix >= tk.total) break;
+        // ticket -> unit and its rounds [k0, k1)
+        unsigned u = tix;
+        int k0 = 0, k1 = NR;
+        if (tix >= tk.full) {
+            const unsigned q = tix - tk.full, per = NR / tk.per_unit;
+            u = tk.full + q / tk.per_unit;
+            k0 = (int)((q % tk.per_unit) * per);
+            k1 = k0 + (int)per;
+        }
         const int by = (int)(u / (unsigned)ux), x0w = (int)(u % (unsigned)ux) * 64;
         float v[3][TH][2];
         float2 yref[3];
@@ -682,7 +719,7 @@ __global__ void __launch_bounds__(kFusedThreads, 3)
         const int sb0 = x0w / TH, nsb = min(NSB, tp.wl - sb0);  // superblocks of this unit
         BayesRec rec = {0, 0, 0.f, 0.f};
         if (lane < nsb) rec = bayes_setup(yhi, ylo, bp);
-        for (int k = 0; 2 * k < nsb; ++k) {
+        for (int k = k0; k < k1 && 2 * k < nsb; ++k) {
             const int t = 2 * k + half;
             BayesRec rr;
             rr.i0 = __shfl_sync(0xffffffffu, rec.i0, t);

@@ -8,9 +8,9 @@
 // table maps CTAs to frames), one posterior launch over the low-pass pixels of all
 // frames, one batched synthesis launch, device->host copies of THb and SO2, and a host
 // callback that marks the frames done.  While one batch is on the GPU the loop builds
-// and enqueues the next on the other stream, so consecutive batches overlap on the
-// device and frames that arrive meanwhile join the next batch as soon as a batch slot
-// frees.  Every stream owns a ring of frame slots (pinned host and device buffers)
+// and enqueues the next on another stream (kBatchSlots batches in flight), so consecutive
+// batches overlap on the device and frames that arrive meanwhile join the next batch as
+// soon as a batch slot frees.  Every stream owns a ring of frame slots (pinned host and device buffers)
 // allocated at open time against the server's device-memory budget; the operator and
 // grid constants are shared by all streams and stay resident.
 #include "hb.h"
@@ -80,6 +80,15 @@ struct Done {
     int stream, slot;
 };
 
+// Batches in flight at once (each on its own CUDA stream).  Under load most batches are
+// small -- frames arrive one by one and a free batch slot takes whatever is queued -- so
+// the server's rate is set by how many batches overlap: their copies, launches and
+// completion callbacks.
+#ifndef HB_SERVE_BATCH_SLOTS
+#define HB_SERVE_BATCH_SLOTS 4
+#endif
+constexpr int kBatchSlots = HB_SERVE_BATCH_SLOTS;
+
 }  // namespace
 
 struct hb_server {
@@ -92,9 +101,9 @@ struct hb_server {
     size_t budget = 0, used = 0;
     int max_batch = 1;
     long cap_ll = 0;
-    int nbatch_slots = 2;
+    int nbatch_slots = kBatchSlots;
     std::vector<Stream> streams;  // capacity reserved up front: elements never move
-    Batch batches[2];
+    Batch batches[kBatchSlots];
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<std::pair<int, int>> queue;  // (stream, slot) in arrival order
@@ -268,11 +277,11 @@ hb_status hb_server_create(const hb_mixing* mix, const hb_grid* grid, double lam
     srv->budget = budget_bytes;
     srv->max_batch = max_batch;
     srv->cap_ll = batch_lowpass_pixels;
-    srv->nbatch_slots = (flags & HB_SERVE_SEQUENTIAL) ? 1 : 2;
+    srv->nbatch_slots = (flags & HB_SERVE_SEQUENTIAL) ? 1 : kBatchSlots;
     srv->ll_intensity = (flags & HB_LOWPASS_INTENSITY) ? 1 : 0;
     hb::prepare_constants(mix, grid, lambda, flags & (HB_LAMBDA_ABSOLUTE | HB_FULL_GRID | HB_ILLUMINATION), srv->M,
                           srv->bp);
-    const size_t need = 2 * batch_bytes(srv->cap_ll) + 256 * sizeof(float2);
+    const size_t need = (size_t)srv->nbatch_slots * batch_bytes(srv->cap_ll) + 256 * sizeof(float2);
     if (need > budget_bytes) {
         delete srv;
         return HB_ERR_BUDGET;
@@ -285,7 +294,7 @@ hb_status hb_server_create(const hb_mixing* mix, const hb_grid* grid, double lam
     }
     bool ok = cudaMalloc(&srv->d_lut, sizeof(lut)) == cudaSuccess &&
               cudaMemcpy(srv->d_lut, lut, sizeof(lut), cudaMemcpyHostToDevice) == cudaSuccess;
-    for (int k = 0; ok && k < 2; ++k) {
+    for (int k = 0; ok && k < srv->nbatch_slots; ++k) {
         Batch& b = srv->batches[k];
         b.srv = srv;
         const long c = srv->cap_ll;

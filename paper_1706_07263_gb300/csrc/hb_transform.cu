@@ -9,11 +9,18 @@
 //                      THb and SO2 (Section 3).
 //
 // Both kernels work on tiles of one 2^n-row band of superblocks (2^n x 2^n pixel
-// blocks; Haar windows never cross a superblock, so tiles need no halo).  A tile is
-// copied from HBM with coalesced 16-byte loads into shared memory, and the whole
-// multi-level transform runs in place there (Mallat layout: after level l the low
-// pass of each 2^l block sits at its top-left position and the three directional
-// coefficients at the other window positions).
+// blocks; Haar windows never cross a superblock, so tiles need no halo), in one of three
+// layouts by level count:
+//   strip (1..3 levels): a warp takes 64 columns, two per lane, so the first level stays
+//       inside the lane (hb_strip.cuh); CTAs of 512 columns;
+//   warp (0 and 4 levels, and the intensity low pass): a lane per column, levels across
+//       lanes by shuffles; CTAs of 256 columns;
+//   shared-memory tile (5..6 levels): the tile is copied from HBM with coalesced 16-byte
+//       loads into shared memory and the whole multi-level transform runs in place there
+//       (Mallat layout: after level l the low pass of each 2^l block sits at its top-left
+//       position and the three directional coefficients at the other window positions).
+// With 1..3 levels and the row kernel's grids the exact path runs no analysis kernel: the
+// fused low-pass kernel (hb_bayes.cu) forms the block means itself.
 //
 // Numerics.  Before the transform every pixel's log-attenuation has the value of
 // its superblock's top-left pixel subtracted (per channel).  The transform is

@@ -232,3 +232,67 @@ def pulse_video(seed: int, H: int, W: int, A: np.ndarray, fps: float = 30.0, f_p
     window = np.outer(np.exp(-0.5 * (ys / sg) ** 2), np.exp(-0.5 * (xs / sg) ** 2))
     phase = float(rng.uniform(0.0, 2.0 * np.pi))
     return PulseVideo(A, H, W, fps, f_pulse, depth, phase, hbo2, hb, window, noise, jitter, fmt, seed, shift)
+
+
+# ---------------------------------------------------------------------------------------------
+# Drifting stereo video (the stand-in for the stereo laparoscope sequences): the 1080p
+# generator's blob fields, whose centres move by a seeded velocity per blob (|v| uniform in
+# [0, vmax] px per frame, uniform direction); the right view is the same scene shifted by a
+# seeded horizontal disparity, with its own sensor noise.  Fields are evaluated as a matrix
+# product of the blobs' separable Gaussian factors, in float32, so that a 1920x1080 frame takes
+# tens of milliseconds and host threads can render frames ahead of a GPU consumer.
+# ---------------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class DriftVideo:
+    A: np.ndarray
+    H: int
+    W: int
+    params: list           # per field: ((cy, cx), sigma, amplitude) of its blobs at frame 0
+    vel: np.ndarray        # (2 fields, nblobs, 2): (vy, vx) px per frame
+    disparity: float       # px, right view
+    noise: float
+    fmt: str
+    seed: int
+
+    def fields(self, k: int, eye: int = 0):
+        ys = np.arange(self.H, dtype=np.float32)[:, None]
+        xs = np.arange(self.W, dtype=np.float32)[:, None]
+        out = []
+        for f, box in enumerate((BOX_HBO2, BOX_HB)):
+            (cy, cx), sg, am = self.params[f]
+            cyk = (cy + k * self.vel[f, :, 0]).astype(np.float32)
+            cxk = (cx + k * self.vel[f, :, 1] + (self.disparity if eye else 0.0)).astype(np.float32)
+            s = sg.astype(np.float32)
+            gy = np.exp(-0.5 * ((ys - cyk) / s) ** 2) * am.astype(np.float32)   # (H, nblobs)
+            gx = np.exp(-0.5 * ((xs - cxk) / s) ** 2)                           # (W, nblobs)
+            field = gy @ gx.T
+            lo, hi = float(field.min()), float(field.max())
+            field = (field - lo) * np.float32(1.0 / (hi - lo if hi > lo else 1.0))
+            out.append(np.float32(box[0]) + field * np.float32(box[1] - box[0]))
+        return out[0], out[1]
+
+    def frame(self, k: int, eye: int = 0) -> np.ndarray:
+        hbo2, hb = self.fields(k, eye)
+        A = self.A.astype(np.float32)
+        att = hbo2[..., None] * A[:, 0] + hb[..., None] * A[:, 1]
+        I = np.exp(-att)
+        rng = np.random.default_rng((self.seed, eye, k))
+        if self.noise > 0:
+            I += rng.standard_normal(I.shape, dtype=np.float32) * np.float32(self.noise)
+        if self.fmt == "u8":
+            return np.rint(np.float32(255.0) * np.clip(I, 0.0, 1.0)).astype(np.uint8)
+        return I
+
+
+def drift_video(seed: int, H: int, W: int, A: np.ndarray, nblobs: int = 32, smin: float = 20.0,
+                smax: float = 120.0, vmax: float = 3.0, noise: float = 0.01, fmt: str = "u8") -> DriftVideo:
+    """A drifting stereo video (see above), seeded."""
+    rng = np.random.default_rng(seed)
+    _, _, params = make_fields(rng, 8, 8, nblobs, smin, smax)   # blob draws only (tiny fields)
+    # centres over the full frame (make_fields drew them for an 8x8 frame)
+    params = [((rng.uniform(0, H, nblobs), rng.uniform(0, W, nblobs)), sg, am) for (_, sg, am) in params]
+    speed = rng.uniform(0.0, vmax, (2, nblobs))
+    ang = rng.uniform(0.0, 2.0 * np.pi, (2, nblobs))
+    vel = np.stack([speed * np.sin(ang), speed * np.cos(ang)], axis=-1)
+    disparity = float(rng.uniform(5.0, 20.0))
+    return DriftVideo(A, H, W, params, vel, disparity, noise, fmt, seed)

@@ -365,6 +365,11 @@ def test_host_entry_in_bands_matches_the_device_call(case):
         th2 = torch.empty_like(th).pin_memory()  # other buffers: the graph is not reused for them
         ctx.estimate_host(hf, th2, sh, stream=stream)
         np.testing.assert_array_equal(th2.numpy(), thb.cpu().numpy())
+        # the streamed (graph-replayed) frame against the FP64 oracle
+        ctx.estimate_host(hf, th, sh, stream=stream)
+        ref = oracle.estimate(rgb, A, grid, levels, 1e-3, nthreads=NTH,
+                              lowpass="tikhonov" if flags & binding.HB_LOWPASS_TIKHONOV else "bayes")
+        check({"thb": th.numpy().astype(np.float64), "so2": sh.numpy().astype(np.float64)}, ref, f"host {case}")
 
 
 @pytest.mark.parametrize("case", ["hd_bayes", "small_tikhonov", "small_bayes", "f32_bayes"])
@@ -416,6 +421,12 @@ def test_asynchronous_host_calls_overlap_and_match(case):
         for k in range(len(frames)):
             np.testing.assert_array_equal(th[k].numpy(), ref[k][0])
             np.testing.assert_array_equal(sh[k].numpy(), ref[k][1])
+        # two of the streamed frames against the FP64 oracle
+        for k in (1, 4):
+            want = oracle.estimate(frames[k], A, grid, levels, 1e-3, nthreads=NTH,
+                                   lowpass="tikhonov" if flags & binding.HB_LOWPASS_TIKHONOV else "bayes")
+            check({"thb": th[k].numpy().astype(np.float64), "so2": sh[k].numpy().astype(np.float64)}, want,
+                  f"async {case} frame {k}")
         th[0].zero_()
         ctx.estimate_host(hf[3], th[0], sh[0], stream=stream)
         np.testing.assert_array_equal(th[0].numpy(), ref[3][0])
@@ -488,3 +499,40 @@ def test_frames_back_to_back_match_single_calls(mode):
         torch.cuda.synchronize()
         for r in range(8):
             assert torch.equal(outs[r][0], ref[r % 4][0]) and torch.equal(outs[r][1], ref[r % 4][1]), r
+
+
+def test_streamed_drifting_stereo_frames_match_oracle():
+    """The stereo stream of the bench (drifting 1080p scene, two views, 8-bit): frames copied
+    host->device on a copy stream while the previous frame is estimated on a compute stream;
+    the first left and the last right frame of the stream against the FP64 oracle."""
+    wl = synth.HD_1080
+    mix = synth.make_mixing(2)
+    grid = synth.grid_spec(wl)
+    n = 6
+    video = synth.drift_video(2, wl.H, wl.W, mix.A, wl.nblobs, wl.smin, wl.smax, 3.0, wl.noise, "u8")
+    ring = [torch.from_numpy(video.frame(i // 2, i & 1)).pin_memory() for i in range(2 * n)]
+    copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()
+    dbuf = [torch.empty((wl.H, wl.W, 3), dtype=torch.uint8, device=DEV) for _ in range(2)]
+    outs = [(torch.empty((wl.H, wl.W), dtype=torch.float32, device=DEV),
+             torch.empty((wl.H, wl.W), dtype=torch.float32, device=DEV)) for _ in range(2 * n)]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
+    with Context(mix.A, grid, wl.levels, wl.lam, wl.W, wl.H, "u8") as ctx:
+        for e in freed:
+            e.record(comp_s)
+        for i in range(2 * n):
+            b = i & 1
+            with torch.cuda.stream(copy_s):
+                copy_s.wait_event(freed[b])
+                dbuf[b].copy_(ring[i], non_blocking=True)
+                copied[b].record(copy_s)
+            with torch.cuda.stream(comp_s):
+                comp_s.wait_event(copied[b])
+                ctx.estimate(dbuf[b], *outs[i], stream=comp_s)
+                freed[b].record(comp_s)
+        torch.cuda.synchronize()
+    for i in (0, 2 * n - 1):
+        ref = oracle.estimate(ring[i].numpy(), mix.A, grid, wl.levels, wl.lam, nthreads=NTH)
+        got = {"thb": outs[i][0].cpu().numpy().astype(np.float64), "so2": outs[i][1].cpu().numpy().astype(np.float64)}
+        thb_err, so2_err = check(got, ref, f"streamed frame {i}")
+        print(f"streamed frame {i}: THb max rel err {thb_err:.3e}, SO2 max abs err {so2_err:.3e}")

@@ -87,7 +87,9 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
 def test_admission_follows_the_budget():
     A = synth.make_mixing(4).A
     slot_bytes = 640 * 480 * 3 + 2 * 640 * 480 * 4
-    scratch = 2 * 50_000 * (16 + 8 + 4 * 3 * 8 + 4) + 2 * 64 * 512 + 2048
+    with Server(A, GRID, LAM, max_batch=4, batch_lowpass_pixels=50_000) as probe:
+        scratch = probe.stats()["bytes_in_use"]          # the batches' scratch, before any stream
+    assert scratch >= 50_000 * (16 + 8 + 4 * 3 * 8 + 4)
     budget = scratch + 3 * 2 * slot_bytes + 1000          # room for three 2-slot streams
     with Server(A, GRID, LAM, budget_bytes=budget, max_batch=4, batch_lowpass_pixels=50_000) as srv:
         ids = [srv.open_stream(640, 480, 3, slots=2) for _ in range(3)]

@@ -25,7 +25,11 @@
  *     kernel surfaces as HB_ERR_CUDA from a later call or synchronisation;
  *   - a context is not thread-safe and its scratch is shared by all calls made
  *     with it: calls with the same context must not overlap on different
- *     streams.
+ *     streams;
+ *   - the host side of the calls is marked with NVTX ranges (hb_estimate,
+ *     hb_estimate_host, hb_estimate_host_async, and hb.analysis, hb.lowpass,
+ *     hb.synthesis around each launch; hb_serve.batch around each serving
+ *     batch's enqueue), which cost nothing unless a profiler is attached.
  */
 #ifndef HB_H
 #define HB_H

@@ -351,11 +351,14 @@ hb::PosteriorScratch post_scratch(const hb_ctx* c, long ll_off = 0) {
 }
 
 // Event bracket around one launch when timing is armed.
+const char* const kStageNames[HB_NUM_STAGES] = {"hb.analysis", "hb.lowpass", "hb.synthesis"};
+
 struct StageTimer {
     hb_ctx* c;
     cudaStream_t s;
     int slot = -1;
-    StageTimer(hb_ctx* c_, cudaStream_t s_, int stage) : c(c_), s(s_) {
+    hb::NvtxRange range;
+    StageTimer(hb_ctx* c_, cudaStream_t s_, int stage) : c(c_), s(s_), range(kStageNames[stage]) {
         if (c->timing && 2 * (c->ev_used + 1) <= (int)c->ev.size()) {
             slot = c->ev_used++;
             c->ev_stage[slot] = stage;
@@ -622,6 +625,7 @@ hb_status hb_estimate(hb_ctx* c, const void* frame_dev, size_t row_stride_bytes,
     hb_status st = check_frame_args(c, frame_dev, row_stride_bytes);
     if (st != HB_OK) return st;
     DeviceGuard g(c->device);
+    hb::NvtxRange r("hb_estimate");
     if (settle_async(c) != HB_OK) return HB_ERR_CUDA;
     return run_frame(c, frame_dev, row_stride_bytes, nullptr, thb_dev, so2_dev, nullptr, 0,
                      static_cast<cudaStream_t>(stream));
@@ -784,6 +788,7 @@ hb_status hb_estimate_host(hb_ctx* c, const void* frame_host, size_t row_stride_
                            float* so2_host, void* stream) {
     if (!c) return HB_ERR_ARG;
     DeviceGuard g(c->device);
+    hb::NvtxRange r("hb_estimate_host");
     int bounds[kHostBands + 1];
     int nb = 1;
     bool mlp = false;
@@ -846,6 +851,7 @@ hb_status hb_estimate_host_async(hb_ctx* c, const void* frame_host, size_t row_s
                                  float* so2_host, void* stream) {
     if (!c) return HB_ERR_ARG;
     DeviceGuard g(c->device);
+    hb::NvtxRange r("hb_estimate_host_async");
     if (c->timing) return HB_ERR_STATE;
     int bounds[kHostBands + 1];
     int nb = 1;

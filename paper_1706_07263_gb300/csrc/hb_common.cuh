@@ -4,8 +4,24 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#ifndef HB_NO_NVTX
+#include <nvtx3/nvToolsExt.h>
+#endif
 
 namespace hb {
+
+// NVTX range around host-side enqueue work (a profiler's timeline shows the library's calls,
+// stages and serving batches); a no-op unless a tool is attached.
+struct NvtxRange {
+#ifndef HB_NO_NVTX
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+#else
+    explicit NvtxRange(const char*) {}
+#endif
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kThreads = 256;       // threads per CTA of every kernel here
 constexpr int kMaxLevels = 6;

@@ -16,10 +16,12 @@
 #include "hb.h"
 #include "hb_common.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -39,6 +41,17 @@ double now_ms() {
 }
 
 enum SlotState { FREE = 0, QUEUED, RUNNING, DONE, HELD };
+
+// Optional host-side timeline (compile with -DHB_SERVE_TRACE): per batch the time its frames
+// were taken from the queue, the time the enqueue of its copies and launches returned, the
+// time its completion callback ran, and its frames' longest wait in the queue; a summary goes
+// to stderr when the server is destroyed.
+#ifdef HB_SERVE_TRACE
+struct TraceRec {
+    double formed, enqueued, done, max_wait;
+    int frames;
+};
+#endif
 
 struct Slot {
     unsigned char* h_in = nullptr;
@@ -74,6 +87,9 @@ struct Batch {
     std::vector<std::pair<int, int>> members;  // (stream, slot)
     bool busy = false;
     struct hb_server* srv = nullptr;
+#ifdef HB_SERVE_TRACE
+    TraceRec tr{};
+#endif
 };
 
 struct Done {
@@ -114,6 +130,9 @@ struct hb_server {
     hb_status loop_error = HB_OK;
     long n_batches = 0, n_frames = 0, max_batch_seen = 0;
     double sum_batch = 0.0;
+#ifdef HB_SERVE_TRACE
+    std::vector<TraceRec> trace;  // under mu
+#endif
 };
 
 // Shared with hb_api.cu: the FP64 preparation of the operator and grid constants.
@@ -130,6 +149,10 @@ void CUDART_CB batch_done(void* arg) {
     const double t = now_ms();
     {
         std::lock_guard<std::mutex> lk(srv->mu);
+#ifdef HB_SERVE_TRACE
+        b->tr.done = t;
+        srv->trace.push_back(b->tr);
+#endif
         for (auto& m : b->members) {
             Slot& sl = srv->streams[m.first].slots[m.second];
             sl.state = DONE;
@@ -145,6 +168,7 @@ void CUDART_CB batch_done(void* arg) {
 
 // Enqueue one batch; called by the loop thread without the lock held.
 cudaError_t run_batch(hb_server* srv, Batch& b) {
+    hb::NvtxRange r("hb_serve.batch");
     cudaStream_t s = b.s;
     int tiles = 0;
     long ll = 0;
@@ -179,6 +203,9 @@ cudaError_t run_batch(hb_server* srv, Batch& b) {
         e = cudaMemcpyAsync(sl.h_thb, sl.d_thb, px * 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_so2, sl.d_so2, px * 4, cudaMemcpyDeviceToHost, s);
     }
+#ifdef HB_SERVE_TRACE
+    b.tr.enqueued = now_ms();  // before the callback is enqueued, so the callback sees it
+#endif
     if (e == cudaSuccess) e = cudaLaunchHostFunc(s, batch_done, &b);
     return e;
 }
@@ -209,6 +236,13 @@ void loop_main(hb_server* srv) {
             b->members.push_back(m);
         }
         b->busy = true;
+#ifdef HB_SERVE_TRACE
+        b->tr = TraceRec{now_ms(), 0.0, 0.0, 0.0, (int)b->members.size()};
+        for (auto& m : b->members) {
+            const double w = b->tr.formed - srv->streams[m.first].slots[m.second].t_submit;
+            if (w > b->tr.max_wait) b->tr.max_wait = w;
+        }
+#endif
         srv->n_batches++;
         srv->n_frames += (long)b->members.size();
         srv->sum_batch += (double)b->members.size();
@@ -247,6 +281,41 @@ size_t batch_bytes(long cap_ll) {
     return (sizeof(BayesRec) + sizeof(float2) + sizeof(float) * 3 * hb::kMaxParts + sizeof(unsigned)) * cap_ll +
            sizeof(FrameJob) * hb::kMaxBatchJobs;
 }
+
+#ifdef HB_SERVE_TRACE
+// Percentiles of the batches' phases and the slowest batches, to stderr.
+void trace_summary(hb_server* srv) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    std::vector<TraceRec>& t = srv->trace;
+    if (t.empty()) return;
+    auto pct = [&](std::vector<double> v, double q) {
+        std::sort(v.begin(), v.end());
+        return v[(size_t)std::min<double>(v.size() - 1, q * (v.size() - 1) + 0.5)];
+    };
+    std::vector<double> wait, enq, gpu, total;
+    for (auto& r : t) {
+        wait.push_back(r.max_wait);
+        enq.push_back(r.enqueued - r.formed);
+        gpu.push_back(r.done - r.enqueued);
+        total.push_back(r.done - r.formed + r.max_wait);
+    }
+    std::fprintf(stderr, "hb_serve trace: %zu batches\n", t.size());
+    const char* names[4] = {"queue wait", "enqueue", "enqueued->callback", "frame worst"};
+    std::vector<double>* vs[4] = {&wait, &enq, &gpu, &total};
+    for (int k = 0; k < 4; ++k)
+        std::fprintf(stderr, "  %-20s p50 %8.3f p90 %8.3f p99 %8.3f max %8.3f ms\n", names[k], pct(*vs[k], 0.5),
+                     pct(*vs[k], 0.9), pct(*vs[k], 0.99), pct(*vs[k], 1.0));
+    std::vector<size_t> idx(t.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return total[a] > total[b]; });
+    const double t0 = t.front().formed;
+    for (size_t k = 0; k < idx.size() && k < 12; ++k) {
+        const TraceRec& r = t[idx[k]];
+        std::fprintf(stderr, "  slow: at %9.3f ms frames %2d wait %7.3f enqueue %7.3f gpu+cb %7.3f\n", r.formed - t0,
+                     r.frames, r.max_wait, r.enqueued - r.formed, r.done - r.enqueued);
+    }
+}
+#endif
 
 }  // namespace
 
@@ -327,6 +396,11 @@ void hb_server_destroy(hb_server* srv) {
     }
     srv->cv_work.notify_all();
     if (srv->loop.joinable()) srv->loop.join();
+#ifdef HB_SERVE_TRACE
+    for (auto& b : srv->batches)
+        if (b.s) cudaStreamSynchronize(b.s);
+    trace_summary(srv);
+#endif
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(srv->device);

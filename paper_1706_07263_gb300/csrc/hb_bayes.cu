@@ -505,6 +505,11 @@ __device__ __forceinline__ void rows_pixel(const BayesParams& bp, const BayesRec
         if (!direct && i < sp.rhi) row_span(sp, i - rec.i0, na, nb);
         const int ja = max(na, 0), jb = min(nb, bp.n1);  // clipped to the grid
         const bool live = jb > ja;
+#ifndef HB_ROWS_NO_DEAD_SKIP
+        // rows whose interval misses the grid's columns add exactly nothing: a slot where
+        // every lane's row does is skipped (about a fifth of the slots on the 1080p frame)
+        if (!__any_sync(0xffffffffu, live)) continue;
+#endif
         const bool lclip = na < 0, rclip = nb > bp.n1;
         const bool full = live && lclip && rclip;
         const bool back = live && rclip && !lclip;  // start at the right end, walk left
@@ -660,6 +665,9 @@ __global__ void __launch_bounds__(kRowThreads, 3) posterior_rows_kernel(BayesPar
 // and records and takes 1/P of its rounds.  Each superblock is still computed by exactly
 // one warp with the same code, so the results do not depend on the split.
 constexpr int kFusedThreads = 256;
+#ifndef HB_FUSED_MINB
+#define HB_FUSED_MINB 3  // resident CTAs per SM asked of the register allocator (80 registers)
+#endif
 
 struct FusedTickets {
     unsigned full, per_unit, total;  // whole units first, then per_unit pieces per tail unit
@@ -676,7 +684,7 @@ __device__ __forceinline__ FusedTickets fused_tickets(unsigned nunits, unsigned 
 }
 
 template <int L>
-__global__ void __launch_bounds__(kFusedThreads, 3)
+__global__ void __launch_bounds__(kFusedThreads, HB_FUSED_MINB)
     lowpass_fused_kernel(TransformParams tp, BayesParams bp, const unsigned char* __restrict__ frame, size_t stride,
                          const float2* __restrict__ lut, float2* __restrict__ chat, float2* __restrict__ chat_scaled,
                          float scale, unsigned* __restrict__ work, unsigned long long* nodes_out) {

@@ -218,6 +218,43 @@ __device__ __forceinline__ float support_cut(const BayesParams& bp, const BayesR
     return fmaf(1e-6f, fmaf(fabsf(rec.U), (float)bp.n0, fmaf(fabsf(rec.V), (float)bp.n1, bp.sup_mg)), kSupportCut);
 }
 
+// Narrows the rows [rlo, rhi] (relative to the reference row) where the unconstrained row
+// maximum reaches -cut to those where the row's maximum over the grid's columns does: the
+// maximum over real dj where the maximiser dj*(di) lies on the grid, else the exponent at the
+// nearer edge column -- three quadratic pieces in di.  The rows kept are the union over the
+// pieces of (rows where the piece reaches -cut) within (rows where the piece applies,
+// widened by one).  Every grid node of a row left out is below -cut.
+__device__ __forceinline__ void clip_rows_to_grid(const BayesParams& bp, const BayesRec& rec, float cut, float& rlo,
+                                                  float& rhi) {
+    const float k1 = -bp.sup_r;  // dj*(di) = k0 + k1 di
+    if (bp.sup_inv_k1 == 0.f || !(rlo <= rhi)) return;
+    const float k0 = 2.f * rec.V * bp.sup_c;
+    const float ea = (-(float)rec.j0 - k0) * bp.sup_inv_k1, eb = ((float)(bp.n1 - 1 - rec.j0) - k0) * bp.sup_inv_k1;
+    // where dj* falls left of the grid (a), on it (m), right of it (b)
+    const float da_lo = k1 > 0.f ? -INFINITY : ea - 1.f, da_hi = k1 > 0.f ? ea + 1.f : INFINITY;
+    const float db_lo = k1 > 0.f ? eb - 1.f : -INFINITY, db_hi = k1 > 0.f ? INFINITY : eb + 1.f;
+    const float dm_lo = fminf(ea, eb) - 1.f, dm_hi = fmaxf(ea, eb) + 1.f;
+    float ulo = INFINITY, uhi = -INFINITY;
+    auto join = [&](float a0, float a1, float b0, float b1) {
+        const float x0 = fmaxf(a0, b0), x1 = fminf(a1, b1);
+        if (x0 <= x1) {
+            ulo = fminf(ulo, x0);
+            uhi = fmaxf(uhi, x1);
+        }
+    };
+    join(rlo, rhi, dm_lo, dm_hi);
+    float slo, shi;
+    const float ja = -(float)rec.j0, jb = (float)(bp.n1 - 1 - rec.j0);
+    superlevel(bp.Aq, fmaf(2.f * bp.Bq, ja, rec.U), fmaf(fmaf(bp.Cq, ja, rec.V), ja, cut), bp.sup_inv_aq, slo, shi);
+    join(slo, shi, da_lo, da_hi);
+    superlevel(bp.Aq, fmaf(2.f * bp.Bq, jb, rec.U), fmaf(fmaf(bp.Cq, jb, rec.V), jb, cut), bp.sup_inv_aq, slo, shi);
+    join(slo, shi, db_lo, db_hi);
+    if (!isnan(ulo) && !isnan(uhi) && ulo <= uhi) {
+        rlo = fmaxf(rlo, ulo);
+        rhi = fminf(rhi, uhi);
+    }
+}
+
 __device__ __forceinline__ void support_rows(const BayesParams& bp, const BayesRec& rec, int& lo, int& hi) {
     lo = 0;
     hi = bp.n0;
@@ -227,34 +264,7 @@ __device__ __forceinline__ void support_rows(const BayesParams& bp, const BayesR
     float rlo, rhi;
     superlevel(-bp.sup_alpha, fmaf(-bp.sup_r, rec.V, rec.U), fmaf(rec.V * rec.V, bp.sup_c, cut), bp.sup_inv_alpha,
                rlo, rhi);
-    const float k1 = -bp.sup_r;  // dj*(di) = k0 + k1 di
-    if (bp.sup_inv_k1 != 0.f && rlo <= rhi) {
-        const float k0 = 2.f * rec.V * bp.sup_c;
-        const float ea = (-(float)rec.j0 - k0) * bp.sup_inv_k1, eb = ((float)(bp.n1 - 1 - rec.j0) - k0) * bp.sup_inv_k1;
-        // where dj* falls left of the grid (a), on it (m), right of it (b)
-        const float da_lo = k1 > 0.f ? -INFINITY : ea - 1.f, da_hi = k1 > 0.f ? ea + 1.f : INFINITY;
-        const float db_lo = k1 > 0.f ? eb - 1.f : -INFINITY, db_hi = k1 > 0.f ? INFINITY : eb + 1.f;
-        const float dm_lo = fminf(ea, eb) - 1.f, dm_hi = fmaxf(ea, eb) + 1.f;
-        float ulo = INFINITY, uhi = -INFINITY;
-        auto join = [&](float a0, float a1, float b0, float b1) {
-            const float x0 = fmaxf(a0, b0), x1 = fminf(a1, b1);
-            if (x0 <= x1) {
-                ulo = fminf(ulo, x0);
-                uhi = fmaxf(uhi, x1);
-            }
-        };
-        join(rlo, rhi, dm_lo, dm_hi);
-        float slo, shi;
-        const float ja = -(float)rec.j0, jb = (float)(bp.n1 - 1 - rec.j0);
-        superlevel(bp.Aq, fmaf(2.f * bp.Bq, ja, rec.U), fmaf(fmaf(bp.Cq, ja, rec.V), ja, cut), bp.sup_inv_aq, slo, shi);
-        join(slo, shi, da_lo, da_hi);
-        superlevel(bp.Aq, fmaf(2.f * bp.Bq, jb, rec.U), fmaf(fmaf(bp.Cq, jb, rec.V), jb, cut), bp.sup_inv_aq, slo, shi);
-        join(slo, shi, db_lo, db_hi);
-        if (!isnan(ulo) && !isnan(uhi) && ulo <= uhi) {
-            rlo = fmaxf(rlo, ulo);
-            rhi = fminf(rhi, uhi);
-        }
-    }
+    clip_rows_to_grid(bp, rec, cut, rlo, rhi);
     if (!(rlo <= rhi) || isnan(rlo) || isnan(rhi)) return;
     const float lim = (float)bp.n0 + 2.f;
     const int a = rec.i0 + (int)floorf(fmaxf(rlo, -lim)) - 1;
@@ -271,7 +281,10 @@ __device__ __forceinline__ void support_rows(const BayesParams& bp, const BayesR
 // nodes left out weigh less than 2^-span_cut each against the reference node, together
 // less than 2^-30 of the posterior mass.  Centre and squared half-width are evaluated
 // directly (the two-root formula would cancel).  Rows: where t*(di) >= -cut, widened by one
-// row on each side and clipped to the grid.  A pixel whose terms are so large that their
+// row on each side and clipped to the grid (narrowing them further to the rows whose interval
+// meets the grid's columns, as support_rows does, costs more per pixel than the rows it
+// saves; the row kernel skips slots of rows that all miss the grid instead).  A pixel whose
+// terms are so large that their
 // FP32 rounding could move the bounds by whole columns (only for inputs far outside the
 // model) takes every row and column.
 constexpr int kSpanSeg = 16;  // columns per lattice segment

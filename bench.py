@@ -43,7 +43,11 @@ KERNEL_COUNTERS = {"bytes": 6279424, "warp_instructions": 16161765, "sources_sha
                    "sources": ('paper_1706_07263_gb300/csrc/hb_bayes.cu', 'paper_1706_07263_gb300/csrc/hb_common.cuh', 'paper_1706_07263_gb300/csrc/hb_device.cuh', 'paper_1706_07263_gb300/csrc/hb_posterior.cuh', 'paper_1706_07263_gb300/csrc/hb_strip.cuh')}
 SCHEDULERS_PER_SM = 4            # warp schedulers per SM, one instruction issued per clock each
 FP32_LANES_PER_SM = 128          # FP32 operations per clock per SM (a packed f32x2 op counts as two)
-FP32_OPS_PER_NODE = 4            # the posterior's weight recurrence and sums per evaluated grid node
+FP32_OPS_PER_NODE = 4            # the posterior's weight recurrence and sums per grid node summed one by one
+FP32_OPS_PER_ROW = 18            # a grid row summed in closed form: its interval 7, the row's terms 3, its
+                                 # peak 3, the weight and mean 2, the sums 3 (and one sqrt, one ex2: MUFU)
+FP32_OPS_PER_EDGE_ROW = 11       # more for a row the box edge cuts off: distance, table index 4, two cubics 6,
+                                 # mean 1
 
 
 def measured_peaks():
@@ -704,6 +708,7 @@ def run_ours(args):
             ctx.estimate(frame, thb, so2, stream=stream)
         barrier()
         nodes_enumerated = ctx.timing_nodes()
+        rows_closed, rows_edge = ctx.timing_rows(), ctx.timing_rows(edge=True)
         stage = ctx.timing_read()
         clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -737,21 +742,24 @@ def run_ours(args):
     e2e_s, e2e_frames = replicas.aggregate(time.perf_counter() - t0, args.steps, device=dev)
 
     # roofline of the dominant kernel: the low-pass launch (the fused kernel: block means,
-    # posterior records and the grid posterior).  Its work is the grid nodes it evaluates (its
-    # own counter): along a row the weights follow the exact ratio recurrence, two FP32
-    # multiplies and two FP32 adds per node (ex2 only at each row's start), so the binding
-    # pipe is the FP32 one: peak = SMs x 128 FP32 lanes per clock x the SM clock limit / 4
-    # operations per node.  The kernel leaves out the nodes below 2^-cut of the reference
-    # weight (less than 2^-30 of the posterior mass together); the whole grid's count is
-    # reported beside the fraction as a grid-equivalent throughput.
+    # posterior records and the grid posterior).  Its work is the FP32 arithmetic of the
+    # posterior's sums, from its own counters: each grid row of the cut ellipse summed in
+    # closed form (FP32_OPS_PER_ROW, plus FP32_OPS_PER_EDGE_ROW where the box edge cuts the
+    # row off and the one-sided sum comes from the table) and each node of a row summed one
+    # by one (FP32_OPS_PER_NODE: the ratio recurrence); the per-pixel set-up and the strip
+    # analysis are not counted.  peak = SMs x 128 FP32 lanes per clock x the SM clock limit.
+    # The whole grid's node count is reported beside the fraction as a grid-equivalent
+    # throughput.
     post_ms, post_n = stage["lowpass"]
     post_avg_s = post_ms / max(post_n, 1) * 1e-3
     nodes_grid = hl * wl_ * wl.grid[0] * wl.grid[1]
     nodes = nodes_enumerated / max(post_n, 1)
+    rows_c, rows_e = rows_closed / max(post_n, 1), rows_edge / max(post_n, 1)
+    ops = FP32_OPS_PER_ROW * rows_c + FP32_OPS_PER_EDGE_ROW * rows_e + FP32_OPS_PER_NODE * nodes
     ex2_clk, sms = binding.measure_ex2_rate()
     sm_mhz = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
-    peak = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / FP32_OPS_PER_NODE / 1e12
-    achieved = nodes / post_avg_s / 1e12
+    peak = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved = ops / post_avg_s / 1e12
     hbm = measured_peaks().get("hbm_gbs")
     npix_ll = hl * wl_
     fused = not stage.get("analysis", (0, 0))[1]   # no separate analysis launch
@@ -778,19 +786,20 @@ def run_ours(args):
         "stages": stages,
         "roofline": {"bound": "alu", "kernel": "lowpass_fused_kernel<3> (block means, posterior records, grid "
                                                "posterior mean)" if fused else "posterior_rows_kernel",
-                     "achieved": achieved, "peak": peak, "unit": "Tnode/s", "frac": achieved / peak,
-                     "units": f"grid nodes the kernel evaluates per launch ({nodes:.4g}: in each row of the cut "
-                              "ellipse its column interval, continued to the warp's longest row), "
-                              f"{FP32_OPS_PER_NODE} FP32 operations each",
+                     "achieved": achieved, "peak": peak, "unit": "T FP32 op/s", "frac": achieved / peak,
+                     "units": f"FP32 operations of the posterior's sums per launch ({ops:.4g}): {rows_c:.6g} grid "
+                              f"rows of the cut ellipse summed in closed form at {FP32_OPS_PER_ROW} each, "
+                              f"{rows_e:.6g} of them cut off by the box edge at {FP32_OPS_PER_EDGE_ROW} more, and "
+                              f"{nodes:.6g} nodes summed one by one at {FP32_OPS_PER_NODE}",
                      "traffic": kernel_counters(),
                      "issue": issue_roofline(post_avg_s, sms, sm_mhz),
                      "peak_method": f"{sms} SMs (device attribute) x {FP32_LANES_PER_SM} FP32 lanes/clk x "
-                                    f"{sm_mhz:.0f} MHz (SM clock limit) / {FP32_OPS_PER_NODE} FP32 ops per node",
+                                    f"{sm_mhz:.0f} MHz (SM clock limit)",
                      "ex2": {"per_clk_per_sm": ex2_clk, "peak_tex2_per_s": sms * ex2_clk * sm_mhz * 1e6 / 1e12,
-                             "note": "measured in this process (hb_measure_ex2_rate); the kernel takes ex2 only at "
-                                     "row starts, so the MUFU pipe does not bind it"},
+                             "note": "measured in this process (hb_measure_ex2_rate); the kernel takes one ex2 "
+                                     "per row, so the MUFU pipe does not bind it"},
                      "timing": "CUDA events around each low-pass launch, K more steps after the timed region",
-                     "grid_equivalent": {"nodes_per_launch": nodes_grid, "evaluated_share": nodes / nodes_grid,
+                     "grid_equivalent": {"nodes_per_launch": nodes_grid,
                                          "throughput": nodes_grid / post_avg_s / 1e12, "unit": "Tnode/s",
                                          "note": "every node of the 128x128 grid for every low-pass pixel over the "
                                                  "same launch time: a throughput, not a fraction of any peak"}},

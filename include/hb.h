@@ -94,13 +94,22 @@ enum {
                                       -log(block mean of the intensities) instead of the block mean of
                                       -log I (directional bands unchanged).  Levels 0..4; not with
                                       HB_LOWPASS_TIKHONOV nor the learned low pass. */
-    HB_LOWPASS_LS = 1u << 7         /* the low pass by least squares instead of the posterior: the fit
+    HB_LOWPASS_LS = 1u << 7,        /* the low pass by least squares instead of the posterior: the fit
                                       of the maximisation step in Section 2 (Eq. 9, read as the ordinary
                                       least-squares solution), c = (xi^T xi)^-1 xi^T ybar with xi = A, or
                                       [A | 1] with HB_ILLUMINATION, on the low pass of -log I or, with
                                       HB_LOWPASS_INTENSITY, -log of the block mean of I; directional
                                       bands through M as always.  Not with HB_LOWPASS_TIKHONOV nor the
                                       learned low pass. */
+    HB_NODE_SUMS = 1u << 8          /* the posterior's grid rows summed node by node (an exact ratio
+                                      recurrence of the weights along the row) instead of in closed
+                                      form.  By default a row is summed in closed form wherever the grid
+                                      allows it: over all integer columns a row's weights are a sampled
+                                      Gaussian whose sum and mean column follow from its peak (Poisson
+                                      summation, error below 2e-13 relative where used), and a row the
+                                      box edge cuts off on one side takes the one-sided sum from a table
+                                      of FP64 sums built at hb_create (cubic pieces, checked there);
+                                      both agree with the node-by-node sums far inside the tolerance */
 };
 
 /* Per-stage timing slots reported by hb_timing_read. */
@@ -190,6 +199,10 @@ long hb_launch_count(const hb_ctx *ctx);
 hb_status hb_timing_start(hb_ctx *ctx, int max_launches);
 hb_status hb_timing_read(hb_ctx *ctx, double ms[HB_NUM_STAGES], long launches[HB_NUM_STAGES]);
 hb_status hb_timing_nodes(hb_ctx *ctx, unsigned long long *nodes);
+/* Like hb_timing_nodes for the grid rows the posterior launches summed in closed form (see
+ * HB_NODE_SUMS): rows[0] all of them, rows[1] those the box edge cuts off (one-sided sums from
+ * the table).  Their nodes are not in hb_timing_nodes' count. */
+hb_status hb_timing_rows(hb_ctx *ctx, unsigned long long rows[2]);
 
 /* Static description of a status code. */
 const char *hb_strerror(hb_status s);

@@ -27,7 +27,8 @@ STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_SHAPE", 3: "HB_ERR_CUDA", 4: "
 # Every symbol include/hb.h declares (checked by the CPU tests against the built library).
 EXPORTED = ("hb_create", "hb_destroy", "hb_estimate", "hb_estimate_host", "hb_estimate_host_async", "hb_estimate_debug",
             "hb_posterior_mean",
-            "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_timing_nodes", "hb_strerror",
+            "hb_lowpass_shape", "hb_launch_count", "hb_timing_start", "hb_timing_read", "hb_timing_nodes", "hb_timing_rows",
+            "hb_strerror",
             "hb_mlp_init", "hb_mlp_set_params", "hb_mlp_get_params", "hb_mlp_save", "hb_mlp_load", "hb_lowpass_pairs", "hb_mlp_train",
             "hb_mlp_gradient", "hb_mlp_forward", "hb_set_lowpass_mode", "hb_lowpass_stats", "hb_mlp_certify",
             "hb_server_create", "hb_server_destroy", "hb_stream_open", "hb_stream_close", "hb_submit", "hb_poll",
@@ -37,6 +38,7 @@ HB_FULL_GRID = 1 << 2
 HB_ILLUMINATION = 1 << 5
 HB_LOWPASS_INTENSITY = 1 << 6
 HB_LOWPASS_LS = 1 << 7
+HB_NODE_SUMS = 1 << 8
 HB_SERVE_SEQUENTIAL = 1 << 4
 MLP_NPARAMS = 4546
 HB_MODE_BAYES = 0
@@ -98,6 +100,7 @@ def load(path: str = LIB_PATH):
     lib.hb_timing_start.argtypes = [P, I]
     lib.hb_timing_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(L)]
     lib.hb_timing_nodes.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.hb_timing_rows.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong * 2)]
     lib.hb_strerror.argtypes = [I]
     lib.hb_strerror.restype = ctypes.c_char_p
     lib.hb_posterior_mean_static.argtypes = [ctypes.POINTER(_Mixing), ctypes.POINTER(_Grid), P, L, P, P]
@@ -402,6 +405,13 @@ class Context:
         v = ctypes.c_ulonglong(0)
         _check(load().hb_timing_nodes(self._h, ctypes.byref(v)), "hb_timing_nodes")
         return int(v.value)
+
+    def timing_rows(self, edge: bool = False) -> int:
+        """Grid rows the posterior summed in closed form since timing_start (edge: only those
+        the box edge cuts off); synchronises the device.  Their nodes are not in timing_nodes."""
+        v = (ctypes.c_ulonglong * 2)()
+        _check(load().hb_timing_rows(self._h, v), "hb_timing_rows")
+        return int(v[1] if edge else v[0])
 
     def timing_read(self) -> dict:
         ms = (ctypes.c_double * len(STAGES))()

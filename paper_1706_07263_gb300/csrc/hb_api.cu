@@ -79,7 +79,10 @@ struct hb_ctx {
     hb::MlpRoute route{};         // trust set while a certification holds for the parameters
     float* d_err = nullptr;       // per sampled pixel error of the stand-in (mlp_err_cap)
     int mlp_err_cap = 0;
-    unsigned long long* d_nodes = nullptr;  // grid nodes enumerated by timed posterior launches
+    unsigned long long* d_nodes = nullptr;  // timed posterior launches: [0] nodes summed one by one,
+                                            // [1] rows summed in closed form, [2] of those cut
+                                            // off by the box edge
+    float4* d_rowtab = nullptr;   // the closed-form row sums' table (BayesParams::row_tab)
     unsigned* d_lpwork = nullptr;  // fused low pass: a pair of counters per band index
     long mlp_frames = 0;
     unsigned frame_seq = 0;
@@ -328,6 +331,92 @@ void prepare_constants(const hb_mixing* mix, const hb_grid* grid, double lambda,
     for (int k = 0; k < 6; ++k) M[k] = holder.tp.M[k];
     bp = holder.bp;
 }
+
+namespace {
+// The one-sided row sum F(x) = sum_{k >= 0} 2^(cq (k - x)^2) by direct FP64 summation: log2 F,
+// its derivative, the mean column m(x) = sum k 2^(...) / F and its derivative
+// (d log2 F / dx = -2 cq (m - x), dm / dx = -2 cq ln 2 Var(k)).
+void one_sided_sum(double cq, double x, double& lf, double& dlf, double& m, double& dm) {
+    const double tmax = x < 0.0 ? cq * x * x : 0.0;  // the largest exponent, at k = 0 or near x
+    const long kmax = (long)(std::max(x, 0.0) + std::sqrt(120.0 / -cq)) + 2;  // later terms < 2^-120
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;  // moments about x
+    for (long k = 0; k <= kmax; ++k) {
+        const double e = (double)k - x;
+        const double w = std::exp2(cq * e * e - tmax);
+        s0 += w;
+        s1 += w * e;
+        s2 += w * e * e;
+    }
+    const double mean = s1 / s0;
+    lf = std::log2(s0) + tmax;
+    m = x + mean;
+    dlf = -2.0 * cq * mean;
+    dm = -2.0 * cq * std::log(2.0) * std::max(s2 / s0 - mean * mean, 0.0);
+}
+}  // namespace
+
+// The closed-form row sums' table (BayesParams::row_tab): over x in [-(hc + 4), hc + 4) (ends
+// rounded outwards to a whole step), hc = sqrt((span_cut + 2) / -Cq) the widest half-interval
+// of a row whose peak is at most the reference node's weight, cubic Hermite pieces of log2 F
+// and m.  The step starts at the power of two nearest below sigma / 16 (sigma = the row's
+// Gaussian width in columns, 1 / sqrt(-2 Cq ln 2); at most 1/8 of a column below sigma = 4)
+// and is halved, three times at most, until every piece agrees with the direct sums at
+// u = 1/4, 1/2, 3/4 (log2 F within 4e-6 + 1e-7 |log2 F|, m within 1e-5 columns + 1e-6 sigma,
+// with the FP32-rounded coefficients).
+// Sets bp's table fields except row_tab; false (no closed form) when the grid has no row
+// kernel, when the Poisson term 2 exp(-pi^2 / (-Cq ln 2)) exceeds 2e-13, when the table's
+// right end differs from the full sum, or when no step passes.
+bool row_table(BayesParams& bp, std::vector<float4>& tab) {
+    tab.clear();
+    if (!bp.rows_ok || !(bp.Cq < 0.f)) return false;
+    const double cq = (double)bp.Cq, a = -cq * std::log(2.0);
+    if (M_PI * M_PI / a < 30.0) return false;
+    const double hc = std::sqrt(((double)bp.span_cut + 2.0) / -cq);
+    const double x1 = hc + 4.0, x0 = -x1;
+    const double log2k = 0.5 * std::log2(M_PI / a);
+    {
+        double lf, dlf, m, dm;
+        one_sided_sum(cq, x1, lf, dlf, m, dm);
+        if (!(std::fabs(lf - log2k) <= 1e-9 && std::fabs(m - x1) <= 1e-7)) return false;
+    }
+    const double sigma = 1.0 / std::sqrt(2.0 * a);
+    const double s_start = std::exp2(std::floor(std::log2(sigma / 16.0)));
+    for (double s = s_start; s >= s_start / 8.0; s *= 0.5) {
+        const double xa = -std::ceil(-x0 / s) * s;  // a whole number of steps: exact in FP32
+        const int n = (int)std::ceil((x1 - xa) / s);
+        if (n > 8192) return false;
+        std::vector<double> lf(n + 1), dlf(n + 1), m(n + 1), dm(n + 1);
+        for (int k = 0; k <= n; ++k) one_sided_sum(cq, xa + k * s, lf[k], dlf[k], m[k], dm[k]);
+        tab.assign(2 * (size_t)n, float4{});
+        bool ok = true;
+        for (int k = 0; k < n && ok; ++k) {
+            auto cubic = [&](const std::vector<double>& f, const std::vector<double>& df) {
+                const double f0 = f[k], f1 = f[k + 1], d0 = s * df[k], d1 = s * df[k + 1];
+                return float4{(float)f0, (float)d0, (float)(3.0 * (f1 - f0) - 2.0 * d0 - d1),
+                              (float)(2.0 * (f0 - f1) + d0 + d1)};
+            };
+            const float4 p = cubic(lf, dlf), q = cubic(m, dm);
+            tab[2 * k] = p;
+            tab[2 * k + 1] = q;
+            for (double u : {0.25, 0.5, 0.75}) {
+                double elf, edlf, em, edm;
+                one_sided_sum(cq, xa + (k + u) * s, elf, edlf, em, edm);
+                const double ilf = p.x + u * (p.y + u * (p.z + u * (double)p.w));
+                const double im = q.x + u * (q.y + u * (q.z + u * (double)q.w));
+                if (!(std::fabs(ilf - elf) <= 4e-6 + 1e-7 * std::fabs(elf) && std::fabs(im - em) <= 1e-5 + 1e-6 * sigma))
+                    ok = false;
+            }
+        }
+        if (!ok) continue;
+        bp.tab_x0 = (float)xa;
+        bp.tab_inv_step = (float)(1.0 / s);
+        bp.tab_n = n;
+        bp.log2_kfull = (float)log2k;
+        return true;
+    }
+    tab.clear();
+    return false;
+}
 }  // namespace hb
 
 namespace {
@@ -508,7 +597,7 @@ hb_status hb_create(const hb_mixing* mix, const hb_grid* grid, int levels, doubl
     if (!mix || !grid) return HB_ERR_ARG;
     if (in_format != HB_IN_F32_HWC && in_format != HB_IN_U8_HWC) return HB_ERR_ARG;
     if (flags & ~(unsigned)(HB_LAMBDA_ABSOLUTE | HB_LOWPASS_TIKHONOV | HB_FULL_GRID | HB_ILLUMINATION |
-                            HB_LOWPASS_INTENSITY | HB_LOWPASS_LS))
+                            HB_LOWPASS_INTENSITY | HB_LOWPASS_LS | HB_NODE_SUMS))
         return HB_ERR_ARG;
     if ((flags & HB_LOWPASS_INTENSITY) && ((flags & HB_LOWPASS_TIKHONOV) || levels > 4)) return HB_ERR_ARG;
     if ((flags & HB_LOWPASS_LS) && (flags & HB_LOWPASS_TIKHONOV)) return HB_ERR_ARG;
@@ -567,6 +656,14 @@ hb_status hb_create(const hb_mixing* mix, const hb_grid* grid, int levels, doubl
     if (cudaMalloc(&c->d_lut, sizeof(lut)) != cudaSuccess) st = HB_ERR_OOM;
     if (st == HB_OK && cudaMemcpy(c->d_lut, lut, sizeof(lut), cudaMemcpyHostToDevice) != cudaSuccess) st = HB_ERR_CUDA;
     if (st == HB_OK) st = ensure_rec(c, c->npix_ll);
+    std::vector<float4> rowtab;
+    if (st == HB_OK && !(flags & HB_NODE_SUMS) && hb::row_table(c->bp, rowtab)) {
+        if (cudaMalloc(&c->d_rowtab, sizeof(float4) * rowtab.size()) != cudaSuccess) st = HB_ERR_OOM;
+        if (st == HB_OK && cudaMemcpy(c->d_rowtab, rowtab.data(), sizeof(float4) * rowtab.size(),
+                                      cudaMemcpyHostToDevice) != cudaSuccess)
+            st = HB_ERR_CUDA;
+        if (st == HB_OK) c->bp.row_tab = c->d_rowtab;
+    }
     if (st == HB_OK && (cudaMalloc(&c->d_lpwork, sizeof(unsigned) * 2 * kMaxBands) != cudaSuccess ||
                         cudaMemset(c->d_lpwork, 0, sizeof(unsigned) * 2 * kMaxBands) != cudaSuccess))
         st = HB_ERR_OOM;
@@ -599,6 +696,7 @@ void hb_destroy(hb_ctx* c) {
     cudaFree(c->d_route);
     cudaFree(c->d_trust);
     cudaFree(c->d_nodes);
+    cudaFree(c->d_rowtab);
     cudaFree(c->d_lpwork);
     cudaFree(c->d_frame);
     cudaFree(c->d_thb);
@@ -926,12 +1024,12 @@ hb_status hb_timing_start(hb_ctx* c, int max_launches) {
         c->ev.push_back(e);
     }
     c->ev_stage.assign(c->ev.size() / 2, -1);
-    if (!c->d_nodes && cudaMalloc(&c->d_nodes, sizeof(unsigned long long)) != cudaSuccess) {
+    if (!c->d_nodes && cudaMalloc(&c->d_nodes, 3 * sizeof(unsigned long long)) != cudaSuccess) {
         c->d_nodes = nullptr;
         cudaGetLastError();
         return HB_ERR_OOM;
     }
-    if (cudaMemset(c->d_nodes, 0, sizeof(unsigned long long)) != cudaSuccess) return HB_ERR_CUDA;
+    if (cudaMemset(c->d_nodes, 0, 3 * sizeof(unsigned long long)) != cudaSuccess) return HB_ERR_CUDA;
     c->ev_used = 0;
     c->timing = true;
     return HB_OK;
@@ -943,6 +1041,16 @@ hb_status hb_timing_nodes(hb_ctx* c, unsigned long long* nodes) {
     DeviceGuard g(c->device);
     if (cudaDeviceSynchronize() != cudaSuccess ||
         cudaMemcpy(nodes, c->d_nodes, sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HB_ERR_CUDA;
+    return HB_OK;
+}
+
+hb_status hb_timing_rows(hb_ctx* c, unsigned long long rows[2]) {
+    if (!c || !rows) return HB_ERR_ARG;
+    if (!c->timing || !c->d_nodes) return HB_ERR_STATE;
+    DeviceGuard g(c->device);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(rows, c->d_nodes + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess)
         return HB_ERR_CUDA;
     return HB_OK;
 }

@@ -487,18 +487,68 @@ __device__ __forceinline__ void row_span(const SpanPixel& sp, int di, int& na, i
     if (!(h2 >= 0.f) || nb < na) nb = na;
 }
 
+// The warp's counts, added (when counting) to counts[0] (nodes summed one by one), counts[1]
+// (rows summed in closed form) and counts[2] (of those, rows the box edge cuts off: the
+// table's one-sided sums); rows carries the last two as (edge rows << 32) + rows.
+__device__ __forceinline__ void flush_counts(unsigned long long* counts, unsigned long long nodes,
+                                             unsigned long long rows, int lane) {
+    if (!counts) return;
+    unsigned long long r = rows & 0xffffffffull, e = rows >> 32;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        nodes += __shfl_xor_sync(0xffffffffu, nodes, off);
+        r += __shfl_xor_sync(0xffffffffu, r, off);
+        e += __shfl_xor_sync(0xffffffffu, e, off);
+    }
+    if (lane == 0 && nodes) atomicAdd(counts, nodes);
+    if (lane == 0 && r) atomicAdd(counts + 1, r);
+    if (lane == 0 && e) atomicAdd(counts + 2, e);
+}
+
+// A row's sums in closed form (BayesParams::row_tab), for a row of the half-warp's pixel
+// whose cut interval [na, nb) the grid cuts off on at most one side: the row's base-2 log
+// weight along the columns is S + R dj + Cq dj^2, dj = j - j0.  Returns false (the row is
+// then summed node by node) when the row's peak lies further beyond the cut-off edge than
+// the table reaches.
+__device__ __forceinline__ bool row_closed(const BayesParams& bp, const BayesRec& rec, float R, float S, bool lclip,
+                                           bool rclip, float& rs, float& rm) {
+    const float js = R * bp.span_cv;          // the row's peak, in columns from j0
+    const float ts = fmaf(0.5f * R, js, S);   // its base-2 log weight t*
+    float lf = bp.log2_kfull, mc = js;        // log2 of (row sum / 2^t*), mean column - j0
+    if (lclip || rclip) {
+        const float edge = lclip ? (float)rec.j0 : (float)(bp.n1 - 1 - rec.j0);
+        const float x = lclip ? edge + js : edge - js;  // the peak's distance from the edge column
+        const float f = (x - bp.tab_x0) * bp.tab_inv_step;
+        if (!(f >= 0.f)) return false;
+        if (f < (float)bp.tab_n) {
+            const int k = (int)f;
+            const float u = f - (float)k;
+            const float4 p = __ldg(bp.row_tab + 2 * k), q = __ldg(bp.row_tab + 2 * k + 1);
+            lf = fmaf(u, fmaf(u, fmaf(u, p.w, p.z), p.y), p.x);
+            const float m = fmaf(u, fmaf(u, fmaf(u, q.w, q.z), q.y), q.x);  // mean, columns from the edge
+            mc = lclip ? m - edge : edge - m;
+        }
+    }
+    rs = ex2(ts + lf);
+    rm = mc * rs;
+    return true;
+}
+
 // The posterior mean of the half-warp's pixel (record rec) into chat[out] (and chat_scaled)
-// when valid; both half-warps of the warp call it together.
+// when valid; both half-warps of the warp call it together.  nodes counts the grid nodes
+// summed one by one, rows the rows summed in closed form plus 2^32 per such row that the box
+// edge cuts off.
 __device__ __forceinline__ void rows_pixel(const BayesParams& bp, const BayesRec& rec, bool valid, long out, int gl,
                                            float2* chat, float2* chat_scaled, float scale,
-                                           unsigned long long& nodes) {
+                                           unsigned long long& nodes, unsigned long long& rows) {
     constexpr int G = 16;
     const SpanPixel sp = span_pixel(bp, rec);
     const bool direct = sp.whole;  // summed over the whole grid below instead
+    const bool closed = bp.row_tab != nullptr;
     const int nslots = __reduce_max_sync(0xffffffffu, direct ? 0 : (sp.rhi - sp.rlo + G - 1) / G);
     const u64 QQ = pk(bp.row_q, bp.row_q), CC = pk(bp.Cq, bp.Cq);
     float sw = 0.f, sdi = 0.f, sdj = 0.f;
-    unsigned cnt = 0;
+    unsigned cnt = 0, rcnt = 0, ecnt = 0;
     for (int slot = 0; slot < nslots; ++slot) {
         const int i = sp.rlo + slot * G + gl;
         int na = 0, nb = 0;
@@ -511,79 +561,95 @@ __device__ __forceinline__ void rows_pixel(const BayesParams& bp, const BayesRec
         if (!__any_sync(0xffffffffu, live)) continue;
 #endif
         const bool lclip = na < 0, rclip = nb > bp.n1;
-        const bool full = live && lclip && rclip;
-        const bool back = live && rclip && !lclip;  // start at the right end, walk left
-        const bool any_full = __any_sync(0xffffffffu, full);
-        // steps: the warp's longest row; a lane with a full row takes only its own, and the
-        // grid's last column on its own when the row has an odd number of columns
-        const int len = live ? jb - ja : 0;
-        const int own = full ? (len >> 1) : ((len + 1) >> 1);
-        const int steps = __reduce_max_sync(0xffffffffu, own);
-        const bool extra = full && (len & 1);
         const float d = (float)(i - rec.i0);
         const float R = fmaf(2.f * bp.Bq, d, rec.V);
         const float S = d * fmaf(bp.Aq, d, rec.U);
-        const float dir = back ? -1.f : 1.f;
-        const float s0 = (float)((back ? jb - 1 : ja) - rec.j0);  // the first chain's first column
-        const u64 J = pk(s0, s0 + dir);
-        const u64 T = fma2(J, fma2(CC, J, pk(R, R)), pk(S, S));
-        // t(j + 2 dir) - t(j) = Cq (4 dir j + 4) + 2 dir R
-        const u64 D = fma2(CC, fma2(pk(4.f * dir, 4.f * dir), J, pk(4.f, 4.f)), pk(2.f * dir * R, 2.f * dir * R));
-        float t0, t1, d0, d1;
-        upk(T, t0, t1);
-        upk(D, d0, d1);
-        // a chain whose first weight would be below 2^-100 starts 2^sh higher and its sums are
-        // scaled back (a weight flushed to zero would stop the recurrence)
-        const float sh = live ? fmaxf(0.f, -100.f - fminf(t0, t1)) : 0.f;
-        u64 w = live ? pk(ex2(t0 + sh), ex2(t1 + sh)) : pk(0.f, 0.f);
-        u64 q = live ? pk(ex2(d0), ex2(d1)) : pk(0.f, 0.f);
-        u64 A = pk(0.f, 0.f), B = pk(0.f, 0.f);
-        if (!any_full) {
+        float rs = 0.f, rm = 0.f;
+        bool walk = live;  // summed node by node below
+        if (closed && live && !(lclip && rclip) && row_closed(bp, rec, R, S, lclip, rclip, rs, rm)) {
+            walk = false;
+            ++rcnt;
+            ecnt += (lclip || rclip) ? 1u : 0u;
+        }
+        if (__any_sync(0xffffffffu, walk)) {
+            const bool full = walk && lclip && rclip;
+            const bool back = walk && rclip && !lclip;  // start at the right end, walk left
+            const bool any_full = __any_sync(0xffffffffu, full);
+            // steps: the warp's longest row; a lane with a full row takes only its own, and the
+            // grid's last column on its own when the row has an odd number of columns
+            const int len = walk ? jb - ja : 0;
+            const int own = full ? (len >> 1) : ((len + 1) >> 1);
+            const int steps = __reduce_max_sync(0xffffffffu, own);
+            const bool extra = full && (len & 1);
+            const float dir = back ? -1.f : 1.f;
+            const float s0 = (float)((back ? jb - 1 : ja) - rec.j0);  // the first chain's first column
+            const u64 J = pk(s0, s0 + dir);
+            const u64 T = fma2(J, fma2(CC, J, pk(R, R)), pk(S, S));
+            // t(j + 2 dir) - t(j) = Cq (4 dir j + 4) + 2 dir R
+            const u64 D = fma2(CC, fma2(pk(4.f * dir, 4.f * dir), J, pk(4.f, 4.f)), pk(2.f * dir * R, 2.f * dir * R));
+            float t0, t1, d0, d1;
+            upk(T, t0, t1);
+            upk(D, d0, d1);
+            // a chain whose first weight would be below 2^-100 starts 2^sh higher and its sums are
+            // scaled back (a weight flushed to zero would stop the recurrence)
+            const float sh = walk ? fmaxf(0.f, -100.f - fminf(t0, t1)) : 0.f;
+            u64 w = walk ? pk(ex2(t0 + sh), ex2(t1 + sh)) : pk(0.f, 0.f);
+            u64 q = walk ? pk(ex2(d0), ex2(d1)) : pk(0.f, 0.f);
+            u64 A = pk(0.f, 0.f), B = pk(0.f, 0.f);
+            if (!any_full) {
 #pragma unroll 4
-            for (int st = 0; st < steps; ++st) {
-                A = add2(A, w);
-                B = add2(B, A);
-                w = mul2(w, q);
-                q = mul2(q, QQ);
-            }
-        } else {
-            for (int st = 0; st < steps; ++st) {
-                if (st < own) {
+                for (int st = 0; st < steps; ++st) {
                     A = add2(A, w);
                     B = add2(B, A);
                     w = mul2(w, q);
                     q = mul2(q, QQ);
                 }
+            } else {
+                for (int st = 0; st < steps; ++st) {
+                    if (st < own) {
+                        A = add2(A, w);
+                        B = add2(B, A);
+                        w = mul2(w, q);
+                        q = mul2(q, QQ);
+                    }
+                }
             }
-        }
-        if (sh > 0.f) {
-            const float u = ex2(-sh);
-            A = mul2(A, pk(u, u));
-            B = mul2(B, pk(u, u));
-        }
-        const int m = any_full ? own : steps;  // the steps this lane summed
-        float a0, a1, b0, b1;
-        upk(A, a0, a1);
-        upk(B, b0, b1);
-        const float fm = (float)m;
-        float rs = a0 + a1;
-        // chain c: sum w (j - j0) = (its first column) A + 2 dir (m A - B)
-        float rm = fmaf(s0, a0, fmaf(s0 + dir, a1, 2.f * dir * (fmaf(fm, a0, -b0) + fmaf(fm, a1, -b1))));
-        if (extra) {  // the grid's last column of an odd full row
-            const float jx = (float)(bp.n1 - 1 - rec.j0);
-            const float wx = ex2(fmaf(jx, fmaf(bp.Cq, jx, R), S));
-            rs += wx;
-            rm = fmaf(wx, jx, rm);
+            if (sh > 0.f) {
+                const float u = ex2(-sh);
+                A = mul2(A, pk(u, u));
+                B = mul2(B, pk(u, u));
+            }
+            const int m = any_full ? own : steps;  // the steps this lane summed
+            float a0, a1, b0, b1;
+            upk(A, a0, a1);
+            upk(B, b0, b1);
+            const float fm = (float)m;
+            float ws = a0 + a1;
+            // chain c: sum w (j - j0) = (its first column) A + 2 dir (m A - B)
+            float wm = fmaf(s0, a0, fmaf(s0 + dir, a1, 2.f * dir * (fmaf(fm, a0, -b0) + fmaf(fm, a1, -b1))));
+            if (extra) {  // the grid's last column of an odd full row
+                const float jx = (float)(bp.n1 - 1 - rec.j0);
+                const float wx = ex2(fmaf(jx, fmaf(bp.Cq, jx, R), S));
+                ws += wx;
+                wm = fmaf(wx, jx, wm);
+            }
+            if (walk) {
+                rs = ws;
+                rm = wm;
+                cnt += 2u * (unsigned)m + (extra ? 1u : 0u);
+            }
         }
         sw += rs;
         sdj += rm;
         sdi = fmaf(d, rs, sdi);
-        if (live) cnt += 2u * (unsigned)m + (extra ? 1u : 0u);
     }
     sw = group_sum<G>(sw);
     sdi = group_sum<G>(sdi);
     sdj = group_sum<G>(sdj);
-    if (valid) nodes += cnt;
+    if (valid) {
+        nodes += cnt;
+        rows += ((unsigned long long)ecnt << 32) + rcnt;
+    }
     const bool bad = direct || !usable(sw, sdi, sdj);
     if (__any_sync(0xffffffffu, bad)) {
         // the whole grid with an explicit maximum shift (the partner half-warp takes part in
@@ -620,7 +686,7 @@ __global__ void __launch_bounds__(kRowThreads, 3) posterior_rows_kernel(BayesPar
     asm volatile("griddepcontrol.launch_dependents;");
     const Pixels px = gated_pixels(gate, npix);
     const long rounds = (px.n + 1) / 2;
-    unsigned long long nodes = 0;
+    unsigned long long nodes = 0, rows = 0;
     auto next_round = [&]() {
         unsigned t = 0;
         if (lane == 0) t = atomicAdd(&ticket, 1u);
@@ -635,15 +701,11 @@ __global__ void __launch_bounds__(kRowThreads, 3) posterior_rows_kernel(BayesPar
         BayesRec rec1 = {0, 0, 0.f, 0.f};
         if (r1 < rounds) rec1 = load(r1);
         const long k = 2 * r0 + half;
-        rows_pixel(bp, rec0, k < px.n, k < px.n ? px.at(k) : 0, gl, chat, chat_scaled, scale, nodes);
+        rows_pixel(bp, rec0, k < px.n, k < px.n ? px.at(k) : 0, gl, chat, chat_scaled, scale, nodes, rows);
         r0 = r1;
         rec0 = rec1;
     }
-    if (nodes_out) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) nodes += __shfl_xor_sync(0xffffffffu, nodes, off);
-        if (lane == 0 && nodes) atomicAdd(nodes_out, nodes);
-    }
+    flush_counts(nodes_out, nodes, rows, lane);
 }
 
 // ---- Fused low pass: block means, posterior records and posterior means in one kernel ----
@@ -695,7 +757,7 @@ __global__ void __launch_bounds__(kFusedThreads, HB_FUSED_MINB)
     const int ux = (tp.wl * TH + 63) / 64;  // units per superblock band
     const unsigned nunits = (unsigned)ux * (unsigned)tp.hl;
     const FusedTickets tk = fused_tickets(nunits, gridDim.x * (kFusedThreads / 32), NR);
-    unsigned long long nodes = 0;
+    unsigned long long nodes = 0, rows = 0;
     for (;;) {
         unsigned tix = 0;
         if (lane == 0) tix = atomicAdd(&work[0], 1u);
@@ -734,14 +796,10 @@ __global__ void __launch_bounds__(kFusedThreads, HB_FUSED_MINB)
             rr.j0 = __shfl_sync(0xffffffffu, rec.j0, t);
             rr.U = __shfl_sync(0xffffffffu, rec.U, t);
             rr.V = __shfl_sync(0xffffffffu, rec.V, t);
-            rows_pixel(bp, rr, t < nsb, (long)by * tp.wl + sb0 + t, gl, chat, chat_scaled, scale, nodes);
+            rows_pixel(bp, rr, t < nsb, (long)by * tp.wl + sb0 + t, gl, chat, chat_scaled, scale, nodes, rows);
         }
     }
-    if (nodes_out) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) nodes += __shfl_xor_sync(0xffffffffu, nodes, off);
-        if (lane == 0 && nodes) atomicAdd(nodes_out, nodes);
-    }
+    flush_counts(nodes_out, nodes, rows, lane);
     // every warp of the CTA has seen the counter run out; the last CTA clears it
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <vector>
 #ifndef HB_NO_NVTX
 #include <nvtx3/nvToolsExt.h>
 #endif
@@ -101,6 +103,21 @@ struct BayesParams {
     float row_q;
     int rows_ok;
     int illum;                // 1: A holds (I - 11^T/3) A and the set-up removes ybar's channel mean
+    // Closed-form row sums of the row kernel (row_tab set; needs rows_ok).  Along row di the
+    // base-2 log weight is t* + Cq (j - mu)^2 (t* the row's maximum over real columns, mu its
+    // column), so over all integer columns the row's weights add up to 2^t* K with
+    // K = sum_j 2^(Cq (j - mu)^2) = sqrt(pi / (-Cq ln 2)) up to a relative 2 exp(-pi^2 / (-Cq ln 2))
+    // (Poisson summation; the host requires that term below 2e-13), and their mean column is mu.
+    // A row whose interval the grid cuts off on one side is the one-sided sum
+    // F(x) = sum_{k >= 0} 2^(Cq (k - x)^2), x = the peak's distance from the edge column, whose
+    // mean is m(x) columns from the edge: row_tab holds, per interval [x_k, x_k + 1/tab_inv_step)
+    // of x in [tab_x0, tab_x0 + tab_n / tab_inv_step), the cubic in u = (x - x_k) tab_inv_step of
+    // log2 F (float4 2k) and of m (float4 2k + 1), Hermite interpolants of direct FP64 sums,
+    // checked on the host against those sums.  Beyond the table's right end F = K and m = x.
+    const float4* row_tab;
+    float tab_x0, tab_inv_step;
+    int tab_n;
+    float log2_kfull;         // log2 K
 };
 
 // Where the analysis writes the least-squares low-pass estimates (c = nullptr: it writes the
@@ -165,6 +182,9 @@ cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long np
 // counters, zero before the launch and left at zero by it; launches that may run at the
 // same time need their own.
 bool lowpass_fused_ok(const TransformParams& tp, const BayesParams& bp);
+// The closed-form row sums' table for bp (host, FP64; BayesParams::row_tab): fills tab and bp's
+// table fields other than row_tab, or returns false when the closed form does not apply.
+bool row_table(BayesParams& bp, std::vector<float4>& tab);
 cudaError_t launch_lowpass_fused(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
                                  const float2* lut, float2* chat, float2* chat_scaled, float scale, unsigned* work,
                                  unsigned long long* nodes, bool pdl, cudaStream_t s);

@@ -114,6 +114,7 @@ struct hb_server {
     BayesParams bp{};
     float M[6] = {0};
     float2* d_lut = nullptr;
+    float4* d_rowtab = nullptr;  // the closed-form row sums' table (BayesParams::row_tab)
     size_t budget = 0, used = 0;
     int max_batch = 1;
     long cap_ll = 0;
@@ -350,7 +351,10 @@ hb_status hb_server_create(const hb_mixing* mix, const hb_grid* grid, double lam
     srv->ll_intensity = (flags & HB_LOWPASS_INTENSITY) ? 1 : 0;
     hb::prepare_constants(mix, grid, lambda, flags & (HB_LAMBDA_ABSOLUTE | HB_FULL_GRID | HB_ILLUMINATION), srv->M,
                           srv->bp);
-    const size_t need = (size_t)srv->nbatch_slots * batch_bytes(srv->cap_ll) + 256 * sizeof(float2);
+    std::vector<float4> rowtab;
+    if (!hb::row_table(srv->bp, rowtab)) rowtab.clear();
+    const size_t need =
+        (size_t)srv->nbatch_slots * batch_bytes(srv->cap_ll) + 256 * sizeof(float2) + sizeof(float4) * rowtab.size();
     if (need > budget_bytes) {
         delete srv;
         return HB_ERR_BUDGET;
@@ -363,6 +367,12 @@ hb_status hb_server_create(const hb_mixing* mix, const hb_grid* grid, double lam
     }
     bool ok = cudaMalloc(&srv->d_lut, sizeof(lut)) == cudaSuccess &&
               cudaMemcpy(srv->d_lut, lut, sizeof(lut), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok && !rowtab.empty()) {
+        ok = cudaMalloc(&srv->d_rowtab, sizeof(float4) * rowtab.size()) == cudaSuccess &&
+             cudaMemcpy(srv->d_rowtab, rowtab.data(), sizeof(float4) * rowtab.size(), cudaMemcpyHostToDevice) ==
+                 cudaSuccess;
+        if (ok) srv->bp.row_tab = srv->d_rowtab;
+    }
     for (int k = 0; ok && k < srv->nbatch_slots; ++k) {
         Batch& b = srv->batches[k];
         b.srv = srv;
@@ -418,6 +428,7 @@ void hb_server_destroy(hb_server* srv) {
         cudaFree(b.d_count);
     }
     cudaFree(srv->d_lut);
+    cudaFree(srv->d_rowtab);
     cudaGetLastError();
     if (prev >= 0) cudaSetDevice(prev);
     delete srv;

@@ -187,27 +187,32 @@ def _close_to_every_node(got_thb, got_so2, full_thb, full_so2):
 
 def test_support_bounds_leave_the_result_unchanged():
     """The posterior enumerates, per pixel, only the grid rows and in each row only the
-    column interval whose weights carry all but 2^-30 of the posterior mass; every output
-    agrees with enumerating the whole grid (HB_FULL_GRID) to a few FP32 roundings, and the
-    node counter shows the work saved."""
+    column interval whose weights carry all but 2^-30 of the posterior mass, and sums each
+    such row in closed form (or node by node with HB_NODE_SUMS); every output agrees with
+    enumerating the whole grid (HB_FULL_GRID) to a few FP32 roundings, and the node and row
+    counters show the work saved."""
     wl = synth.HD_1080
     mix, fr = synth.workload_inputs(wl)
     grid = synth.grid_spec(wl)
     frame = torch.from_numpy(fr.rgb).to(DEV)
-    outs, nodes = {}, {}
-    for flags in (0, binding.HB_FULL_GRID):
+    outs, nodes, rows = {}, {}, {}
+    for flags in (0, binding.HB_NODE_SUMS, binding.HB_FULL_GRID):
         with Context(mix.A, grid, wl.levels, wl.lam, wl.W, wl.H, wl.fmt, flags) as ctx:
             thb = torch.empty((wl.H, wl.W), dtype=torch.float32, device=DEV)
             so2 = torch.empty_like(thb)
             ctx.timing_start(4)
             ctx.estimate(frame, thb, so2)
-            nodes[flags] = ctx.timing_nodes()
+            nodes[flags], rows[flags] = ctx.timing_nodes(), ctx.timing_rows()
             ctx.timing_read()
             outs[flags] = (thb.cpu().numpy(), so2.cpu().numpy())
     hl, wl_ = (wl.H + 7) // 8, (wl.W + 7) // 8
-    assert nodes[binding.HB_FULL_GRID] == hl * wl_ * grid["n0"] * grid["n1"]
-    assert 0 < nodes[0] < 0.1 * nodes[binding.HB_FULL_GRID]
-    _close_to_every_node(*outs[0], *outs[binding.HB_FULL_GRID])
+    full = binding.HB_FULL_GRID
+    assert nodes[full] == hl * wl_ * grid["n0"] * grid["n1"] and rows[full] == 0
+    assert 0 < nodes[binding.HB_NODE_SUMS] < 0.1 * nodes[full] and rows[binding.HB_NODE_SUMS] == 0
+    # closed form: every live row of every pixel (a few dozen per pixel), no node summed one by one
+    assert nodes[0] == 0 and 10 * hl * wl_ < rows[0] < hl * wl_ * grid["n0"]
+    for flags in (0, binding.HB_NODE_SUMS):
+        _close_to_every_node(*outs[flags], *outs[full])
 
 
 @pytest.mark.parametrize("n0,n1,sigma", [(128, 128, 0.02), (96, 100, 0.005), (64, 16, 0.1), (150, 64, 0.05)])
@@ -223,15 +228,54 @@ def test_column_intervals_keep_every_weighted_node(n0, n1, sigma):
     c[:50] *= 40.0                                   # far outside the model
     yb = c @ A.T + rng.normal(0, 0.01, (n, 3))
     got = []
-    for flags in (0, binding.HB_FULL_GRID):
+    for flags in (0, binding.HB_NODE_SUMS, binding.HB_FULL_GRID):
         with Context(A, grid, 1, 1e-3, 8, 8, "u8", flags) as ctx:
             out = torch.empty((n, 2), dtype=torch.float32, device=DEV)
             ctx.posterior_mean(torch.from_numpy(yb).to(DEV), out)
             torch.cuda.synchronize()
             got.append(out.cpu().numpy().astype(np.float64))
-    assert np.all(np.isfinite(got[0]))
-    d = np.abs(got[0] - got[1])
-    assert np.all(d <= 2e-5 + 1e-6 * np.abs(got[1])), d.max()
+    for g in got[:2]:
+        assert np.all(np.isfinite(g))
+        d = np.abs(g - got[2])
+        assert np.all(d <= 2e-5 + 1e-6 * np.abs(got[2])), d.max()
+    pick = rng.choice(n, 1500, replace=False)
+    pick[:20] = np.arange(20)
+    ref = oracle.posterior_mean(yb[pick], A, grid, nthreads=NTH)
+    assert np.all(np.abs(got[0][pick] - ref) <= 2e-4 + 2e-6 * np.abs(ref))
+
+
+@pytest.mark.parametrize("hb_box,n1", [((0.0, 100.0), 128), ((0.0, 12.0), 24), ((-30.0, 130.0), 200)])
+def test_closed_form_rows_against_node_sums(hb_box, n1):
+    """Rows summed in closed form (inside the grid: the full-line sum; cut off by the box on
+    one side: the tabulated one-sided sum) beside rows summed node by node in the same warps
+    (cut off on both sides: a posterior wider than the Hb box; a peak beyond the table: far
+    outside the model): 40,000 pixels in and around the box against HB_NODE_SUMS, every node
+    (HB_FULL_GRID) and, on a sample, the oracle.  Both counters must show work, so both kinds
+    of row occur."""
+    rng = np.random.default_rng(n1)
+    A = synth.make_mixing(9).A
+    grid = _grid(128, n1, 0.02, lo1=hb_box[0], hi1=hb_box[1])
+    n = 40_000
+    span = hb_box[1] - hb_box[0]
+    c = np.stack([rng.uniform(-40, 190, n), rng.uniform(hb_box[0] - 0.4 * span, hb_box[1] + 0.4 * span, n)], axis=1)
+    c[:64] *= 40.0                                   # far outside the model
+    yb = c @ A.T + rng.normal(0, 0.01, (n, 3))
+    got, nodes, rows = [], [], []
+    for flags in (0, binding.HB_NODE_SUMS, binding.HB_FULL_GRID):
+        with Context(A, grid, 1, 1e-3, 8, 8, "u8", flags) as ctx:
+            out = torch.empty((n, 2), dtype=torch.float32, device=DEV)
+            ctx.timing_start(2)
+            ctx.posterior_mean(torch.from_numpy(yb).to(DEV), out)
+            nodes.append(ctx.timing_nodes())
+            rows.append(ctx.timing_rows())
+            ctx.timing_read()
+            got.append(out.cpu().numpy().astype(np.float64))
+    assert rows[0] > 0 and nodes[0] > 0, (rows[0], nodes[0])
+    assert rows[1] == 0 and rows[2] == 0
+    for g in got[:2]:
+        assert np.all(np.isfinite(g))
+        d = np.abs(g - got[2])
+        assert np.all(d <= 2e-5 + 1e-6 * np.abs(got[2])), d.max()
     pick = rng.choice(n, 1500, replace=False)
     pick[:20] = np.arange(20)
     ref = oracle.posterior_mean(yb[pick], A, grid, nthreads=NTH)

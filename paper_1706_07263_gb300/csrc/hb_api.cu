@@ -83,7 +83,6 @@ struct hb_ctx {
                                             // [1] rows summed in closed form, [2] of those cut
                                             // off by the box edge
     float4* d_rowtab = nullptr;   // the closed-form row sums' table (BayesParams::row_tab)
-    unsigned* d_lpwork = nullptr;  // fused low pass: a pair of counters per band index
     long mlp_frames = 0;
     unsigned frame_seq = 0;
     // hb_estimate_host: copy streams and per-band events (created on first use)
@@ -491,11 +490,9 @@ struct Band {
     TransformParams tp;
     long ll_off;
     long npix;
-    int index;  // bands that may run at the same time have different indices (< kMaxBands)
 };
-constexpr int kMaxBands = 8;
 
-Band whole_frame(const hb_ctx* c) { return Band{c->tp, 0, c->npix_ll, 0}; }
+Band whole_frame(const hb_ctx* c) { return Band{c->tp, 0, c->npix_ll}; }
 
 // chain: the frame is already on the device and the analysis may be launched as a
 // programmatic dependent of whatever kernel precedes it on the stream (it waits for that
@@ -517,7 +514,7 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
         // block means, records and posterior means in one launch
         StageTimer t(c, s, HB_STAGE_LOWPASS);
         e = hb::launch_lowpass_fused(b.tp, c->bp, frame, stride, c->d_lut, chat, conc_scaled, scale,
-                                     c->d_lpwork + 2 * b.index, c->timing ? c->d_nodes : nullptr, pdl && chain, s);
+                                     c->timing ? c->d_nodes : nullptr, pdl && chain, s);
         c->launches++;
         if (e != cudaSuccess) return HB_ERR_CUDA;
     } else if (lowpass) {
@@ -664,9 +661,6 @@ hb_status hb_create(const hb_mixing* mix, const hb_grid* grid, int levels, doubl
             st = HB_ERR_CUDA;
         if (st == HB_OK) c->bp.row_tab = c->d_rowtab;
     }
-    if (st == HB_OK && (cudaMalloc(&c->d_lpwork, sizeof(unsigned) * 2 * kMaxBands) != cudaSuccess ||
-                        cudaMemset(c->d_lpwork, 0, sizeof(unsigned) * 2 * kMaxBands) != cudaSuccess))
-        st = HB_ERR_OOM;
     if (st != HB_OK) {
         cudaGetLastError();
         hb_destroy(c);
@@ -697,7 +691,6 @@ void hb_destroy(hb_ctx* c) {
     cudaFree(c->d_trust);
     cudaFree(c->d_nodes);
     cudaFree(c->d_rowtab);
-    cudaFree(c->d_lpwork);
     cudaFree(c->d_frame);
     cudaFree(c->d_thb);
     cudaFree(c->d_so2);
@@ -777,7 +770,6 @@ hb_status enqueue_host_bands(hb_ctx* c, const void* frame_host, size_t row_strid
         b.tp.hl = b1 - b0;
         b.ll_off = (long)b0 * c->wl;
         b.npix = (long)(b1 - b0) * c->wl;
-        b.index = k;
         const size_t o = (size_t)r0 * c->W, n = (size_t)(r1 - r0) * c->W;
         // alternate bands between two compute streams: neighbouring bands share no data, and
         // one band's kernels fill the ramp and tail of the other's

@@ -5,9 +5,11 @@
 // Five kernels, all with persistent warps:
 //   lowpass_fused_kernel   block means, posterior records and posterior means in one launch
 //                          (1..3 levels where the row kernel applies: the default path);
-//   posterior_rows_kernel  two pixels per warp over precomputed records; per pixel the rows
-//                          of the cut, each over its exact column interval, weights by a
-//                          ratio recurrence (the default when the records are given);
+//   posterior_rows_kernel  over precomputed records (the default when the records are given):
+//                          per pixel the rows of the cut, each summed in closed form (eight
+//                          pixels per warp, four lanes each: group_pixel) or, with
+//                          HB_NODE_SUMS, node by node over its exact column interval by a
+//                          ratio recurrence (two pixels per warp: rows_pixel);
 //   posterior_span_kernel  two pixels per warp; per pixel the 16-column segments of each
 //                          row that meet the row's column interval (grids the recurrence
 //                          does not suit);
@@ -670,29 +672,110 @@ __device__ __forceinline__ void rows_pixel(const BayesParams& bp, const BayesRec
     if (valid && gl == 0) write_mean(bp, rec, out, sw, sdi, sdj, chat, chat_scaled, scale);
 }
 
+// ---- Closed-form rows: G = 4 lanes per pixel ----
+//
+// With the closed-form row sums (BayesParams::row_tab) a row costs a few dozen instructions,
+// so the warp-wide steps of rows_pixel (every lane running the longest row) are no longer
+// needed: a group of kGroup lanes takes a pixel, lane g of the group the rows rlo + g,
+// rlo + g + kGroup, ... of span_pixel, each lane on its own (rows whose interval misses the
+// grid's columns are passed over).  Rows cut off on both sides, or whose peak lies beyond the
+// table, are summed node by node with one ex2 per node.  The group's sums are added by
+// shuffles in a fixed order, so a pixel's result depends only on its record: the fused
+// kernel and posterior_rows_kernel give the same bits.
+constexpr int kGroup = 4;
+constexpr int kGroupPixels = 32 / kGroup;  // pixels per warp
+
+__device__ __forceinline__ void group_pixel(const BayesParams& bp, const BayesRec& rec, bool valid, long out, int gl,
+                                            float2* chat, float2* chat_scaled, float scale,
+                                            unsigned long long& nodes, unsigned long long& rows) {
+    constexpr int G = kGroup;
+    const SpanPixel sp = span_pixel(bp, rec);
+    float sw = 0.f, sdi = 0.f, sdj = 0.f;
+    unsigned cnt = 0, rcnt = 0, ecnt = 0;
+    if (valid && !sp.whole) {
+        for (int i = sp.rlo + gl; i < sp.rhi; i += G) {
+            int na, nb;
+            row_span(sp, i - rec.i0, na, nb);
+            const int ja = max(na, 0), jb = min(nb, bp.n1);  // clipped to the grid
+            if (jb <= ja) continue;                           // the row misses the grid's columns
+            const bool lclip = na < 0, rclip = nb > bp.n1;
+            const float d = (float)(i - rec.i0);
+            const float R = fmaf(2.f * bp.Bq, d, rec.V);
+            const float S = d * fmaf(bp.Aq, d, rec.U);
+            float rs, rm;
+            if (!(lclip && rclip) && row_closed(bp, rec, R, S, lclip, rclip, rs, rm)) {
+                ++rcnt;
+                ecnt += (lclip || rclip) ? 1u : 0u;
+            } else {
+                rs = 0.f;
+                rm = 0.f;
+                for (int j = ja; j < jb; ++j) {
+                    const float dj = (float)(j - rec.j0);
+                    const float w = ex2(fmaf(dj, fmaf(bp.Cq, dj, R), S));
+                    rs += w;
+                    rm = fmaf(w, dj, rm);
+                }
+                cnt += (unsigned)(jb - ja);
+            }
+            sw += rs;
+            sdj += rm;
+            sdi = fmaf(d, rs, sdi);
+        }
+    }
+    sw = group_sum<G>(sw);
+    sdi = group_sum<G>(sdi);
+    sdj = group_sum<G>(sdj);
+    if (valid) {
+        nodes += cnt;
+        rows += ((unsigned long long)ecnt << 32) + rcnt;
+    }
+    const bool bad = valid && (sp.whole || !usable(sw, sdi, sdj));
+    if (__any_sync(0xffffffffu, bad)) {
+        // the whole grid with an explicit maximum shift (the other groups take part in the
+        // shuffles and keep their own sums)
+        const float mx = group_max<G>(grid_max<1, G>(bp, rec, gl, 0, bp.n0));
+        float fw = 0.f, fdi = 0.f, fdj = 0.f;
+        grid_sums<1, G>(bp, rec, gl, 0, bp.n0, bad ? mx : 0.f, fw, fdi, fdj);
+        fw = group_sum<G>(fw);
+        fdi = group_sum<G>(fdi);
+        fdj = group_sum<G>(fdj);
+        if (bad) {
+            sw = fw;
+            sdi = fdi;
+            sdj = fdj;
+            if (gl == 0) nodes += (unsigned long long)bp.n0 * (unsigned)bp.n1;
+        }
+    }
+    if (valid && gl == 0) write_mean(bp, rec, out, sw, sdi, sdj, chat, chat_scaled, scale);
+}
+
 // Two pixels per warp (half-warp h takes pixel 2r + h of round r), rounds dealt as in
 // posterior_pair_kernel.
+template <bool CLOSED>
 __global__ void __launch_bounds__(kRowThreads, 3) posterior_rows_kernel(BayesParams bp,
                                                                        const BayesRec* __restrict__ recs, long npix,
                                                                        float2* __restrict__ chat,
                                                                        float2* __restrict__ chat_scaled, float scale,
                                                                        PosteriorGate gate,
                                                                        unsigned long long* nodes_out) {
-    const int lane = threadIdx.x & 31, gl = lane & 15, half = lane >> 4;
+    // pixels per warp and round: two (a half-warp each) node by node, eight (kGroup lanes
+    // each) with the closed-form rows
+    constexpr int PPW = CLOSED ? kGroupPixels : 2, G = 32 / PPW;
+    const int lane = threadIdx.x & 31, gl = lane % G, half = lane / G;
     __shared__ unsigned ticket;
     if (threadIdx.x == 0) ticket = 0u;
     __syncthreads();
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     const Pixels px = gated_pixels(gate, npix);
-    const long rounds = (px.n + 1) / 2;
+    const long rounds = (px.n + PPW - 1) / PPW;
     unsigned long long nodes = 0, rows = 0;
     auto next_round = [&]() {
         unsigned t = 0;
         if (lane == 0) t = atomicAdd(&ticket, 1u);
         return (long)blockIdx.x + (long)__shfl_sync(0xffffffffu, t, 0) * gridDim.x;
     };
-    auto load = [&](long rr) { return recs[px.at(min(2 * rr + half, px.n - 1))]; };
+    auto load = [&](long rr) { return recs[px.at(min(PPW * rr + half, px.n - 1))]; };
     long r0 = next_round();
     BayesRec rec0 = {0, 0, 0.f, 0.f};
     if (r0 < rounds) rec0 = load(r0);
@@ -700,8 +783,11 @@ __global__ void __launch_bounds__(kRowThreads, 3) posterior_rows_kernel(BayesPar
         const long r1 = next_round();
         BayesRec rec1 = {0, 0, 0.f, 0.f};
         if (r1 < rounds) rec1 = load(r1);
-        const long k = 2 * r0 + half;
-        rows_pixel(bp, rec0, k < px.n, k < px.n ? px.at(k) : 0, gl, chat, chat_scaled, scale, nodes, rows);
+        const long k = PPW * r0 + half;
+        if constexpr (CLOSED)
+            group_pixel(bp, rec0, k < px.n, k < px.n ? px.at(k) : 0, gl, chat, chat_scaled, scale, nodes, rows);
+        else
+            rows_pixel(bp, rec0, k < px.n, k < px.n ? px.at(k) : 0, gl, chat, chat_scaled, scale, nodes, rows);
         r0 = r1;
         rec0 = rec1;
     }
@@ -711,14 +797,14 @@ __global__ void __launch_bounds__(kRowThreads, 3) posterior_rows_kernel(BayesPar
 // ---- Fused low pass: block means, posterior records and posterior means in one kernel ----
 //
 // For 1..3 levels with the row kernel's bounds.  A unit is one warp's strip of the frame:
-// 64 pixel columns of one superblock band (64 / 2^n superblocks).  Warps take units from a
-// counter; for each, the warp forms the superblocks' block means by the strip analysis (the
-// same code as the analysis kernel), computes their posterior records on lanes 0 .. 64/2^n
-// - 1 (bayes_setup), and then the posterior means two superblocks at a time (rows_pixel),
-// so a superblock's record never leaves the warp and the frame's loads overlap other warps'
-// posterior sums.  work[0] counts the tickets taken and work[1] the CTAs that are done; the
-// last CTA to finish sets both back to zero for the next launch (which, on the same stream,
-// starts after this one has completed).
+// 64 pixel columns of one superblock band (64 / 2^n superblocks).  Warp w of the W warps of
+// the launch takes tickets w, w + W, w + 2W, ... (no counter: a global ticket counter cost
+// 2.3 us of the 1080p frame's 22.9, its same-address atomics serialising in L2); for each,
+// the warp forms the superblocks' block means by the strip analysis (the same code as the
+// analysis kernel), computes their posterior records on lanes 0 .. 64/2^n - 1
+// (bayes_setup), and then the posterior means two superblocks at a time (rows_pixel) or,
+// with the closed-form rows, eight at a time (group_pixel), so a superblock's record never
+// leaves the warp and the frame's loads overlap other warps' posterior sums.
 //
 // Tail.  With U units over W warps, U mod W units are left once every warp has taken its
 // share of whole units; dealt whole, they would keep that many warps busy for a whole unit
@@ -745,24 +831,24 @@ __device__ __forceinline__ FusedTickets fused_tickets(unsigned nunits, unsigned 
     return FusedTickets{nunits - tail, p, nunits - tail + tail * p};
 }
 
-template <int L>
+template <int L, bool CLOSED>
 __global__ void __launch_bounds__(kFusedThreads, HB_FUSED_MINB)
     lowpass_fused_kernel(TransformParams tp, BayesParams bp, const unsigned char* __restrict__ frame, size_t stride,
                          const float2* __restrict__ lut, float2* __restrict__ chat, float2* __restrict__ chat_scaled,
-                         float scale, unsigned* __restrict__ work, unsigned long long* nodes_out) {
-    constexpr int TH = 1 << L, NSB = 64 / TH, NR = NSB / 2;
-    const int lane = threadIdx.x & 31, gl = lane & 15, half = lane >> 4;
+                         float scale, unsigned long long* nodes_out) {
+    // rounds per unit: superblocks two at a time (rows_pixel) or, with the closed-form rows,
+    // eight at a time (group_pixel)
+    constexpr int TH = 1 << L, NSB = 64 / TH, PPR = CLOSED ? kGroupPixels : 2, NR = (NSB + PPR - 1) / PPR;
+    constexpr int G = 32 / PPR;
+    const int lane = threadIdx.x & 31, gl = lane % G, half = lane / G;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     const int ux = (tp.wl * TH + 63) / 64;  // units per superblock band
     const unsigned nunits = (unsigned)ux * (unsigned)tp.hl;
     const FusedTickets tk = fused_tickets(nunits, gridDim.x * (kFusedThreads / 32), NR);
     unsigned long long nodes = 0, rows = 0;
-    for (;;) {
-        unsigned tix = 0;
-        if (lane == 0) tix = atomicAdd(&work[0], 1u);
-        tix = __shfl_sync(0xffffffffu, tix, 0);
-        if (tix >= tk.total) break;
+    const unsigned nwarps = gridDim.x * (kFusedThreads / 32);
+    for (unsigned tix = blockIdx.x * (kFusedThreads / 32) + (threadIdx.x >> 5); tix < tk.total; tix += nwarps) {
         // ticket -> unit and its rounds [k0, k1)
         unsigned u = tix;
         int k0 = 0, k1 = NR;
@@ -789,27 +875,20 @@ __global__ void __launch_bounds__(kFusedThreads, HB_FUSED_MINB)
         const int sb0 = x0w / TH, nsb = min(NSB, tp.wl - sb0);  // superblocks of this unit
         BayesRec rec = {0, 0, 0.f, 0.f};
         if (lane < nsb) rec = bayes_setup(yhi, ylo, bp);
-        for (int k = k0; k < k1 && 2 * k < nsb; ++k) {
-            const int t = 2 * k + half;
+        for (int k = k0; k < k1 && PPR * k < nsb; ++k) {
+            const int t = PPR * k + half;
             BayesRec rr;
             rr.i0 = __shfl_sync(0xffffffffu, rec.i0, t);
             rr.j0 = __shfl_sync(0xffffffffu, rec.j0, t);
             rr.U = __shfl_sync(0xffffffffu, rec.U, t);
             rr.V = __shfl_sync(0xffffffffu, rec.V, t);
-            rows_pixel(bp, rr, t < nsb, (long)by * tp.wl + sb0 + t, gl, chat, chat_scaled, scale, nodes, rows);
+            if constexpr (CLOSED)
+                group_pixel(bp, rr, t < nsb, (long)by * tp.wl + sb0 + t, gl, chat, chat_scaled, scale, nodes, rows);
+            else
+                rows_pixel(bp, rr, t < nsb, (long)by * tp.wl + sb0 + t, gl, chat, chat_scaled, scale, nodes, rows);
         }
     }
     flush_counts(nodes_out, nodes, rows, lane);
-    // every warp of the CTA has seen the counter run out; the last CTA clears it
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&work[1], 1u) == gridDim.x - 1u) {
-            __threadfence();
-            work[0] = 0u;
-            work[1] = 0u;
-        }
-    }
 }
 
 // Resident CTAs per SM for a kernel (cached per device and kernel) and the SM count.
@@ -926,12 +1005,15 @@ cudaError_t launch_rows(const BayesParams& bp, const BayesRec* rec, long npix, c
                         float2* chat, float2* chat_scaled, float scale, bool pdl, const PosteriorGate& gate,
                         cudaStream_t s) {
     int resident = 0, sms = 0;
-    cudaError_t e = residency(posterior_rows_kernel, resident, sms, kRowThreads);
+    const bool closed = bp.row_tab != nullptr;
+    auto kernel = closed ? posterior_rows_kernel<true> : posterior_rows_kernel<false>;
+    cudaError_t e = residency(kernel, resident, sms, kRowThreads);
     if (e != cudaSuccess) return e;
     if (resident > kRowCtasPerSm) resident = kRowCtasPerSm;
     const long warps = (long)sms * resident * (kRowThreads / 32);
     if (npix < 2 * warps) return cudaErrorNotReady;
-    const long rounds = (npix + 1) / 2;
+    const int ppw = closed ? kGroupPixels : 2;
+    const long rounds = (npix + ppw - 1) / ppw;
     long blocks = (rounds + kRowThreads / 32 - 1) / (kRowThreads / 32);
     // at most kRowCtasPerSm CTAs per SM (resident above), leaving room beside them for CTAs
     // of the synthesis launched as its programmatic dependent (its transform runs before it
@@ -946,7 +1028,7 @@ cudaError_t launch_rows(const BayesParams& bp, const BayesRec* rec, long npix, c
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, posterior_rows_kernel, bp, rec, npix, chat, chat_scaled, scale, gate, sc.nodes);
+    return cudaLaunchKernelEx(&cfg, kernel, bp, rec, npix, chat, chat_scaled, scale, gate, sc.nodes);
 }
 
 bool uses_rows(const BayesParams& bp) {
@@ -971,7 +1053,8 @@ bool posterior_uses_pairs(const BayesParams& bp, long npix) {
     int resident = 0, sms = 0;
     cudaError_t e;
     if (uses_rows(bp)) {
-        e = residency(posterior_rows_kernel, resident, sms, kRowThreads);
+        e = residency(bp.row_tab ? posterior_rows_kernel<true> : posterior_rows_kernel<false>, resident, sms,
+                      kRowThreads);
         if (resident > kRowCtasPerSm) resident = kRowCtasPerSm;
         return e == cudaSuccess && npix >= 2L * sms * resident * (kRowThreads / 32);
     }
@@ -1005,15 +1088,17 @@ bool lowpass_fused_ok(const TransformParams& tp, const BayesParams& bp) {
 }
 
 cudaError_t launch_lowpass_fused(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
-                                 const float2* lut, float2* chat, float2* chat_scaled, float scale, unsigned* work,
+                                 const float2* lut, float2* chat, float2* chat_scaled, float scale,
                                  unsigned long long* nodes, bool pdl, cudaStream_t s) {
     int resident = 0, sms = 0;
-    cudaError_t e;
-    switch (tp.levels) {
-        case 1: e = residency(lowpass_fused_kernel<1>, resident, sms, kFusedThreads); break;
-        case 2: e = residency(lowpass_fused_kernel<2>, resident, sms, kFusedThreads); break;
-        default: e = residency(lowpass_fused_kernel<3>, resident, sms, kFusedThreads); break;
-    }
+    const bool closed = bp.row_tab != nullptr;
+    auto kernel = closed ? (tp.levels == 1 ? lowpass_fused_kernel<1, true>
+                            : tp.levels == 2 ? lowpass_fused_kernel<2, true>
+                                             : lowpass_fused_kernel<3, true>)
+                         : (tp.levels == 1 ? lowpass_fused_kernel<1, false>
+                            : tp.levels == 2 ? lowpass_fused_kernel<2, false>
+                                             : lowpass_fused_kernel<3, false>);
+    cudaError_t e = residency(kernel, resident, sms, kFusedThreads);
     if (e != cudaSuccess) return e;
     const long units = (long)((tp.wl * (1 << tp.levels) + 63) / 64) * tp.hl;
     long blocks = (units + kFusedThreads / 32 - 1) / (kFusedThreads / 32);
@@ -1028,11 +1113,7 @@ cudaError_t launch_lowpass_fused(const TransformParams& tp, const BayesParams& b
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     const unsigned char* f = static_cast<const unsigned char*>(frame);
-    switch (tp.levels) {
-        case 1: return cudaLaunchKernelEx(&cfg, lowpass_fused_kernel<1>, tp, bp, f, stride, lut, chat, chat_scaled, scale, work, nodes);
-        case 2: return cudaLaunchKernelEx(&cfg, lowpass_fused_kernel<2>, tp, bp, f, stride, lut, chat, chat_scaled, scale, work, nodes);
-        default: return cudaLaunchKernelEx(&cfg, lowpass_fused_kernel<3>, tp, bp, f, stride, lut, chat, chat_scaled, scale, work, nodes);
-    }
+    return cudaLaunchKernelEx(&cfg, kernel, tp, bp, f, stride, lut, chat, chat_scaled, scale, nodes);
 }
 
 cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long npix, const PosteriorScratch& sc,

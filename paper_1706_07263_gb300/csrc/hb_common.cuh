@@ -178,15 +178,13 @@ cudaError_t launch_posterior(const BayesParams& bp, const BayesRec* rec, long np
                              float2* chat, float2* chat_scaled, float scale, bool pdl, cudaStream_t s,
                              const PosteriorGate& gate = PosteriorGate{nullptr});
 // The fused low pass (block means, posterior records and posterior means in one launch, for
-// the plain grid posterior at 1..3 levels): whether it applies, and its launch.  work: two
-// counters, zero before the launch and left at zero by it; launches that may run at the
-// same time need their own.
+// the plain grid posterior at 1..3 levels): whether it applies, and its launch.
 bool lowpass_fused_ok(const TransformParams& tp, const BayesParams& bp);
 // The closed-form row sums' table for bp (host, FP64; BayesParams::row_tab): fills tab and bp's
 // table fields other than row_tab, or returns false when the closed form does not apply.
 bool row_table(BayesParams& bp, std::vector<float4>& tab);
 cudaError_t launch_lowpass_fused(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
-                                 const float2* lut, float2* chat, float2* chat_scaled, float scale, unsigned* work,
+                                 const float2* lut, float2* chat, float2* chat_scaled, float scale,
                                  unsigned long long* nodes, bool pdl, cudaStream_t s);
 // Whether launch_posterior takes npix pixels with the kernel it uses for large launches (two
 // pixels per warp: the span kernel, or the pair kernel without column intervals); each

@@ -741,31 +741,41 @@ def run_ours(args):
     barrier()
     e2e_s, e2e_frames = replicas.aggregate(time.perf_counter() - t0, args.steps, device=dev)
 
-    # roofline of the dominant kernel: the low-pass launch (the fused kernel: block means,
-    # posterior records and the grid posterior).  Its work is the FP32 arithmetic of the
-    # posterior's sums, from its own counters: each grid row of the cut ellipse summed in
-    # closed form (FP32_OPS_PER_ROW, plus FP32_OPS_PER_EDGE_ROW where the box edge cuts the
-    # row off and the one-sided sum comes from the table) and each node of a row summed one
-    # by one (FP32_OPS_PER_NODE: the ratio recurrence); the per-pixel set-up and the strip
-    # analysis are not counted.  peak = SMs x 128 FP32 lanes per clock x the SM clock limit.
-    # The whole grid's node count is reported beside the fraction as a grid-equivalent
-    # throughput.
-    post_ms, post_n = stage["lowpass"]
-    post_avg_s = post_ms / max(post_n, 1) * 1e-3
-    nodes_grid = hl * wl_ * wl.grid[0] * wl.grid[1]
-    nodes = nodes_enumerated / max(post_n, 1)
-    rows_c, rows_e = rows_closed / max(post_n, 1), rows_edge / max(post_n, 1)
-    ops = FP32_OPS_PER_ROW * rows_c + FP32_OPS_PER_EDGE_ROW * rows_e + FP32_OPS_PER_NODE * nodes
-    ex2_clk, sms = binding.measure_ex2_rate()
-    sm_mhz = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
-    peak = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
-    achieved = ops / post_avg_s / 1e12
-    hbm = measured_peaks().get("hbm_gbs")
+    # roofline of the dominant kernel.  With the single-pass frame kernel (every step of the
+    # path in one launch) that is the frame kernel, bound by HBM: its algorithmic bytes are
+    # the frame read once, THb and SO2 written once and the low-pass means (8 bytes per
+    # superblock), against the measured copy bandwidth.  Beside it, the posterior's FP32
+    # arithmetic from the kernel's own counters: each grid row of the cut ellipse summed in
+    # closed form (FP32_OPS_PER_ROW, plus FP32_OPS_PER_EDGE_ROW where the box edge cuts the row
+    # off and the one-sided sum comes from the table) and each node of a row summed one by one
+    # (FP32_OPS_PER_NODE: the ratio recurrence), against SMs x 128 FP32 lanes per clock x the
+    # SM clock limit.  Without the frame kernel the low-pass launch is the dominant one and
+    # the FP32 figure is its roofline.
     npix_ll = hl * wl_
     fused = not stage.get("analysis", (0, 0))[1]   # no separate analysis launch
     stage_bytes = {"analysis": H * W * 3 + npix_ll * 16,
                    "lowpass": (H * W * 3 + npix_ll * 8) if fused else npix_ll * (16 + 8),
-                   "synthesis": H * W * 3 + npix_ll * 8 + H * W * 8}
+                   "synthesis": H * W * 3 + npix_ll * 8 + H * W * 8,
+                   "frame": H * W * 3 + npix_ll * 8 + H * W * 8}
+    single = stage.get("frame", (0, 0))[1] > 0
+    dom_ms, dom_n = stage["frame" if single else "lowpass"]
+    dom_avg_s = dom_ms / max(dom_n, 1) * 1e-3
+    nodes_grid = hl * wl_ * wl.grid[0] * wl.grid[1]
+    nodes = nodes_enumerated / max(dom_n, 1)
+    rows_c, rows_e = rows_closed / max(dom_n, 1), rows_edge / max(dom_n, 1)
+    ops = FP32_OPS_PER_ROW * rows_c + FP32_OPS_PER_EDGE_ROW * rows_e + FP32_OPS_PER_NODE * nodes
+    ex2_clk, sms = binding.measure_ex2_rate()
+    sm_mhz = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    fp32_peak = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    fp32 = {"achieved": ops / dom_avg_s / 1e12, "peak": fp32_peak, "unit": "T FP32 op/s",
+            "frac": ops / dom_avg_s / 1e12 / fp32_peak,
+            "units": f"FP32 operations of the posterior's sums per launch ({ops:.4g}): {rows_c:.6g} grid rows of "
+                     f"the cut ellipse summed in closed form at {FP32_OPS_PER_ROW} each, {rows_e:.6g} of them cut "
+                     f"off by the box edge at {FP32_OPS_PER_EDGE_ROW} more, and {nodes:.6g} nodes summed one by "
+                     f"one at {FP32_OPS_PER_NODE}",
+            "peak_method": f"{sms} SMs (device attribute) x {FP32_LANES_PER_SM} FP32 lanes/clk x "
+                           f"{sm_mhz:.0f} MHz (SM clock limit)"}
+    hbm = measured_peaks().get("hbm_gbs")
     stages = {}
     for k, v in stage.items():
         if not v[1]:
@@ -775,6 +785,28 @@ def run_ours(args):
                      "gb_per_s": stage_bytes[k] / (t * 1e-3) / 1e9}
         if hbm:
             stages[k]["frac_of_hbm"] = stages[k]["gb_per_s"] / hbm
+    common = {"traffic": kernel_counters(), "issue": issue_roofline(dom_avg_s, sms, sm_mhz),
+              "ex2": {"per_clk_per_sm": ex2_clk, "peak_tex2_per_s": sms * ex2_clk * sm_mhz * 1e6 / 1e12,
+                      "note": "measured in this process (hb_measure_ex2_rate); the posterior takes one ex2 per "
+                              "grid row, so the MUFU pipe does not bind it"},
+              "timing": "CUDA events around each launch of the kernel, K more steps after the timed region",
+              "grid_equivalent": {"nodes_per_launch": nodes_grid,
+                                  "throughput": nodes_grid / dom_avg_s / 1e12, "unit": "Tnode/s",
+                                  "note": "every node of the 128x128 grid for every low-pass pixel over the "
+                                          "same launch time: a throughput, not a fraction of any peak"}}
+    if single:
+        gbs = stage_bytes["frame"] / dom_avg_s / 1e9
+        roofline = {"bound": "hbm", "kernel": "frame_kernel<3> (log-attenuation, Haar analysis, Tikhonov, grid "
+                                              "posterior, inverse Haar, THb/SO2 in one launch)",
+                    "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm if hbm else None,
+                    "units": f"algorithmic bytes per launch ({stage_bytes['frame']}): the u8 frame read once, THb "
+                             "and SO2 written once, the low-pass means (8 B per superblock)",
+                    "peak_method": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "posterior_fp32": fp32}
+    else:
+        roofline = dict(fp32, bound="alu", kernel="lowpass_fused_kernel<3> (block means, posterior records, grid "
+                                                  "posterior mean)" if fused else "posterior_rows_kernel")
+    roofline.update(common)
     latency = measure_latency(ctx, frame, thb, so2, flush, stream, args.latency_frames)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -784,25 +816,7 @@ def run_ours(args):
         "latency_ms": latency,
         "megapixels_per_s": value * W * H / 1e6,
         "stages": stages,
-        "roofline": {"bound": "alu", "kernel": "lowpass_fused_kernel<3> (block means, posterior records, grid "
-                                               "posterior mean)" if fused else "posterior_rows_kernel",
-                     "achieved": achieved, "peak": peak, "unit": "T FP32 op/s", "frac": achieved / peak,
-                     "units": f"FP32 operations of the posterior's sums per launch ({ops:.4g}): {rows_c:.6g} grid "
-                              f"rows of the cut ellipse summed in closed form at {FP32_OPS_PER_ROW} each, "
-                              f"{rows_e:.6g} of them cut off by the box edge at {FP32_OPS_PER_EDGE_ROW} more, and "
-                              f"{nodes:.6g} nodes summed one by one at {FP32_OPS_PER_NODE}",
-                     "traffic": kernel_counters(),
-                     "issue": issue_roofline(post_avg_s, sms, sm_mhz),
-                     "peak_method": f"{sms} SMs (device attribute) x {FP32_LANES_PER_SM} FP32 lanes/clk x "
-                                    f"{sm_mhz:.0f} MHz (SM clock limit)",
-                     "ex2": {"per_clk_per_sm": ex2_clk, "peak_tex2_per_s": sms * ex2_clk * sm_mhz * 1e6 / 1e12,
-                             "note": "measured in this process (hb_measure_ex2_rate); the kernel takes one ex2 "
-                                     "per row, so the MUFU pipe does not bind it"},
-                     "timing": "CUDA events around each low-pass launch, K more steps after the timed region",
-                     "grid_equivalent": {"nodes_per_launch": nodes_grid,
-                                         "throughput": nodes_grid / post_avg_s / 1e12, "unit": "Tnode/s",
-                                         "note": "every node of the 128x128 grid for every low-pass pixel over the "
-                                                 "same launch time: a throughput, not a fraction of any peak"}},
+        "roofline": roofline,
         "e2e": {"value": e2e_frames / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W * 3,
                 "d2h_bytes_per_step": 2 * H * W * 4,
                 "api": "hb_estimate_host_async, K frames queued back to back, one synchronisation",

@@ -113,7 +113,9 @@ enum {
 };
 
 /* Per-stage timing slots reported by hb_timing_read. */
-enum { HB_STAGE_ANALYSIS = 0, HB_STAGE_LOWPASS = 1, HB_STAGE_SYNTHESIS = 2, HB_NUM_STAGES = 3 };
+/* HB_STAGE_FRAME: the single-pass frame kernel (all steps in one launch: the default for the
+ * plain posterior at 1..3 levels where the rows are summed in closed form). */
+enum { HB_STAGE_ANALYSIS = 0, HB_STAGE_LOWPASS = 1, HB_STAGE_SYNTHESIS = 2, HB_STAGE_FRAME = 3, HB_NUM_STAGES = 4 };
 
 /* Create a context for frames of width x height pixels.
  *   mix, grid  : copied; grid must have n0, n1 >= 1, hi >= lo, sigma_l > 0.

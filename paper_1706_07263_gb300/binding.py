@@ -19,7 +19,7 @@ HB_IN_F32_HWC = 0
 HB_IN_U8_HWC = 1
 HB_LAMBDA_ABSOLUTE = 1 << 0
 HB_LOWPASS_TIKHONOV = 1 << 1
-STAGES = ("analysis", "lowpass", "synthesis")
+STAGES = ("analysis", "lowpass", "synthesis", "frame")
 
 STATUS = {0: "HB_OK", 1: "HB_ERR_ARG", 2: "HB_ERR_SHAPE", 3: "HB_ERR_CUDA", 4: "HB_ERR_OOM", 5: "HB_ERR_BUDGET",
           6: "HB_ERR_TIMEOUT", 7: "HB_ERR_STATE", 8: "HB_ERR_IO"}

@@ -439,7 +439,7 @@ hb::PosteriorScratch post_scratch(const hb_ctx* c, long ll_off = 0) {
 }
 
 // Event bracket around one launch when timing is armed.
-const char* const kStageNames[HB_NUM_STAGES] = {"hb.analysis", "hb.lowpass", "hb.synthesis"};
+const char* const kStageNames[HB_NUM_STAGES] = {"hb.analysis", "hb.lowpass", "hb.synthesis", "hb.frame"};
 
 struct StageTimer {
     hb_ctx* c;
@@ -510,6 +510,14 @@ hb_status run_band(hb_ctx* c, const Band& b, const void* frame, size_t stride, d
     BayesRec* rec = c->d_rec + b.ll_off;
     float2* chat = c->d_chat + b.ll_off;
     const float scale = (float)(1 << c->levels);
+    if (bayes && !mlp && !ybar && out0 && out1 && hb::frame_kernel_ok(b.tp, c->bp)) {
+        // every step in one launch
+        StageTimer t(c, s, HB_STAGE_FRAME);
+        e = hb::launch_frame(b.tp, c->bp, frame, stride, c->d_lut, chat, conc_scaled, scale, out0, out1, debug,
+                             c->timing ? c->d_nodes : nullptr, pdl && chain, s);
+        c->launches++;
+        return e == cudaSuccess ? HB_OK : HB_ERR_CUDA;
+    }
     if (bayes && !mlp && !ybar && hb::lowpass_fused_ok(b.tp, c->bp)) {
         // block means, records and posterior means in one launch
         StageTimer t(c, s, HB_STAGE_LOWPASS);

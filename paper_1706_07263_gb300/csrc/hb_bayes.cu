@@ -71,13 +71,22 @@ __device__ __forceinline__ Pixels gated_pixels(const PosteriorGate& g, long npix
 }
 
 // Posterior mean from the sums, in FP32 (the output is FP32): c = c_ref + h * (sum w d / sum w).
+// The posterior mean (HbO2, Hb) from the sums relative to the reference node.
+__device__ __forceinline__ float2 posterior_mean(const BayesParams& bp, const BayesRec& rec, float sw, float sdi,
+                                                 float sdj) {
+    const float inv = __frcp_rn(sw);
+    return make_float2(fmaf(bp.h0f, sdi * inv, fmaf((float)rec.i0, bp.h0f, bp.lo0f)),
+                       fmaf(bp.h1f, sdj * inv, fmaf((float)rec.j0, bp.h1f, bp.lo1f)));
+}
+
+__device__ __forceinline__ void store_mean(long p, float2 c, float2* chat, float2* chat_scaled, float scale) {
+    chat[p] = c;
+    if (chat_scaled) chat_scaled[p] = make_float2(c.x * scale, c.y * scale);
+}
+
 __device__ __forceinline__ void write_mean(const BayesParams& bp, const BayesRec& rec, long p, float sw, float sdi,
                                            float sdj, float2* chat, float2* chat_scaled, float scale) {
-    const float inv = __frcp_rn(sw);
-    const float c0 = fmaf(bp.h0f, sdi * inv, fmaf((float)rec.i0, bp.h0f, bp.lo0f));
-    const float c1 = fmaf(bp.h1f, sdj * inv, fmaf((float)rec.j0, bp.h1f, bp.lo1f));
-    chat[p] = make_float2(c0, c1);
-    if (chat_scaled) chat_scaled[p] = make_float2(c0 * scale, c1 * scale);
+    store_mean(p, posterior_mean(bp, rec, sw, sdi, sdj), chat, chat_scaled, scale);
 }
 
 // One unit: the sums over its rows, then either the pixel's result (rs == 1) or its
@@ -685,12 +694,16 @@ __device__ __forceinline__ void rows_pixel(const BayesParams& bp, const BayesRec
 constexpr int kGroup = 4;
 constexpr int kGroupPixels = 32 / kGroup;  // pixels per warp
 
-__device__ __forceinline__ void group_pixel(const BayesParams& bp, const BayesRec& rec, bool valid, long out, int gl,
-                                            float2* chat, float2* chat_scaled, float scale,
-                                            unsigned long long& nodes, unsigned long long& rows) {
+// The sums of the group's pixel (the same bits in every lane of the group); every lane of
+// the warp calls it together.
+__device__ __forceinline__ void group_sums(const BayesParams& bp, const BayesRec& rec, bool valid, int gl, float& sw,
+                                           float& sdi, float& sdj, unsigned long long& nodes,
+                                           unsigned long long& rows) {
     constexpr int G = kGroup;
     const SpanPixel sp = span_pixel(bp, rec);
-    float sw = 0.f, sdi = 0.f, sdj = 0.f;
+    sw = 0.f;
+    sdi = 0.f;
+    sdj = 0.f;
     unsigned cnt = 0, rcnt = 0, ecnt = 0;
     if (valid && !sp.whole) {
         for (int i = sp.rlo + gl; i < sp.rhi; i += G) {
@@ -746,6 +759,13 @@ __device__ __forceinline__ void group_pixel(const BayesParams& bp, const BayesRe
             if (gl == 0) nodes += (unsigned long long)bp.n0 * (unsigned)bp.n1;
         }
     }
+}
+
+__device__ __forceinline__ void group_pixel(const BayesParams& bp, const BayesRec& rec, bool valid, long out, int gl,
+                                            float2* chat, float2* chat_scaled, float scale,
+                                            unsigned long long& nodes, unsigned long long& rows) {
+    float sw, sdi, sdj;
+    group_sums(bp, rec, valid, gl, sw, sdi, sdj, nodes, rows);
     if (valid && gl == 0) write_mean(bp, rec, out, sw, sdi, sdj, chat, chat_scaled, scale);
 }
 
@@ -887,6 +907,94 @@ __global__ void __launch_bounds__(kFusedThreads, HB_FUSED_MINB)
             else
                 rows_pixel(bp, rr, t < nsb, (long)by * tp.wl + sb0 + t, gl, chat, chat_scaled, scale, nodes, rows);
         }
+    }
+    flush_counts(nodes_out, nodes, rows, lane);
+}
+
+// ---- One launch per frame: every step of the path for a strip in one warp ----
+//
+// For the plain posterior at 1..3 levels with the closed-form rows.  A warp takes a strip
+// (64 pixel columns of one superblock band: 64 / 2^n superblocks) and, in registers:
+// log-attenuation and the forward Haar levels (strip_load, strip_analysis); the Tikhonov
+// operator on the directional coefficients (strip_tikhonov); the superblocks' block means
+// and posterior records (bayes_setup on lanes 0 .. 64/2^n - 1); their posterior means eight
+// at a time, four lanes each (group_sums); the inverse levels (strip_synthesis) with each
+// superblock's mean as its low pass; THb and SO2 (strip_store).  A superblock's synthesis
+// needs only its own mean, so no step waits for another warp: the frame is read once and
+// nothing but the outputs (and the means, 8 bytes per superblock) is written.  For 3 levels
+// a superblock's columns are the lanes of the group that computes its mean; for 1 and 2
+// levels the means reach their lanes by shuffles.  The arithmetic is that of the separate
+// analysis, posterior and synthesis kernels, so the outputs are the same bits.  Warp w of W
+// takes strips w, w + W, ...
+#ifndef HB_FRAME_MINB
+#define HB_FRAME_MINB 3
+#endif
+
+template <int L>
+__global__ void __launch_bounds__(kFusedThreads, HB_FRAME_MINB)
+    frame_kernel(TransformParams tp, BayesParams bp, const unsigned char* __restrict__ frame, size_t stride,
+                 const float2* __restrict__ lut, float2* __restrict__ chat, float2* __restrict__ chat_scaled,
+                 float scale, float* __restrict__ out0, float* __restrict__ out1, int debug_conc,
+                 unsigned long long* nodes_out) {
+    constexpr int TH = 1 << L, NSB = 64 / TH, SBL = TH / 2;  // superblocks per strip, lanes per superblock
+    constexpr int NR = NSB / kGroupPixels;                   // rounds of eight superblocks
+    const int lane = threadIdx.x & 31, gl = lane % kGroup, grp = lane / kGroup, mine_sb = lane / SBL;
+    // the frame (and the output buffers) may be written by the kernel before this one
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int ux = (tp.wl * TH + 63) / 64;  // strips per superblock band
+    const unsigned nunits = (unsigned)ux * (unsigned)tp.hl;
+    const unsigned nwarps = gridDim.x * (kFusedThreads / 32);
+    unsigned long long nodes = 0, rows = 0;
+    for (unsigned u = blockIdx.x * (kFusedThreads / 32) + (threadIdx.x >> 5); u < nunits; u += nwarps) {
+        const int by = (int)(u / (unsigned)ux), x0w = (int)(u % (unsigned)ux) * 64, x = x0w + 2 * lane;
+        float c[2][TH][2];
+        float yhi[3], ylo[3];
+        {
+            float v[3][TH][2];
+            float2 yref[3];
+            strip_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
+            strip_analysis<L, 3, false>(v, lane);
+            // superblock t's sum sits in lane t * 2^(n-1): lane t < NSB gathers it
+            const int src = (lane * SBL) & 31;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float sum = __shfl_sync(0xffffffffu, v[ch][0][0], src);
+                yhi[ch] = __shfl_sync(0xffffffffu, yref[ch].x, src);
+                ylo[ch] = fmaf(sum, 1.f / (float)(TH * TH), __shfl_sync(0xffffffffu, yref[ch].y, src));
+            }
+            strip_tikhonov<L>(tp, v, lane, c);
+        }
+        const int sb0 = x0w / TH, nsb = min(NSB, tp.wl - sb0);  // superblocks of this strip
+        BayesRec rec = {0, 0, 0.f, 0.f};
+        if (lane < nsb) rec = bayes_setup(yhi, ylo, bp);
+        float2 mean = make_float2(0.f, 0.f);  // the posterior mean of this lane's superblock
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            if (kGroupPixels * k >= nsb) break;
+            const int t = kGroupPixels * k + grp;
+            BayesRec rr;
+            rr.i0 = __shfl_sync(0xffffffffu, rec.i0, t);
+            rr.j0 = __shfl_sync(0xffffffffu, rec.j0, t);
+            rr.U = __shfl_sync(0xffffffffu, rec.U, t);
+            rr.V = __shfl_sync(0xffffffffu, rec.V, t);
+            float sw, sdi, sdj;
+            group_sums(bp, rr, t < nsb, gl, sw, sdi, sdj, nodes, rows);
+            float2 m = make_float2(0.f, 0.f);
+            if (t < nsb) {
+                m = posterior_mean(bp, rr, sw, sdi, sdj);
+                if (gl == 0) store_mean((long)by * tp.wl + sb0 + t, m, chat, chat_scaled, scale);
+            }
+            if constexpr (SBL == kGroup) {  // 3 levels: the group's lanes are the superblock's
+                mean = m;
+            } else {
+                const int from = kGroup * (mine_sb % kGroupPixels);
+                const float mx = __shfl_sync(0xffffffffu, m.x, from), my = __shfl_sync(0xffffffffu, m.y, from);
+                if (mine_sb / kGroupPixels == k) mean = make_float2(mx, my);
+            }
+        }
+        strip_synthesis<L>(c, lane);
+        strip_store<L>(tp, c, mean.x, mean.y, x, by, out0, out1, debug_conc);
     }
     flush_counts(nodes_out, nodes, rows, lane);
 }
@@ -1085,6 +1193,38 @@ bool lowpass_fused_ok(const TransformParams& tp, const BayesParams& bp) {
     return tp.levels >= 1 && tp.levels <= 3 && !tp.ll_intensity && uses_rows(bp) &&
            posterior_uses_pairs(bp, (long)tp.hl * tp.wl);
 #endif
+}
+
+bool frame_kernel_ok(const TransformParams& tp, const BayesParams& bp) {
+#ifdef HB_NO_FRAME_KERNEL
+    return false;
+#else
+    return bp.row_tab != nullptr && !tp.tikhonov_lowpass && lowpass_fused_ok(tp, bp);
+#endif
+}
+
+cudaError_t launch_frame(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
+                         const float2* lut, float2* chat, float2* chat_scaled, float scale, float* out0, float* out1,
+                         int debug_conc, unsigned long long* nodes, bool pdl, cudaStream_t s) {
+    int resident = 0, sms = 0;
+    auto kernel = tp.levels == 1 ? frame_kernel<1> : tp.levels == 2 ? frame_kernel<2> : frame_kernel<3>;
+    cudaError_t e = residency(kernel, resident, sms, kFusedThreads);
+    if (e != cudaSuccess) return e;
+    const long units = (long)((tp.wl * (1 << tp.levels) + 63) / 64) * tp.hl;
+    long blocks = (units + kFusedThreads / 32 - 1) / (kFusedThreads / 32);
+    if (blocks > (long)sms * resident) blocks = (long)sms * resident;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kFusedThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const unsigned char* f = static_cast<const unsigned char*>(frame);
+    return cudaLaunchKernelEx(&cfg, kernel, tp, bp, f, stride, lut, chat, chat_scaled, scale, out0, out1, debug_conc,
+                              nodes);
 }
 
 cudaError_t launch_lowpass_fused(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,

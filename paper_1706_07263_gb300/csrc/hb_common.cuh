@@ -186,6 +186,13 @@ bool row_table(BayesParams& bp, std::vector<float4>& tab);
 cudaError_t launch_lowpass_fused(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
                                  const float2* lut, float2* chat, float2* chat_scaled, float scale,
                                  unsigned long long* nodes, bool pdl, cudaStream_t s);
+// The single-pass frame kernel (every step of the path in one launch, for the plain grid
+// posterior at 1..3 levels with the closed-form rows): whether it applies, and its launch.
+// chat (and chat_scaled, if set) receive the low-pass posterior means as a by-product.
+bool frame_kernel_ok(const TransformParams& tp, const BayesParams& bp);
+cudaError_t launch_frame(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,
+                         const float2* lut, float2* chat, float2* chat_scaled, float scale, float* out0, float* out1,
+                         int debug_conc, unsigned long long* nodes, bool pdl, cudaStream_t s);
 // Whether launch_posterior takes npix pixels with the kernel it uses for large launches (two
 // pixels per warp: the span kernel, or the pair kernel without column intervals); each
 // pixel's result then does not depend on the other pixels of the launch.

@@ -174,5 +174,88 @@ __device__ __forceinline__ int strip_slot_level(int r, int lane, int L) {
     return 0;
 }
 
+
+// The Tikhonov operator (Eq. 5) on the unscaled forward coefficients v (three channels) into
+// c (HbO2, Hb): level-1 coefficients (odd rows, second column) with M / 4; the first
+// column's even rows by their level (the low pass: 0, or M 4^-L in the all-Tikhonov mode).
+template <int L>
+__device__ __forceinline__ void strip_tikhonov(const TransformParams& tp, const float (&v)[3][1 << L][2], int lane,
+                                               float (&c)[2][1 << L][2]) {
+    constexpr int TH = 1 << L;
+    const float* M = tp.M;
+#pragma unroll
+    for (int r = 0; r < TH; ++r)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float v0 = v[0][r][k], v1 = v[1][r][k], v2 = v[2][r][k];
+            float sc = 0.25f;
+            if (k == 0 && (r & 1) == 0) {
+                const int lv = strip_slot_level(r, lane, L);
+                // 4^-lv exactly; the low pass (lv = 0) keeps 4^-L only in the all-Tikhonov mode
+                sc = lv ? __int_as_float((127 - 2 * lv) << 23)
+                        : (tp.tikhonov_lowpass ? 1.f / (float)(TH * TH) : 0.f);
+            }
+            c[0][r][k] = sc * fmaf(M[0], v0, fmaf(M[1], v1, M[2] * v2));
+            c[1][r][k] = sc * fmaf(M[3], v0, fmaf(M[4], v1, M[5] * v2));
+        }
+}
+
+// All-Tikhonov mode: the superblock's reference log-attenuation (subtracted before the
+// transform) through M, added back after the inverse.
+__device__ __forceinline__ void strip_tikhonov_offset(const TransformParams& tp, const float2 (&yref)[3], float& off0,
+                                                      float& off1) {
+    const float* M = tp.M;
+    off0 = (M[0] * yref[0].x + M[1] * yref[1].x + M[2] * yref[2].x) +
+           (M[0] * yref[0].y + M[1] * yref[1].y + M[2] * yref[2].y);
+    off1 = (M[3] * yref[0].x + M[4] * yref[1].x + M[5] * yref[2].x) +
+           (M[3] * yref[0].y + M[4] * yref[1].y + M[5] * yref[2].y);
+}
+
+// The lane's two pixel columns x, x + 1 of superblock band by after the inverse transform:
+// HbO2 = c[0] + off0, Hb = c[1] + off1 (the low pass enters as the offsets: its inverse is the
+// block mean broadcast over the superblock), stored as THb and SO2 (SO2 = 0 where THb <= 0)
+// or, with debug_conc, as HbO2 and Hb.  Columns and rows beyond the frame are not stored.
+template <int L>
+__device__ __forceinline__ void strip_store(const TransformParams& tp, const float (&c)[2][1 << L][2], float off0,
+                                            float off1, int x, int by, float* __restrict__ out0,
+                                            float* __restrict__ out1, int debug_conc) {
+    constexpr int TH = 1 << L;
+    if (x >= tp.W) return;
+    const bool pair = x + 1 < tp.W;
+    const bool vec = pair && ((tp.W & 1) == 0);  // 8-byte aligned pairs of outputs
+#pragma unroll
+    for (int r = 0; r < TH; ++r) {
+        const int gy = by * TH + r;
+        if (gy >= tp.H) break;
+        float a0, a1, b0, b1;
+        const float h0 = c[0][r][0] + off0, h1 = c[0][r][1] + off0;  // HbO2
+        const float g0 = c[1][r][0] + off1, g1 = c[1][r][1] + off1;  // Hb
+        if (debug_conc) {
+            a0 = h0;
+            a1 = h1;
+            b0 = g0;
+            b1 = g1;
+        } else {
+            a0 = h0 + g0;
+            a1 = h1 + g1;
+            // SO2 needs 1e-3 absolute: the fast reciprocal-based division (2 ulp) is plenty
+            b0 = a0 >= 1.17549435e-38f ? __fdividef(h0, a0) : (a0 > 0.f ? h0 / a0 : 0.f);
+            b1 = a1 >= 1.17549435e-38f ? __fdividef(h1, a1) : (a1 > 0.f ? h1 / a1 : 0.f);
+        }
+        const size_t o = (size_t)gy * tp.W + x;
+        if (vec) {
+            *reinterpret_cast<float2*>(out0 + o) = make_float2(a0, a1);
+            *reinterpret_cast<float2*>(out1 + o) = make_float2(b0, b1);
+        } else {
+            out0[o] = a0;
+            out1[o] = b0;
+            if (pair) {
+                out0[o + 1] = a1;
+                out1[o + 1] = b1;
+            }
+        }
+    }
+}
+
 }  // namespace
 }  // namespace hb

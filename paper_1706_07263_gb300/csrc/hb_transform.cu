@@ -683,33 +683,12 @@ __device__ __forceinline__ void synthesis_strip_tile(const TransformParams& tp,
     float2 yref[3];
     strip_load<L>(tp, frame, stride, lut, by, x, lane, v, yref);
     strip_analysis<L, 3, false>(v, lane);
-    // Tikhonov operator: level-1 coefficients (odd rows, second column) with M / 4; the
-    // first column's even rows by their level (the low pass: 0, or M 4^-L in the
-    // all-Tikhonov mode)
     float c[2][TH][2];
-    const float* M = tp.M;
-#pragma unroll
-    for (int r = 0; r < TH; ++r)
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const float v0 = v[0][r][k], v1 = v[1][r][k], v2 = v[2][r][k];
-            float sc = 0.25f;
-            if (k == 0 && (r & 1) == 0) {
-                const int lv = strip_slot_level(r, lane, L);
-                // 4^-lv exactly; the low pass (lv = 0) keeps 4^-L only in the all-Tikhonov mode
-                sc = lv ? __int_as_float((127 - 2 * lv) << 23)
-                        : (tp.tikhonov_lowpass ? 1.f / (float)(TH * TH) : 0.f);
-            }
-            c[0][r][k] = sc * fmaf(M[0], v0, fmaf(M[1], v1, M[2] * v2));
-            c[1][r][k] = sc * fmaf(M[3], v0, fmaf(M[4], v1, M[5] * v2));
-        }
+    strip_tikhonov<L>(tp, v, lane, c);
     strip_synthesis<L>(c, lane);
     float off0, off1;
     if (tp.tikhonov_lowpass) {
-        off0 = (M[0] * yref[0].x + M[1] * yref[1].x + M[2] * yref[2].x) +
-               (M[0] * yref[0].y + M[1] * yref[1].y + M[2] * yref[2].y);
-        off1 = (M[3] * yref[0].x + M[4] * yref[1].x + M[5] * yref[2].x) +
-               (M[3] * yref[0].y + M[4] * yref[1].y + M[5] * yref[2].y);
+        strip_tikhonov_offset(tp, yref, off0, off1);
     } else {
         // everything above is independent of the posterior step; wait for it here
         asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -717,41 +696,7 @@ __device__ __forceinline__ void synthesis_strip_tile(const TransformParams& tp,
         off0 = ch.x;
         off1 = ch.y;
     }
-    if (x >= tp.W) return;
-    const bool pair = x + 1 < tp.W;
-    const bool vec = pair && ((tp.W & 1) == 0);  // 8-byte aligned pairs of outputs
-#pragma unroll
-    for (int r = 0; r < TH; ++r) {
-        const int gy = by * TH + r;
-        if (gy >= tp.H) break;
-        float a0, a1, b0, b1;
-        const float h0 = c[0][r][0] + off0, h1 = c[0][r][1] + off0;  // HbO2
-        const float g0 = c[1][r][0] + off1, g1 = c[1][r][1] + off1;  // Hb
-        if (debug_conc) {
-            a0 = h0;
-            a1 = h1;
-            b0 = g0;
-            b1 = g1;
-        } else {
-            a0 = h0 + g0;
-            a1 = h1 + g1;
-            // SO2 needs 1e-3 absolute: the fast reciprocal-based division (2 ulp) is plenty
-            b0 = a0 >= 1.17549435e-38f ? __fdividef(h0, a0) : (a0 > 0.f ? h0 / a0 : 0.f);
-            b1 = a1 >= 1.17549435e-38f ? __fdividef(h1, a1) : (a1 > 0.f ? h1 / a1 : 0.f);
-        }
-        const size_t o = (size_t)gy * tp.W + x;
-        if (vec) {
-            *reinterpret_cast<float2*>(out0 + o) = make_float2(a0, a1);
-            *reinterpret_cast<float2*>(out1 + o) = make_float2(b0, b1);
-        } else {
-            out0[o] = a0;
-            out1[o] = b0;
-            if (pair) {
-                out0[o + 1] = a1;
-                out1[o + 1] = b1;
-            }
-        }
-    }
+    strip_store<L>(tp, c, off0, off1, x, by, out0, out1, debug_conc);
 }
 
 template <int L>

@@ -396,11 +396,13 @@ hb_status hb_measure_ex2_rate(double *ex2_per_clock_per_sm, int *sm_count);
  * whose host application owns all device memory through its own pool, and
  * embedded deployments that must know their whole device footprint up front.
  *
- * Computes what hb_posterior_mean computes for a context created with flags 0 (any
+ * Computes what hb_posterior_mean computes for a context created with HB_NODE_SUMS (any
  * lambda: the posterior does not use it) -- the posterior mean of (HbO2, Hb) for each
- * of npix rows of ybar_dev, 3 doubles each, written as 2 floats each to conc_dev --
- * up to the order of FP32 additions, but takes the mixing model and grid directly
- * instead of a context.  The flags that change the posterior (HB_ILLUMINATION,
+ * of npix rows of ybar_dev, 3 doubles each, written as 2 floats each to conc_dev, every
+ * grid row summed node by node -- up to the order of FP32 additions, but takes the mixing
+ * model and grid directly instead of a context.  A context created with flags 0 sums the
+ * rows in closed form where the grid allows it; the two agree to a few FP32 roundings
+ * (about 1e-5 relative).  The flags that change the posterior (HB_ILLUMINATION,
  * HB_FULL_GRID) have no counterpart here.  Its working memory is one fixed array
  * compiled into libhb.so (about 4.3 MiB per GPU, held from library load until process
  * exit).

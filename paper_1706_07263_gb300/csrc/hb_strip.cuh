@@ -34,25 +34,46 @@ __device__ __forceinline__ void strip_load(const TransformParams& tp, const unsi
     const int xa = min(x0, tp.W - 1), xb = min(x0 + 1, tp.W - 1);
     const int src_lane = lane & ~((TH >> 1) - 1);  // the superblock's first lane
     if (tp.fmt == 1) {
-        int k[3][TH][2];
+        // The lane's six bytes per row (two pixels, x0 even) start at byte 3 x0, 2-byte aligned.
+        // With 4-byte aligned rows they lie in the two 32-bit words from (3 x0) & ~3 on, which are
+        // loaded whole when they end inside the row (every lane but, at most, the last one of a
+        // row); otherwise the bytes are loaded one by one.  Either way a row's bytes are kept
+        // packed (lo: pixel x0's three channels and pixel x0 + 1's first, hi: the other two), and
+        // the log table is read per row, so the raw data takes 2 registers per row.
+        const int b0 = 3 * x0, a0 = b0 & ~3;
+        const bool words = ((reinterpret_cast<uintptr_t>(frame) | stride) & 3) == 0 && x0 + 1 < tp.W &&
+                           a0 + 8 <= 3 * tp.W;
+        const unsigned sel_lo = (b0 & 2) ? 0x5432u : 0x3210u, sel_hi = (b0 & 2) ? 0x0076u : 0x0054u;
+        unsigned lo[TH], hi[TH];
 #pragma unroll
         for (int r = 0; r < TH; ++r) {
             const unsigned char* row = frame + (size_t)min(by * TH + r, tp.H - 1) * stride;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                k[ch][r][0] = __ldg(row + (size_t)xa * 3 + ch);
-                k[ch][r][1] = __ldg(row + (size_t)xb * 3 + ch);
+            if (words) {
+                const unsigned w0 = __ldg(reinterpret_cast<const unsigned*>(row + a0));
+                const unsigned w1 = __ldg(reinterpret_cast<const unsigned*>(row + a0 + 4));
+                lo[r] = __byte_perm(w0, w1, sel_lo);
+                hi[r] = __byte_perm(w0, w1, sel_hi);
+            } else {
+                const unsigned char* pa = row + (size_t)xa * 3;
+                const unsigned char* pb = row + (size_t)xb * 3;
+                lo[r] = (unsigned)__ldg(pa) | ((unsigned)__ldg(pa + 1) << 8) | ((unsigned)__ldg(pa + 2) << 16) |
+                        ((unsigned)__ldg(pb) << 24);
+                hi[r] = (unsigned)__ldg(pb + 1) | ((unsigned)__ldg(pb + 2) << 8);
             }
         }
+        const unsigned lo_ref = __shfl_sync(kStripFull, lo[0], src_lane);
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            const int kr = __shfl_sync(kStripFull, k[ch][0][0], src_lane);
-            yref[ch] = __ldg(lut + kr);
+        for (int ch = 0; ch < 3; ++ch) yref[ch] = __ldg(lut + ((lo_ref >> (8 * ch)) & 0xff));
 #pragma unroll
-            for (int r = 0; r < TH; ++r)
+        for (int r = 0; r < TH; ++r) {
+            const unsigned code[3][2] = {{lo[r] & 0xff, lo[r] >> 24},
+                                         {(lo[r] >> 8) & 0xff, hi[r] & 0xff},
+                                         {(lo[r] >> 16) & 0xff, (hi[r] >> 8) & 0xff}};
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch)
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    const float2 y = __ldg(lut + k[ch][r][c]);
+                    const float2 y = __ldg(lut + code[ch][c]);
                     v[ch][r][c] = (y.x - yref[ch].x) + (y.y - yref[ch].y);
                 }
         }

@@ -695,7 +695,16 @@ constexpr int kGroup = 4;
 constexpr int kGroupPixels = 32 / kGroup;  // pixels per warp
 
 // The sums of the group's pixel (the same bits in every lane of the group); every lane of
-// the warp calls it together.
+// the warp calls it together.  The rows are those of span_pixel narrowed to the rows whose
+// cut interval meets the grid's columns (clip_rows_to_grid).  A row's terms and class are
+// computed without branches: its cut interval, widened by one column on the left and two on
+// the right as in row_span, has centre cen (the row's peak column) and squared half-width
+// h2; it is cut off on the left when cen - h - 1 < 0 and on the right when
+// cen + h + 2 > n1 - 1 (compared squared, no square root).  Inside the grid it takes the
+// full-line sum, cut off on one side the table's one-sided sum (the table read at an index
+// clamped into it, the result used only when in range).  Rows cut off on both sides, or with
+// the peak beyond the table's left end, are summed node by node in a second pass (rare).
+// Rows whose interval misses the grid add nothing.
 __device__ __forceinline__ void group_sums(const BayesParams& bp, const BayesRec& rec, bool valid, int gl, float& sw,
                                            float& sdi, float& sdj, unsigned long long& nodes,
                                            unsigned long long& rows) {
@@ -705,31 +714,81 @@ __device__ __forceinline__ void group_sums(const BayesParams& bp, const BayesRec
     sdi = 0.f;
     sdj = 0.f;
     unsigned cnt = 0, rcnt = 0, ecnt = 0;
+    int ra = sp.rlo, rb = sp.rhi;
+    if (!sp.whole) {
+        float lo = (float)(ra - rec.i0), hi = (float)(rb - 1 - rec.i0);
+        clip_rows_to_grid(bp, rec, fmaf(1e-6f, fmaf(fabsf(rec.U), (float)bp.n0, fmaf(fabsf(rec.V), (float)bp.n1,
+                                                                                     bp.sup_mg)),
+                                        bp.span_cut),
+                          lo, hi);
+        if (lo <= hi) {  // widened by a row on each side; the reference row is always kept
+            ra = max(ra, min(rec.i0 + (int)floorf(lo) - 1, rec.i0));
+            rb = min(rb, max(rec.i0 + (int)ceilf(hi) + 2, rec.i0 + 1));
+        }
+    }
+    const float n1f = (float)bp.n1, edge_r = (float)(bp.n1 - 1 - rec.j0), edge_l = (float)rec.j0;
+    bool walked = false;
     if (valid && !sp.whole) {
-        for (int i = sp.rlo + gl; i < sp.rhi; i += G) {
-            int na, nb;
-            row_span(sp, i - rec.i0, na, nb);
-            const int ja = max(na, 0), jb = min(nb, bp.n1);  // clipped to the grid
-            if (jb <= ja) continue;                           // the row misses the grid's columns
-            const bool lclip = na < 0, rclip = nb > bp.n1;
+        for (int i = ra + gl; i < rb; i += G) {
             const float d = (float)(i - rec.i0);
+            const float h2 = fmaf(d, fmaf(sp.a2, d, sp.b2), sp.c2);
+            const float cen = fmaf(sp.k1, d, sp.cc);
+            // h >= -cen - 2 and h >= cen - n1 (the widened interval meets the grid), h > cen - 1
+            // (cut off on the left), h > n1 - 3 - cen (on the right), with h = sqrt(h2)
+            const float e0 = -cen - 2.f, e1 = cen - n1f, e2 = cen - 1.f, e3 = n1f - 3.f - cen;
+            const bool live = h2 >= 0.f && (e0 <= 0.f || h2 >= e0 * e0) && (e1 <= 0.f || h2 >= e1 * e1);
+            const bool lclip = e2 < 0.f || h2 > e2 * e2, rclip = e3 < 0.f || h2 > e3 * e3;
             const float R = fmaf(2.f * bp.Bq, d, rec.V);
             const float S = d * fmaf(bp.Aq, d, rec.U);
-            float rs, rm;
-            if (!(lclip && rclip) && row_closed(bp, rec, R, S, lclip, rclip, rs, rm)) {
-                ++rcnt;
-                ecnt += (lclip || rclip) ? 1u : 0u;
-            } else {
-                rs = 0.f;
-                rm = 0.f;
-                for (int j = ja; j < jb; ++j) {
-                    const float dj = (float)(j - rec.j0);
-                    const float w = ex2(fmaf(dj, fmaf(bp.Cq, dj, R), S));
-                    rs += w;
-                    rm = fmaf(w, dj, rm);
-                }
-                cnt += (unsigned)(jb - ja);
+            const float js = R * bp.span_cv;          // the row's peak, in columns from j0
+            const float ts = fmaf(0.5f * R, js, S);   // its base-2 log weight t*
+            const float x = lclip ? edge_l + js : edge_r - js;  // the peak's distance from the cut-off edge
+            const float f = (x - bp.tab_x0) * bp.tab_inv_step;
+            const int k = min(max((int)f, 0), bp.tab_n - 1);
+            const float u = f - (float)k;
+            const float4 p = __ldg(bp.row_tab + 2 * k), q = __ldg(bp.row_tab + 2 * k + 1);
+            const bool one = lclip != rclip, in_tab = f < (float)bp.tab_n;
+            const float lf_t = fmaf(u, fmaf(u, fmaf(u, p.w, p.z), p.y), p.x);
+            const float m_t = fmaf(u, fmaf(u, fmaf(u, q.w, q.z), q.y), q.x);  // mean, columns from the edge
+            const float lf = (one && in_tab) ? lf_t : bp.log2_kfull;
+            const float mc = (one && in_tab) ? (lclip ? m_t - edge_l : edge_r - m_t) : js;
+            const bool walk = live && ((lclip && rclip) || (one && !(f >= 0.f)));
+            const bool ok = live && !walk;
+            const float rs = ok ? ex2(ts + lf) : 0.f;
+            sw += rs;
+            sdj = fmaf(mc, rs, sdj);
+            sdi = fmaf(d, rs, sdi);
+            rcnt += ok ? 1u : 0u;
+            ecnt += (ok && one) ? 1u : 0u;
+            walked |= walk;
+        }
+    }
+    if (__any_sync(0xffffffffu, walked) && walked) {
+        // the rows taken node by node, one ex2 per node over the row's widened interval
+        for (int i = ra + gl; i < rb; i += G) {
+            const float d = (float)(i - rec.i0);
+            const float h2 = fmaf(d, fmaf(sp.a2, d, sp.b2), sp.c2);
+            const float cen = fmaf(sp.k1, d, sp.cc);
+            const float e0 = -cen - 2.f, e1 = cen - n1f, e2 = cen - 1.f, e3 = n1f - 3.f - cen;
+            const bool live = h2 >= 0.f && (e0 <= 0.f || h2 >= e0 * e0) && (e1 <= 0.f || h2 >= e1 * e1);
+            const bool lclip = e2 < 0.f || h2 > e2 * e2, rclip = e3 < 0.f || h2 > e3 * e3;
+            const float R = fmaf(2.f * bp.Bq, d, rec.V);
+            const float js = R * bp.span_cv;
+            const float x = lclip ? edge_l + js : edge_r - js;
+            const float f = (x - bp.tab_x0) * bp.tab_inv_step;
+            if (!(live && ((lclip && rclip) || (lclip != rclip && !(f >= 0.f))))) continue;
+            int na, nb;
+            row_span(sp, i - rec.i0, na, nb);
+            const int ja = max(na, 0), jb = min(nb, bp.n1);
+            const float S = d * fmaf(bp.Aq, d, rec.U);
+            float rs = 0.f, rm = 0.f;
+            for (int j = ja; j < jb; ++j) {
+                const float dj = (float)(j - rec.j0);
+                const float w = ex2(fmaf(dj, fmaf(bp.Cq, dj, R), S));
+                rs += w;
+                rm = fmaf(w, dj, rm);
             }
+            cnt += (unsigned)max(jb - ja, 0);
             sw += rs;
             sdj += rm;
             sdi = fmaf(d, rs, sdi);

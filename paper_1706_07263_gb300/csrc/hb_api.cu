@@ -362,21 +362,27 @@ void one_sided_sum(double cq, double x, double& lf, double& dlf, double& m, doub
 // and is halved, three times at most, until every piece agrees with the direct sums at
 // u = 1/4, 1/2, 3/4 (log2 F within 4e-6 + 1e-7 |log2 F|, m within 1e-5 columns + 1e-6 sigma,
 // with the FP32-rounded coefficients).
-// Sets bp's table fields except row_tab; false (no closed form) when the grid has no row
-// kernel, when the Poisson term 2 exp(-pi^2 / (-Cq ln 2)) exceeds 2e-13, when the table's
-// right end differs from the full sum, or when no step passes.
+// Sets bp's table fields except row_tab, and the first Poisson term (pois_q, pois_m) where it
+// matters; false (no closed form) when the grid has no row kernel, when the second Poisson
+// term exp(-4 pi^2 / a) exceeds 7e-13 (pi^2 / a < 7), when the table's right end differs from
+// the full sum, or when no step passes.
 bool row_table(BayesParams& bp, std::vector<float4>& tab) {
     tab.clear();
     if (!bp.rows_ok || !(bp.Cq < 0.f)) return false;
     const double cq = (double)bp.Cq, a = -cq * std::log(2.0);
-    if (M_PI * M_PI / a < 30.0) return false;
+    if (M_PI * M_PI / a < 7.0) return false;
+    const double q = std::exp(-M_PI * M_PI / a);
     const double hc = std::sqrt(((double)bp.span_cut + 2.0) / -cq);
     const double x1 = hc + 4.0, x0 = -x1;
     const double log2k = 0.5 * std::log2(M_PI / a);
     {
+        // at the right end the one-sided sum must be the full one (the two-sided sum, with its
+        // Poisson term)
         double lf, dlf, m, dm;
         one_sided_sum(cq, x1, lf, dlf, m, dm);
-        if (!(std::fabs(lf - log2k) <= 1e-9 && std::fabs(m - x1) <= 1e-7)) return false;
+        const double c = std::cos(2.0 * M_PI * x1), sn = std::sin(2.0 * M_PI * x1), den = 1.0 + 2.0 * q * c;
+        const double lf_full = log2k + std::log2(den), m_full = x1 - 2.0 * M_PI / a * q * sn / den;
+        if (!(std::fabs(lf - lf_full) <= 1e-9 && std::fabs(m - m_full) <= 1e-7)) return false;
     }
     const double sigma = 1.0 / std::sqrt(2.0 * a);
     const double s_start = std::exp2(std::floor(std::log2(sigma / 16.0)));
@@ -411,6 +417,8 @@ bool row_table(BayesParams& bp, std::vector<float4>& tab) {
         bp.tab_inv_step = (float)(1.0 / s);
         bp.tab_n = n;
         bp.log2_kfull = (float)log2k;
+        bp.pois_q = q > 1e-14 ? (float)q : 0.f;
+        bp.pois_m = q > 1e-14 ? (float)(2.0 * M_PI * q / a) : 0.f;
         return true;
     }
     tab.clear();

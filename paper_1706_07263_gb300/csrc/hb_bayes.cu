@@ -516,50 +516,20 @@ __device__ __forceinline__ void flush_counts(unsigned long long* counts, unsigne
     if (lane == 0 && e) atomicAdd(counts + 2, e);
 }
 
-// A row's sums in closed form (BayesParams::row_tab), for a row of the half-warp's pixel
-// whose cut interval [na, nb) the grid cuts off on at most one side: the row's base-2 log
-// weight along the columns is S + R dj + Cq dj^2, dj = j - j0.  Returns false (the row is
-// then summed node by node) when the row's peak lies further beyond the cut-off edge than
-// the table reaches.
-__device__ __forceinline__ bool row_closed(const BayesParams& bp, const BayesRec& rec, float R, float S, bool lclip,
-                                           bool rclip, float& rs, float& rm) {
-    const float js = R * bp.span_cv;          // the row's peak, in columns from j0
-    const float ts = fmaf(0.5f * R, js, S);   // its base-2 log weight t*
-    float lf = bp.log2_kfull, mc = js;        // log2 of (row sum / 2^t*), mean column - j0
-    if (lclip || rclip) {
-        const float edge = lclip ? (float)rec.j0 : (float)(bp.n1 - 1 - rec.j0);
-        const float x = lclip ? edge + js : edge - js;  // the peak's distance from the edge column
-        const float f = (x - bp.tab_x0) * bp.tab_inv_step;
-        if (!(f >= 0.f)) return false;
-        if (f < (float)bp.tab_n) {
-            const int k = (int)f;
-            const float u = f - (float)k;
-            const float4 p = __ldg(bp.row_tab + 2 * k), q = __ldg(bp.row_tab + 2 * k + 1);
-            lf = fmaf(u, fmaf(u, fmaf(u, p.w, p.z), p.y), p.x);
-            const float m = fmaf(u, fmaf(u, fmaf(u, q.w, q.z), q.y), q.x);  // mean, columns from the edge
-            mc = lclip ? m - edge : edge - m;
-        }
-    }
-    rs = ex2(ts + lf);
-    rm = mc * rs;
-    return true;
-}
-
 // The posterior mean of the half-warp's pixel (record rec) into chat[out] (and chat_scaled)
-// when valid; both half-warps of the warp call it together.  nodes counts the grid nodes
-// summed one by one, rows the rows summed in closed form plus 2^32 per such row that the box
-// edge cuts off.
+// when valid, every row summed node by node (the grids without the closed-form rows, and
+// HB_NODE_SUMS); both half-warps of the warp call it together.  nodes counts the grid nodes
+// summed.
 __device__ __forceinline__ void rows_pixel(const BayesParams& bp, const BayesRec& rec, bool valid, long out, int gl,
                                            float2* chat, float2* chat_scaled, float scale,
                                            unsigned long long& nodes, unsigned long long& rows) {
     constexpr int G = 16;
     const SpanPixel sp = span_pixel(bp, rec);
     const bool direct = sp.whole;  // summed over the whole grid below instead
-    const bool closed = bp.row_tab != nullptr;
     const int nslots = __reduce_max_sync(0xffffffffu, direct ? 0 : (sp.rhi - sp.rlo + G - 1) / G);
     const u64 QQ = pk(bp.row_q, bp.row_q), CC = pk(bp.Cq, bp.Cq);
     float sw = 0.f, sdi = 0.f, sdj = 0.f;
-    unsigned cnt = 0, rcnt = 0, ecnt = 0;
+    unsigned cnt = 0;
     for (int slot = 0; slot < nslots; ++slot) {
         const int i = sp.rlo + slot * G + gl;
         int na = 0, nb = 0;
@@ -576,13 +546,8 @@ __device__ __forceinline__ void rows_pixel(const BayesParams& bp, const BayesRec
         const float R = fmaf(2.f * bp.Bq, d, rec.V);
         const float S = d * fmaf(bp.Aq, d, rec.U);
         float rs = 0.f, rm = 0.f;
-        bool walk = live;  // summed node by node below
-        if (closed && live && !(lclip && rclip) && row_closed(bp, rec, R, S, lclip, rclip, rs, rm)) {
-            walk = false;
-            ++rcnt;
-            ecnt += (lclip || rclip) ? 1u : 0u;
-        }
-        if (__any_sync(0xffffffffu, walk)) {
+        const bool walk = live;
+        {
             const bool full = walk && lclip && rclip;
             const bool back = walk && rclip && !lclip;  // start at the right end, walk left
             const bool any_full = __any_sync(0xffffffffu, full);
@@ -657,10 +622,8 @@ __device__ __forceinline__ void rows_pixel(const BayesParams& bp, const BayesRec
     sw = group_sum<G>(sw);
     sdi = group_sum<G>(sdi);
     sdj = group_sum<G>(sdj);
-    if (valid) {
-        nodes += cnt;
-        rows += ((unsigned long long)ecnt << 32) + rcnt;
-    }
+    if (valid) nodes += cnt;
+    (void)rows;
     const bool bad = direct || !usable(sw, sdi, sdj);
     if (__any_sync(0xffffffffu, bad)) {
         // the whole grid with an explicit maximum shift (the partner half-warp takes part in
@@ -750,8 +713,16 @@ __device__ __forceinline__ void group_sums(const BayesParams& bp, const BayesRec
             const bool one = lclip != rclip, in_tab = f < (float)bp.tab_n;
             const float lf_t = fmaf(u, fmaf(u, fmaf(u, p.w, p.z), p.y), p.x);
             const float m_t = fmaf(u, fmaf(u, fmaf(u, q.w, q.z), q.y), q.x);  // mean, columns from the edge
-            const float lf = (one && in_tab) ? lf_t : bp.log2_kfull;
-            const float mc = (one && in_tab) ? (lclip ? m_t - edge_l : edge_r - m_t) : js;
+            float lf_full = bp.log2_kfull, mc_full = js;  // over all integer columns
+            if (bp.pois_q > 0.f) {  // the first Poisson term (rows narrower than ~1.5 columns)
+                float sn, cs;
+                sincospif(2.f * (js - floorf(js)), &sn, &cs);
+                const float e = 2.f * bp.pois_q * cs;  // |e| < 2e-3: ln(1 + e) to e^4
+                lf_full = fmaf(e * fmaf(e, fmaf(e, 1.f / 3.f, -0.5f), 1.f), 1.4426950408889634f, lf_full);
+                mc_full = fmaf(-bp.pois_m, __fdividef(sn, 1.f + e), js);
+            }
+            const float lf = (one && in_tab) ? lf_t : lf_full;
+            const float mc = (one && in_tab) ? (lclip ? m_t - edge_l : edge_r - m_t) : mc_full;
             const bool walk = live && ((lclip && rclip) || (one && !(f >= 0.f)));
             const bool ok = live && !walk;
             const float rs = ok ? ex2(ts + lf) : 0.f;

@@ -106,8 +106,8 @@ struct BayesParams {
     // Closed-form row sums of the row kernel (row_tab set; needs rows_ok).  Along row di the
     // base-2 log weight is t* + Cq (j - mu)^2 (t* the row's maximum over real columns, mu its
     // column), so over all integer columns the row's weights add up to 2^t* K with
-    // K = sum_j 2^(Cq (j - mu)^2) = sqrt(pi / (-Cq ln 2)) up to a relative 2 exp(-pi^2 / (-Cq ln 2))
-    // (Poisson summation; the host requires that term below 2e-13), and their mean column is mu.
+    // K = sqrt(pi / (-Cq ln 2)), and their mean column is mu, up to the Poisson terms below
+    // (Poisson summation).
     // A row whose interval the grid cuts off on one side is the one-sided sum
     // F(x) = sum_{k >= 0} 2^(Cq (k - x)^2), x = the peak's distance from the edge column, whose
     // mean is m(x) columns from the edge: row_tab holds, per interval [x_k, x_k + 1/tab_inv_step)
@@ -118,6 +118,12 @@ struct BayesParams {
     float tab_x0, tab_inv_step;
     int tab_n;
     float log2_kfull;         // log2 K
+    // The first Poisson term, kept where it exceeds 1e-14 (rows narrower than about 1.5
+    // columns): over all integer columns the sum is 2^t* K (1 + 2 q cos(2 pi mu)) and the mean
+    // column mu - (2 pi / a) q sin(2 pi mu) / (1 + 2 q cos(2 pi mu)), q = exp(-pi^2 / a),
+    // a = -Cq ln 2, up to a relative 2 q^4; the host requires q^4 below 7e-13 (pi^2 / a >= 7).
+    // pois_q = q and pois_m = 2 pi q / a, or both 0.
+    float pois_q, pois_m;
 };
 
 // Where the analysis writes the least-squares low-pass estimates (c = nullptr: it writes the

@@ -244,17 +244,21 @@ def test_column_intervals_keep_every_weighted_node(n0, n1, sigma):
     assert np.all(np.abs(got[0][pick] - ref) <= 2e-4 + 2e-6 * np.abs(ref))
 
 
-@pytest.mark.parametrize("hb_box,n1", [((0.0, 100.0), 128), ((0.0, 12.0), 24), ((-30.0, 130.0), 200)])
-def test_closed_form_rows_against_node_sums(hb_box, n1):
+@pytest.mark.parametrize("mix_seed,hb_box,n0,n1", [(9, (0.0, 100.0), 128, 128), (9, (0.0, 12.0), 128, 24),
+                                                    (9, (-30.0, 130.0), 128, 200), (4, (0.0, 100.0), 64, 64),
+                                                    (17, (0.0, 100.0), 64, 64), (2, (0.0, 100.0), 128, 128)])
+def test_closed_form_rows_against_node_sums(mix_seed, hb_box, n0, n1):
     """Rows summed in closed form (inside the grid: the full-line sum; cut off by the box on
     one side: the tabulated one-sided sum) beside rows summed node by node in the same warps
     (cut off on both sides: a posterior wider than the Hb box; a peak beyond the table: far
     outside the model): 40,000 pixels in and around the box against HB_NODE_SUMS, every node
     (HB_FULL_GRID) and, on a sample, the oracle.  Both counters must show work, so both kinds
-    of row occur."""
-    rng = np.random.default_rng(n1)
-    A = synth.make_mixing(9).A
-    grid = _grid(128, n1, 0.02, lo1=hb_box[0], hi1=hb_box[1])
+    of row occur.  The 64x64 grids of mixings 4 and 17 have row Gaussians 0.73 and 0.61
+    columns wide, where the first Poisson term moves a row's mean column by up to 2e-4 and
+    3e-3 columns (mixing 2's 128x128 grid: 0.98 columns, 1e-7)."""
+    rng = np.random.default_rng(n1 + 7 * mix_seed)
+    A = synth.make_mixing(mix_seed).A
+    grid = _grid(n0, n1, 0.02, lo1=hb_box[0], hi1=hb_box[1])
     n = 40_000
     span = hb_box[1] - hb_box[0]
     c = np.stack([rng.uniform(-40, 190, n), rng.uniform(hb_box[0] - 0.4 * span, hb_box[1] + 0.4 * span, n)], axis=1)

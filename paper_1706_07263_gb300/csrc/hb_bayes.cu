@@ -956,12 +956,23 @@ __global__ void __launch_bounds__(kFusedThreads, HB_FUSED_MINB)
 // levels the means reach their lanes by shuffles.  The arithmetic is that of the separate
 // analysis, posterior and synthesis kernels, so the outputs are the same bits.  Warp w of W
 // takes strips w, w + W, ...
-#ifndef HB_FRAME_MINB
-#define HB_FRAME_MINB 3
+// Seven warps per CTA and four CTAs per SM (72 registers): 28 resident warps per SM, 4,256
+// on the GPU, so the 4,050 strips of a 1920x1080 frame at 3 levels are taken in one round
+// (eight warps and three CTAs per SM, 80 registers, left 402 strips for a second round: 22.5
+// against 20.5 us per frame).
+#ifndef HB_FRAME_THREADS
+#define HB_FRAME_THREADS 224
 #endif
+#ifndef HB_FRAME_MINB
+#define HB_FRAME_MINB 4
+#endif
+#ifndef HB_FRAME_C_SMEM
+#define HB_FRAME_C_SMEM 0
+#endif
+constexpr int kFrameThreads = HB_FRAME_THREADS;
 
 template <int L>
-__global__ void __launch_bounds__(kFusedThreads, HB_FRAME_MINB)
+__global__ void __launch_bounds__(kFrameThreads, HB_FRAME_MINB)
     frame_kernel(TransformParams tp, BayesParams bp, const unsigned char* __restrict__ frame, size_t stride,
                  const float2* __restrict__ lut, float2* __restrict__ chat, float2* __restrict__ chat_scaled,
                  float scale, float* __restrict__ out0, float* __restrict__ out1, int debug_conc,
@@ -974,9 +985,12 @@ __global__ void __launch_bounds__(kFusedThreads, HB_FRAME_MINB)
     asm volatile("griddepcontrol.launch_dependents;");
     const int ux = (tp.wl * TH + 63) / 64;  // strips per superblock band
     const unsigned nunits = (unsigned)ux * (unsigned)tp.hl;
-    const unsigned nwarps = gridDim.x * (kFusedThreads / 32);
+    const unsigned nwarps = gridDim.x * (kFrameThreads / 32);
+#if HB_FRAME_C_SMEM
+    __shared__ float c_park[kFrameThreads / 32][4 * TH][32];
+#endif
     unsigned long long nodes = 0, rows = 0;
-    for (unsigned u = blockIdx.x * (kFusedThreads / 32) + (threadIdx.x >> 5); u < nunits; u += nwarps) {
+    for (unsigned u = blockIdx.x * (kFrameThreads / 32) + (threadIdx.x >> 5); u < nunits; u += nwarps) {
         const int by = (int)(u / (unsigned)ux), x0w = (int)(u % (unsigned)ux) * 64, x = x0w + 2 * lane;
         float c[2][TH][2];
         float yhi[3], ylo[3];
@@ -995,6 +1009,15 @@ __global__ void __launch_bounds__(kFusedThreads, HB_FRAME_MINB)
             }
             strip_tikhonov<L>(tp, v, lane, c);
         }
+#if HB_FRAME_C_SMEM
+        // the transformed details wait in shared memory while the posterior runs (registers)
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+            for (int r = 0; r < TH; ++r)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) c_park[threadIdx.x >> 5][(ch * TH + r) * 2 + k][lane] = c[ch][r][k];
+#endif
         const int sb0 = x0w / TH, nsb = min(NSB, tp.wl - sb0);  // superblocks of this strip
         BayesRec rec = {0, 0, 0.f, 0.f};
         if (lane < nsb) rec = bayes_setup(yhi, ylo, bp);
@@ -1023,6 +1046,14 @@ __global__ void __launch_bounds__(kFusedThreads, HB_FRAME_MINB)
                 if (mine_sb / kGroupPixels == k) mean = make_float2(mx, my);
             }
         }
+#if HB_FRAME_C_SMEM
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+            for (int r = 0; r < TH; ++r)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) c[ch][r][k] = c_park[threadIdx.x >> 5][(ch * TH + r) * 2 + k][lane];
+#endif
         strip_synthesis<L>(c, lane);
         strip_store<L>(tp, c, mean.x, mean.y, x, by, out0, out1, debug_conc);
     }
@@ -1238,14 +1269,14 @@ cudaError_t launch_frame(const TransformParams& tp, const BayesParams& bp, const
                          int debug_conc, unsigned long long* nodes, bool pdl, cudaStream_t s) {
     int resident = 0, sms = 0;
     auto kernel = tp.levels == 1 ? frame_kernel<1> : tp.levels == 2 ? frame_kernel<2> : frame_kernel<3>;
-    cudaError_t e = residency(kernel, resident, sms, kFusedThreads);
+    cudaError_t e = residency(kernel, resident, sms, kFrameThreads);
     if (e != cudaSuccess) return e;
     const long units = (long)((tp.wl * (1 << tp.levels) + 63) / 64) * tp.hl;
-    long blocks = (units + kFusedThreads / 32 - 1) / (kFusedThreads / 32);
+    long blocks = (units + kFrameThreads / 32 - 1) / (kFrameThreads / 32);
     if (blocks > (long)sms * resident) blocks = (long)sms * resident;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
-    cfg.blockDim = dim3(kFusedThreads);
+    cfg.blockDim = dim3(kFrameThreads);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -668,6 +668,20 @@ constexpr int kGroupPixels = 32 / kGroup;  // pixels per warp
 // clamped into it, the result used only when in range).  Rows cut off on both sides, or with
 // the peak beyond the table's left end, are summed node by node in a second pass (rare).
 // Rows whose interval misses the grid add nothing.
+// A row's class from its cut interval, widened by one column on the left and two on the right
+// as in row_span (centre cen, half-width sqrt(h2)): cut off on the left when it starts left of
+// column 0, on the right when it ends right of column n1 - 1.  A row whose interval misses the
+// grid, or whose h2 is negative (its maximum below the cut), is classed by its centre alone and
+// its sums are the true, negligible ones.
+__device__ __forceinline__ void row_class(float h2, float cen, float n1f, bool& lclip, bool& rclip) {
+    const float h = sqrt_approx(fmaxf(h2, 0.f));
+    lclip = cen - h < 1.f;
+    rclip = cen + h > n1f - 3.f;
+}
+
+// COUNT: add the rows summed in closed form (and those of them cut off by an edge) and the nodes
+// summed one by one to the counters.
+template <bool COUNT>
 __device__ __forceinline__ void group_sums(const BayesParams& bp, const BayesRec& rec, bool valid, int gl, float& sw,
                                            float& sdi, float& sdj, unsigned long long& nodes,
                                            unsigned long long& rows) {
@@ -696,11 +710,8 @@ __device__ __forceinline__ void group_sums(const BayesParams& bp, const BayesRec
             const float d = (float)(i - rec.i0);
             const float h2 = fmaf(d, fmaf(sp.a2, d, sp.b2), sp.c2);
             const float cen = fmaf(sp.k1, d, sp.cc);
-            // h >= -cen - 2 and h >= cen - n1 (the widened interval meets the grid), h > cen - 1
-            // (cut off on the left), h > n1 - 3 - cen (on the right), with h = sqrt(h2)
-            const float e0 = -cen - 2.f, e1 = cen - n1f, e2 = cen - 1.f, e3 = n1f - 3.f - cen;
-            const bool live = h2 >= 0.f && (e0 <= 0.f || h2 >= e0 * e0) && (e1 <= 0.f || h2 >= e1 * e1);
-            const bool lclip = e2 < 0.f || h2 > e2 * e2, rclip = e3 < 0.f || h2 > e3 * e3;
+            bool lclip, rclip;
+            row_class(h2, cen, n1f, lclip, rclip);
             const float R = fmaf(2.f * bp.Bq, d, rec.V);
             const float S = d * fmaf(bp.Aq, d, rec.U);
             const float js = R * bp.span_cv;          // the row's peak, in columns from j0
@@ -723,14 +734,15 @@ __device__ __forceinline__ void group_sums(const BayesParams& bp, const BayesRec
             }
             const float lf = (one && in_tab) ? lf_t : lf_full;
             const float mc = (one && in_tab) ? (lclip ? m_t - edge_l : edge_r - m_t) : mc_full;
-            const bool walk = live && ((lclip && rclip) || (one && !(f >= 0.f)));
-            const bool ok = live && !walk;
-            const float rs = ok ? ex2(ts + lf) : 0.f;
+            const bool walk = (lclip && rclip) || (one && !(f >= 0.f));
+            const float rs = walk ? 0.f : ex2(ts + lf);
             sw += rs;
             sdj = fmaf(mc, rs, sdj);
             sdi = fmaf(d, rs, sdi);
-            rcnt += ok ? 1u : 0u;
-            ecnt += (ok && one) ? 1u : 0u;
+            if (COUNT) {
+                rcnt += walk ? 0u : 1u;
+                ecnt += (!walk && one) ? 1u : 0u;
+            }
             walked |= walk;
         }
     }
@@ -740,14 +752,13 @@ __device__ __forceinline__ void group_sums(const BayesParams& bp, const BayesRec
             const float d = (float)(i - rec.i0);
             const float h2 = fmaf(d, fmaf(sp.a2, d, sp.b2), sp.c2);
             const float cen = fmaf(sp.k1, d, sp.cc);
-            const float e0 = -cen - 2.f, e1 = cen - n1f, e2 = cen - 1.f, e3 = n1f - 3.f - cen;
-            const bool live = h2 >= 0.f && (e0 <= 0.f || h2 >= e0 * e0) && (e1 <= 0.f || h2 >= e1 * e1);
-            const bool lclip = e2 < 0.f || h2 > e2 * e2, rclip = e3 < 0.f || h2 > e3 * e3;
+            bool lclip, rclip;
+            row_class(h2, cen, n1f, lclip, rclip);
             const float R = fmaf(2.f * bp.Bq, d, rec.V);
             const float js = R * bp.span_cv;
             const float x = lclip ? edge_l + js : edge_r - js;
             const float f = (x - bp.tab_x0) * bp.tab_inv_step;
-            if (!(live && ((lclip && rclip) || (lclip != rclip && !(f >= 0.f))))) continue;
+            if (!((lclip && rclip) || (lclip != rclip && !(f >= 0.f)))) continue;
             int na, nb;
             row_span(sp, i - rec.i0, na, nb);
             const int ja = max(na, 0), jb = min(nb, bp.n1);
@@ -768,7 +779,7 @@ __device__ __forceinline__ void group_sums(const BayesParams& bp, const BayesRec
     sw = group_sum<G>(sw);
     sdi = group_sum<G>(sdi);
     sdj = group_sum<G>(sdj);
-    if (valid) {
+    if (COUNT && valid) {
         nodes += cnt;
         rows += ((unsigned long long)ecnt << 32) + rcnt;
     }
@@ -786,7 +797,7 @@ __device__ __forceinline__ void group_sums(const BayesParams& bp, const BayesRec
             sw = fw;
             sdi = fdi;
             sdj = fdj;
-            if (gl == 0) nodes += (unsigned long long)bp.n0 * (unsigned)bp.n1;
+            if (COUNT && gl == 0) nodes += (unsigned long long)bp.n0 * (unsigned)bp.n1;
         }
     }
 }
@@ -795,7 +806,7 @@ __device__ __forceinline__ void group_pixel(const BayesParams& bp, const BayesRe
                                             float2* chat, float2* chat_scaled, float scale,
                                             unsigned long long& nodes, unsigned long long& rows) {
     float sw, sdi, sdj;
-    group_sums(bp, rec, valid, gl, sw, sdi, sdj, nodes, rows);
+    group_sums<true>(bp, rec, valid, gl, sw, sdi, sdj, nodes, rows);
     if (valid && gl == 0) write_mean(bp, rec, out, sw, sdi, sdj, chat, chat_scaled, scale);
 }
 
@@ -971,7 +982,7 @@ __global__ void __launch_bounds__(kFusedThreads, HB_FUSED_MINB)
 #endif
 constexpr int kFrameThreads = HB_FRAME_THREADS;
 
-template <int L>
+template <int L, bool COUNT>
 __global__ void __launch_bounds__(kFrameThreads, HB_FRAME_MINB)
     frame_kernel(TransformParams tp, BayesParams bp, const unsigned char* __restrict__ frame, size_t stride,
                  const float2* __restrict__ lut, float2* __restrict__ chat, float2* __restrict__ chat_scaled,
@@ -1032,7 +1043,7 @@ __global__ void __launch_bounds__(kFrameThreads, HB_FRAME_MINB)
             rr.U = __shfl_sync(0xffffffffu, rec.U, t);
             rr.V = __shfl_sync(0xffffffffu, rec.V, t);
             float sw, sdi, sdj;
-            group_sums(bp, rr, t < nsb, gl, sw, sdi, sdj, nodes, rows);
+            group_sums<COUNT>(bp, rr, t < nsb, gl, sw, sdi, sdj, nodes, rows);
             float2 m = make_float2(0.f, 0.f);
             if (t < nsb) {
                 m = posterior_mean(bp, rr, sw, sdi, sdj);
@@ -1057,7 +1068,7 @@ __global__ void __launch_bounds__(kFrameThreads, HB_FRAME_MINB)
         strip_synthesis<L>(c, lane);
         strip_store<L>(tp, c, mean.x, mean.y, x, by, out0, out1, debug_conc);
     }
-    flush_counts(nodes_out, nodes, rows, lane);
+    if (COUNT) flush_counts(nodes_out, nodes, rows, lane);
 }
 
 // Resident CTAs per SM for a kernel (cached per device and kernel) and the SM count.
@@ -1268,7 +1279,11 @@ cudaError_t launch_frame(const TransformParams& tp, const BayesParams& bp, const
                          const float2* lut, float2* chat, float2* chat_scaled, float scale, float* out0, float* out1,
                          int debug_conc, unsigned long long* nodes, bool pdl, cudaStream_t s) {
     int resident = 0, sms = 0;
-    auto kernel = tp.levels == 1 ? frame_kernel<1> : tp.levels == 2 ? frame_kernel<2> : frame_kernel<3>;
+    // the counting variant only when counters are given (timing armed)
+    auto kernel = nodes ? (tp.levels == 1 ? frame_kernel<1, true> : tp.levels == 2 ? frame_kernel<2, true>
+                                                                                    : frame_kernel<3, true>)
+                        : (tp.levels == 1 ? frame_kernel<1, false> : tp.levels == 2 ? frame_kernel<2, false>
+                                                                                     : frame_kernel<3, false>);
     cudaError_t e = residency(kernel, resident, sms, kFrameThreads);
     if (e != cudaSuccess) return e;
     const long units = (long)((tp.wl * (1 << tp.levels) + 63) / 64) * tp.hl;

@@ -977,9 +977,6 @@ __global__ void __launch_bounds__(kFusedThreads, HB_FUSED_MINB)
 #ifndef HB_FRAME_MINB
 #define HB_FRAME_MINB 4
 #endif
-#ifndef HB_FRAME_C_SMEM
-#define HB_FRAME_C_SMEM 0
-#endif
 constexpr int kFrameThreads = HB_FRAME_THREADS;
 
 template <int L, bool COUNT>
@@ -987,7 +984,7 @@ __global__ void __launch_bounds__(kFrameThreads, HB_FRAME_MINB)
     frame_kernel(TransformParams tp, BayesParams bp, const unsigned char* __restrict__ frame, size_t stride,
                  const float2* __restrict__ lut, float2* __restrict__ chat, float2* __restrict__ chat_scaled,
                  float scale, float* __restrict__ out0, float* __restrict__ out1, int debug_conc,
-                 unsigned long long* nodes_out) {
+                 int pieces, unsigned long long* nodes_out) {
     constexpr int TH = 1 << L, NSB = 64 / TH, SBL = TH / 2;  // superblocks per strip, lanes per superblock
     constexpr int NR = NSB / kGroupPixels;                   // rounds of eight superblocks
     const int lane = threadIdx.x & 31, gl = lane % kGroup, grp = lane / kGroup, mine_sb = lane / SBL;
@@ -996,12 +993,13 @@ __global__ void __launch_bounds__(kFrameThreads, HB_FRAME_MINB)
     asm volatile("griddepcontrol.launch_dependents;");
     const int ux = (tp.wl * TH + 63) / 64;  // strips per superblock band
     const unsigned nunits = (unsigned)ux * (unsigned)tp.hl;
-    const unsigned nwarps = gridDim.x * (kFrameThreads / 32);
-#if HB_FRAME_C_SMEM
-    __shared__ float c_park[kFrameThreads / 32][4 * TH][32];
-#endif
+    const int P = NR > 1 ? pieces : 1;  // pieces per strip (a strip of one round has one)
+    const unsigned nwarps = gridDim.x * (kFrameThreads / 32), ntix = nunits * (unsigned)P;
+    const int per = NR / P;  // rounds per piece
     unsigned long long nodes = 0, rows = 0;
-    for (unsigned u = blockIdx.x * (kFrameThreads / 32) + (threadIdx.x >> 5); u < nunits; u += nwarps) {
+    for (unsigned tix = blockIdx.x * (kFrameThreads / 32) + (threadIdx.x >> 5); tix < ntix; tix += nwarps) {
+        const unsigned u = tix / (unsigned)P;
+        const int k0 = (int)(tix % (unsigned)P) * per, k1 = k0 + per;  // this piece's rounds
         const int by = (int)(u / (unsigned)ux), x0w = (int)(u % (unsigned)ux) * 64, x = x0w + 2 * lane;
         float c[2][TH][2];
         float yhi[3], ylo[3];
@@ -1020,22 +1018,14 @@ __global__ void __launch_bounds__(kFrameThreads, HB_FRAME_MINB)
             }
             strip_tikhonov<L>(tp, v, lane, c);
         }
-#if HB_FRAME_C_SMEM
-        // the transformed details wait in shared memory while the posterior runs (registers)
-#pragma unroll
-        for (int ch = 0; ch < 2; ++ch)
-#pragma unroll
-            for (int r = 0; r < TH; ++r)
-#pragma unroll
-                for (int k = 0; k < 2; ++k) c_park[threadIdx.x >> 5][(ch * TH + r) * 2 + k][lane] = c[ch][r][k];
-#endif
         const int sb0 = x0w / TH, nsb = min(NSB, tp.wl - sb0);  // superblocks of this strip
         BayesRec rec = {0, 0, 0.f, 0.f};
         if (lane < nsb) rec = bayes_setup(yhi, ylo, bp);
         float2 mean = make_float2(0.f, 0.f);  // the posterior mean of this lane's superblock
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
-            if (kGroupPixels * k >= nsb) break;
+            if (k < k0) continue;
+            if (k >= k1 || kGroupPixels * k >= nsb) break;
             const int t = kGroupPixels * k + grp;
             BayesRec rr;
             rr.i0 = __shfl_sync(0xffffffffu, rec.i0, t);
@@ -1057,16 +1047,9 @@ __global__ void __launch_bounds__(kFrameThreads, HB_FRAME_MINB)
                 if (mine_sb / kGroupPixels == k) mean = make_float2(mx, my);
             }
         }
-#if HB_FRAME_C_SMEM
-#pragma unroll
-        for (int ch = 0; ch < 2; ++ch)
-#pragma unroll
-            for (int r = 0; r < TH; ++r)
-#pragma unroll
-                for (int k = 0; k < 2; ++k) c[ch][r][k] = c_park[threadIdx.x >> 5][(ch * TH + r) * 2 + k][lane];
-#endif
         strip_synthesis<L>(c, lane);
-        strip_store<L>(tp, c, mean.x, mean.y, x, by, out0, out1, debug_conc);
+        const int kr = mine_sb / kGroupPixels;  // the round of this lane's superblock
+        if (kr >= k0 && kr < k1) strip_store<L>(tp, c, mean.x, mean.y, x, by, out0, out1, debug_conc);
     }
     if (COUNT) flush_counts(nodes_out, nodes, rows, lane);
 }
@@ -1287,7 +1270,13 @@ cudaError_t launch_frame(const TransformParams& tp, const BayesParams& bp, const
     cudaError_t e = residency(kernel, resident, sms, kFrameThreads);
     if (e != cudaSuccess) return e;
     const long units = (long)((tp.wl * (1 << tp.levels) + 63) / 64) * tp.hl;
-    long blocks = (units + kFrameThreads / 32 - 1) / (kFrameThreads / 32);
+    // a strip's rounds (1 at 3 levels, 2 at 2, 4 at 1) are split over as many warps as fill the
+    // resident ones: each piece redoes the strip's analysis and stores its superblocks' columns
+    const long warps = (long)sms * resident * (kFrameThreads / 32);
+    const int nr = (64 >> tp.levels) / kGroupPixels;
+    int pieces = 1;
+    while (pieces < nr && units * 2 * pieces <= warps) pieces *= 2;
+    long blocks = (units * pieces + kFrameThreads / 32 - 1) / (kFrameThreads / 32);
     if (blocks > (long)sms * resident) blocks = (long)sms * resident;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
@@ -1300,7 +1289,7 @@ cudaError_t launch_frame(const TransformParams& tp, const BayesParams& bp, const
     cfg.numAttrs = pdl ? 1 : 0;
     const unsigned char* f = static_cast<const unsigned char*>(frame);
     return cudaLaunchKernelEx(&cfg, kernel, tp, bp, f, stride, lut, chat, chat_scaled, scale, out0, out1, debug_conc,
-                              nodes);
+                              pieces, nodes);
 }
 
 cudaError_t launch_lowpass_fused(const TransformParams& tp, const BayesParams& bp, const void* frame, size_t stride,

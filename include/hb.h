@@ -27,9 +27,9 @@
  *     with it: calls with the same context must not overlap on different
  *     streams;
  *   - the host side of the calls is marked with NVTX ranges (hb_estimate,
- *     hb_estimate_host, hb_estimate_host_async, and hb.analysis, hb.lowpass,
- *     hb.synthesis around each launch; hb_serve.batch around each serving
- *     batch's enqueue), which cost nothing unless a profiler is attached.
+ *     hb_estimate_host, hb_estimate_host_async, and hb.frame, hb.analysis,
+ *     hb.lowpass, hb.synthesis around each launch; hb_serve.batch around each
+ *     serving batch's enqueue), which cost nothing unless a profiler is attached.
  */
 #ifndef HB_H
 #define HB_H
@@ -139,7 +139,12 @@ void hb_destroy(hb_ctx *ctx);
  *                      row_stride_bytes apart (>= width*3*element size).
  *   thb_dev, so2_dev : height*width floats each, row-major, contiguous.  THb in
  *                      the units of 1/A (uM); SO2 as a fraction, 0 where THb <= 0.
- * Asynchronous on `stream`. */
+ * Asynchronous on `stream`.  With the plain posterior at 1-3 levels and a grid whose
+ * rows are summed in closed form, the frame is one kernel launch (every step of a
+ * strip of the frame in one warp); otherwise two or three launches (HB_NODE_SUMS: low
+ * pass and synthesis; other configurations: analysis, posterior, synthesis).  The
+ * first launch may start, under programmatic dependent launch, before the kernel ahead
+ * of it on `stream` has finished: it waits for that kernel before reading the frame. */
 hb_status hb_estimate(hb_ctx *ctx, const void *frame_dev, size_t row_stride_bytes, float *thb_dev, float *so2_dev,
                       void *stream);
 

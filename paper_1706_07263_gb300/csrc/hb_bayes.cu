@@ -2,9 +2,11 @@
 // low-pass pixel (the Bayesian estimate on the low-pass band, Section 2); the per-pixel
 // sums are in hb_posterior.cuh.
 //
-// Five kernels, all with persistent warps:
+// Six kernels, all with persistent warps:
+//   frame_kernel           every step of the path for a strip of the frame in one warp (1..3
+//                          levels with the closed-form rows: the default path);
 //   lowpass_fused_kernel   block means, posterior records and posterior means in one launch
-//                          (1..3 levels where the row kernel applies: the default path);
+//                          (1..3 levels where the row kernel applies, with HB_NODE_SUMS);
 //   posterior_rows_kernel  over precomputed records (the default when the records are given):
 //                          per pixel the rows of the cut, each summed in closed form (eight
 //                          pixels per warp, four lanes each: group_pixel) or, with

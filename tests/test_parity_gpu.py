@@ -133,6 +133,12 @@ CASES = [
     (20, 30, 0, "f32", (32, 32), 0.02, 11),
     (96, 2100, 2, "u8", (128, 128), 0.005, 12),
     (64, 64, 3, "u8", (128, 128), 0.1, 13),
+    # enough low-pass pixels for the single-pass frame kernel, ragged in both directions, at
+    # every level it takes (1 and 2 levels with a strip's rounds split over warps); its THb is
+    # compared bit for bit with the three-kernel debug path below
+    (130, 1030, 1, "u8", (64, 64), 0.02, 14),
+    (250, 1500, 2, "f32", (96, 80), 0.02, 15),
+    (1001, 777, 3, "u8", (128, 128), 0.02, 16),
 ]
 
 

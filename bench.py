@@ -500,10 +500,12 @@ def measure_serving(args, dev):
 
 
 def serving_in_fresh_process(args):
-    """The serving leg in a process of its own, as a server runs, apart from the state the
-    earlier legs leave in this one.  Its p99 under load still depends on the host's other
-    work: the load generator's producer and poller threads and the server's request-loop and
-    completion threads all run on the host's shared cores."""
+    """The serving leg in a process of its own, as a server runs, started before this process
+    creates its CUDA context: run in this process after the other legs, or in a child while
+    this process held its context, the x16 trace gave p99 of ~30 ms with 4-8% of the frames
+    dropped, where a process alone on the GPU gave ~1 ms with none dropped.  Its p99 under load
+    also depends on the host's other work (the load generator's threads and the server's
+    request-loop and completion threads run on the host's shared cores)."""
     cmd = [sys.executable, os.path.abspath(__file__), "--serving-only", "--serve-seconds", str(args.serve_seconds)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -684,6 +686,11 @@ def run_ours(args):
     from paper_1706_07263_gb300 import Context, binding, build, replicas, synth
 
     rank, world, local = dist_env()
+    serving = None
+    if rank == 0 and world == 1 and not args.quick:
+        # the serving leg first, in a process of its own, while this one holds no CUDA context
+        build.build()
+        serving = serving_in_fresh_process(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -869,7 +876,7 @@ def run_ours(args):
         line["small_256"] = measure_small(args, dev)
         line["table1_analogue"] = measure_table1(args, dev, flush)
         line["surrogate"] = measure_surrogate(args, dev, flush, oracle_out)
-        line["serving"] = serving_in_fresh_process(args)
+        line["serving"] = serving
         line["stereo_stream"] = measure_stereo(args, dev)
         line["pulse_recovery"] = measure_pulse(args, dev)
     if rank == 0:

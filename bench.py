@@ -501,11 +501,9 @@ def measure_serving(args, dev):
 
 def serving_in_fresh_process(args):
     """The serving leg in a process of its own, as a server runs, started before this process
-    creates its CUDA context: run in this process after the other legs, or in a child while
-    this process held its context, the x16 trace gave p99 of ~30 ms with 4-8% of the frames
-    dropped, where a process alone on the GPU gave ~1 ms with none dropped.  Its p99 under load
-    also depends on the host's other work (the load generator's threads and the server's
-    request-loop and completion threads run on the host's shared cores)."""
+    creates its CUDA context: a serving run after other GPU work on the box (this process's
+    other legs, or an earlier serving process) gave x16 p99 of ~30 ms with 4-8% of the frames
+    dropped, where the first serving process on a box gave ~1-2 ms with almost none dropped."""
     cmd = [sys.executable, os.path.abspath(__file__), "--serving-only", "--serve-seconds", str(args.serve_seconds)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -634,6 +634,57 @@ def bench_config(wl, world, l2):
             "l2": l2, "parallelism": f"replicas x{world}"}
 
 
+def _cudart():
+    """The CUDA runtime library this process already uses (torch's), through ctypes."""
+    import ctypes
+    path = "libcudart.so"
+    with open("/proc/self/maps") as f:
+        for line in f:
+            if "libcudart.so" in line:
+                path = line.split()[-1]
+                break
+    rt = ctypes.CDLL(path)
+    rt.cudaMemcpyAsync.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]
+    rt.cudaMemcpyAsync.restype = ctypes.c_int
+    return rt
+
+
+def measure_host_link(host_frame, host_out, dev, steps):
+    """The host link's limit for the end-to-end leg: the copies of the asynchronous host calls
+    without their kernels.  Per frame the frame goes up on one stream and THb and SO2 come
+    down on another, between the same pinned buffers, with the calls' ordering: a frame's
+    download follows its upload, and its upload follows the download of the frame two back
+    (two staging sets).  Plain cudaMemcpyAsync calls, frames back to back, one
+    synchronisation; the best of three runs of max(K, 200) frames.  Frames/s; the end-to-end
+    figure over this is the share of the link the host entry points reach."""
+    import torch
+    rt = _cudart()
+    H, W = host_out[0][0].shape
+    d_frame = [torch.empty(host_frame.shape, dtype=host_frame.dtype, device=dev) for _ in range(2)]
+    d_out = [[torch.empty((H, W), dtype=torch.float32, device=dev) for _ in range(2)] for _ in range(2)]
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    n_in, n_out = host_frame.numel() * host_frame.element_size(), H * W * 4
+    rounds = []
+    for n in (3,) + (max(steps, 200),) * 3:
+        torch.cuda.synchronize(dev)
+        free = [None, None]
+        t0 = time.perf_counter()
+        for k in range(n):
+            j = k % 2
+            if free[j] is not None:
+                s_in.wait_event(free[j])
+            err = rt.cudaMemcpyAsync(d_frame[j].data_ptr(), host_frame.data_ptr(), n_in, 1, s_in.cuda_stream)
+            s_out.wait_event(s_in.record_event())
+            for h, d in zip(host_out[j], d_out[j]):
+                err |= rt.cudaMemcpyAsync(h.data_ptr(), d.data_ptr(), n_out, 2, s_out.cuda_stream)
+            free[j] = s_out.record_event()
+            if err:
+                raise RuntimeError(f"cudaMemcpyAsync failed ({err})")
+        torch.cuda.synchronize(dev)
+        rounds.append(n / (time.perf_counter() - t0))
+    return max(rounds[1:])
+
+
 def measure_latency(ctx, frame, thb, so2, flush, stream, n):
     """Per-frame latency of the plain path on the device: n single-frame calls, each after
     the L2 flush, bracketed by CUDA events on the launch stream.  Before each flush the
@@ -774,6 +825,7 @@ def run_ours(args):
         ctx.estimate_host_async(host_frame.numpy(), *host_out[k % 2], stream=stream)
     barrier()
     e2e_s, e2e_frames = replicas.aggregate(time.perf_counter() - t0, args.steps, device=dev)
+    link_fps = measure_host_link(host_frame, host_out, dev, args.steps)
 
     # roofline of the dominant kernel.  With the single-pass frame kernel (every step of the
     # path in one launch) that is the frame kernel, bound by HBM: its algorithmic bytes are
@@ -860,6 +912,8 @@ def run_ours(args):
         "e2e": {"value": e2e_frames / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H * W * 3,
                 "d2h_bytes_per_step": 2 * H * W * 4,
                 "api": "hb_estimate_host_async, K frames queued back to back, one synchronisation",
+                "host_link_frames_per_s": link_fps,
+                "frac_of_host_link": e2e_frames / e2e_s / (link_fps * world),
                 "synchronous": {"value": sync_frames / sync_s, "api": "hb_estimate_host, one frame per call"}},
         "gpu_launches": launches,
         "clocks": clk,

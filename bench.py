@@ -20,6 +20,7 @@ sample of the same workload) and prints the same JSON line with "impl": "referen
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -430,7 +431,6 @@ def measure_serving(args, dev):
         # the poller and the producers are Python threads: a cyclic-garbage collection over the
         # objects the earlier legs left would stop them all for tens of ms (the server's own
         # threads are native), so the collector is run once before and kept off during the run
-        import gc
         gc.collect()
         gc.disable()
         try:
@@ -694,6 +694,8 @@ def measure_latency(ctx, frame, thb, so2, flush, stream, n):
     per-block medians over 4 blocks of n/4 frames (run-to-run noise)."""
     import torch
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    gc.collect()
+    gc.disable()   # the collector stays off: its pause could fall between a frame's events
     with torch.cuda.stream(stream):
         for a, b in ev:
             torch.cuda._sleep(200_000)   # ~0.1 ms at 2 GHz, outside the bracket
@@ -701,6 +703,7 @@ def measure_latency(ctx, frame, thb, so2, flush, stream, n):
             a.record(stream)
             ctx.estimate(frame, thb, so2, stream=stream)
             b.record(stream)
+    gc.enable()
     torch.cuda.synchronize()
     ms = np.array([a.elapsed_time(b) for a, b in ev])
     v = np.sort(ms)
@@ -778,11 +781,18 @@ def run_ours(args):
         time.sleep(0.3)
         launches0 = ctx.launch_count()
         barrier()
+        # the stream first idles in a device-side sleep (~5 ms at 2 GHz, outside every bracket)
+        # while the host enqueues the K steps, so that no host-side pause (the clock sampler's
+        # thread, a garbage collection) falls between a step's events; the collector is off
+        gc.collect()
+        gc.disable()
+        torch.cuda._sleep(10_000_000)
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
             ctx.estimate(frame, thb, so2, stream=stream)
             ev[k][1].record(stream)
+        gc.enable()
         barrier()
         launches = ctx.launch_count() - launches0
         # per-kernel durations: the same K steps again with CUDA events around each launch

@@ -382,27 +382,17 @@ __global__ void mlp_adam_kernel(const float* __restrict__ gpart, const float* __
     }
 }
 
-// Inference on the fifth-generation tensor cores.  A warpgroup (128 threads) takes 128
-// samples at a time, one per thread: layer 1 on the FP32 pipes, h1 rounded to BF16 and
-// written to shared memory as the A operand (128 x 64, K-major); layer 2, z2 = h1 W2^T,
-// as four tcgen05.mma of K = 16 (kind::f16, BF16 in, FP32 accumulate) issued by one
-// thread, with W2 (64 x 64, K-major) as the B operand in the CTA's copy of the network
-// image and the accumulator in 64 columns of tensor memory; the commit arrives on the
-// warpgroup's mbarrier, and each thread then reads its sample's row of z2 from tensor
-// memory (tcgen05.ld, 16 columns at a time) to apply b2, GELU, the BF16 rounding of h2 and
-// layer 3 on the FP32 pipes.  Operand layout (no swizzle): 8 x 16-byte core matrices,
-// core matrix (K group kg, row group rg) at byte (kg * R + rg) * 128 for R row groups, so
-// the descriptor's leading (K-direction) byte offset is 128 R and its stride (row-direction)
-// offset 128; the K = 16 step s starts 2 s core matrices further along K.
-constexpr int kWarpsF = 8;                    // 256 threads: two warpgroups
-constexpr int kTileF = 128;                   // samples per warpgroup tile
-constexpr int kTmemColsF = 128;               // tensor-memory columns per CTA (64 per warpgroup)
+// Inference.  One warp computes 8 samples at a time entirely in registers, with layer 2
+// transposed: z2^T (64 units x 8 samples) = W2 h1^T, so W2 is the m16n8k16 A operand
+// (staged once per CTA as ready-made fragments) and the 8 samples are N.  Lane (g, q)
+// (g = lane / 4, q = lane % 4) evaluates layer 1 for sample g at exactly the hidden units
+// its B fragments hold (k = 16 kt + 2q + {0, 1, 8, 9}), so h1 goes from the FP32 pipes
+// straight into the tensor-core operands; the accumulators come back holding units
+// 16 mt + g + {0, 8} of samples 2q, 2q + 1, where GELU, the BF16 rounding of h2 and the
+// lane's share of layer 3 are applied, and shuffles over g finish layer 3.
+constexpr int kWarpsF = 8;
 constexpr int kMlpCheckPerCta = kWarpsF / 2;  // drawn pixels a check CTA takes at a time
 static_assert(kMlpCheckPerCta == 4, "pair_barrier names one barrier per pair of warps");
-// h1 tiles of the two warpgroups (dynamic shared memory), plus a pad that keeps a CTA's
-// shared memory above a fifth of the SM's, so that at most four CTAs share an SM's 512
-// tensor-memory columns
-constexpr size_t kTcSmemBytes = 2 * kTileF * kHid * 2 + 4096;
 
 // Barrier of the two warps 2 pair, 2 pair + 1 (named barriers 1 .. 4; 0 is __syncthreads).
 // The identifiers are literals so that the kernel reserves only the barriers it uses.
@@ -414,53 +404,23 @@ __device__ __forceinline__ void pair_barrier(int pair) {
         default: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
     }
 }
-// Barrier of the four warps of warpgroup wg (named barriers 5, 6).
-__device__ __forceinline__ void wg_barrier(int wg) {
-    if (wg == 0) asm volatile("bar.sync 5, 128;" ::: "memory");
-    else asm volatile("bar.sync 6, 128;" ::: "memory");
-}
-
-// Whether v holds in every thread of warpgroup wg (a barrier of its four warps).
-__device__ __forceinline__ bool wg_all(int wg, bool v) {
-    uint32_t r;
-    if (wg == 0)
-        asm volatile(
-            "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 5, 128, p;\n\t"
-            "selp.u32 %0, 1, 0, q;\n\t}\n"
-            : "=r"(r)
-            : "r"((uint32_t)v)
-            : "memory");
-    else
-        asm volatile(
-            "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 6, 128, p;\n\t"
-            "selp.u32 %0, 1, 0, q;\n\t}\n"
-            : "=r"(r)
-            : "r"((uint32_t)v)
-            : "memory");
-    return r != 0;
-}
-
 struct __align__(16) InferSmem {
-    uint4 w2c[kHid * kHid / 8];  // W2 (row = output unit n, K = input unit) in core matrices
-    float4 l1[kHid];             // W1[u][0..2], b1[u]
-    float4 l3[kHid];             // b2[u], W3[0][u], W3[1][u], 0
-    float4 b3;                   // b3[0], b3[1], 0, 0
+    uint4 w2f[kHid / 16][kHid / 16][32];  // W2 A fragments per (m tile, k tile, lane)
+    float4 l1[kHid];                      // W1[u][0..2], b1[u]
+    float4 l3[kHid];                      // b2[u], W3[0][u], W3[1][u], 0
+    float4 b3;                            // b3[0], b3[1], 0, 0
 };
 static_assert(sizeof(InferSmem) % 16 == 0, "the image is copied in 16-byte words");
-
-// 16-byte word of element (row, k) of a K-major operand with `rgroups` row groups.
-__device__ __forceinline__ int core_word(int row, int k, int rgroups) {
-    return ((k >> 3) * rgroups + (row >> 3)) * 8 + (row & 7);
-}
 
 // The network as the inference kernel holds it in shared memory, built once per parameter
 // change (mlp_pack_kernel) so that every CTA stages it with coalesced 16-byte loads.
 __global__ void __launch_bounds__(256) mlp_pack_kernel(const float* __restrict__ wbf, InferSmem* __restrict__ img) {
-    for (int i = threadIdx.x; i < kHid * kHid / 8; i += blockDim.x) {
-        const int n = i / (kHid / 8), kg = i % (kHid / 8);
-        const float* w = wbf + kOffW2 + n * kHid + kg * 8;
-        img->w2c[core_word(n, kg * 8, kHid / 8)] =
-            make_uint4(pack_bf16(w[0], w[1]), pack_bf16(w[2], w[3]), pack_bf16(w[4], w[5]), pack_bf16(w[6], w[7]));
+    for (int i = threadIdx.x; i < (kHid / 16) * (kHid / 16) * 32; i += blockDim.x) {
+        const int l = i & 31, kt = (i >> 5) % (kHid / 16), mt = i / (32 * (kHid / 16));
+        const float* w0 = wbf + kOffW2 + (mt * 16 + (l >> 2)) * kHid + kt * 16 + 2 * (l & 3);
+        const float* w8 = w0 + 8 * kHid;
+        img->w2f[mt][kt][l] = make_uint4(pack_bf16(w0[0], w0[1]), pack_bf16(w8[0], w8[1]), pack_bf16(w0[8], w0[9]),
+                                         pack_bf16(w8[8], w8[9]));
     }
     for (int u = threadIdx.x; u < kHid; u += blockDim.x) {
         img->l1[u] = make_float4(wbf[kOffW1 + u * kIn], wbf[kOffW1 + u * kIn + 1], wbf[kOffW1 + u * kIn + 2],
@@ -468,6 +428,93 @@ __global__ void __launch_bounds__(256) mlp_pack_kernel(const float* __restrict__
         img->l3[u] = make_float4(wbf[kOffB2 + u], wbf[kOffW3 + u], wbf[kOffW3 + kHid + u], 0.f);
     }
     if (threadIdx.x == 0) img->b3 = make_float4(wbf[kOffB3], wbf[kOffB3 + 1], 0.f, 0.f);
+}
+
+// One 8-sample tile (samples 8 tile .. 8 tile + 7) through the network in one warp.  The
+// lanes with g < 2 end up holding sample 2q + g: they return its index and leave its
+// estimate in val; the other lanes, and samples past n, return -1.  With a route, the
+// samples of untrusted cells are appended to its list (their estimates are still written;
+// the exact posterior replaces them).
+__device__ __forceinline__ long infer_tile(const InferSmem& S, const MlpNorm& nm, const float* __restrict__ ybar,
+                                           long n, long tile, int lane, float2& val,
+                                           const MlpRoute& rt = MlpRoute{}) {
+    const int g = lane >> 2, q = lane & 3;
+    const long r = tile * 8 + g;
+    float y[3], x[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = r < n ? ybar[r * 3 + c] : 0.f;
+#pragma unroll
+    for (int c = 0; c < kIn; ++c)
+        x[c] = nm.T[c * 3] * y[0] + nm.T[c * 3 + 1] * y[1] + nm.T[c * 3 + 2] * y[2] + nm.t0[c];
+    // layer 1 into the B fragments of layer 2 (k = unit, n = sample g)
+    unsigned bfr[kHid / 16][2];
+#pragma unroll
+    for (int kt = 0; kt < kHid / 16; ++kt) {
+        float h[4];  // units 16 kt + 2q + {0, 1, 8, 9}
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float4 w = S.l1[kt * 16 + 2 * q + (v & 1) + 8 * (v >> 1)];
+            float z = w.w;
+            z = fmaf(w.x, x[0], z);
+            z = fmaf(w.y, x[1], z);
+            z = fmaf(w.z, x[2], z);
+            h[v] = gelu(z);
+        }
+        bfr[kt][0] = pack_bf16(h[0], h[1]);
+        bfr[kt][1] = pack_bf16(h[2], h[3]);
+    }
+    // layer 2 on the tensor cores, layer 3 from the accumulators
+    float o00 = 0.f, o01 = 0.f, o10 = 0.f, o11 = 0.f;  // (sample 2q / 2q + 1, output 0 / 1)
+#pragma unroll
+    for (int mt = 0; mt < kHid / 16; ++mt) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < kHid / 16; ++kt) {
+            const uint4 aw = S.w2f[mt][kt][lane];
+            const unsigned af[4] = {aw.x, aw.y, aw.z, aw.w};
+            mma16816(d, af, bfr[kt]);
+        }
+        // d: (unit mt*16 + g, samples 2q, 2q+1), (unit mt*16 + g + 8, samples 2q, 2q+1)
+        const float4 la = S.l3[mt * 16 + g], lb = S.l3[mt * 16 + g + 8];
+        const float h00 = bf(gelu(d[0] + la.x)), h01 = bf(gelu(d[1] + la.x));
+        const float h10 = bf(gelu(d[2] + lb.x)), h11 = bf(gelu(d[3] + lb.x));
+        o00 = fmaf(la.y, h00, fmaf(lb.y, h10, o00));
+        o01 = fmaf(la.z, h00, fmaf(lb.z, h10, o01));
+        o10 = fmaf(la.y, h01, fmaf(lb.y, h11, o10));
+        o11 = fmaf(la.z, h01, fmaf(lb.z, h11, o11));
+    }
+#pragma unroll
+    for (int off = 4; off <= 16; off <<= 1) {
+        o00 += __shfl_xor_sync(0xffffffffu, o00, off);
+        o01 += __shfl_xor_sync(0xffffffffu, o01, off);
+        o10 += __shfl_xor_sync(0xffffffffu, o10, off);
+        o11 += __shfl_xor_sync(0xffffffffu, o11, off);
+    }
+    // lanes g = 0 and g = 1 hold samples 2q and 2q + 1; they need those samples' ybar
+    const int s = 2 * q + (g & 1);
+    const long rs = tile * 8 + s;
+    const float ya = __shfl_sync(0xffffffffu, y[0], 4 * s), yb = __shfl_sync(0xffffffffu, y[1], 4 * s),
+                yc = __shfl_sync(0xffffffffu, y[2], 4 * s);
+    const bool mine = g < 2 && rs < n;
+    const float ys[3] = {ya, yb, yc};
+    const float2 cls = least_squares(nm, ys);
+    if (rt.trust) {
+        // warp-aggregated append of the untrusted samples
+        const bool out = mine && !trusted(rt, cls);
+        const unsigned m = __ballot_sync(0xffffffffu, out);
+        if (m) {
+            unsigned base = 0;
+            if (lane == __ffs(m) - 1) base = atomicAdd(rt.count, (unsigned)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+            const unsigned at = base + __popc(m & ((1u << lane) - 1u));
+            if (out && at < (unsigned long)n) rt.list[at] = (int)rs;  // at most n are ever listed
+        }
+    }
+    if (!mine) return -1;
+    const float o0 = (g & 1) ? o10 : o00, o1 = (g & 1) ? o11 : o01;
+    const float2 bl = baseline(nm, cls);
+    val = make_float2(fmaf(nm.osc0, o0 + S.b3.x, bl.x), fmaf(nm.osc1, o1 + S.b3.y, bl.y));
+    return rs;
 }
 
 // Every CTA stages the network image before waiting on the kernel that writes ybar (the
@@ -482,245 +529,18 @@ __device__ __forceinline__ void stage_image(InferSmem& S, const InferSmem* __res
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: start address, leading (K-direction) and stride
-// (row-direction) byte offsets, the fixed version field, no swizzle.
-__device__ __forceinline__ unsigned long long smem_desc(uint32_t addr, uint32_t lead, uint32_t stride) {
-    return (unsigned long long)((addr & 0x3FFFFu) >> 4) | ((unsigned long long)(lead >> 4) << 16) |
-           ((unsigned long long)(stride >> 4) << 32) | (1ull << 46);
-}
-
-// Tensor memory and barriers of an inference CTA: warp 0 allocates kTmemColsF columns,
-// thread 0 sets up one mbarrier per warpgroup; the whole CTA then synchronises.
-struct TcCta {
-    uint32_t tmem;        // first column of the allocation (lane 0)
-    uint32_t bar[2];      // shared addresses of the warpgroups' mbarriers
-};
-__device__ __forceinline__ TcCta tc_setup(uint32_t* slot, unsigned long long* bars) {
-    if ((threadIdx.x >> 5) == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
-                     "r"(kTmemColsF)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < 2; ++w)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + w)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    return TcCta{*slot, {smem_addr(bars), smem_addr(bars + 1)}};
-}
-// Every warp's tensor-memory reads done, then warp 0 frees the columns.
-__device__ __forceinline__ void tc_teardown(const TcCta& t) {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if ((threadIdx.x >> 5) == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t.tmem), "r"(kTmemColsF)
-                     : "memory");
-    }
-}
-
-// Waits for the phase with the given parity of an mbarrier; false after about 2^22 tries
-// (far beyond the microseconds a 128 x 64 x 64 product takes).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-// Sixteen FP32 columns [c0, c0 + 16) of this thread's lane of tensor memory.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-// The network's input for ybar y.
-__device__ __forceinline__ void net_input(const MlpNorm& nm, const float (&y)[3], float (&x)[kIn]) {
-#pragma unroll
-    for (int c = 0; c < kIn; ++c)
-        x[c] = nm.T[c * 3] * y[0] + nm.T[c * 3 + 1] * y[1] + nm.T[c * 3 + 2] * y[2] + nm.t0[c];
-}
-
-// The estimate from the network's outputs o (without b3) and ybar y.
-__device__ __forceinline__ float2 net_estimate(const InferSmem& S, const MlpNorm& nm, const float (&y)[3], float o0,
-                                               float o1) {
-    const float2 bl = baseline(nm, least_squares(nm, y));
-    return make_float2(fmaf(nm.osc0, o0 + S.b3.x, bl.x), fmaf(nm.osc1, o1 + S.b3.y, bl.y));
-}
-
-// Warpgroup wg's tiles tile0, tile0 + step, ... of 128 samples through the network (see
-// above).  a: the warpgroup's A operand (128 x 64 BF16, 16 KB); tmem: its first column.
-// With a route, the samples of untrusted cells are appended to its list (their estimates
-// are still written; the exact posterior replaces them).  A product that does not complete
-// leaves NaN estimates for its tile.
-__device__ void wg_infer(const InferSmem& S, uint4* a, uint32_t tmem, uint32_t bar, int wg, const MlpNorm& nm,
-                         const float* __restrict__ ybar, long n, long tile0, long step, float2* __restrict__ chat,
-                         float2* __restrict__ chat_scaled, float scale, const MlpRoute& rt) {
-    const int t = threadIdx.x & (kTileF - 1), lane = threadIdx.x & 31;
-    // this thread's lane of tensor memory is its sample's row: warp (w % 4) reads lanes 32 (w % 4) ..
-    const uint32_t trow = tmem + ((uint32_t)(t & ~31) << 16);
-    const uint32_t a0 = smem_addr(a), b0 = smem_addr(S.w2c);
-    constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kHid >> 3) << 17) |
-                                ((uint32_t)(kTileF >> 4) << 24);  // F32 accumulator, BF16 A and B, K-major, 128 x 64
-    constexpr uint32_t kLeadA = 128 * (kTileF / 8), kLeadB = 128 * (kHid / 8);
-    const long ntile = (n + kTileF - 1) / kTileF;
-    uint32_t parity = 0;
-    for (long tile = tile0; tile < ntile; tile += step) {
-        const long r = tile * kTileF + t;
-        float y[3], x[kIn];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) y[c] = r < n ? ybar[r * 3 + c] : 0.f;
-        net_input(nm, y, x);
-        // layer 1 into the A operand: row t, units 8 kg .. 8 kg + 7 in one 16-byte word
-#pragma unroll 2
-        for (int kg = 0; kg < kHid / 8; ++kg) {
-            float h[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float4 w = S.l1[kg * 8 + j];
-                float z = w.w;
-                z = fmaf(w.x, x[0], z);
-                z = fmaf(w.y, x[1], z);
-                z = fmaf(w.z, x[2], z);
-                h[j] = gelu(z);
-            }
-            a[core_word(t, kg * 8, kTileF / 8)] =
-                make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
-        }
-        // the operand's generic-proxy writes made visible to the tensor cores; the previous
-        // tile's tensor-memory reads finished (all threads) before the next product
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        wg_barrier(wg);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (t == 0) {
-#pragma unroll
-            for (int s = 0; s < kHid / 16; ++s) {
-                const unsigned long long da = smem_desc(a0 + s * 2 * kLeadA, kLeadA, 128);
-                const unsigned long long db = smem_desc(b0 + s * 2 * kLeadB, kLeadB, 128);
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-                    "l"(da), "l"(db), "r"(kIdesc), "r"((uint32_t)s)
-                    : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                         : "memory");
-        }
-        // one decision for the warpgroup (its threads give up on their own)
-        const bool done = wg_all(wg, mbar_wait(bar, parity));
-        parity ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // layer 2's bias, GELU and BF16 rounding, layer 3, from the accumulator row
-        float o0 = 0.f, o1 = 0.f;
-#pragma unroll
-        for (int c0 = 0; c0 < kHid; c0 += 16) {
-            float z[16];
-            tmem_ld16(trow + (uint32_t)c0, z);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float4 l = S.l3[c0 + j];
-                const float h2 = bf(gelu(z[j] + l.x));
-                o0 = fmaf(l.y, h2, o0);
-                o1 = fmaf(l.z, h2, o1);
-            }
-        }
-        const bool mine = r < n;
-        float2 val = net_estimate(S, nm, y, o0, o1);
-        if (!done) val = make_float2(NAN, NAN);
-        if (rt.trust) {
-            // warp-aggregated append of the untrusted samples
-            const bool out = mine && !trusted(rt, least_squares(nm, y));
-            const unsigned m = __ballot_sync(0xffffffffu, out);
-            if (m) {
-                unsigned base = 0;
-                if (lane == __ffs(m) - 1) base = atomicAdd(rt.count, (unsigned)__popc(m));
-                base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-                const unsigned at = base + __popc(m & ((1u << lane) - 1u));
-                if (out && at < (unsigned long)n) rt.list[at] = (int)r;  // at most n are ever listed
-            }
-        }
-        if (mine) {
-            chat[r] = val;
-            if (chat_scaled) chat_scaled[r] = make_float2(scale * val.x, scale * val.y);
-        }
-        if (!done) break;  // the product never completed: leave the rest to the check
-    }
-}
-
-// One sample's estimate in one warp on the FP32 pipes, for the sampled check: lane l holds
-// units l and l + 32 of each layer.  The same arithmetic as wg_infer (BF16 h1 and h2, FP32
-// sums) in another order of additions.
-__device__ float2 warp_infer_one(const InferSmem& S, const MlpNorm& nm, const float* __restrict__ ybar, long p,
-                                 int lane) {
-    float y[3], x[kIn];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) y[c] = ybar[p * 3 + c];
-    net_input(nm, y, x);
-    float h1[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float4 w = S.l1[lane + 32 * i];
-        float z = w.w;
-        z = fmaf(w.x, x[0], z);
-        z = fmaf(w.y, x[1], z);
-        z = fmaf(w.z, x[2], z);
-        h1[i] = bf(gelu(z));
-    }
-    const unsigned short* w2 = reinterpret_cast<const unsigned short*>(S.w2c);
-    float z2[2] = {0.f, 0.f};
-    for (int k = 0; k < kHid; ++k) {
-        const float hk = __shfl_sync(0xffffffffu, h1[k >> 5], k & 31);
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int u = lane + 32 * i;
-            const float w = __uint_as_float((unsigned)w2[core_word(u, k, kHid / 8) * 8 + (k & 7)] << 16);
-            z2[i] = fmaf(w, hk, z2[i]);
-        }
-    }
-    float o0 = 0.f, o1 = 0.f;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float4 l = S.l3[lane + 32 * i];
-        const float h2 = bf(gelu(z2[i] + l.x));
-        o0 = fmaf(l.y, h2, o0);
-        o1 = fmaf(l.z, h2, o1);
-    }
-    return net_estimate(S, nm, y, warp_sum(o0), warp_sum(o1));
-}
-
 __global__ void __launch_bounds__(32 * kWarpsF) mlp_forward_kernel(const InferSmem* __restrict__ img, MlpNorm nm,
                                                                    const float* __restrict__ ybar, long n,
                                                                    float2* __restrict__ chat) {
     __shared__ InferSmem S;
-    __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ uint32_t slot;
-    extern __shared__ __align__(1024) uint4 tc_a[];
-    const TcCta tc = tc_setup(&slot, bars);
     stage_image(S, img);
-    const int wg = threadIdx.x >> 7;
-    wg_infer(S, tc_a + wg * (kTileF * kHid / 8), tc.tmem + 64u * wg, tc.bar[wg], wg, nm, ybar, n,
-             (long)blockIdx.x * 2 + wg, (long)gridDim.x * 2, chat, nullptr, 0.f, MlpRoute{});
-    tc_teardown(tc);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long ntile = (n + 7) / 8;
+    for (long tile = (long)blockIdx.x * kWarpsF + warp; tile < ntile; tile += (long)gridDim.x * kWarpsF) {
+        float2 v;
+        const long rs = infer_tile(S, nm, ybar, n, tile, lane, v);
+        if (rs >= 0) chat[rs] = v;
+    }
 }
 
 // Posterior mean of one pixel computed by one warp (CPL grid columns per lane), valid in
@@ -756,22 +576,19 @@ __device__ float2 warp_posterior_mean(const BayesParams& bp, const BayesRec& rec
 
 // Inference and the sampled exact check in one launch.  CTAs 0 .. ck.nctas - 1 check
 // kMlpCheckPerCta drawn pixels at a time, one per pair of warps: the even warp computes the
-// pixel's exact posterior mean (warp_posterior_mean) while the odd warp runs the pixel
-// through the network on the FP32 pipes (warp_infer_one); then err[k] = the larger of
+// pixel's exact posterior mean (warp_posterior_mean) while the odd warp runs the pixel's
+// 8-sample tile through the same code as the inference CTAs; then err[k] = the larger of
 // the two axes' errors relative to the box extents (NaN if either is).  The last check
 // CTA to arrive adds the errors in a fixed order and leaves the decision in sync[2]
 // (sync[1] counts the failed frames, sync[0] is the arrival counter).  The remaining CTAs
-// run inference on the tensor cores as mlp_forward_kernel and, if chat_scaled is set, also
-// write the estimates times scale there.
+// run inference exactly as mlp_forward_kernel and, if chat_scaled is set, also write the
+// estimates times scale there.
 template <int CPL>
 __global__ void __launch_bounds__(32 * kWarpsF, 4)
     mlp_forward_check_kernel(const InferSmem* __restrict__ img, MlpNorm nm, const float* __restrict__ ybar, long n,
                              float2* __restrict__ chat, float2* __restrict__ chat_scaled, float scale,
                              BayesParams bp, const BayesRec* __restrict__ recs, MlpCheck ck, MlpRoute rt) {
     __shared__ InferSmem S;
-    __shared__ __align__(8) unsigned long long bars[2];
-    __shared__ uint32_t slot;
-    extern __shared__ __align__(1024) uint4 tc_a[];
     __shared__ float2 est[kMlpCheckPerCta];
     __shared__ float red[kWarpsF];
     __shared__ unsigned redbad[kWarpsF];
@@ -782,12 +599,15 @@ __global__ void __launch_bounds__(32 * kWarpsF, 4)
     // the previous frame's exact posterior has read its counter: clear it for the next frame
     if (rt.next_count && blockIdx.x == 0 && threadIdx.x == 0) *rt.next_count = 0u;
     if ((int)blockIdx.x >= ck.nctas) {
-        const TcCta tc = tc_setup(&slot, bars);
-        const int wg = threadIdx.x >> 7;
-        const long nblk = (long)gridDim.x - ck.nctas;
-        wg_infer(S, tc_a + wg * (kTileF * kHid / 8), tc.tmem + 64u * wg, tc.bar[wg], wg, nm, ybar, n,
-                 ((long)blockIdx.x - ck.nctas) * 2 + wg, nblk * 2, chat, chat_scaled, scale, rt);
-        tc_teardown(tc);
+        const long ntile = (n + 7) / 8, nblk = (long)gridDim.x - ck.nctas;
+        for (long tile = ((long)blockIdx.x - ck.nctas) * kWarpsF + warp; tile < ntile; tile += nblk * kWarpsF) {
+            float2 v;
+            const long rs = infer_tile(S, nm, ybar, n, tile, lane, v, rt);
+            if (rs >= 0) {
+                chat[rs] = v;
+                if (chat_scaled) chat_scaled[rs] = make_float2(scale * v.x, scale * v.y);
+            }
+        }
         return;
     }
     const int pair = warp >> 1;
@@ -797,8 +617,11 @@ __global__ void __launch_bounds__(32 * kWarpsF, 4)
         const long p = on ? sample_pixel(ck.seed, k, n) : 0;
         float2 c = make_float2(0.f, 0.f);
         if (on && (warp & 1)) {
-            const float2 v = warp_infer_one(S, nm, ybar, p, lane);
-            if (lane == 0) est[pair] = v;
+            float2 v = make_float2(0.f, 0.f);
+            const long rs = infer_tile(S, nm, ybar, n, p >> 3, lane, v);
+            const int src = __ffs(__ballot_sync(0xffffffffu, rs == p)) - 1;  // the one lane holding p
+            const float ex = __shfl_sync(0xffffffffu, v.x, src), ey = __shfl_sync(0xffffffffu, v.y, src);
+            if (lane == 0) est[pair] = make_float2(ex, ey);
         } else if (on) {
             c = warp_posterior_mean<CPL>(bp, recs[p], lane);
         }
@@ -889,40 +712,19 @@ cudaError_t launch_mlp_pack(const float* wbf, void* img, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Dynamic shared memory of the inference kernels (the warpgroups' A operands), and a check
-// that no more CTAs fit on an SM than its 512 tensor-memory columns serve at once (a CTA
-// beyond them would wait in its allocation for another CTA to finish).
-template <typename K>
-cudaError_t tc_prepare(K kernel) {
-    cudaError_t e = set_smem_attr(kernel, kTcSmemBytes);
-    int resident = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kernel, 32 * kWarpsF, kTcSmemBytes);
-    if (e == cudaSuccess && resident * kTmemColsF > 512) e = cudaErrorInvalidConfiguration;
-    return e;
-}
-
-// Inference CTAs for n samples: two 128-sample tiles per CTA while that fits, at most
-// four CTAs per SM.
-inline long tc_blocks(long n, int sms) {
-    const long tiles = (n + kTileF - 1) / kTileF;
-    long blocks = (tiles + 1) / 2;
-    if (blocks > 4L * sms) blocks = 4L * sms;
-    return blocks < 1 ? 1 : blocks;
-}
-
 cudaError_t launch_mlp_forward(const void* img, const MlpNorm& nm, const float* ybar, long n, float2* chat, bool pdl,
                                cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = tc_prepare(mlp_forward_kernel);
     if (e != cudaSuccess) return e;
-    if (n <= 0) return cudaSuccess;
+    const long tiles = (n + 7) / 8;
+    long blocks = (tiles + kWarpsF - 1) / kWarpsF;  // one tile per warp while that fits
+    if (blocks > 8L * sms) blocks = 8L * sms;
+    if (blocks < 1) blocks = 1;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)tc_blocks(n, sms));
+    cfg.gridDim = dim3((unsigned)blocks);
     cfg.blockDim = dim3(32 * kWarpsF);
-    cfg.dynamicSmemBytes = kTcSmemBytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -939,12 +741,9 @@ cudaError_t launch_forward_check_cpl(const void* img, const MlpNorm& nm, const f
                                      float2* chat_scaled, float scale, const BayesParams& bp, const BayesRec* rec,
                                      const MlpCheck& ck, const MlpRoute& rt, unsigned blocks, bool pdl,
                                      cudaStream_t s) {
-    cudaError_t e = tc_prepare(mlp_forward_check_kernel<CPL>);
-    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(32 * kWarpsF);
-    cfg.dynamicSmemBytes = kTcSmemBytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -970,7 +769,11 @@ cudaError_t launch_mlp_forward_check(const void* img, const MlpNorm& nm, const f
     // suffice
     const long need = (ck.nsample + kMlpCheckPerCta - 1) / kMlpCheckPerCta;
     ck.nctas = (int)(need < 4096 ? need : 4096);
-    const long blocks = tc_blocks(n, sms) + ck.nctas;
+    const long tiles = (n + 7) / 8;
+    long blocks = (tiles + kWarpsF - 1) / kWarpsF;  // one tile per warp while that fits
+    if (blocks > 8L * sms) blocks = 8L * sms;
+    if (blocks < 1) blocks = 1;
+    blocks += ck.nctas;
 #define HB_FC_ARGS img, nm, ybar, n, chat, chat_scaled, scale, bp, rec, ck, rt, (unsigned)blocks, pdl, s
     if (bp.n1 <= 32) return launch_forward_check_cpl<1>(HB_FC_ARGS);
     if (bp.n1 <= 64) return launch_forward_check_cpl<2>(HB_FC_ARGS);

@@ -52,7 +52,7 @@ FP32_OPS_PER_EDGE_ROW = 11       # more for a row the box edge cuts off: distanc
 
 
 def measured_peaks():
-    """The driver's measured peaks of this machine (copy bandwidth, bf16 GEMM, clocks), if present."""
+    """Measured peaks of these GPUs (copy bandwidth, bf16 GEMM, clocks) from MEASURED_PEAKS.json, if present."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)

@@ -501,9 +501,10 @@ def measure_serving(args, dev):
 
 def serving_in_fresh_process(args):
     """The serving leg in a process of its own, as a server runs, started before this process
-    creates its CUDA context: a serving run after other GPU work on the box (this process's
-    other legs, or an earlier serving process) gave x16 p99 of ~30 ms with 4-8% of the frames
-    dropped, where the first serving process on a box gave ~1-2 ms with almost none dropped."""
+    creates its CUDA context: serving runs after other work on the same GPU (this process's
+    other legs, or an earlier serving process) often gave x16 p99 of 24-33 ms with 4-8% of the
+    frames dropped, where the first serving process on a freshly started machine gave ~1-7 ms
+    with at most 0.3% dropped."""
     cmd = [sys.executable, os.path.abspath(__file__), "--serving-only", "--serve-seconds", str(args.serve_seconds)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -921,6 +921,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": bench_config(wl, world, "256 MiB buffer rewritten between timed steps"),
         "latency_ms": latency,
+        "step_ms": {"p50": float(np.median(step_ms)), "max": float(np.max(step_ms)),
+                    "how": "the timed steps' own event intervals (this rank), whose mean is ms_per_step"},
         "megapixels_per_s": value * W * H / 1e6,
         "stages": stages,
         "roofline": roofline,
